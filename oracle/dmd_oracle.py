@@ -1,0 +1,414 @@
+"""FP64 CPU oracle for the DMD / DMDc hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite, the package smoke check and the benchmark's CPU-baseline
+leg may import this module; the product path never does.  It shares no code
+with the CUDA library: it is a plain, slow, literal restatement of the paper's
+equations in NumPy float64, with LAPACK routines (SVD, eig, least squares) as
+its only library steps.
+
+Definitions followed (paper sections / equations):
+
+* snapshot matrices X = [x_0 .. x_{m-1}], X' = [x_1 .. x_m]      (Eq. reduced_koopman)
+* K = X' V Sigma^{-1} U^T from the rank-r truncated SVD X = U Sigma V^T
+                                                                 (Eq. reduced_koopman_solution)
+* reduced operator  A~ = U^T X' V Sigma^{-1}                     (Sec. 3.1, text after the solution)
+* A~ w_i = lambda_i w_i; exact modes Phi = X' V Sigma^{-1} W     (Sec. 3.1; exact-DMD modes)
+* amplitudes z = Phi^+ u  (least squares, not normal equations)  (Eq. projection)
+* prediction u(t + k dt) = Phi Lambda^k z(t), any integer k      (Eq. large_time_step)
+* reversal  u(t) = Phi Lambda^{-1} z(t + dt)                     (Eq. reverse_simulation)
+* randomized SVD: range finder Q with X ~ Q Q^T X, B = Q^T X,
+  B = U_B Sigma V^T, X ~ (Q U_B) Sigma V^T                       (Sec. 4.3)
+* DMD with control, z(t+dt) = Lambda z(t) + Phi^+ B q(t) dt      (Eq. external_forces)
+  with the unknown-B least-squares fit of [A B] (the DMDc the paper cites)
+
+Readings where the paper is silent or garbled are the ones listed in the
+design notes: m+1 snapshot columns, exact (not projected) modes, b = Phi^+ x_0
+by least squares, canonical eigenvalue order (|lambda| descending, then Im
+descending, conjugate pairs adjacent with Im > 0 first), dt = 1.
+
+Real form.  Prediction treats each conjugate pair as a real 2x2 block: for a
+pair (lambda, conj lambda) with mode phi and amplitude b the pair contributes
+2 Re(phi lambda^k b) = Re(phi) c0_k + Im(phi) c1_k with
+c0_k = Re(lambda^k zeta), c1_k = -Im(lambda^k zeta), zeta = 2 b.  The real
+amplitude vector stores beta = (Re zeta, -Im zeta) in the pair's two columns,
+so C[:, 0] = beta.  A real eigenvalue keeps one real column with beta = b.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# snapshot matrices, SVD, reduced operator, eigendecomposition
+# ----------------------------------------------------------------------------
+
+
+def split_snapshots(S: np.ndarray):
+    """X = S[:, :m], X' = S[:, 1:] for S = [x_0 .. x_m] (Eq. reduced_koopman)."""
+    S = np.asarray(S, dtype=np.float64)
+    return S[:, :-1], S[:, 1:]
+
+
+def svd_truncated(X: np.ndarray, r: int):
+    """Rank-r thin SVD X ~ U diag(s) V^T (Eq. reduced_koopman_solution).
+
+    Singular values descending; each singular pair's sign is fixed so that the
+    largest-magnitude entry of v is positive (signs do not affect lambda, Phi).
+    """
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    U, s, V = U[:, :r].copy(), s[:r].copy(), Vt[:r].T.copy()
+    piv = np.argmax(np.abs(V), axis=0)
+    sgn = np.sign(V[piv, np.arange(r)])
+    sgn[sgn == 0] = 1.0
+    return U * sgn, s, V * sgn
+
+
+def reduced_operator(U: np.ndarray, s: np.ndarray, V: np.ndarray, Xp: np.ndarray) -> np.ndarray:
+    """A~ = U^T X' V Sigma^{-1}  (r x r), Sec. 3.1."""
+    return (U.T @ Xp @ V) / s[None, :]
+
+
+def canonical_order(lam: np.ndarray) -> np.ndarray:
+    """Permutation: |lambda| descending, then Im descending; each conjugate
+    partner placed right after its Im > 0 member; real eigenvalues in place."""
+    r = len(lam)
+    used = np.zeros(r, dtype=bool)
+    heads = [i for i in range(r) if lam[i].imag >= 0.0]
+    heads.sort(key=lambda i: (-abs(lam[i]), -lam[i].imag, i))
+    order = []
+    for i in heads:
+        if used[i]:
+            continue
+        used[i] = True
+        order.append(i)
+        if lam[i].imag > 0.0:
+            cand = [j for j in range(r) if not used[j] and lam[j].imag < 0.0]
+            j = min(cand, key=lambda j: abs(lam[j] - np.conj(lam[i])))
+            used[j] = True
+            order.append(j)
+    rest = [i for i in range(r) if not used[i]]   # unmatched Im < 0 (not from real data)
+    return np.array(order + rest, dtype=int)
+
+
+def eig_canonical(A: np.ndarray):
+    """Eigenpairs A w = lambda w (Sec. 3.1) in canonical order.
+
+    Each w has unit 2-norm and its largest-magnitude entry real positive.
+    """
+    lam, W = np.linalg.eig(A)
+    order = canonical_order(lam)
+    lam, W = lam[order], W[:, order].astype(complex)
+    W /= np.linalg.norm(W, axis=0)[None, :]
+    piv = np.argmax(np.abs(W), axis=0)
+    ph = W[piv, np.arange(W.shape[1])]
+    W *= (np.abs(ph) / ph)[None, :]
+    return lam, W
+
+
+def amplitudes(Phi: np.ndarray, x0: np.ndarray) -> np.ndarray:
+    """b = Phi^+ x_0 as a least-squares solve (Eq. projection)."""
+    b, *_ = np.linalg.lstsq(Phi, x0.astype(complex), rcond=None)
+    return b
+
+
+def exact_dmd(S: np.ndarray, r: int) -> dict:
+    """Exact DMD of S = [x_0 .. x_m] at rank r (Sec. 3.1, Eqs. reduced_koopman..projection)."""
+    X, Xp = split_snapshots(S)
+    U, s, V = svd_truncated(X, r)
+    At = reduced_operator(U, s, V, Xp)
+    lam, W = eig_canonical(At)
+    M = (V / s[None, :]) @ W            # m x r: Phi = X' M
+    Phi = Xp @ M
+    b = amplitudes(Phi, X[:, 0])
+    return dict(U=U, s=s, V=V, Atilde=At, lam=lam, W=W, M=M, Phi=Phi, b=b)
+
+
+# ----------------------------------------------------------------------------
+# prediction (Eq. large_time_step) and its real 2x2-block form
+# ----------------------------------------------------------------------------
+
+
+def int_power(z: np.ndarray, k: int) -> np.ndarray:
+    """z**k for integer k by repeated squaring (k < 0 uses (1/z)**|k|)."""
+    z = np.asarray(z, dtype=complex)
+    if k < 0:
+        z, k = 1.0 / z, -k
+    out = np.ones_like(z)
+    base = z.copy()
+    while k:
+        if k & 1:
+            out = out * base
+        base = base * base
+        k >>= 1
+    return out
+
+
+def predict(Phi: np.ndarray, lam: np.ndarray, b: np.ndarray, ks) -> np.ndarray:
+    """x_k = Phi Lambda^k b for each k in ks; returns the real part (n x K).
+
+    For real data the eigen-triplets are closed under conjugation, so the
+    imaginary part is rounding only.
+    """
+    D = np.stack([int_power(lam, int(k)) * b for k in ks], axis=1)   # r x K
+    return (Phi @ D).real
+
+
+def pair_kinds(lam: np.ndarray, tol: float = 0.0) -> np.ndarray:
+    """Per column: 1 = first of a conjugate pair (Im > 0), 2 = its partner,
+    0 = real eigenvalue.  Assumes canonical order."""
+    kinds = np.zeros(len(lam), dtype=int)
+    i = 0
+    while i < len(lam):
+        if lam[i].imag > tol and i + 1 < len(lam):
+            kinds[i], kinds[i + 1] = 1, 2
+            i += 2
+        else:
+            i += 1
+    return kinds
+
+
+def to_real_form(Phi: np.ndarray, lam: np.ndarray, b: np.ndarray):
+    """(Phi_R, beta) of the real 2x2-block form (module docstring)."""
+    kinds = pair_kinds(lam)
+    n, r = Phi.shape
+    PhiR = np.empty((n, r))
+    beta = np.empty(r)
+    for c in range(r):
+        if kinds[c] == 1:
+            zeta = 2.0 * b[c]
+            PhiR[:, c], PhiR[:, c + 1] = Phi[:, c].real, Phi[:, c].imag
+            beta[c], beta[c + 1] = zeta.real, -zeta.imag
+        elif kinds[c] == 0:
+            PhiR[:, c] = Phi[:, c].real
+            beta[c] = b[c].real
+    return PhiR, beta, kinds
+
+
+def coefficients(lam: np.ndarray, beta: np.ndarray, ks, kinds=None) -> np.ndarray:
+    """C (r x K): column k is the real-form coefficient vector of Lambda^k b."""
+    if kinds is None:
+        kinds = pair_kinds(lam)
+    r = len(lam)
+    C = np.zeros((r, len(ks)))
+    for j, k in enumerate(ks):
+        pw = int_power(lam, int(k))
+        for c in range(r):
+            if kinds[c] == 1:
+                y = pw[c] * (beta[c] - 1j * beta[c + 1])
+                C[c, j], C[c + 1, j] = y.real, -y.imag
+            elif kinds[c] == 0:
+                C[c, j] = (pw[c] * beta[c]).real
+    return C
+
+
+def predict_real(PhiR: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Reconstruction as one real product F = Phi_R C."""
+    return PhiR @ C
+
+
+def mode_products(PhiR: np.ndarray, beta: np.ndarray, kinds) -> np.ndarray:
+    """Scale-free per-mode fields phi_j b_j (complex, n x #modes with Im >= 0).
+
+    phi b = (Re phi + i Im phi) (beta_c - i beta_{c+1}) / 2 for a pair; phi b for
+    a real mode.  Independent of each mode's arbitrary complex scale.
+    """
+    cols = []
+    for c in range(PhiR.shape[1]):
+        if kinds[c] == 1:
+            phi = PhiR[:, c] + 1j * PhiR[:, c + 1]
+            cols.append(phi * (beta[c] - 1j * beta[c + 1]) / 2.0)
+        elif kinds[c] == 0:
+            cols.append(PhiR[:, c] * beta[c] + 0j)
+    return np.stack(cols, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# randomized SVD (Sec. 4.3)
+# ----------------------------------------------------------------------------
+
+
+def rsvd(X: np.ndarray, Omega: np.ndarray, r: int, power_iters: int):
+    """Randomized SVD of X with test matrix Omega (m x l), Sec. 4.3.
+
+    Range finder with re-orthonormalisation after every product:
+    Q = orth(X Omega); repeat power_iters times: Z = orth(X^T Q), Q = orth(X Z).
+    Then B = Q^T X = U_B Sigma V^T and X ~ (Q U_B) Sigma V^T, truncated to r.
+    orth() is Householder QR (LAPACK).
+    """
+    Q, _ = np.linalg.qr(X @ Omega)
+    for _ in range(power_iters):
+        Z, _ = np.linalg.qr(X.T @ Q)
+        Q, _ = np.linalg.qr(X @ Z)
+    B = Q.T @ X
+    Ub, s, Vt = np.linalg.svd(B, full_matrices=False)
+    U, s, V = Q @ Ub[:, :r], s[:r], Vt[:r].T
+    piv = np.argmax(np.abs(V), axis=0)
+    sgn = np.sign(V[piv, np.arange(r)])
+    sgn[sgn == 0] = 1.0
+    return U * sgn, s, V * sgn, Q
+
+
+def rsvd_dmd(S: np.ndarray, Omega: np.ndarray, r: int, power_iters: int) -> dict:
+    """Exact DMD where the SVD of X is the randomized one of Sec. 4.3."""
+    X, Xp = split_snapshots(S)
+    U, s, V, Q = rsvd(X, Omega, r, power_iters)
+    At = reduced_operator(U, s, V, Xp)
+    lam, W = eig_canonical(At)
+    M = (V / s[None, :]) @ W
+    Phi = Xp @ M
+    b = amplitudes(Phi, X[:, 0])
+    return dict(U=U, s=s, V=V, Q=Q, Atilde=At, lam=lam, W=W, M=M, Phi=Phi, b=b)
+
+
+# ----------------------------------------------------------------------------
+# DMD with control (Eq. external_forces; unknown-B least squares fit)
+# ----------------------------------------------------------------------------
+
+
+def dmdc(S: np.ndarray, Ups: np.ndarray, r: int, p: int | None = None) -> dict:
+    """DMDc of S = [x_0..x_m] with inputs Ups = [u_0..u_{m-1}] (q x m).
+
+    [A B] is the least-squares map from Omega = [X; Ups] to X', with Omega's
+    SVD truncated to p (input space) and the output space U_hat the rank-r
+    left singular vectors of X'.  A~ = U_hat^T X' Vt St^{-1} Ut1^T U_hat,
+    A~ W = W Lambda; modes Phi = X' Vt St^{-1} Ut1^T U_hat W; b = Phi^+ x_0;
+    the reduced forcing is G = Phi^+ B with B = X' Vt St^{-1} Ut2^T, so that
+    z_{k+1} = Lambda z_k + G u_k and x_k = Phi z_k (Eq. external_forces, dt = 1).
+    """
+    X, Xp = split_snapshots(S)
+    n = X.shape[0]
+    q = Ups.shape[0]
+    if p is None:
+        p = r + q
+    Om = np.vstack([X, Ups])
+    Ut, st, Vt = svd_truncated(Om, p)
+    Ut1, Ut2 = Ut[:n], Ut[n:]
+    Uh, _, _ = svd_truncated(Xp, r)
+    core = Xp @ (Vt / st[None, :])              # n x p
+    At = Uh.T @ core @ (Ut1.T @ Uh)            # r x r
+    Bt = Uh.T @ core @ Ut2.T                   # r x q
+    lam, W = eig_canonical(At)
+    Phi = core @ (Ut1.T @ Uh) @ W
+    Bfull = core @ Ut2.T                       # n x q
+    b = amplitudes(Phi, X[:, 0])
+    G, *_ = np.linalg.lstsq(Phi, Bfull.astype(complex), rcond=None)
+    return dict(Atilde=At, Btilde=Bt, lam=lam, W=W, Phi=Phi, b=b, G=G, B=Bfull, Uhat=Uh)
+
+
+def dmdc_rollout(lam: np.ndarray, b: np.ndarray, G: np.ndarray, U: np.ndarray, steps: int) -> np.ndarray:
+    """z_0 = b, z_{k+1} = Lambda z_k + G u_k (Eq. external_forces); returns r x (steps+1)."""
+    Z = np.empty((len(lam), steps + 1), dtype=complex)
+    Z[:, 0] = b
+    for k in range(steps):
+        Z[:, k + 1] = lam * Z[:, k] + G @ U[:, k]
+    return Z
+
+
+def real_block_operator(lam: np.ndarray, kinds) -> np.ndarray:
+    """The real r x r operator L with xi_{k+1} = L xi_k in real-form coordinates.
+
+    For a pair column c: (c0, c1) = (Re y, -Im y) with y -> lambda y, i.e. the
+    block [[Re l, Im l], [-Im l, Re l]]; a real eigenvalue is a 1x1 block.
+    """
+    r = len(lam)
+    L = np.zeros((r, r))
+    for c in range(r):
+        if kinds[c] == 1:
+            lr, li = lam[c].real, lam[c].imag
+            L[c:c + 2, c:c + 2] = [[lr, li], [-li, lr]]
+        elif kinds[c] == 0:
+            L[c, c] = lam[c].real
+    return L
+
+
+def real_form_control(G: np.ndarray, kinds) -> np.ndarray:
+    """Real-form forcing G_R (r x q): the pair rows are (Re 2g, -Im 2g) like beta."""
+    r, q = G.shape
+    GR = np.zeros((r, q))
+    for c in range(r):
+        if kinds[c] == 1:
+            GR[c], GR[c + 1] = (2 * G[c]).real, -(2 * G[c]).imag
+        elif kinds[c] == 0:
+            GR[c] = G[c].real
+    return GR
+
+
+def rollout_real(L: np.ndarray, beta: np.ndarray, GR: np.ndarray, U: np.ndarray, steps: int) -> np.ndarray:
+    """xi_0 = beta, xi_{k+1} = L xi_k + G_R u_k; returns r x (steps+1)."""
+    Xi = np.empty((len(beta), steps + 1))
+    Xi[:, 0] = beta
+    for k in range(steps):
+        Xi[:, k + 1] = L @ Xi[:, k] + GR @ U[:, k]
+    return Xi
+
+
+# ----------------------------------------------------------------------------
+# adjoint of the prediction (gradients for the inverse-design use, Sec. 7.2)
+# ----------------------------------------------------------------------------
+
+
+def predict_adjoint(lam: np.ndarray, beta: np.ndarray, ks, dC: np.ndarray, kinds=None):
+    """Gradients of a loss L(C) w.r.t. (Re lambda, Im lambda) and beta.
+
+    dC (r x K) = dL/dC.  For a pair with y_k = lambda^k zeta, zeta = beta_c - i beta_{c+1},
+    C[c,k] = Re y_k, C[c+1,k] = -Im y_k, so the real gradient of y_k is
+    g_k = dC[c,k] - i dC[c+1,k] and, y being holomorphic in (lambda, zeta),
+    dL/dzeta = sum_k conj(lambda^k) g_k, dL/dlambda = sum_k conj(k lambda^{k-1} zeta) g_k
+    (each as dRe + i dIm).  Then dbeta_c = Re dL/dzeta, dbeta_{c+1} = -Im dL/dzeta.
+    The pair's (Re lambda, Im lambda) gradient is stored in both its columns
+    (the conjugate member is tied to the first).  Real modes: C = lambda^k beta.
+    """
+    if kinds is None:
+        kinds = pair_kinds(lam)
+    r = len(lam)
+    dlam_re, dlam_im, dbeta = np.zeros(r), np.zeros(r), np.zeros(r)
+    for c in range(r):
+        if kinds[c] == 1:
+            zeta = beta[c] - 1j * beta[c + 1]
+            gz = 0j
+            gl = 0j
+            for j, k in enumerate(ks):
+                k = int(k)
+                g = dC[c, j] - 1j * dC[c + 1, j]
+                gz += np.conj(int_power(lam[c:c + 1], k)[0]) * g
+                if k != 0:
+                    gl += np.conj(k * int_power(lam[c:c + 1], k - 1)[0] * zeta) * g
+            dbeta[c], dbeta[c + 1] = gz.real, -gz.imag
+            dlam_re[c] = dlam_re[c + 1] = gl.real
+            dlam_im[c] = dlam_im[c + 1] = gl.imag
+        elif kinds[c] == 0:
+            lr = lam[c].real
+            for j, k in enumerate(ks):
+                k = int(k)
+                dbeta[c] += lr ** k * dC[c, j]
+                if k != 0:
+                    dlam_re[c] += k * lr ** (k - 1) * beta[c] * dC[c, j]
+    return dlam_re, dlam_im, dbeta
+
+
+def rollout_adjoint(L: np.ndarray, GR: np.ndarray, Xi: np.ndarray, dXi: np.ndarray, kinds):
+    """Reverse recursion of xi_{k+1} = L xi_k + G_R u_k.
+
+    dXi (r x (T+1)) = dL/dxi_k taken directly by the loss.  mu_T = dXi_T,
+    mu_k = L^T mu_{k+1} + dXi_k; dL/du_k = G_R^T mu_{k+1}; dL/dbeta = mu_0;
+    dL/dL_block accumulates mu_{k+1} xi_k^T over k and maps to (Re l, Im l)
+    through the block pattern [[a, b], [-b, a]].
+    """
+    r, T1 = Xi.shape
+    T = T1 - 1
+    mu = dXi[:, T].copy()
+    du = np.zeros((GR.shape[1], T))
+    dLmat = np.zeros((r, r))
+    for k in range(T - 1, -1, -1):
+        du[:, k] = GR.T @ mu
+        dLmat += np.outer(mu, Xi[:, k])
+        mu = L.T @ mu + dXi[:, k]
+    dlam_re, dlam_im = np.zeros(r), np.zeros(r)
+    for c in range(r):
+        if kinds[c] == 1:
+            a = dLmat[c, c] + dLmat[c + 1, c + 1]
+            bb = dLmat[c, c + 1] - dLmat[c + 1, c]
+            dlam_re[c] = dlam_re[c + 1] = a
+            dlam_im[c] = dlam_im[c + 1] = bb
+        elif kinds[c] == 0:
+            dlam_re[c] = dLmat[c, c]
+    return dlam_re, dlam_im, mu, du

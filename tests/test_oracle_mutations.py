@@ -1,0 +1,154 @@
+"""Planted mistakes in the oracle (on the CPU) must each fail a pin.
+
+Every mutation below is a plausible slip -- a dropped or swapped term, a wrong
+sign or index, a transposed operand -- applied to one oracle function with
+monkeypatch; the pins of test_oracle_pins.py are then re-run from scratch and
+at least one of them has to fail.
+"""
+import numpy as np
+import pytest
+
+from oracle import dmd_oracle as O
+from oracle import philox
+from paper_2502_05339_gb300 import synth
+import tests.test_oracle_pins as P
+
+
+def _cfg0_exact():
+    sc = synth.config0(noise=0.0, keep_fp64=True)
+    return sc, O.exact_dmd(sc.extra["S64"], 20)
+
+
+def _pins():
+    yield lambda: P.pin_bruteforce(12, 8)
+    yield lambda: P.pin_bruteforce(12, 8, r=5)
+    yield P.test_reduced_operator_projects_full_operator
+    fx = _cfg0_exact()
+    yield lambda: P.test_known_operator_eigenvalues(fx)
+    yield lambda: P.test_known_operator_reconstructs_window(fx)
+    yield lambda: P.test_exponential_integration_equals_operator_power(fx)
+    yield lambda: P.test_real_form_matches_complex(fx)
+    yield lambda: P.test_reversal(fx)
+    yield lambda: P.test_mode_products_match_ground_truth(fx)
+    yield P.test_int_power_matches_polar
+    yield P.test_rsvd_exact_when_rank_le_sketch
+    yield P.test_philox_published_vectors
+    yield P.test_adjoint_matches_central_differences
+
+
+def _count_failures():
+    fails = 0
+    for pin in _pins():
+        try:
+            pin()
+        except (AssertionError, np.linalg.LinAlgError, ValueError, IndexError):
+            fails += 1
+    return fails
+
+
+def _mut_split(S):
+    S = np.asarray(S, dtype=np.float64)
+    return S[:, :-1], S[:, :-1]                 # X' replaced by X
+
+
+def _mut_reduced_scale(U, s, V, Xp):
+    return (U.T @ Xp @ V) * s[None, :]         # Sigma instead of Sigma^-1
+
+
+def _mut_reduced_transpose(U, s, V, Xp):
+    return ((U.T @ Xp @ V) / s[None, :]).T
+
+
+def _mut_reduced_rowscale(U, s, V, Xp):
+    return (U.T @ Xp @ V) / s[:, None]         # Sigma^-1 on the wrong side
+
+
+_orig_int_power = O.int_power
+
+
+def _mut_power(z, k):
+    return _orig_int_power(z, k - 1 if k > 0 else k)
+
+
+_orig_real_form = O.to_real_form
+
+
+def _mut_real_form(Phi, lam, b):
+    PhiR, beta, kinds = _orig_real_form(Phi, lam, b)
+    beta = beta.copy()
+    beta[kinds == 2] *= -1.0                    # sign of Im(zeta) flipped
+    return PhiR, beta, kinds
+
+
+_orig_coefficients = O.coefficients
+
+
+def _mut_coefficients(lam, beta, ks, kinds=None):
+    C = _orig_coefficients(lam, beta, ks, kinds)
+    kk = O.pair_kinds(lam) if kinds is None else kinds
+    C[kk == 2] *= -1.0                          # + Im instead of - Im
+    return C
+
+
+_orig_svd = O.svd_truncated
+
+
+def _mut_svd(X, r):
+    U, s, V = _orig_svd(X, r)
+    return U[:, ::-1].copy(), s, V             # U columns out of order
+
+
+def _mut_amplitudes(Phi, x0):
+    b, *_ = np.linalg.lstsq(Phi, (1.0001 * x0).astype(complex), rcond=None)
+    return b
+
+
+_orig_adjoint = O.predict_adjoint
+
+
+def _mut_adjoint(lam, beta, ks, dC, kinds=None):
+    a, b, c = _orig_adjoint(lam, np.conj(beta), ks, dC, kinds)
+    kk = O.pair_kinds(lam) if kinds is None else kinds
+    c = c.copy()
+    c[kk == 2] *= -1.0
+    return a, b, c
+
+
+def _mut_philox(ctr, key):
+    c = list(ctr)
+    c[0], c[2] = c[2], c[0]                     # multipliers on swapped words
+    return _orig_philox(c, key)
+
+
+_orig_philox = philox.philox4x32_10
+_orig_mode_products = O.mode_products
+
+
+def _mut_mode_products(PhiR, beta, kinds):
+    return 2.0 * _orig_mode_products(PhiR, beta, kinds)   # dropped the 1/2
+
+
+MUTATIONS = [
+    ("split_snapshots", _mut_split, O),
+    ("reduced_operator", _mut_reduced_scale, O),
+    ("reduced_operator", _mut_reduced_transpose, O),
+    ("reduced_operator", _mut_reduced_rowscale, O),
+    ("int_power", _mut_power, O),
+    ("to_real_form", _mut_real_form, O),
+    ("coefficients", _mut_coefficients, O),
+    ("svd_truncated", _mut_svd, O),
+    ("amplitudes", _mut_amplitudes, O),
+    ("predict_adjoint", _mut_adjoint, O),
+    ("philox4x32_10", _mut_philox, philox),
+    ("mode_products", _mut_mode_products, O),
+]
+
+
+@pytest.mark.parametrize("name,fn,mod", MUTATIONS, ids=[f"{m[0]}-{i}" for i, m in enumerate(MUTATIONS)])
+def test_planted_mistake_is_caught(monkeypatch, name, fn, mod):
+    monkeypatch.setattr(mod, name, fn)
+    assert _count_failures() >= 1
+
+
+def test_unmutated_oracle_passes_all_pins():
+    assert _count_failures() == 0

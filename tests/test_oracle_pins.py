@@ -1,0 +1,429 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula: each checks the oracle against an
+independent fact -- brute force on tiny inputs, eigenvalues of a known
+generating operator, closed-form identities, invariants, published test
+vectors -- chosen so that a dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them (see
+test_oracle_mutations.py, which plants such mistakes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dmd_oracle as O
+from oracle import philox
+from paper_2502_05339_gb300 import synth
+
+GOLDEN = __file__.rsplit("/", 1)[0] + "/golden"
+
+
+def match_eigs(lam, ref):
+    """Greedy minimum-distance matching; returns max |lam_i - ref_j|."""
+    ref = list(ref)
+    worst = 0.0
+    for v in lam:
+        j = int(np.argmin([abs(v - t) for t in ref]))
+        worst = max(worst, abs(v - ref[j]))
+        ref.pop(j)
+    return worst
+
+
+@pytest.fixture(scope="module")
+def exact_cfg0():
+    sc = synth.config0(noise=0.0, keep_fp64=True)
+    return sc, O.exact_dmd(sc.extra["S64"], 20)
+
+
+# ---------------------------------------------------------------- brute force
+
+
+def pin_bruteforce(n=12, m=8, r=None, seed=3):
+    """Tiny case: exact DMD eigenpairs are eigenpairs of K = X' V_r S_r^-1 U_r^T.
+
+    With r = rank(X) this is the full least-squares operator X' X^+ (Eq.
+    reduced_koopman / reduced_koopman_solution); its nonzero spectrum is brute
+    forced with a dense n x n eigensolve.
+    """
+    g = np.random.default_rng(seed)
+    S = g.standard_normal((n, m + 1))
+    X, Xp = S[:, :m], S[:, 1:]
+    r = r or m
+    res = O.exact_dmd(S, r)
+    if r == m:
+        K = Xp @ np.linalg.pinv(X)
+    else:
+        U, s, Vt = np.linalg.svd(X)
+        K = Xp @ Vt[:r].T @ np.diag(1 / s[:r]) @ U[:, :r].T
+    ev = np.linalg.eigvals(K)
+    ev = ev[np.argsort(-np.abs(ev))][:r]
+    assert match_eigs(res["lam"], ev) < 1e-12 * max(1, np.abs(ev).max())
+    # exact modes are eigenvectors of the full operator
+    Phi, lam = res["Phi"], res["lam"]
+    resid = np.linalg.norm(K @ Phi - Phi * lam[None, :]) / np.linalg.norm(Phi)
+    assert resid < 1e-11
+    # amplitudes: minimum-norm residual, characterised by orthogonality of the
+    # residual to range(Phi)
+    b = res["b"]
+    rvec = Phi @ b - X[:, 0]
+    assert np.linalg.norm(Phi.conj().T @ rvec) < 1e-11 * np.linalg.norm(Phi) * np.linalg.norm(X[:, 0])
+    # the full operator maps each snapshot to the next exactly when r = rank
+    if r == m:
+        np.testing.assert_allclose(K @ X, Xp, atol=1e-10)
+    return res
+
+
+def test_bruteforce_full_rank():
+    pin_bruteforce(12, 8)
+
+
+def test_bruteforce_truncated():
+    pin_bruteforce(12, 8, r=5)
+    pin_bruteforce(10, 6, r=3, seed=11)
+
+
+def test_reduced_operator_projects_full_operator():
+    """A~ = U^T K~ U (Sec. 3.1): the reduced operator is the projection of the
+    truncated full operator onto the left singular basis."""
+    g = np.random.default_rng(5)
+    S = g.standard_normal((30, 11))
+    X, Xp = S[:, :10], S[:, 1:]
+    r = 6
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    Kt = Xp @ Vt[:r].T @ np.diag(1 / s[:r]) @ U[:, :r].T
+    res = O.exact_dmd(S, r)
+    Ur = res["U"]
+    np.testing.assert_allclose(res["Atilde"], Ur.T @ Kt @ Ur, atol=1e-12)
+
+
+# ---------------------------------------------------------- known operator
+
+
+def test_known_operator_eigenvalues(exact_cfg0):
+    """Snapshots generated exactly by a linear map with known spectrum return
+    that spectrum (cfg0 generator, noise 0) to 1e-10."""
+    sc, res = exact_cfg0
+    assert match_eigs(res["lam"], sc.lam_true) < 1e-10
+
+
+def test_known_operator_3d():
+    sc = synth.linear_modes_scene(12, 3, 5, 30, 77, keep_fp64=True)
+    res = O.exact_dmd(sc.extra["S64"], 10)
+    assert match_eigs(res["lam"], sc.lam_true) < 1e-10
+
+
+def test_known_operator_reconstructs_window(exact_cfg0):
+    sc, res = exact_cfg0
+    S = sc.extra["S64"]
+    F = O.predict(res["Phi"], res["lam"], res["b"], range(S.shape[1]))
+    assert np.linalg.norm(F - S) / np.linalg.norm(S) < 1e-11
+
+
+# ----------------------------------------------------- exponential integration
+
+
+def test_exponential_integration_equals_operator_power(exact_cfg0):
+    """Phi Lambda^k b = X' V S^-1 A~^k W b since W Lambda = A~ W (Eq. large_time_step)."""
+    sc, res = exact_cfg0
+    S = sc.extra["S64"]
+    Xp = S[:, 1:]
+    V, s, W, b, At = res["V"], res["s"], res["W"], res["b"], res["Atilde"]
+    Wb = W @ b
+    Ak = np.eye(At.shape[0], dtype=complex)
+    ks = list(range(0, 501))
+    F = O.predict(res["Phi"], res["lam"], b, ks)
+    lift = Xp @ (V / s[None, :])
+    for k in ks:
+        ref = (lift @ (Ak @ Wb)).real
+        assert np.linalg.norm(F[:, k] - ref) <= 1e-10 * max(np.linalg.norm(ref), 1e-300) + 1e-13
+        Ak = At @ Ak
+
+
+def test_real_form_matches_complex(exact_cfg0):
+    sc, res = exact_cfg0
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    ks = [0, 1, 7, 99, 100, 250, 500, -3]
+    C = O.coefficients(res["lam"], beta, ks, kinds)
+    F = O.predict_real(PhiR, C)
+    Fc = O.predict(res["Phi"], res["lam"], res["b"], ks)
+    assert np.linalg.norm(F - Fc) / np.linalg.norm(Fc) < 1e-13
+    np.testing.assert_allclose(C[:, 0], beta, atol=0)
+
+
+def test_int_power_matches_polar():
+    z = np.array([0.97 * np.exp(0.3j), 1.01 * np.exp(-2.0j), -0.5 + 0j, 0.8j])
+    for k in [0, 1, 2, 3, 17, 500, 1000, -1, -7]:
+        np.testing.assert_allclose(O.int_power(z, k), np.abs(z) ** k * np.exp(1j * k * np.angle(z)),
+                                   rtol=1e-12)
+
+
+# ------------------------------------------------------------------ reversal
+
+
+def test_reversal(exact_cfg0):
+    """K~^{-1} = Phi Lambda^{-1} Phi^+ undoes one step (Eq. reverse_simulation),
+    and Lambda^{-k} Lambda^k = I on the reduced state."""
+    sc, res = exact_cfg0
+    Phi, lam, b = res["Phi"], res["lam"], res["b"]
+    for k in [1, 5, 60, 200]:
+        xk1 = O.predict(Phi, lam, b, [k + 1])[:, 0]
+        xk = O.predict(Phi, lam, b, [k])[:, 0]
+        z = np.linalg.lstsq(Phi, xk1.astype(complex), rcond=None)[0]
+        back = (Phi @ (z / lam)).real
+        assert np.linalg.norm(back - xk) < 1e-10 * np.linalg.norm(xk)
+        zk = O.int_power(lam, k) * b
+        np.testing.assert_allclose(O.int_power(lam, -k) * zk, b, rtol=1e-11, atol=1e-14)
+    # backward frames from negative k satisfy the forward step
+    xm = O.predict(Phi, lam, b, [-10, -9])
+    z = np.linalg.lstsq(Phi, xm[:, 0].astype(complex), rcond=None)[0]
+    assert np.linalg.norm((Phi @ (lam * z)).real - xm[:, 1]) < 1e-10 * np.linalg.norm(xm[:, 1])
+
+
+# --------------------------------------------------------- divergence free
+
+
+def test_divergence_free_2d(exact_cfg0):
+    """C X = 0 implies C Phi = 0 (Sec. 4.5): reconstructions stay divergence-free."""
+    sc, res = exact_cfg0
+    S = sc.extra["S64"]
+    div_in = synth.div2d(__import__("torch").as_tensor(S.T), sc.N).numpy()
+    assert np.abs(div_in).max() < 1e-12 * np.abs(S).max()
+    F = O.predict(res["Phi"], res["lam"], res["b"], [0, 1, 50, 99, 100, 300, 500])
+    import torch
+    d = synth.div2d(torch.as_tensor(F.T), sc.N).numpy()
+    rel = np.linalg.norm(d, axis=1) / np.linalg.norm(F, axis=0)
+    assert rel.max() < 1e-13
+
+
+def test_divergence_free_3d():
+    import torch
+    sc = synth.linear_modes_scene(16, 3, 6, 40, 91, keep_fp64=True)
+    res = O.exact_dmd(sc.extra["S64"], 12)
+    F = O.predict(res["Phi"], res["lam"], res["b"], [0, 3, 39, 40, 120])
+    d = synth.div3d(torch.as_tensor(F.T), sc.N).numpy()
+    rel = np.linalg.norm(d, axis=1) / np.linalg.norm(F, axis=0)
+    assert rel.max() < 1e-13
+
+
+def test_divergence_detects_non_solenoidal():
+    """The divergence check itself is not vacuous."""
+    import torch
+    g = np.random.default_rng(0)
+    x = torch.as_tensor(g.standard_normal(2 * 16 * 16))
+    assert float(synth.div2d(x, 16).norm()) > 1.0
+
+
+# ------------------------------------------------------------------- rSVD
+
+
+def test_rsvd_exact_when_rank_le_sketch():
+    """rSVD with rank(X) <= l reproduces the exact SVD and the exact DMD (Sec. 4.3)."""
+    sc = synth.linear_modes_scene(32, 2, 6, 40, 123, keep_fp64=True)   # rank 12
+    S = sc.extra["S64"]
+    X = S[:, :-1]
+    l = 16
+    Om = synth.random_sketch(X.shape[1], l, 5)
+    for q in (0, 1, 2):
+        U, s, V, Q = O.rsvd(X, Om, 12, q)
+        Ue, se, Ve = O.svd_truncated(X, 12)
+        np.testing.assert_allclose(s, se, rtol=1e-10)
+        assert np.linalg.norm(Q.T @ Q - np.eye(l)) < 1e-12
+        np.testing.assert_allclose(np.abs(V.T @ Ve), np.eye(12), atol=1e-8)
+    ex = O.exact_dmd(S, 12)
+    rs = O.rsvd_dmd(S, Om, 12, 1)
+    assert match_eigs(rs["lam"], ex["lam"]) < 1e-10
+    pe = O.mode_products(*O.to_real_form(ex["Phi"], ex["lam"], ex["b"]))
+    pr = O.mode_products(*O.to_real_form(rs["Phi"], rs["lam"], rs["b"]))
+    assert np.linalg.norm(pe - pr) / np.linalg.norm(pe) < 1e-9
+
+
+def test_rsvd_power_iterations_improve_subspace():
+    """With a slowly decaying spectrum, power iterations shrink the range error
+    (a standard property of the randomized range finder)."""
+    g = np.random.default_rng(1)
+    U, _ = np.linalg.qr(g.standard_normal((400, 60)))
+    V, _ = np.linalg.qr(g.standard_normal((60, 60)))
+    s = 1.0 / (1 + np.arange(60)) ** 0.5
+    X = U @ np.diag(s) @ V.T
+    Om = g.standard_normal((60, 15))
+    errs = []
+    for q in (0, 1, 3):
+        *_, Q = O.rsvd(X, Om, 10, q)
+        errs.append(np.linalg.norm(X - Q @ (Q.T @ X), 2))
+    assert errs[0] > errs[1] > errs[2] * 0.999
+    assert errs[2] < 1.2 * s[15]
+
+
+# ---------------------------------------------------------------- Philox
+
+
+def test_philox_published_vectors():
+    """Known-answer vectors of Philox4x32-10 (Salmon et al., SC'11; golden file)."""
+    rows = [l.split() for l in open(f"{GOLDEN}/philox4x32_10_kat.txt") if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        vals = [int(v, 16) for v in row]
+        ctr, key, out = vals[0:4], vals[4:6], vals[6:10]
+        assert list(philox.philox4x32_10(ctr, key)) == out
+
+
+def test_sketch_matrix_is_standard_normal():
+    Om = philox.sketch_matrix(200, 40, 1234)
+    assert abs(Om.mean()) < 0.03 and abs(Om.std() - 1) < 0.03
+    # two Box-Muller outputs of one pair are uncorrelated
+    assert abs(np.corrcoef(Om.T.ravel()[0::2], Om.T.ravel()[1::2])[0, 1]) < 0.05
+    assert not np.allclose(Om, philox.sketch_matrix(200, 40, 1235))
+
+
+# --------------------------------------------------------------- adjoint
+
+
+def _quad_loss_setup(seed=4):
+    sc = synth.linear_modes_scene(16, 2, 4, 30, seed, keep_fp64=True)
+    res = O.exact_dmd(sc.extra["S64"], 8)
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    g = np.random.default_rng(seed)
+    ks = [0, 3, 10, 29, 45]
+    tgt = g.standard_normal(PhiR.shape[0])
+    w = g.uniform(0, 1, len(ks))
+    return res["lam"], beta, kinds, PhiR, ks, tgt, w
+
+
+def _loss(lam, beta, kinds, PhiR, ks, tgt, w):
+    F = O.predict_real(PhiR, O.coefficients(lam, beta, ks, kinds))
+    return 0.5 * float(np.sum(w * np.sum((F - tgt[:, None]) ** 2, axis=0)))
+
+
+def test_adjoint_matches_central_differences():
+    """Hand-written adjoint vs central FD (h = 1e-3) on the FP64 forward; for this
+    quadratic-in-beta loss FD in beta is exact up to rounding."""
+    lam, beta, kinds, PhiR, ks, tgt, w = _quad_loss_setup()
+    F = O.predict_real(PhiR, O.coefficients(lam, beta, ks, kinds))
+    dF = (F - tgt[:, None]) * w[None, :]
+    dC = PhiR.T @ dF
+    dlr, dli, db = O.predict_adjoint(lam, beta, ks, dC, kinds)
+    h = 1e-3
+    for c in range(len(beta)):
+        bp, bm = beta.copy(), beta.copy()
+        bp[c] += h
+        bm[c] -= h
+        fd = (_loss(lam, bp, kinds, PhiR, ks, tgt, w) - _loss(lam, bm, kinds, PhiR, ks, tgt, w)) / (2 * h)
+        assert abs(fd - db[c]) <= 1e-8 * max(1.0, abs(fd))
+    h = 1e-6
+    for c in range(len(beta)):
+        if kinds[c] == 2:
+            continue
+        for part, ref in ((1, dlr[c]), (1j, dli[c])):
+            if kinds[c] == 0 and part == 1j:
+                continue
+            lp, lm = lam.copy(), lam.copy()
+            lp[c] += h * part
+            lm[c] -= h * part
+            if kinds[c] == 1:
+                lp[c + 1], lm[c + 1] = np.conj(lp[c]), np.conj(lm[c])
+            fd = (_loss(lp, beta, kinds, PhiR, ks, tgt, w) - _loss(lm, beta, kinds, PhiR, ks, tgt, w)) / (2 * h)
+            assert abs(fd - ref) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------------ DMDc
+
+
+@pytest.fixture(scope="module")
+def dmdc_small():
+    sc = synth.controlled_scene(16, 2, 4, 60, 2, 31)
+    res = O.dmdc(sc.extra["S64"], sc.extra["U"], 8)
+    return sc, res
+
+
+def test_dmdc_recovers_eigenvalues(dmdc_small):
+    sc, res = dmdc_small
+    assert match_eigs(res["lam"], sc.lam_true) < 1e-10
+
+
+def test_dmdc_reproduces_controlled_trajectory(dmdc_small):
+    """Rolling out z_{k+1} = Lambda z_k + G u_k (Eq. external_forces) from b
+    reproduces the training window, and a fresh input sequence reproduces the
+    generator's response to it."""
+    sc, res = dmdc_small
+    S = sc.extra["S64"]
+    m = S.shape[1] - 1
+    Z = O.dmdc_rollout(res["lam"], res["b"], res["G"], sc.extra["U"], m)
+    F = (res["Phi"] @ Z).real
+    assert np.linalg.norm(F - S) / np.linalg.norm(S) < 1e-10
+    g = np.random.default_rng(9)
+    U2 = synth.piecewise_controls(g, 2, 80)
+    z = sc.extra["z"][:, 0].copy()
+    modes = sc.modes_true.numpy()
+    for k in range(80):
+        z = sc.extra["L"] @ z + sc.extra["PF"] @ U2[:, k]
+    truth = modes.T @ z
+    Z2 = O.dmdc_rollout(res["lam"], res["b"], res["G"], U2, 80)
+    pred = (res["Phi"] @ Z2[:, -1]).real
+    assert np.linalg.norm(pred - truth) / np.linalg.norm(truth) < 1e-9
+
+
+def test_dmdc_real_form_rollout_and_adjoint(dmdc_small):
+    """Real 2x2-block rollout equals the complex one; its reverse recursion
+    matches central differences of ||x_T - x_tgt||^2 in u_k and beta."""
+    sc, res = dmdc_small
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    L = O.real_block_operator(res["lam"], kinds)
+    GR = O.real_form_control(res["G"], kinds)
+    U = sc.extra["U"][:, :25]
+    T = 25
+    Xi = O.rollout_real(L, beta, GR, U, T)
+    Zc = O.dmdc_rollout(res["lam"], res["b"], res["G"], U, T)
+    np.testing.assert_allclose(PhiR @ Xi, (res["Phi"] @ Zc).real, atol=1e-10)
+    g = np.random.default_rng(2)
+    tgt = g.standard_normal(PhiR.shape[0])
+
+    def loss(beta_, U_):
+        xi = O.rollout_real(L, beta_, GR, U_, T)
+        x = PhiR @ xi[:, -1]
+        return float(np.sum((x - tgt) ** 2))
+
+    xT = PhiR @ Xi[:, -1]
+    dXi = np.zeros_like(Xi)
+    dXi[:, -1] = PhiR.T @ (2 * (xT - tgt))
+    dlr, dli, db, du = O.rollout_adjoint(L, GR, Xi, dXi, kinds)
+    h = 1e-3
+    for (i, k) in [(0, 0), (1, 7), (0, 24), (1, 13)]:
+        Up, Um = U.copy(), U.copy()
+        Up[i, k] += h
+        Um[i, k] -= h
+        fd = (loss(beta, Up) - loss(beta, Um)) / (2 * h)
+        assert abs(fd - du[i, k]) <= 1e-8 * max(1, abs(fd))
+    for c in [0, 1, 5]:
+        bp, bm = beta.copy(), beta.copy()
+        bp[c] += h
+        bm[c] -= h
+        fd = (loss(bp, U) - loss(bm, U)) / (2 * h)
+        assert abs(fd - db[c]) <= 1e-8 * max(1, abs(fd))
+
+
+# ------------------------------------------------------------- paper table
+
+
+def test_runtime_table_ratios():
+    """Internal consistency of the paper's runtime table (Tab. dmd_runtime):
+    754 ms / 8.9 us ~ 84,719x, 754 / 16.15 ~ 47x, 754 / 0.95 ~ 794x."""
+    assert round(754e-3 / 8.9e-6) == 84719
+    assert round(754 / 16.15) == 47
+    assert round(754 / 0.95) == 794
+
+
+def test_mode_products_match_ground_truth(exact_cfg0):
+    """The scale-free per-mode field phi_j b_j equals the generator's
+    a_j * phi_true_j (the pair contributes 2 Re(phi b lambda^k))."""
+    sc, res = exact_cfg0
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    got = O.mode_products(PhiR, beta, kinds)
+    heads = [c for c in range(len(kinds)) if kinds[c] != 2]
+    lam_heads = res["lam"][heads]
+    modes = sc.modes_true.numpy()
+    lam_true = sc.lam_true[0::2]
+    for j, lt in enumerate(lam_true):
+        c = int(np.argmin(np.abs(lam_heads - lt)))
+        truth = sc.amps_true[j] * (modes[2 * j] + 1j * modes[2 * j + 1])
+        assert np.linalg.norm(got[:, c] - truth) < 1e-10 * np.linalg.norm(truth)
