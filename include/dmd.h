@@ -1,0 +1,227 @@
+/*
+ * libdmd -- C ABI of the GB300 (sm_103a) DMD / DMDc hot path.
+ *
+ * Method: "Fast Subspace Fluid Simulation with a Temporally-Aware Basis"
+ * (arXiv 2502.05339).  The library fits an exact DMD operator from a tall
+ * snapshot matrix through a randomized SVD (Sec. 3.1, Sec. 4.3, Sec. 4.6) and
+ * predicts many time points at once by exponential integration
+ * u(t + k dt) = Phi Lambda^k z(t) (Eq. large_time_step), with a hand-written
+ * adjoint of the prediction.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major.  A tall matrix with n rows uses a leading
+ *   dimension ld >= n with ld % 4 == 0 (16-byte column starts, as TMA needs).
+ * - Every pointer argument is a DEVICE pointer unless stated otherwise.  The
+ *   caller owns all memory (inputs, outputs, workspace); the library never
+ *   allocates or frees device memory and keeps no pointer after the stream
+ *   work it enqueued has finished.
+ * - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL
+ *   for the legacy default stream).  The return value reports argument errors
+ *   (DMD_EINVAL), a workspace that is too small (DMD_ENOMEM) and launch
+ *   failures (DMD_ECUDA).  Failures found on the device (numerical breakdown,
+ *   rank deficiency, non-finite input, a bounded wait that ran out) are
+ *   written to the device status word info[0]; read it after synchronising.
+ * - No C++ exception crosses this boundary.  dmd_last_error() returns a
+ *   thread-local description of the last host-side failure.
+ * - Precision: DMD_FP32 runs the passes over the snapshots in plain FP32 on
+ *   the CUDA cores; DMD_MIXED_BF16X3 runs them on the tcgen05 tensor cores
+ *   with every FP32 operand split into bf16 hi + lo and the products
+ *   hi*hi + hi*lo + lo*hi accumulated in FP32.  The small dense solvers
+ *   (Cholesky, SVD of B, the reduced operator, its eigendecomposition, the
+ *   least-squares amplitudes) run in FP64 in both forms.
+ *
+ * Real 2x2-block model layout ("modal" buffer, FP64, device)
+ * -----------------------------------------------------------
+ * For rank r and q control channels the model occupies DMD_MODAL_DOUBLES(r, q)
+ * doubles:
+ *   lam_re[r], lam_im[r]   eigenvalue of each column of Phi_R;
+ *   beta[r]                real amplitudes (the coefficient vector at k = 0);
+ *   sigma[r]               singular values of the snapshot matrix X (descending);
+ *   G[r*q]                 real-form forcing (column-major r x q), DMDc only.
+ * A conjugate pair (lambda, conj lambda) with mode phi and amplitude b owns two
+ * adjacent columns c, c+1: Phi_R[:, c] = Re phi, Phi_R[:, c+1] = Im phi,
+ * lam_im[c] > 0, lam_im[c+1] = -lam_im[c], beta[c] = Re(2b), beta[c+1] = -Im(2b).
+ * A real eigenvalue owns one column with lam_im = 0.  Frame k is
+ * x_k = Phi_R C[:, k] with, for a pair, y = lambda^k (beta[c] - i beta[c+1]),
+ * C[c, k] = Re y, C[c+1, k] = -Im y, and C[c, k] = lambda^k beta[c] for a real
+ * column.  Columns are in canonical order: |lambda| descending, then Im
+ * descending, each pair's Im > 0 member first.
+ */
+#ifndef DMD_H
+#define DMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DMD_EXPORT __attribute__((visibility("default")))
+#else
+#define DMD_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dmd_status;
+enum {
+  DMD_OK = 0,
+  DMD_EINVAL = 1,      /* invalid argument (host check)                         */
+  DMD_ENOMEM = 2,      /* workspace smaller than the size query returned        */
+  DMD_ENUMERIC = 3,    /* numerical breakdown (Cholesky pivot <= 0, no QR convergence) */
+  DMD_ERANK = 4,       /* sigma_r <= 1e-6 sigma_1: requested rank not supported by the data */
+  DMD_ENONFINITE = 5,  /* NaN or Inf in the snapshots                            */
+  DMD_ETIMEOUT = 6,    /* a bounded device-side wait ran out                    */
+  DMD_ECUDA = 7        /* a CUDA runtime call or kernel launch failed            */
+};
+
+enum { DMD_FP32 = 0, DMD_MIXED_BF16X3 = 1 };
+
+/* Device status words (int32[DMD_INFO_WORDS]) written by dmd_fit:
+ *   info[0] status (dmd_status), info[1] number of conjugate pairs,
+ *   info[2] number of real eigenvalues, info[3] QR sweeps used,
+ *   info[4] tag of the first failure, info[5] number of Cholesky pivots
+ *   raised to the rank floor (directions the snapshots do not span). */
+#define DMD_INFO_WORDS 8
+
+#define DMD_MODAL_DOUBLES(r, q) ((size_t)(r) * (4 + (size_t)(q)))
+
+/* Fit problem (Sec. 3.1 and Sec. 4.3).  S = [x_0 .. x_m] is n x (m+1) FP32 with
+ * leading dimension ldS; X = S[:, 0:m] and X' = S[:, 1:m+1] are views of it.
+ * l = min(r + oversample, m) is the sketch width; power_iters the number of
+ * power iterations.  q > 0 selects DMD with control (Eq. external_forces):
+ * Ups is then q x m FP32 (column k = u_k, leading dimension q).  If Omega is
+ * non-NULL it is the m x l FP64 Gaussian test matrix (column-major, ld m);
+ * otherwise the library draws it on the device from Philox4x32-10 keyed by
+ * `seed`. */
+typedef struct dmd_fit_desc {
+  int64_t n;
+  int64_t ldS;
+  int64_t ldPhi;       /* leading dimension of the Phi_R output             */
+  int32_t m;
+  int32_t r;
+  int32_t oversample;
+  int32_t power_iters;
+  int32_t q;           /* control channels, 0 = plain DMD                    */
+  int32_t precision;   /* DMD_FP32 or DMD_MIXED_BF16X3                       */
+  uint64_t seed;
+} dmd_fit_desc;
+
+/* Frames request for dmd_predict / dmd_predict_backward (Eq. large_time_step).
+ * k[0..K) are integer time indices (device int32).  Without control (q == 0)
+ * any k is allowed, negative k reverses time (Eq. reverse_simulation).  With
+ * control, the reduced state is rolled out z_{t+1} = Lambda z_t + G u_t
+ * (Eq. external_forces) for t < steps from z_0 = beta, and every k must lie in
+ * [0, steps]; u is q x steps FP32 (column t = u_t, leading dimension q). */
+typedef struct dmd_predict_desc {
+  int64_t n;
+  int64_t ldPhi;
+  int64_t ldOut;
+  int32_t r;
+  int32_t K;
+  int32_t q;
+  int32_t steps;
+  int32_t precision;
+  int32_t chunk;       /* frames per recompute chunk in the loss entry points (0 = 50) */
+} dmd_predict_desc;
+
+DMD_EXPORT const char* dmd_last_error(void);
+DMD_EXPORT const char* dmd_version(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side counter, for accounting in benchmarks). */
+DMD_EXPORT uint64_t dmd_launch_count(void);
+
+/* ---- fit ---------------------------------------------------------------- */
+
+/* Workspace bytes dmd_fit needs for this problem (host-side query, no GPU). */
+DMD_EXPORT dmd_status dmd_fit_workspace_bytes(const dmd_fit_desc* desc, size_t* bytes);
+
+/* Fit the exact DMD (or DMDc) model of S.
+ * Outputs: Phi_R (n x r FP32, ld desc->ldPhi), modal (DMD_MODAL_DOUBLES(r, q)
+ * doubles, layout above), info (DMD_INFO_WORDS int32).  Steps: Philox sketch
+ * Omega; Y = X Omega; CholeskyQR2; power iterations; P = Q^T S; SVD of
+ * B = P[:, 0:m]; reduced operator A~ = U_B^T (Q^T X') V Sigma^{-1} (Sec. 3.1);
+ * eigendecomposition A~ W = W Lambda; modes Phi = X' V Sigma^{-1} W written in
+ * real form; amplitudes b = Phi^+ x_0 by least squares in the Q basis
+ * (Eq. projection).  Errors: EINVAL if n < 1, m < 2, r < 1, r > min(m, n),
+ * r > 512, ldS < n, ldS % 4, ldPhi < n, ldPhi % 4 or a NULL pointer; ENOMEM
+ * if ws_bytes is below the query.  The workspace must be 256-byte aligned. */
+DMD_EXPORT dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const float* Ups,
+                   const double* Omega, float* Phi_R, double* modal, int32_t* info,
+                   void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- prediction (Eq. large_time_step, Eq. reverse_simulation, Eq. external_forces) */
+
+DMD_EXPORT dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);
+
+/* out (n x K FP32, ld desc->ldOut): frame j is x_{k[j]} = Phi_R C[:, j].
+ * The coefficients C are formed in FP64 on the device (lambda^k in polar form:
+ * |lambda|^k = exp(k log|lambda|), angle k*arg(lambda)); the reconstruction is
+ * one real GEMM Phi_R * C in the requested precision. */
+DMD_EXPORT dmd_status dmd_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                       const int32_t* k, const float* u, float* out,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/* Adjoint of dmd_predict.  dOut (n x K FP32, ld desc->ldOut) is dL/d(out).
+ * Writes d_modal (same layout as modal: dL/dRe(lambda), dL/dIm(lambda) per
+ * column -- a pair's value is stored in both its columns and belongs to the
+ * Im > 0 member --, dL/dbeta, zero for sigma, dL/dG for DMDc) and, with
+ * control, d_u (q x steps FP32) = dL/du_t.  Steps: dC = Phi_R^T dOut (split
+ * over n, FP64 reduction), then the FP64 chain rule through lambda^k and the
+ * reverse recursion mu_t = L^T mu_{t+1} + dC_t of the rollout. */
+DMD_EXPORT dmd_status dmd_predict_backward(const dmd_predict_desc* desc, const float* Phi_R,
+                                const double* modal, const int32_t* k, const float* u,
+                                const float* dOut, double* d_modal, float* d_u,
+                                void* workspace, size_t ws_bytes, void* stream);
+
+/* Streamed per-frame loss L = sum_j w_j * 0.5 * ||x_{k[j]} - target||^2 without
+ * storing the trajectory: frames are recomputed in chunks of desc->chunk,
+ * each chunk's residual is formed in the GEMM epilogue and reduced on the fly.
+ * target: n FP32; w: K FP64 weights (device).  loss: one double (device).
+ * With want_grad != 0 the same chunked recompute also accumulates
+ * dC = Phi_R^T (w_j (x_j - target)) and writes d_modal / d_u as
+ * dmd_predict_backward does. */
+DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                            const int32_t* k, const float* u, const float* target,
+                            const double* w, int32_t want_grad, double* loss,
+                            double* d_modal, float* d_u, void* workspace, size_t ws_bytes,
+                            void* stream);
+
+/* ---- component entry points (the building blocks, exposed for tests) ------ */
+
+/* Omega (m x l FP64, ld m) ~ N(0, 1) from Philox4x32-10 (Salmon et al. 2011):
+ * element e uses counter (e/4 lo, e/4 hi, 0x0D3D0001, 0), key (seed lo, seed hi)
+ * and output e % 4 of two Box-Muller pairs.  The randomized range finder of
+ * Sec. 4.3 multiplies X by this matrix. */
+DMD_EXPORT dmd_status dmd_sketch_matrix(int32_t m, int32_t l, uint64_t seed, double* Omega, void* stream);
+
+/* Raw Philox4x32-10 blocks: out[4*i .. 4*i+3] = philox(ctr = (i lo, i hi, stream_id, 0), key). */
+DMD_EXPORT dmd_status dmd_philox_blocks(int64_t count, uint32_t stream_id, uint64_t key, uint32_t* out,
+                             void* stream);
+
+/* Tall product C = A * B (the sketch X*Omega, the power step X*Z, the modes
+ * X'*M of Sec. 4.3 / Sec. 3.1 and the reconstruction Phi_R*C of
+ * Eq. large_time_step).  A: n x Kd FP32 (lda); B: Kd x N FP64 (ld Kd),
+ * rounded to FP32 or split to bf16 hi/lo inside; C: n x N FP32 (ldc).
+ * If gram != NULL it also writes the N x N FP64 Gram C^T C of the FP32 result. */
+DMD_EXPORT dmd_status dmd_gemm_tall_workspace_bytes(int32_t precision, int64_t n, int32_t Kd, int32_t N,
+                                         size_t* bytes);
+DMD_EXPORT dmd_status dmd_gemm_tall(int32_t precision, int64_t n, int32_t Kd, int32_t N, const float* A,
+                         int64_t lda, const double* B, float* C, int64_t ldc, double* gram,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* Reduction over the tall dimension C = A^T B (the power step X^T Q, the
+ * projection Q^T S of Sec. 4.3 and Gram matrices).  A: n x Ka FP32 (lda),
+ * B: n x N FP32 (ldb), C: Ka x N FP64 (ld Ka).  Per-block partial sums are
+ * FP64 and are added in a fixed order, so the result is bitwise reproducible. */
+DMD_EXPORT dmd_status dmd_gemm_tn_workspace_bytes(int32_t precision, int64_t n, int32_t Ka, int32_t N,
+                                       size_t* bytes);
+DMD_EXPORT dmd_status dmd_gemm_tn(int32_t precision, int64_t n, int32_t Ka, int32_t N, const float* A,
+                       int64_t lda, const float* B, int64_t ldb, double* C,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMD_H */

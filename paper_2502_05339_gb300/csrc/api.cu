@@ -1,0 +1,542 @@
+// C ABI of libdmd: argument checks, workspace carving and the orchestration
+// of the fit, prediction and adjoint on the caller's stream.
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "common.cuh"
+
+namespace dmd {
+
+// ---- host error string and launch counter -----------------------------------
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+// ---- kernels implemented in the other translation units ----------------------
+dmd_status launch_sketch(int m, int l, uint64_t seed, double* Om, cudaStream_t st);
+dmd_status launch_philox_blocks(int64_t count, uint32_t sid, uint64_t key, uint32_t* out, cudaStream_t st);
+int tn_splits(int64_t n, int Ka, int N);
+size_t tn_partial_doubles(int64_t n, int Ka, int N);
+dmd_status f32_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const float* B32, float* C,
+                       int64_t ldc, cudaStream_t st);
+dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                       double* C, double* part, cudaStream_t st);
+dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st);
+size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N);
+dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C,
+                        int64_t ldc, void* ws, cudaStream_t st);
+size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
+dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                        double* C, void* ws, cudaStream_t st);
+dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
+                 bool tb, double beta, double* C, int ldc, cudaStream_t st);
+dmd_status cholesky_upper(int n, double* G, int ld, int32_t* info, int tag, cudaStream_t st);
+dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st);
+dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st);
+dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y, int ldy, int nvec,
+                   cudaStream_t st);
+dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
+               cudaStream_t st);
+dmd_status collect_heads(int n, const double* wi, int* heads, int* nheads, int32_t* info, cudaStream_t st);
+dmd_status hess_eigvecs(int n, const double* H, int ldh, const double* wr, const double* wi, const int* heads,
+                        int nheads_max, double* Yre, double* Yim, double* work, const double* hnorm,
+                        cudaStream_t st);
+dmd_status normalize_complex(int n, double* Yre, double* Yim, int ncols, cudaStream_t st);
+dmd_status eig_layout(int n, const double* wr, const double* wi, const int* heads, const int* nheads,
+                      const double* Yre, const double* Yim, double* WR, double* lam_re, double* lam_im,
+                      int* order_scratch, int32_t* info, cudaStream_t st);
+dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, double* scratch, cudaStream_t st);
+dmd_status lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info, cudaStream_t st);
+dmd_status launch_coefficients(int r, int K, const double* modal, const int32_t* ks, double* C, cudaStream_t st);
+dmd_status launch_rollout(int r, int q, int steps, const double* modal, const float* u, double* Xi,
+                          cudaStream_t st);
+dmd_status launch_gather_cols(int r, int K, const double* Xi, const int32_t* ks, int steps, double* C,
+                              int32_t* info, cudaStream_t st);
+dmd_status launch_chain_closed(int r, int K, const double* modal, const int32_t* ks, const double* dC,
+                               double* dmodal, cudaStream_t st);
+dmd_status launch_rollout_adjoint(int r, int q, int steps, int K, const int32_t* ks, const double* modal,
+                                  const float* u, const double* Xi, const double* dC, double* dXi, double* Mu,
+                                  double* dmodal, float* du, cudaStream_t st);
+int loss_blocks();
+dmd_status launch_loss_chunk(int64_t n, int nf, float* F, int64_t ldf, const float* tgt, const double* w,
+                             bool grad, double* partial, double* loss, bool accumulate, cudaStream_t st);
+dmd_status fit_glue_sigma(int l, int r, const double* ev, double* sigma, double* inv_sq, int32_t* info,
+                          cudaStream_t st);
+dmd_status fit_glue_scale_cols(int rows, int cols, double* A, int lda, const double* s, cudaStream_t st);
+dmd_status fit_glue_check_finite(int64_t count, const double* A, int32_t* info, int tag, cudaStream_t st);
+dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStream_t st);
+dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st);
+dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st);
+
+namespace {
+
+// ---------------------------------------------------------- precision dispatch
+
+struct Tall {
+  int prec;
+  // scratch for the small FP64 operand rounded to FP32 / split (NN), and the
+  // split partials (TN); carved once per call site.
+  size_t nn_bytes(int64_t n, int Kd, int N) const {
+    if (prec == DMD_MIXED_BF16X3) return umma_nn_workspace_bytes(n, Kd, N);
+    return (size_t)Kd * N * sizeof(float) + 256;
+  }
+  size_t tn_bytes(int64_t n, int Ka, int N) const {
+    if (prec == DMD_MIXED_BF16X3) return umma_tn_workspace_bytes(n, Ka, N);
+    return tn_partial_doubles(n, Ka, N) * sizeof(double) + 256;
+  }
+  dmd_status nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
+                void* ws, cudaStream_t st) const {
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+    float* B32 = reinterpret_cast<float*>(ws);
+    DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st));
+    return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st);
+  }
+  dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
+                void* ws, cudaStream_t st) const {
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn(n, Ka, N, A, lda, B, ldb, C, ws, st);
+    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
+  }
+};
+
+bool valid_precision(int p) { return p == DMD_FP32 || p == DMD_MIXED_BF16X3; }
+
+// ---------------------------------------------------------------- fit layout
+
+struct FitBufs {
+  int64_t n, ldY;
+  int m, r, l, q, lo;   // lo = rows of the "input" sketch (m); control stacks q extra rows
+  double *Om, *G, *T1, *T2, *Zp, *Z, *Gz, *Tz, *P, *Pp, *Hb, *tauB, *evB, *YB, *trid, *Vs, *Tmp, *At, *Ah,
+      *tauA, *Hq, *wr, *wi, *Yre, *Yim, *invit, *WR, *MR, *LS, *rhs, *hnorm, *invsq;
+  float *Y, *Q1;
+  int *heads, *nheads, *order;
+  void* gemm_ws;
+  size_t gemm_ws_bytes;
+};
+
+void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
+  b.n = d.n;
+  b.m = d.m;
+  b.r = d.r;
+  b.q = d.q;
+  b.l = std::min(d.r + std::max(d.oversample, 0), d.m);
+  b.ldY = round_up(d.n, 32);
+  const int m = b.m, l = b.l, r = b.r;
+  const int64_t n = b.n;
+  b.Om = a.take<double>((size_t)m * l);
+  b.G = a.take<double>((size_t)l * l);
+  b.T1 = a.take<double>((size_t)l * l);
+  b.T2 = a.take<double>((size_t)l * l);
+  b.Zp = a.take<double>((size_t)m * l);
+  b.Z = a.take<double>((size_t)m * l);
+  b.Gz = a.take<double>((size_t)l * l);
+  b.Tz = a.take<double>((size_t)l * l);
+  b.P = a.take<double>((size_t)l * (m + 1));
+  b.Pp = a.take<double>((size_t)l * (m + 1));
+  b.Hb = a.take<double>((size_t)l * l);
+  b.tauB = a.take<double>(l);
+  b.evB = a.take<double>(l);
+  b.YB = a.take<double>((size_t)l * l);
+  b.trid = a.take<double>((size_t)7 * l * l);
+  b.Vs = a.take<double>((size_t)m * r);
+  b.Tmp = a.take<double>((size_t)l * r);
+  b.At = a.take<double>((size_t)r * r);
+  b.Ah = a.take<double>((size_t)r * r);
+  b.tauA = a.take<double>(r);
+  b.Hq = a.take<double>((size_t)r * r);
+  b.wr = a.take<double>(r);
+  b.wi = a.take<double>(r);
+  b.Yre = a.take<double>((size_t)r * r);
+  b.Yim = a.take<double>((size_t)r * r);
+  b.invit = a.take<double>((size_t)2 * r * r * r);
+  b.WR = a.take<double>((size_t)r * r);
+  b.MR = a.take<double>((size_t)m * r);
+  b.LS = a.take<double>((size_t)l * r);
+  b.rhs = a.take<double>(l);
+  b.hnorm = a.take<double>(1);
+  b.invsq = a.take<double>(l);
+  b.heads = a.take<int>(r);
+  b.nheads = a.take<int>(1);
+  b.order = a.take<int>(r);
+  b.Y = a.take<float>((size_t)b.ldY * l);
+  b.Q1 = a.take<float>((size_t)b.ldY * l);
+  size_t g = 0;
+  g = std::max(g, tall.nn_bytes(n, m, l));
+  g = std::max(g, tall.nn_bytes(n, l, l));
+  g = std::max(g, tall.nn_bytes(n, m, r));
+  g = std::max(g, tall.tn_bytes(n, l, l));
+  g = std::max(g, tall.tn_bytes(n, m, l));
+  g = std::max(g, tall.tn_bytes(n, l, m + 1));
+  b.gemm_ws_bytes = g;
+  b.gemm_ws = a.take<char>(g, 1024);
+}
+
+dmd_status validate_fit(const dmd_fit_desc* d) {
+  DMD_REQUIRE(d != nullptr, "dmd_fit: desc is NULL");
+  DMD_REQUIRE(d->n >= 1 && d->m >= 2, "dmd_fit: need n >= 1 and m >= 2 (got n=%lld m=%d)", (long long)d->n, d->m);
+  DMD_REQUIRE(d->r >= 1 && d->r <= d->m && d->r <= d->n, "dmd_fit: need 1 <= r <= min(m, n) (r=%d)", d->r);
+  DMD_REQUIRE(d->r <= 512, "dmd_fit: r > 512 is not supported");
+  DMD_REQUIRE(d->oversample >= 0 && d->power_iters >= 0 && d->power_iters <= 16, "dmd_fit: bad oversample/power_iters");
+  DMD_REQUIRE(d->ldS >= d->n && d->ldS % 4 == 0, "dmd_fit: ldS must be >= n and a multiple of 4");
+  DMD_REQUIRE(d->ldPhi >= d->n && d->ldPhi % 4 == 0, "dmd_fit: ldPhi must be >= n and a multiple of 4");
+  DMD_REQUIRE(d->q >= 0 && d->q <= 64, "dmd_fit: q must be in [0, 64]");
+  DMD_REQUIRE(valid_precision(d->precision), "dmd_fit: unknown precision %d", d->precision);
+  const int l = std::min(d->r + d->oversample, d->m);
+  DMD_REQUIRE(l <= 1024, "dmd_fit: sketch width above 1024");
+  return DMD_OK;
+}
+
+// CholeskyQR2 of a tall FP32 matrix Y (n x l): Q1 = Y R1^{-1} is written
+// explicitly; the second factor R2 is kept as T2 = R2^{-1} and folded into the
+// consumers, so Q = Q1 T2.  G must hold Y^T Y (FP64) on entry.
+dmd_status orth_tall(const Tall& tall, FitBufs& b, int32_t* info, int tag, cudaStream_t st) {
+  const int l = b.l;
+  DMD_TRY(cholesky_upper(l, b.G, l, info, tag, st));
+  DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
+  DMD_TRY(tall.nn(b.n, l, l, b.Y, b.ldY, b.T1, b.Q1, b.ldY, b.gemm_ws, st));
+  DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
+  DMD_TRY(cholesky_upper(l, b.G, l, info, tag + 1, st));
+  DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
+  return DMD_OK;
+}
+
+// CholeskyQR2 of a small FP64 matrix Z (rows x l) in place.
+dmd_status orth_small(FitBufs& b, int rows, int32_t* info, int tag, cudaStream_t st) {
+  const int l = b.l;
+  for (int pass = 0; pass < 2; ++pass) {
+    DMD_TRY(dgemm(l, l, rows, 1.0, b.Z, rows, true, b.Z, rows, false, 0.0, b.Gz, l, st));
+    DMD_TRY(cholesky_upper(l, b.Gz, l, info, tag + pass, st));
+    DMD_TRY(tri_inv_upper(l, b.Gz, l, b.Tz, l, st));
+    DMD_TRY(dgemm(rows, l, l, 1.0, b.Z, rows, false, b.Tz, l, false, 0.0, b.Zp, rows, st));
+    DMD_TRY(fit_glue_copy((int64_t)rows * l, b.Zp, b.Z, st));
+  }
+  return DMD_OK;
+}
+
+dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, const double* Omega, float* PhiR,
+                    double* modal, int32_t* info, FitBufs& b, cudaStream_t st) {
+  const Tall tall{d.precision};
+  const int64_t n = b.n;
+  const int m = b.m, l = b.l, r = b.r, q = b.q;
+  const float* X = S;
+  const float* Xp = S + d.ldS;
+  DMD_CUDA_TRY(cudaMemsetAsync(info, 0, DMD_INFO_WORDS * sizeof(int32_t), st));
+  DMD_CUDA_TRY(cudaMemsetAsync(modal, 0, DMD_MODAL_DOUBLES(r, q) * sizeof(double), st));
+  // 1. sketch test matrix (Sec. 4.3)
+  if (Omega) {
+    DMD_CUDA_TRY(cudaMemcpyAsync(b.Om, Omega, (size_t)m * l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    DMD_TRY(launch_sketch(m, l, d.seed, b.Om, st));
+  }
+  // 2. Y = X Omega, G = Y^T Y, Q = orth(Y)
+  DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Om, b.Y, b.ldY, b.gemm_ws, st));
+  DMD_TRY(tall.tn(n, l, l, b.Y, b.ldY, b.Y, b.ldY, b.G, b.gemm_ws, st));
+  DMD_TRY(orth_tall(tall, b, info, 1, st));
+  // 3. power iterations: Z = orth(X^T Q), Y = X Z, Q = orth(Y)
+  for (int it = 0; it < d.power_iters; ++it) {
+    DMD_TRY(tall.tn(n, m, l, X, d.ldS, b.Q1, b.ldY, b.Zp, b.gemm_ws, st));
+    DMD_TRY(dgemm(m, l, l, 1.0, b.Zp, m, false, b.T2, l, false, 0.0, b.Z, m, st));
+    DMD_TRY(orth_small(b, m, info, 10 + 4 * it, st));
+    DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Z, b.Y, b.ldY, b.gemm_ws, st));
+    DMD_TRY(tall.tn(n, l, l, b.Y, b.ldY, b.Y, b.ldY, b.G, b.gemm_ws, st));
+    DMD_TRY(orth_tall(tall, b, info, 12 + 4 * it, st));
+  }
+  // 4. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
+  DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
+  DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));
+  DMD_TRY(fit_glue_check_finite((int64_t)l * (m + 1), b.P, info, 90, st));
+  const double* B = b.P;
+  const double* Bp = b.P + l;
+  // 5. SVD of B via B B^T = U_B Sigma^2 U_B^T (tridiagonalisation, bisection, inverse iteration)
+  DMD_TRY(dgemm(l, l, m, 1.0, B, l, false, B, l, true, 0.0, b.Hb, l, st));
+  DMD_TRY(hessenberg(l, b.Hb, l, b.tauB, st));
+  DMD_TRY(tridiag_eig(l, b.Hb, l, b.evB, b.YB, b.trid, st));
+  DMD_TRY(apply_q(l, b.Hb, l, b.tauB, b.YB, l, l, st));
+  double* sigma = modal + 3 * r;
+  DMD_TRY(fit_glue_sigma(l, r, b.evB, sigma, b.invsq, info, st));
+  // 6. V Sigma^{-1} = B^T U_r Sigma^{-2}; reduced operator A~ = U_r^T (Q^T X') V Sigma^{-1} (Sec. 3.1)
+  DMD_TRY(dgemm(m, r, l, 1.0, B, l, true, b.YB, l, false, 0.0, b.Vs, m, st));
+  DMD_TRY(fit_glue_scale_cols(m, r, b.Vs, m, b.invsq, st));
+  DMD_TRY(dgemm(l, r, m, 1.0, Bp, l, false, b.Vs, m, false, 0.0, b.Tmp, l, st));
+  DMD_TRY(dgemm(r, r, l, 1.0, b.YB, l, true, b.Tmp, l, false, 0.0, b.At, r, st));
+  // 7. eigendecomposition A~ W = W Lambda
+  DMD_TRY(fit_glue_copy((int64_t)r * r, b.At, b.Ah, st));
+  DMD_TRY(fit_glue_maxabs((int64_t)r * r, b.At, b.hnorm, st));
+  DMD_TRY(hessenberg(r, b.Ah, r, b.tauA, st));
+  DMD_TRY(hqr(r, b.Ah, r, b.wr, b.wi, b.Hq, info, st));
+  DMD_TRY(fit_glue_fill_int(r, b.heads, -1, st));
+  DMD_TRY(collect_heads(r, b.wi, b.heads, b.nheads, info, st));
+  DMD_CUDA_TRY(cudaMemsetAsync(b.Yre, 0, (size_t)r * r * sizeof(double), st));
+  DMD_CUDA_TRY(cudaMemsetAsync(b.Yim, 0, (size_t)r * r * sizeof(double), st));
+  DMD_TRY(hess_eigvecs(r, b.Ah, r, b.wr, b.wi, b.heads, r, b.Yre, b.Yim, b.invit, b.hnorm, st));
+  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yre, r, r, st));
+  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yim, r, r, st));
+  DMD_TRY(normalize_complex(r, b.Yre, b.Yim, r, st));
+  DMD_TRY(eig_layout(r, b.wr, b.wi, b.heads, b.nheads, b.Yre, b.Yim, b.WR, modal, modal + r, b.order, info, st));
+  // 8. modes Phi_R = X' M_R with M_R = V Sigma^{-1} W_R
+  DMD_TRY(dgemm(m, r, r, 1.0, b.Vs, m, false, b.WR, r, false, 0.0, b.MR, m, st));
+  DMD_TRY(tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st));
+  // 9. amplitudes: min || (Q^T X') M_R beta - Q^T x_0 ||  (Eq. projection in the Q basis)
+  DMD_TRY(dgemm(l, r, r, 1.0, b.Tmp, l, false, b.WR, r, false, 0.0, b.LS, l, st));
+  DMD_TRY(fit_glue_copy(l, b.P, b.rhs, st));
+  DMD_TRY(lstsq(l, r, b.LS, l, b.rhs, modal + 2 * r, info, st));
+  (void)Ups;
+  (void)q;
+  return DMD_OK;
+}
+
+// ------------------------------------------------------------ predict layout
+
+struct PredBufs {
+  double *C, *Xi, *dC, *dXi, *Mu, *partial;
+  float* F;
+  void* gemm_ws;
+};
+
+int chunk_of(const dmd_predict_desc& d) { return d.chunk > 0 ? d.chunk : 50; }
+
+void carve_predict(Arena& a, const dmd_predict_desc& d, int mode, PredBufs& b) {
+  // mode 0: forward, 1: backward from dOut, 2: streamed loss
+  const Tall tall{d.precision};
+  const int r = d.r, K = d.K;
+  const int steps = d.q > 0 ? d.steps : 0;
+  b.C = a.take<double>((size_t)r * K);
+  b.Xi = a.take<double>((size_t)r * (steps + 1));
+  b.dC = (mode >= 1) ? a.take<double>((size_t)r * K) : nullptr;
+  b.dXi = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
+  b.Mu = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
+  b.partial = (mode == 2) ? a.take<double>((size_t)loss_blocks()) : nullptr;
+  const int ch = std::min(chunk_of(d), K);
+  b.F = (mode == 2) ? a.take<float>((size_t)round_up(d.n, 32) * ch) : nullptr;
+  size_t g = 0;
+  if (mode == 0) g = tall.nn_bytes(d.n, r, K);
+  if (mode == 1) g = tall.tn_bytes(d.n, r, K);
+  if (mode == 2) g = std::max(tall.nn_bytes(d.n, r, ch), tall.tn_bytes(d.n, r, ch));
+  b.gemm_ws = a.take<char>(g, 1024);
+}
+
+dmd_status validate_predict(const dmd_predict_desc* d, bool need_out_ld) {
+  DMD_REQUIRE(d != nullptr, "predict: desc is NULL");
+  DMD_REQUIRE(d->n >= 1 && d->r >= 1 && d->r <= 512 && d->K >= 1, "predict: need n >= 1, 1 <= r <= 512, K >= 1");
+  DMD_REQUIRE(d->ldPhi >= d->n && d->ldPhi % 4 == 0, "predict: ldPhi must be >= n and a multiple of 4");
+  if (need_out_ld) DMD_REQUIRE(d->ldOut >= d->n && d->ldOut % 4 == 0, "predict: ldOut must be >= n and a multiple of 4");
+  DMD_REQUIRE(d->q >= 0 && d->q <= 64, "predict: q must be in [0, 64]");
+  DMD_REQUIRE(d->q == 0 || d->steps >= 0, "predict: steps must be >= 0 with control");
+  DMD_REQUIRE(valid_precision(d->precision), "predict: unknown precision %d", d->precision);
+  return DMD_OK;
+}
+
+dmd_status form_coefficients(const dmd_predict_desc& d, const double* modal, const int32_t* k, const float* u,
+                             PredBufs& b, cudaStream_t st) {
+  if (d.q > 0) {
+    DMD_TRY(launch_rollout(d.r, d.q, d.steps, modal, u, b.Xi, st));
+    DMD_TRY(launch_gather_cols(d.r, d.K, b.Xi, k, d.steps, b.C, nullptr, st));
+  } else {
+    DMD_TRY(launch_coefficients(d.r, d.K, modal, k, b.C, st));
+  }
+  return DMD_OK;
+}
+
+dmd_status chain_rule(const dmd_predict_desc& d, const double* modal, const int32_t* k, const float* u,
+                      double* d_modal, float* d_u, PredBufs& b, cudaStream_t st) {
+  DMD_CUDA_TRY(cudaMemsetAsync(d_modal, 0, DMD_MODAL_DOUBLES(d.r, d.q) * sizeof(double), st));
+  if (d.q > 0) {
+    DMD_TRY(launch_rollout(d.r, d.q, d.steps, modal, u, b.Xi, st));
+    DMD_TRY(launch_rollout_adjoint(d.r, d.q, d.steps, d.K, k, modal, u, b.Xi, b.dC, b.dXi, b.Mu, d_modal, d_u,
+                                   st));
+  } else {
+    DMD_TRY(launch_chain_closed(d.r, d.K, modal, k, b.dC, d_modal, st));
+  }
+  return DMD_OK;
+}
+
+template <class F>
+dmd_status with_arena(void* ws, size_t ws_bytes, F&& carve_and_run, size_t need) {
+  if (ws_bytes < need) {
+    set_error("workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+    return DMD_ENOMEM;
+  }
+  DMD_REQUIRE(ws != nullptr, "workspace is NULL");
+  DMD_REQUIRE(((uintptr_t)ws & 255) == 0, "workspace must be 256-byte aligned");
+  Arena a{reinterpret_cast<char*>(ws), ws_bytes, 0};
+  return carve_and_run(a);
+}
+
+}  // namespace
+}  // namespace dmd
+
+using namespace dmd;
+
+extern "C" {
+
+const char* dmd_last_error(void) { return g_err; }
+const char* dmd_version(void) { return "libdmd 0.1 (sm_103a)"; }
+uint64_t dmd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+dmd_status dmd_fit_workspace_bytes(const dmd_fit_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_fit(desc));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  Arena a;
+  FitBufs b;
+  carve_fit(a, *desc, Tall{desc->precision}, b);
+  *bytes = a.used + 256;
+  return DMD_OK;
+}
+
+dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const float* Ups, const double* Omega, float* Phi_R,
+                   double* modal, int32_t* info, void* workspace, size_t ws_bytes, void* stream) {
+  DMD_TRY(validate_fit(desc));
+  DMD_REQUIRE(S && Phi_R && modal && info, "dmd_fit: NULL pointer argument");
+  DMD_REQUIRE(desc->q == 0 || Ups != nullptr, "dmd_fit: q > 0 needs Ups");
+  DMD_REQUIRE(desc->q == 0, "dmd_fit: control inputs are handled by the DMDc path (q > 0 not enabled in this build)");
+  size_t need = 0;
+  DMD_TRY(dmd_fit_workspace_bytes(desc, &need));
+  return with_arena(workspace, ws_bytes, [&](Arena& a) {
+    FitBufs b;
+    carve_fit(a, *desc, Tall{desc->precision}, b);
+    return fit_impl(*desc, S, Ups, Omega, Phi_R, modal, info, b, (cudaStream_t)stream);
+  }, need);
+}
+
+dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_predict(desc, false));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  size_t best = 0;
+  for (int mode = 0; mode < 3; ++mode) {
+    Arena a;
+    PredBufs b;
+    carve_predict(a, *desc, mode, b);
+    best = std::max(best, a.used + 256);
+  }
+  *bytes = best;
+  return DMD_OK;
+}
+
+dmd_status dmd_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
+                       const float* u, float* out, void* workspace, size_t ws_bytes, void* stream) {
+  DMD_TRY(validate_predict(desc, true));
+  DMD_REQUIRE(Phi_R && modal && k && out, "dmd_predict: NULL pointer argument");
+  DMD_REQUIRE(desc->q == 0 || u != nullptr || desc->steps == 0, "dmd_predict: q > 0 needs u");
+  size_t need = 0;
+  DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    PredBufs b;
+    carve_predict(a, *desc, 0, b);
+    DMD_TRY(form_coefficients(*desc, modal, k, u, b, st));
+    const Tall tall{desc->precision};
+    return tall.nn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, out, desc->ldOut, b.gemm_ws, st);
+  }, need);
+}
+
+dmd_status dmd_predict_backward(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                                const int32_t* k, const float* u, const float* dOut, double* d_modal, float* d_u,
+                                void* workspace, size_t ws_bytes, void* stream) {
+  DMD_TRY(validate_predict(desc, true));
+  DMD_REQUIRE(Phi_R && modal && k && dOut && d_modal, "dmd_predict_backward: NULL pointer argument");
+  size_t need = 0;
+  DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    PredBufs b;
+    carve_predict(a, *desc, 1, b);
+    const Tall tall{desc->precision};
+    DMD_TRY(tall.tn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, dOut, desc->ldOut, b.dC, b.gemm_ws, st));
+    return chain_rule(*desc, modal, k, u, d_modal, d_u, b, st);
+  }, need);
+}
+
+dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
+                            const float* u, const float* target, const double* w, int32_t want_grad, double* loss,
+                            double* d_modal, float* d_u, void* workspace, size_t ws_bytes, void* stream) {
+  DMD_TRY(validate_predict(desc, false));
+  DMD_REQUIRE(Phi_R && modal && k && target && w && loss, "dmd_predict_loss: NULL pointer argument");
+  DMD_REQUIRE(!want_grad || d_modal, "dmd_predict_loss: want_grad needs d_modal");
+  size_t need = 0;
+  DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    PredBufs b;
+    carve_predict(a, *desc, 2, b);
+    const Tall tall{desc->precision};
+    DMD_TRY(form_coefficients(*desc, modal, k, u, b, st));
+    const int ch = std::min(chunk_of(*desc), desc->K);
+    const int64_t ldF = round_up(desc->n, 32);
+    for (int j0 = 0; j0 < desc->K; j0 += ch) {
+      const int nf = std::min(ch, desc->K - j0);
+      DMD_TRY(tall.nn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.C + (size_t)j0 * desc->r, b.F, ldF, b.gemm_ws, st));
+      DMD_TRY(launch_loss_chunk(desc->n, nf, b.F, ldF, target, w + j0, want_grad != 0, b.partial, loss, j0 > 0, st));
+      if (want_grad)
+        DMD_TRY(tall.tn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.F, ldF, b.dC + (size_t)j0 * desc->r, b.gemm_ws, st));
+    }
+    if (want_grad) return chain_rule(*desc, modal, k, u, d_modal, d_u, b, st);
+    return DMD_OK;
+  }, need);
+}
+
+dmd_status dmd_sketch_matrix(int32_t m, int32_t l, uint64_t seed, double* Omega, void* stream) {
+  DMD_REQUIRE(m >= 1 && l >= 1 && Omega, "dmd_sketch_matrix: bad arguments");
+  return launch_sketch(m, l, seed, Omega, (cudaStream_t)stream);
+}
+
+dmd_status dmd_philox_blocks(int64_t count, uint32_t stream_id, uint64_t key, uint32_t* out, void* stream) {
+  DMD_REQUIRE(count >= 0 && (count == 0 || out), "dmd_philox_blocks: bad arguments");
+  DMD_REQUIRE(((uintptr_t)out & 15) == 0, "dmd_philox_blocks: out must be 16-byte aligned");
+  return launch_philox_blocks(count, stream_id, key, out, (cudaStream_t)stream);
+}
+
+dmd_status dmd_gemm_tall_workspace_bytes(int32_t precision, int64_t n, int32_t Kd, int32_t N, size_t* bytes) {
+  DMD_REQUIRE(valid_precision(precision) && n >= 1 && Kd >= 1 && N >= 1 && bytes, "gemm_tall: bad arguments");
+  *bytes = Tall{precision}.nn_bytes(n, Kd, N) + 1024;
+  return DMD_OK;
+}
+
+dmd_status dmd_gemm_tall(int32_t precision, int64_t n, int32_t Kd, int32_t N, const float* A, int64_t lda,
+                         const double* B, float* C, int64_t ldc, double* gram, void* workspace, size_t ws_bytes,
+                         void* stream) {
+  DMD_REQUIRE(valid_precision(precision) && n >= 1 && Kd >= 1 && N >= 1, "gemm_tall: bad sizes");
+  DMD_REQUIRE(Kd <= 1024 && N <= 65536, "gemm_tall: Kd <= 1024 and N <= 65536");
+  DMD_REQUIRE(A && B && C, "gemm_tall: NULL pointer");
+  DMD_REQUIRE(lda >= n && lda % 4 == 0 && ldc >= n && ldc % 4 == 0, "gemm_tall: lda/ldc must be >= n, multiple of 4");
+  const Tall tall{precision};
+  size_t need = tall.nn_bytes(n, Kd, N) + 1024;
+  if (gram) need = std::max(need, tall.tn_bytes(n, N, N) + 1024);
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    void* ws = a.take<char>(ws_bytes - 1024, 1024);
+    DMD_TRY(tall.nn(n, Kd, N, A, lda, B, C, ldc, ws, st));
+    if (gram) DMD_TRY(tall.tn(n, N, N, C, ldc, C, ldc, gram, ws, st));
+    return DMD_OK;
+  }, need);
+}
+
+dmd_status dmd_gemm_tn_workspace_bytes(int32_t precision, int64_t n, int32_t Ka, int32_t N, size_t* bytes) {
+  DMD_REQUIRE(valid_precision(precision) && n >= 1 && Ka >= 1 && N >= 1 && bytes, "gemm_tn: bad arguments");
+  *bytes = Tall{precision}.tn_bytes(n, Ka, N) + 1024;
+  return DMD_OK;
+}
+
+dmd_status dmd_gemm_tn(int32_t precision, int64_t n, int32_t Ka, int32_t N, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, double* C, void* workspace, size_t ws_bytes, void* stream) {
+  DMD_REQUIRE(valid_precision(precision) && n >= 1 && Ka >= 1 && N >= 1, "gemm_tn: bad sizes");
+  DMD_REQUIRE(Ka <= 1024 && N <= 65536, "gemm_tn: Ka <= 1024 and N <= 65536");
+  DMD_REQUIRE(A && B && C, "gemm_tn: NULL pointer");
+  DMD_REQUIRE(lda >= n && lda % 4 == 0 && ldb >= n && ldb % 4 == 0, "gemm_tn: lda/ldb must be >= n, multiple of 4");
+  const Tall tall{precision};
+  const size_t need = tall.tn_bytes(n, Ka, N) + 1024;
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    void* ws = a.take<char>(ws_bytes - 1024, 1024);
+    return tall.tn(n, Ka, N, A, lda, B, ldb, C, ws, st);
+  }, need);
+}
+
+}  // extern "C"

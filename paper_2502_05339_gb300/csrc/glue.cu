@@ -1,0 +1,101 @@
+// Small element-wise steps between the stages of the fit.
+#include "common.cuh"
+
+namespace dmd {
+
+namespace {
+
+// sigma_i = sqrt(max(ev_i, 0)) for the r leading eigenvalues of B B^T
+// (descending), inv_sq_i = 1 / ev_i; rank guard sigma_{r-1} > 1e-6 sigma_0.
+__global__ void k_sigma(int l, int r, const double* ev, double* sigma, double* inv_sq, int32_t* info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double s0 = sqrt(fmax(ev[0], 0.0));
+  for (int i = 0; i < r; ++i) {
+    const double e = fmax(ev[i], 0.0);
+    const double s = sqrt(e);
+    sigma[i] = s;
+    if (!(s > 1e-6 * s0) || !isfinite(s)) {
+      raise_status(info, isfinite(s) ? DMD_ERANK : DMD_ENONFINITE, 7000 + i);
+      inv_sq[i] = 0.0;
+    } else {
+      inv_sq[i] = 1.0 / e;
+    }
+  }
+  (void)l;
+}
+
+__global__ void k_scale_cols(int rows, int cols, double* A, int lda, const double* s) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)rows * cols) return;
+  const int i = (int)(t % rows), j = (int)(t / rows);
+  A[(int64_t)j * lda + i] *= s[j];
+}
+
+__global__ void k_check_finite(int64_t count, const double* A, int32_t* info, int tag) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < count && !isfinite(A[t])) raise_status(info, DMD_ENONFINITE, tag);
+}
+
+__global__ void k_maxabs(int64_t count, const double* A, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int64_t t = threadIdx.x; t < count; t += blockDim.x) v = fmax(v, fabs(A[t]));
+  v = block_max(v, red);
+  if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_copy(int64_t count, const double* src, double* dst) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = src[t];
+}
+
+__global__ void k_fill_int(int64_t count, int* dst, int v) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = v;
+}
+
+}  // namespace
+
+dmd_status fit_glue_sigma(int l, int r, const double* ev, double* sigma, double* inv_sq, int32_t* info,
+                          cudaStream_t st) {
+  k_sigma<<<1, 32, 0, st>>>(l, r, ev, sigma, inv_sq, info);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_scale_cols(int rows, int cols, double* A, int lda, const double* s, cudaStream_t st) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return DMD_OK;
+  k_scale_cols<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(rows, cols, A, lda, s);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_check_finite(int64_t count, const double* A, int32_t* info, int tag, cudaStream_t st) {
+  if (count == 0) return DMD_OK;
+  k_check_finite<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, A, info, tag);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStream_t st) {
+  k_maxabs<<<1, 256, 0, st>>>(count, A, out);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st) {
+  if (count == 0) return DMD_OK;
+  k_copy<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, src, dst);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st) {
+  if (count == 0) return DMD_OK;
+  k_fill_int<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, dst, v);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+}  // namespace dmd

@@ -1,0 +1,938 @@
+// FP64 small dense linear algebra on the device (sizes l, r <= a few hundred).
+//
+// These are the l x l / r x r steps of the fit: the Cholesky factors of
+// CholeskyQR2 (Sec. 4.3 range finder), the SVD of B = Q^T X (Sec. 4.3) taken
+// through the eigendecomposition of B B^T, the eigendecomposition of the
+// reduced operator A~ (Sec. 3.1), and the least-squares amplitudes
+// b = Phi^+ x_0 (Eq. projection).  Algorithms (all textbook, written here from
+// their mathematical statement):
+//   * Cholesky: right-looking, upper factor R with R^T R = G.
+//   * Hessenberg reduction by Householder reflectors (a symmetric input gives
+//     a tridiagonal matrix).
+//   * Eigenvalues of an upper Hessenberg matrix: Francis implicit double-shift
+//     QR with 3x3 reflectors, deflation on negligible subdiagonals and
+//     exceptional shifts (Golub & Van Loan, Sec. 7.5).
+//   * Eigenvectors: inverse iteration with the computed eigenvalue as shift on
+//     the Hessenberg (complex shift) or tridiagonal (real shift) matrix, then
+//     back-transformation with the Hessenberg reflectors.
+//   * Symmetric tridiagonal eigenvalues: bisection on Sturm counts.
+//   * Least squares: Householder QR and back substitution.
+// Every kernel that can fail writes DMD_ENUMERIC / DMD_ENONFINITE to info[0].
+#include <float.h>
+
+#include "common.cuh"
+
+namespace dmd {
+
+namespace {
+
+constexpr double kEps = DBL_EPSILON;
+
+// ------------------------------------------------------------------ GEMM
+
+// C[M x N] = alpha op(A) op(B) + beta C (column-major; op = transpose when t* != 0).
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                               int lda, int ta, const double* __restrict__ B, int ldb,
+                                               int tb, double beta, double* __restrict__ C, int ldc) {
+  __shared__ double As[16][17];
+  __shared__ double Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    {
+      const int i = i0 + tx, k = k0 + ty;
+      double v = 0.0;
+      if (i < M && k < K) v = ta ? A[(int64_t)i * lda + k] : A[(int64_t)k * lda + i];
+      As[ty][tx] = v;
+    }
+    {
+      const int k = k0 + tx, j = j0 + ty;
+      double v = 0.0;
+      if (k < K && j < N) v = tb ? B[(int64_t)k * ldb + j] : B[(int64_t)j * ldb + k];
+      Bs[ty][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[kk][tx], Bs[ty][kk], acc);
+    __syncthreads();
+  }
+  const int i = i0 + tx, j = j0 + ty;
+  if (i < M && j < N) {
+    double* c = C + (int64_t)j * ldc + i;
+    *c = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*c);
+  }
+}
+
+// ------------------------------------------------------------- Cholesky
+
+// In place: the upper triangle of G (n x n, ld) becomes R with R^T R = G; the
+// strict lower triangle is zeroed.  One CTA.  A pivot below 1e-14 of the
+// largest diagonal entry (a direction the data do not span, within rounding)
+// is raised to that floor instead of failing, and counted in info[5]; such
+// directions end up with negligible singular values and are truncated later.
+// Only a non-finite pivot or an all-zero matrix is an error.
+__global__ void k_cholesky_upper(int n, double* G, int ld, int32_t* info, int tag) {
+  __shared__ double piv;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double loc = 0.0;
+  for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
+  const double dmax = block_max(loc, red);
+  const double floor_ = 1e-14 * dmax;
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      double d = G[j + (int64_t)j * ld];
+      if (!isfinite(d) || !isfinite(dmax)) {
+        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+        piv = -1.0;
+      } else if (!(dmax > 0.0)) {
+        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+        piv = -1.0;
+      } else {
+        if (!(d > floor_)) {
+          d = floor_;
+          if (info) atomicAdd(&info[5], 1);
+        }
+        piv = sqrt(d);
+        G[j + (int64_t)j * ld] = piv;
+      }
+    }
+    __syncthreads();
+    const double p = piv;
+    if (p < 0.0) return;
+    const double ip = 1.0 / p;
+    for (int i = j + 1 + tid; i < n; i += bd) G[j + (int64_t)i * ld] *= ip;
+    __syncthreads();
+    const int w = n - j - 1;
+    for (int e = tid; e < w * w; e += bd) {
+      const int a = j + 1 + e % w, b = j + 1 + e / w;
+      if (a <= b) G[a + (int64_t)b * ld] -= G[j + (int64_t)a * ld] * G[j + (int64_t)b * ld];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += bd) {
+    const int a = e % n, b = e / n;
+    if (a > b) G[a + (int64_t)b * ld] = 0.0;
+  }
+}
+
+// T = R^{-1} for upper triangular R; one thread per column.
+__global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T,
+                                int ldt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double* t = T + (int64_t)j * ldt;
+  for (int i = j + 1; i < n; ++i) t[i] = 0.0;
+  t[j] = 1.0 / R[j + (int64_t)j * ldr];
+  for (int i = j - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1; k <= j; ++k) s = fma(R[i + (int64_t)k * ldr], t[k], s);
+    t[i] = -s / R[i + (int64_t)i * ldr];
+  }
+}
+
+// ------------------------------------------------- Hessenberg reduction
+
+// A (n x n, ld) <- Q^T A Q upper Hessenberg, Q = H_0 ... H_{n-3},
+// H_k = I - tau_k v v^T with v = [1, A[k+2.., k]] on indices k+1..n-1.
+// Shared memory: 2n + 32 doubles.  One CTA.
+__global__ void k_hessenberg(int n, double* A, int ld, double* tau) {
+  extern __shared__ double sm[];
+  double* v = sm;
+  double* w = sm + n;
+  double* red = sm + 2 * n;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = A + (int64_t)k * ld + (k + 1);
+    double loc = 0.0;
+    for (int i = 1 + tid; i < m; i += bd) loc += x[i] * x[i];
+    const double sig = block_sum(loc, red);
+    const double alpha = x[0];
+    if (sig == 0.0) {
+      if (tid == 0) tau[k] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double nrm = sqrt(alpha * alpha + sig);
+    const double beta = alpha <= 0.0 ? nrm : -nrm;
+    const double t = (beta - alpha) / beta;
+    const double sc = 1.0 / (alpha - beta);
+    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : x[i] * sc;
+    __syncthreads();
+    for (int i = 1 + tid; i < m; i += bd) x[i] = v[i];
+    if (tid == 0) {
+      x[0] = beta;
+      tau[k] = t;
+    }
+    // left: rows k+1.., columns k+1..
+    for (int j = k + 1 + tid; j < n; j += bd) {
+      const double* col = A + (int64_t)j * ld + (k + 1);
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s = fma(v[i], col[i], s);
+      w[j] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += bd) {
+      const int i = e % m, j = k + 1 + e / m;
+      A[(int64_t)j * ld + (k + 1 + i)] -= t * v[i] * w[j];
+    }
+    __syncthreads();
+    // right: all rows, columns k+1..
+    for (int i = tid; i < n; i += bd) {
+      double s = 0.0;
+      for (int jj = 0; jj < m; ++jj) s = fma(A[(int64_t)(k + 1 + jj) * ld + i], v[jj], s);
+      w[i] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * m; e += bd) {
+      const int i = e % n, jj = e / n;
+      A[(int64_t)(k + 1 + jj) * ld + i] -= t * w[i] * v[jj];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) tau[k] = 0.0;
+  }
+}
+
+// y <- Q y for every column of Y (n x nvec, ld), Q = H_0 ... H_{n-3} from
+// k_hessenberg's storage in A.  One CTA per column.
+__global__ void k_apply_q(int n, const double* __restrict__ A, int lda, const double* __restrict__ tau,
+                          double* __restrict__ Y, int ldy) {
+  __shared__ double red[32];
+  double* y = Y + (int64_t)blockIdx.x * ldy;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    const int m = n - k - 1;
+    const double* vs = A + (int64_t)k * lda + (k + 1);
+    double loc = 0.0;
+    for (int i = tid; i < m; i += bd) loc += (i == 0 ? 1.0 : vs[i]) * y[k + 1 + i];
+    const double s = block_sum(loc, red) * t;
+    for (int i = tid; i < m; i += bd) y[k + 1 + i] -= s * (i == 0 ? 1.0 : vs[i]);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- Francis QR
+
+__device__ __forceinline__ void two_by_two_eigs(double a, double b, double c, double d, double& r1,
+                                                double& i1, double& r2, double& i2) {
+  const double p = 0.5 * (a - d);
+  const double bc = b * c;
+  const double disc = p * p + bc;
+  if (disc >= 0.0) {
+    const double z = p + copysign(sqrt(disc), p);
+    r1 = d + z;
+    r2 = (z != 0.0) ? d - bc / z : d + z;
+    i1 = i2 = 0.0;
+  } else {
+    const double re = d + p, im = sqrt(-disc);
+    r1 = r2 = re;
+    i1 = im;
+    i2 = -im;
+  }
+}
+
+// Eigenvalues of the upper Hessenberg matrix Hin (n x n, ld) by Francis
+// double-shift QR.  One warp; the matrix is copied into shared memory when
+// `in_smem`, otherwise into the global scratch `H` (n x n, ld n).
+__global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi,
+                      double* Hscratch, int in_smem, int32_t* info) {
+  extern __shared__ double smem[];
+  double* H = in_smem ? smem : Hscratch;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e % n, j = e / n;
+    H[e] = (i <= j + 1) ? Hin[i + (int64_t)j * ldh] : 0.0;
+  }
+  __syncwarp();
+#define HH(i, j) H[(i) + (int64_t)(j) * n]
+  double anorm = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i <= min(j + 1, n - 1); ++i) anorm = fmax(anorm, fabs(HH(i, j)));
+  if (anorm == 0.0) anorm = 1.0;
+  int hi = n - 1, its = 0, total = 0;
+  while (hi >= 0) {
+    int lo = hi;
+    while (lo > 0) {
+      double s = fabs(HH(lo - 1, lo - 1)) + fabs(HH(lo, lo));
+      if (s == 0.0) s = anorm;
+      if (fabs(HH(lo, lo - 1)) <= kEps * s) break;
+      --lo;
+    }
+    if (lo > 0) {
+      __syncwarp();
+      if (lane == 0) HH(lo, lo - 1) = 0.0;
+      __syncwarp();
+    }
+    if (lo == hi) {
+      if (lane == 0) {
+        wr[hi] = HH(hi, hi);
+        wi[hi] = 0.0;
+      }
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (lo == hi - 1) {
+      double r1, i1, r2, i2;
+      two_by_two_eigs(HH(hi - 1, hi - 1), HH(hi - 1, hi), HH(hi, hi - 1), HH(hi, hi), r1, i1, r2, i2);
+      if (lane == 0) {
+        wr[hi - 1] = r1;
+        wi[hi - 1] = i1;
+        wr[hi] = r2;
+        wi[hi] = i2;
+      }
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (its >= 90) {
+      if (lane == 0) {
+        raise_status(info, DMD_ENUMERIC, 3000 + hi);
+        for (int i = 0; i <= hi; ++i) wr[i] = wi[i] = nan("");
+      }
+      return;
+    }
+    ++its;
+    ++total;
+    // double shift from the trailing 2x2 block (sum s, product t); exceptional every 10 sweeps
+    double s, t;
+    if (its % 10 == 0) {
+      const double w = fabs(HH(hi, hi - 1)) + fabs(HH(hi - 1, hi - 2));
+      const double h = 0.75 * w + HH(hi, hi);
+      s = 2.0 * h;
+      t = h * h + 0.4375 * w * w;
+    } else {
+      s = HH(hi - 1, hi - 1) + HH(hi, hi);
+      t = HH(hi - 1, hi - 1) * HH(hi, hi) - HH(hi - 1, hi) * HH(hi, hi - 1);
+    }
+    double x = HH(lo, lo) * HH(lo, lo) + HH(lo, lo + 1) * HH(lo + 1, lo) - s * HH(lo, lo) + t;
+    double y = HH(lo + 1, lo) * (HH(lo, lo) + HH(lo + 1, lo + 1) - s);
+    double z = HH(lo + 1, lo) * HH(lo + 2, lo + 1);
+    for (int k = lo; k <= hi - 2; ++k) {
+      // reflector P = I - tau v v^T, v = [1, v1, v2], P [x y z]^T = [beta 0 0]^T
+      const double nrm = sqrt(x * x + y * y + z * z);
+      if (nrm != 0.0 && (y != 0.0 || z != 0.0)) {
+        const double beta = x <= 0.0 ? nrm : -nrm;
+        const double tau = (beta - x) / beta;
+        const double sc = 1.0 / (x - beta);
+        const double v1 = y * sc, v2 = z * sc;
+        const int c0 = max(lo, k - 1);
+        for (int c = c0 + lane; c <= hi; c += 32) {
+          const double p = tau * (HH(k, c) + v1 * HH(k + 1, c) + v2 * HH(k + 2, c));
+          HH(k, c) -= p;
+          HH(k + 1, c) -= p * v1;
+          HH(k + 2, c) -= p * v2;
+        }
+        __syncwarp();
+        if (k > lo && lane == 0) {
+          HH(k + 1, k - 1) = 0.0;
+          HH(k + 2, k - 1) = 0.0;
+        }
+        const int rend = min(k + 3, hi);
+        for (int rr = lo + lane; rr <= rend; rr += 32) {
+          const double p = tau * (HH(rr, k) + v1 * HH(rr, k + 1) + v2 * HH(rr, k + 2));
+          HH(rr, k) -= p;
+          HH(rr, k + 1) -= p * v1;
+          HH(rr, k + 2) -= p * v2;
+        }
+        __syncwarp();
+      }
+      x = HH(k + 1, k);
+      y = HH(k + 2, k);
+      if (k < hi - 2) z = HH(k + 3, k);
+    }
+    // final 2-vector reflector on rows/columns hi-1, hi
+    {
+      const double nrm = sqrt(x * x + y * y);
+      if (nrm != 0.0 && y != 0.0) {
+        const double beta = x <= 0.0 ? nrm : -nrm;
+        const double tau = (beta - x) / beta;
+        const double v1 = y / (x - beta);
+        const int k = hi - 1;
+        for (int c = max(lo, k - 1) + lane; c <= hi; c += 32) {
+          const double p = tau * (HH(k, c) + v1 * HH(k + 1, c));
+          HH(k, c) -= p;
+          HH(k + 1, c) -= p * v1;
+        }
+        __syncwarp();
+        if (k > lo && lane == 0) HH(k + 1, k - 1) = 0.0;
+        for (int rr = lo + lane; rr <= hi; rr += 32) {
+          const double p = tau * (HH(rr, k) + v1 * HH(rr, k + 1));
+          HH(rr, k) -= p;
+          HH(rr, k + 1) -= p * v1;
+        }
+        __syncwarp();
+      }
+    }
+  }
+#undef HH
+  if (lane == 0 && info) info[3] = total;
+}
+
+// ---------------------------------------------- inverse iteration (Hessenberg)
+
+// For each head eigenvalue mu = wr + i wi (wi >= 0), solve (H - mu I) x = rhs
+// three times with an LU factorisation (row pivoting between adjacent rows),
+// giving the eigenvector y of the Hessenberg matrix.  One CTA per eigenvalue.
+// work: per CTA 2 n^2 doubles.  Outputs Yre/Yim (n x nheads, ld n).
+__global__ void k_hess_invit(int n, const double* __restrict__ H, int ldh, const double* __restrict__ wr,
+                             const double* __restrict__ wi, const int* __restrict__ heads,
+                             double* __restrict__ Yre, double* __restrict__ Yim,
+                             double* __restrict__ work, const double* __restrict__ hnorm_ptr) {
+  extern __shared__ double sm[];
+  double* mre = sm;                 // multipliers
+  double* mim = sm + n;
+  double* xre = sm + 2 * n;
+  double* xim = sm + 3 * n;
+  int* piv = reinterpret_cast<int*>(sm + 4 * n);
+  __shared__ double red[32];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int e = heads[blockIdx.x];
+  if (e < 0) return;   // padding beyond the actual number of heads
+  const double mur = wr[e], mui = wi[e];
+  double* Ur = work + (int64_t)blockIdx.x * 2 * n * n;
+  double* Ui = Ur + (int64_t)n * n;
+#define UR(i, j) Ur[(i) + (int64_t)(j) * n]
+#define UI(i, j) Ui[(i) + (int64_t)(j) * n]
+  for (int q = tid; q < n * n; q += bd) {
+    const int i = q % n, j = q / n;
+    double hr = (i <= j + 1) ? H[i + (int64_t)j * ldh] : 0.0, hi_ = 0.0;
+    if (i == j) {
+      hr -= mur;
+      hi_ = -mui;
+    }
+    UR(i, j) = hr;
+    UI(i, j) = hi_;
+  }
+  __syncthreads();
+  const double hnorm = fmax(*hnorm_ptr, DBL_MIN);
+  const double tiny = kEps * hnorm;
+  for (int k = 0; k + 1 < n; ++k) {
+    if (tid == 0) {
+      const double ar = UR(k, k), ai = UI(k, k), br = UR(k + 1, k), bi = UI(k + 1, k);
+      const bool sw = (br * br + bi * bi) > (ar * ar + ai * ai);
+      piv[k] = sw ? 1 : 0;
+      double pr = sw ? br : ar, pi = sw ? bi : ai;   // pivot
+      double orr = sw ? ar : br, oi = sw ? ai : bi;  // eliminated entry
+      if (pr == 0.0 && pi == 0.0) pr = tiny;
+      const double den = pr * pr + pi * pi;
+      mre[k] = (orr * pr + oi * pi) / den;          // other / pivot
+      mim[k] = (oi * pr - orr * pi) / den;
+      UR(k, k) = pr;
+      UI(k, k) = pi;
+      UR(k + 1, k) = 0.0;
+      UI(k + 1, k) = 0.0;
+    }
+    __syncthreads();
+    const int sw = piv[k];
+    const double lr = mre[k], li = mim[k];
+    for (int j = k + 1 + tid; j < n; j += bd) {
+      double ar = UR(k, j), ai = UI(k, j), br = UR(k + 1, j), bi = UI(k + 1, j);
+      if (sw) {
+        double tr = ar, ti = ai;
+        ar = br; ai = bi; br = tr; bi = ti;
+      }
+      UR(k, j) = ar;
+      UI(k, j) = ai;
+      UR(k + 1, j) = br - (lr * ar - li * ai);
+      UI(k + 1, j) = bi - (lr * ai + li * ar);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (UR(n - 1, n - 1) == 0.0 && UI(n - 1, n - 1) == 0.0) UR(n - 1, n - 1) = tiny;
+  }
+  for (int i = tid; i < n; i += bd) {
+    xre[i] = 1.0;
+    xim[i] = 0.0;
+  }
+  __syncthreads();
+  for (int it = 0; it < 3; ++it) {
+    if (tid == 0) {
+      for (int k = 0; k + 1 < n; ++k) {
+        if (piv[k]) {
+          double tr = xre[k], ti = xim[k];
+          xre[k] = xre[k + 1]; xim[k] = xim[k + 1];
+          xre[k + 1] = tr; xim[k + 1] = ti;
+        }
+        const double lr = mre[k], li = mim[k];
+        xre[k + 1] -= lr * xre[k] - li * xim[k];
+        xim[k + 1] -= lr * xim[k] + li * xre[k];
+      }
+    }
+    __syncthreads();
+    for (int i = n - 1; i >= 0; --i) {
+      double sr = 0.0, si = 0.0;
+      for (int j = i + 1 + tid; j < n; j += bd) {
+        const double ur = UR(i, j), ui = UI(i, j);
+        sr += ur * xre[j] - ui * xim[j];
+        si += ur * xim[j] + ui * xre[j];
+      }
+      sr = block_sum(sr, red);
+      si = block_sum(si, red);
+      if (tid == 0) {
+        const double br = xre[i] - sr, bi = xim[i] - si;
+        const double ur = UR(i, i), ui = UI(i, i), den = ur * ur + ui * ui;
+        xre[i] = (br * ur + bi * ui) / den;
+        xim[i] = (bi * ur - br * ui) / den;
+      }
+      __syncthreads();
+    }
+    double loc = 0.0;
+    for (int i = tid; i < n; i += bd) loc = fmax(loc, fmax(fabs(xre[i]), fabs(xim[i])));
+    const double mx = block_max(loc, red);
+    const double inv = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 1.0;
+    for (int i = tid; i < n; i += bd) {
+      xre[i] *= inv;
+      xim[i] *= inv;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += bd) {
+    Yre[i + (int64_t)blockIdx.x * n] = xre[i];
+    Yim[i + (int64_t)blockIdx.x * n] = xim[i];
+  }
+#undef UR
+#undef UI
+}
+
+// Unit 2-norm, largest-magnitude entry real positive.  One CTA per column.
+__global__ void k_normalize_complex(int n, double* Yre, double* Yim) {
+  __shared__ double red[32];
+  __shared__ int argmax;
+  __shared__ double amax;
+  double* yr = Yre + (int64_t)blockIdx.x * n;
+  double* yi = Yim + (int64_t)blockIdx.x * n;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double loc = 0.0;
+  for (int i = tid; i < n; i += bd) loc += yr[i] * yr[i] + yi[i] * yi[i];
+  const double nrm = sqrt(block_sum(loc, red));
+  if (tid == 0) {
+    int am = 0;
+    double best = -1.0;
+    for (int i = 0; i < n; ++i) {
+      const double a = yr[i] * yr[i] + yi[i] * yi[i];
+      if (a > best * (1.0 + 1e-12)) {   // first index wins near-ties: deterministic
+        best = a;
+        am = i;
+      }
+    }
+    argmax = am;
+    amax = sqrt(best);
+  }
+  __syncthreads();
+  const double pr = yr[argmax], pi = yi[argmax];
+  // multiply by conj(p)/|p| / nrm
+  const double sc = (amax > 0.0 && nrm > 0.0) ? 1.0 / (amax * nrm) : 1.0;
+  const double cr = pr * sc, ci = -pi * sc;
+  __syncthreads();
+  for (int i = tid; i < n; i += bd) {
+    const double a = yr[i], b = yi[i];
+    yr[i] = a * cr - b * ci;
+    yi[i] = a * ci + b * cr;
+  }
+}
+
+// Canonical order of the eigen-triplets and the real 2x2-block layout.
+// Heads are the eigenvalues with wi >= 0 (one per conjugate pair).  Sorted by
+// |lambda| descending, then Im descending (stable).  Writes, per output column
+// c: lam_re[c], lam_im[c] and the real-form eigenvector column WR[:, c].
+__global__ void k_eig_layout(int n, const double* __restrict__ wr, const double* __restrict__ wi,
+                             const int* __restrict__ heads, const int* __restrict__ nheads_ptr,
+                             const double* __restrict__ Yre,
+                             const double* __restrict__ Yim, double* __restrict__ WR,
+                             double* __restrict__ lam_re, double* __restrict__ lam_im,
+                             int* __restrict__ order_scratch, int32_t* info) {
+  __shared__ int colstart[1024];
+  const int tid = threadIdx.x;
+  const int nheads = *nheads_ptr;
+  if (tid == 0) {
+    int* ord = order_scratch;
+    for (int h = 0; h < nheads; ++h) ord[h] = h;
+    for (int a = 1; a < nheads; ++a) {   // insertion sort: few hundred entries
+      const int key = ord[a];
+      const int ek = heads[key];
+      const double mk = hypot(wr[ek], wi[ek]), ik = wi[ek];
+      int b = a - 1;
+      while (b >= 0) {
+        const int eb = heads[ord[b]];
+        const double mb = hypot(wr[eb], wi[eb]), ib = wi[eb];
+        const bool before = (mk > mb) || (mk == mb && ik > ib);
+        if (!before) break;
+        ord[b + 1] = ord[b];
+        --b;
+      }
+      ord[b + 1] = key;
+    }
+    int c = 0, pairs = 0, reals = 0;
+    for (int h = 0; h < nheads; ++h) {
+      colstart[h] = c;
+      const int e = heads[ord[h]];
+      const int width = (wi[e] > 0.0) ? 2 : 1;
+      if (c + width > n) {            // inconsistent pairing: never write past column n-1
+        raise_status(info, DMD_ENUMERIC, 4998);
+        colstart[h] = -1;
+        continue;
+      }
+      if (wi[e] > 0.0) {
+        lam_re[c] = wr[e]; lam_im[c] = wi[e];
+        lam_re[c + 1] = wr[e]; lam_im[c + 1] = -wi[e];
+        c += 2;
+        ++pairs;
+      } else {
+        lam_re[c] = wr[e]; lam_im[c] = 0.0;
+        c += 1;
+        ++reals;
+      }
+    }
+    if (info) {
+      info[1] = pairs;
+      info[2] = reals;
+    }
+  }
+  __syncthreads();
+  for (int h = 0; h < nheads; ++h) {
+    const int src = order_scratch[h];
+    const int e = heads[src];
+    const int c = colstart[h];
+    if (c < 0) continue;
+    const bool pair = wi[e] > 0.0;
+    for (int i = tid; i < n; i += blockDim.x) {
+      WR[i + (int64_t)c * n] = Yre[i + (int64_t)src * n];
+      if (pair) WR[i + (int64_t)(c + 1) * n] = Yim[i + (int64_t)src * n];
+    }
+  }
+}
+
+// heads[] = indices e with wi[e] >= 0 (in index order).  One thread.
+__global__ void k_collect_heads(int n, const double* wi, int* heads, int* nheads, int32_t* info) {
+  if (threadIdx.x != 0) return;
+  int h = 0, c = 0;
+  for (int e = 0; e < n; ++e) {
+    if (wi[e] > 0.0) {
+      heads[h++] = e;
+      c += 2;
+    } else if (wi[e] == 0.0) {
+      heads[h++] = e;
+      c += 1;
+    } else if (!(wi[e] < 0.0)) {
+      raise_status(info, DMD_ENUMERIC, 4000 + e);   // NaN eigenvalue
+    }
+  }
+  if (c != n) raise_status(info, DMD_ENUMERIC, 4999);
+  *nheads = h;
+}
+
+// ---------------------------------------- symmetric tridiagonal eigenproblem
+
+// From a symmetric matrix reduced by k_hessenberg: d = diag, e = subdiagonal.
+__device__ int sturm_count(int n, const double* d, const double* e, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Eigenvalue i (descending) of the tridiagonal (d, e) by bisection and its
+// eigenvector by inverse iteration (3 solves, partial pivoting); one thread
+// per eigenvalue.  scratch: 7 n doubles per thread.  Outputs ev[i], Y[:, i].
+__global__ void k_tridiag_eig(int n, const double* __restrict__ A, int lda, double* __restrict__ ev,
+                              double* __restrict__ Y, double* __restrict__ scratch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ double sde[];
+  double* d = sde;
+  double* e = sde + n;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    d[t] = A[t + (int64_t)t * lda];
+    e[t] = (t + 1 < n) ? A[(t + 1) + (int64_t)t * lda] : 0.0;
+  }
+  __syncthreads();
+  if (i >= n) return;
+  double tnorm = 0.0, lo = 0.0, hi = 0.0;
+  for (int t = 0; t < n; ++t) {
+    const double off = (t > 0 ? fabs(e[t - 1]) : 0.0) + (t + 1 < n ? fabs(e[t]) : 0.0);
+    lo = (t == 0) ? d[t] - off : fmin(lo, d[t] - off);
+    hi = (t == 0) ? d[t] + off : fmax(hi, d[t] + off);
+    tnorm = fmax(tnorm, fabs(d[t]) + off);
+  }
+  if (tnorm == 0.0) tnorm = 1.0;
+  const double pivmin = DBL_MIN * 4.0 + kEps * kEps * tnorm;
+  lo -= 2.0 * kEps * tnorm;
+  hi += 2.0 * kEps * tnorm;
+  const int k = n - 1 - i;   // ascending index
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) break;
+    if (sturm_count(n, d, e, mid, pivmin) > k) hi = mid; else lo = mid;
+  }
+  const double lam = 0.5 * (lo + hi);
+  ev[i] = lam;
+  double* u0 = scratch + (int64_t)i * 7 * n;
+  double* u1 = u0 + n;
+  double* u2 = u1 + n;
+  double* ml = u2 + n;
+  double* pv = ml + n;
+  double* x = pv + n;
+  const double tiny = kEps * tnorm;
+  // factorise T - lam I with adjacent-row pivoting; U has two superdiagonals
+  double c0 = d[0] - lam, c1 = (n > 1) ? e[0] : 0.0, c2 = 0.0;
+  for (int q = 0; q + 1 < n; ++q) {
+    const double b0 = e[q], b1 = d[q + 1] - lam, b2 = (q + 2 < n) ? e[q + 1] : 0.0;
+    double p0, p1, p2, o0, o1, o2;
+    if (fabs(b0) > fabs(c0)) {
+      pv[q] = 1.0;
+      p0 = b0; p1 = b1; p2 = b2; o0 = c0; o1 = c1; o2 = c2;
+    } else {
+      pv[q] = 0.0;
+      p0 = c0; p1 = c1; p2 = c2; o0 = b0; o1 = b1; o2 = b2;
+    }
+    if (p0 == 0.0) p0 = tiny;
+    const double mult = o0 / p0;
+    u0[q] = p0; u1[q] = p1; u2[q] = p2; ml[q] = mult;
+    c0 = o1 - mult * p1;
+    c1 = o2 - mult * p2;
+    c2 = 0.0;
+  }
+  if (c0 == 0.0) c0 = tiny;
+  u0[n - 1] = c0; u1[n - 1] = 0.0; u2[n - 1] = 0.0;
+  for (int t = 0; t < n; ++t) x[t] = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    for (int q = 0; q + 1 < n; ++q) {
+      if (pv[q] != 0.0) {
+        const double tt = x[q];
+        x[q] = x[q + 1];
+        x[q + 1] = tt;
+      }
+      x[q + 1] -= ml[q] * x[q];
+    }
+    for (int t = n - 1; t >= 0; --t) {
+      double s = x[t];
+      if (t + 1 < n) s -= u1[t] * x[t + 1];
+      if (t + 2 < n) s -= u2[t] * x[t + 2];
+      x[t] = s / u0[t];
+    }
+    double nrm = 0.0;
+    for (int t = 0; t < n; ++t) nrm += x[t] * x[t];
+    nrm = sqrt(nrm);
+    const double inv = (nrm > 0.0 && isfinite(nrm)) ? 1.0 / nrm : 1.0;
+    for (int t = 0; t < n; ++t) x[t] *= inv;
+  }
+  for (int t = 0; t < n; ++t) Y[t + (int64_t)i * n] = x[t];
+}
+
+// Modified Gram-Schmidt inside clusters of (nearly) equal eigenvalues, in
+// descending order; one CTA.  Eigenvectors of well separated eigenvalues are
+// left untouched.
+__global__ void k_cluster_mgs(int n, const double* __restrict__ ev, double* __restrict__ Y, double rel) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double scale = 0.0;
+  for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(ev[i]));
+  const double gap = rel * (scale > 0.0 ? scale : 1.0);
+  int start = 0;
+  for (int i = 1; i < n; ++i) {
+    if (fabs(ev[i - 1] - ev[i]) > gap) {
+      start = i;
+      continue;
+    }
+    double* yi = Y + (int64_t)i * n;
+    for (int j = start; j < i; ++j) {
+      const double* yj = Y + (int64_t)j * n;
+      double loc = 0.0;
+      for (int t = tid; t < n; t += bd) loc += yj[t] * yi[t];
+      const double s = block_sum(loc, red);
+      for (int t = tid; t < n; t += bd) yi[t] -= s * yj[t];
+      __syncthreads();
+    }
+    double loc = 0.0;
+    for (int t = tid; t < n; t += bd) loc += yi[t] * yi[t];
+    const double nrm = sqrt(block_sum(loc, red));
+    for (int t = tid; t < n; t += bd) yi[t] /= nrm;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ least squares
+
+// min || A x - b || for A (mr x nc, ld, mr >= nc) by Householder QR; A and b
+// are overwritten.  One CTA; shared memory: mr + nc + 32 doubles.
+__global__ void k_lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info) {
+  extern __shared__ double sm[];
+  double* v = sm;
+  double* w = sm + mr;
+  double* red = sm + mr + nc;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double rmax = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    double* col = A + (int64_t)k * ld;
+    double loc = 0.0;
+    for (int i = k + 1 + tid; i < mr; i += bd) loc += col[i] * col[i];
+    const double sig = block_sum(loc, red);
+    const double alpha = col[k];
+    double tau = 0.0, beta = alpha;
+    if (sig != 0.0) {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha <= 0.0 ? nrm : -nrm;
+      tau = (beta - alpha) / beta;
+      const double sc = 1.0 / (alpha - beta);
+      for (int i = k + tid; i < mr; i += bd) v[i] = (i == k) ? 1.0 : col[i] * sc;
+    } else {
+      for (int i = k + tid; i < mr; i += bd) v[i] = (i == k) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    rmax = fmax(rmax, fabs(beta));
+    if (tau != 0.0) {
+      // w_j = v^T A[k:, j] for the trailing columns and the right-hand side (j = nc)
+      for (int j = k + 1 + tid; j <= nc; j += bd) {
+        const double* cj = (j < nc) ? A + (int64_t)j * ld : b;
+        double s = 0.0;
+        for (int i = k; i < mr; ++i) s = fma(v[i], cj[i], s);
+        w[j - 1] = s;   // j >= k + 1
+      }
+      __syncthreads();
+      const int wcols = nc - k;   // trailing columns k+1..nc-1 plus b
+      const int hgt = mr - k;
+      for (int q = tid; q < wcols * hgt; q += bd) {
+        const int i = k + q % hgt, j = k + 1 + q / hgt;
+        double* cj = (j < nc) ? A + (int64_t)j * ld : b;
+        cj[i] -= tau * v[i] * w[j - 1];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) col[k] = beta;
+    for (int i = k + 1 + tid; i < mr; i += bd) col[i] = 0.0;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int i = nc - 1; i >= 0; --i) {
+      double s = b[i];
+      for (int j = i + 1; j < nc; ++j) s -= A[i + (int64_t)j * ld] * x[j];
+      const double piv = A[i + (int64_t)i * ld];
+      if (fabs(piv) <= 1e-14 * rmax || !isfinite(piv)) {
+        raise_status(info, DMD_ENUMERIC, 5000 + i);
+        x[i] = 0.0;
+      } else {
+        x[i] = s / piv;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+
+dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
+                 int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DMD_OK;
+  dim3 grid((unsigned)ceil_div(M, 16), (unsigned)ceil_div(N, 16));
+  k_dgemm<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status cholesky_upper(int n, double* G, int ld, int32_t* info, int tag, cudaStream_t st) {
+  k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, info, tag);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st) {
+  k_tri_inv_upper<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, R, ldr, T, ldt);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st) {
+  const size_t smem = (2 * (size_t)n + 32) * sizeof(double);
+  k_hessenberg<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y, int ldy, int nvec,
+                   cudaStream_t st) {
+  if (nvec <= 0) return DMD_OK;
+  k_apply_q<<<(unsigned)nvec, 128, 0, st>>>(n, A, lda, tau, Y, ldy);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+size_t hqr_smem_bytes(int n) { return (size_t)n * n * sizeof(double); }
+bool hqr_fits_smem(int n) { return hqr_smem_bytes(n) <= 200 * 1024; }
+
+dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
+               cudaStream_t st) {
+  const bool in_smem = hqr_fits_smem(n);
+  const size_t smem = in_smem ? hqr_smem_bytes(n) : 0;
+  if (smem > 48 * 1024)
+    DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_hqr<<<1, 32, smem, st>>>(n, H, ldh, wr, wi, scratch, in_smem ? 1 : 0, info);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status collect_heads(int n, const double* wi, int* heads, int* nheads, int32_t* info, cudaStream_t st) {
+  k_collect_heads<<<1, 32, 0, st>>>(n, wi, heads, nheads, info);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+// Launched with the maximum possible number of heads (n); CTAs beyond the
+// actual count exit (the head list is padded with -1 by the caller).
+dmd_status hess_eigvecs(int n, const double* H, int ldh, const double* wr, const double* wi,
+                        const int* heads, int nheads_max, double* Yre, double* Yim, double* work,
+                        const double* hnorm, cudaStream_t st) {
+  const size_t smem = (4 * (size_t)n) * sizeof(double) + (size_t)n * sizeof(int) + 16;
+  k_hess_invit<<<(unsigned)nheads_max, 256, smem, st>>>(n, H, ldh, wr, wi, heads, Yre, Yim, work, hnorm);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status normalize_complex(int n, double* Yre, double* Yim, int ncols, cudaStream_t st) {
+  if (ncols <= 0) return DMD_OK;
+  k_normalize_complex<<<(unsigned)ncols, 128, 0, st>>>(n, Yre, Yim);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status eig_layout(int n, const double* wr, const double* wi, const int* heads, const int* nheads,
+                      const double* Yre, const double* Yim, double* WR, double* lam_re, double* lam_im,
+                      int* order_scratch, int32_t* info, cudaStream_t st) {
+  k_eig_layout<<<1, 256, 0, st>>>(n, wr, wi, heads, nheads, Yre, Yim, WR, lam_re, lam_im, order_scratch,
+                                  info);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, double* scratch,
+                       cudaStream_t st) {
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  k_tridiag_eig<<<(unsigned)ceil_div(n, 128), 128, smem, st>>>(n, A, lda, ev, Y, scratch);
+  DMD_LAUNCH_CHECK();
+  k_cluster_mgs<<<1, 256, 0, st>>>(n, ev, Y, 1e-11);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info, cudaStream_t st) {
+  const size_t smem = ((size_t)mr + nc + 32) * sizeof(double);
+  k_lstsq<<<1, 256, smem, st>>>(mr, nc, A, ld, b, x, info);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+}  // namespace dmd

@@ -1,0 +1,57 @@
+"""The C ABI library loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "dmd.h")).read()
+    return sorted(set(re.findall(r"^DMD_EXPORT [^(]*?\b(dmd_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libdmd():
+    from paper_2502_05339_gb300 import build_lib
+    path = build_lib.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("dmd_fit", "dmd_predict", "dmd_predict_backward", "dmd_fit_workspace_bytes",
+              "dmd_predict_loss", "dmd_gemm_tall", "dmd_gemm_tn", "dmd_sketch_matrix"):
+        assert s in syms
+
+
+def test_every_declared_symbol_is_exported(libdmd):
+    for s in declared_symbols():
+        assert hasattr(libdmd, s), s
+
+
+def test_binding_signatures_cover_header():
+    from paper_2502_05339_gb300 import dmd
+    assert set(declared_symbols()) == set(dmd.SIGNATURES)
+
+
+def test_host_side_queries_without_gpu(libdmd):
+    """Workspace queries and argument checks are host-only and need no GPU."""
+    from paper_2502_05339_gb300 import dmd
+    L = dmd.lib()
+    d = dmd.FitDesc(n=6291456, ldS=6291456, ldPhi=6291456, m=200, r=150, oversample=10, power_iters=2,
+                    q=0, precision=0, seed=1)
+    nb = ctypes.c_size_t(0)
+    assert L.dmd_fit_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)) == 0
+    assert nb.value > 2 * 6291456 * 160 * 4          # Y and Q1 at least
+    bad = dmd.FitDesc(n=100, ldS=98, ldPhi=100, m=10, r=3, oversample=2, power_iters=1, q=0, precision=0, seed=0)
+    assert L.dmd_fit_workspace_bytes(ctypes.byref(bad), ctypes.byref(nb)) == 1   # EINVAL: ldS < n
+    assert b"ldS" in L.dmd_last_error()
+    bad = dmd.FitDesc(n=100, ldS=100, ldPhi=100, m=10, r=11, oversample=2, power_iters=1, q=0, precision=0, seed=0)
+    assert L.dmd_fit_workspace_bytes(ctypes.byref(bad), ctypes.byref(nb)) == 1   # r > m
+    p = dmd.PredictDesc(n=100, ldPhi=100, ldOut=100, r=4, K=10, q=0, steps=0, precision=0, chunk=0)
+    assert L.dmd_predict_workspace_bytes(ctypes.byref(p), ctypes.byref(nb)) == 0
+    # a too-small workspace is refused before any device work
+    assert L.dmd_predict(ctypes.byref(p), 16, 16, 16, None, 16, 256, 8, None) == 2   # ENOMEM
