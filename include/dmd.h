@@ -81,8 +81,9 @@ enum { DMD_FP32 = 0, DMD_MIXED_BF16X3 = 1 };
 /* Device status words (int32[DMD_INFO_WORDS]) written by dmd_fit:
  *   info[0] status (dmd_status), info[1] number of conjugate pairs,
  *   info[2] number of real eigenvalues, info[3] QR sweeps used,
- *   info[4] tag of the first failure, info[5] number of Cholesky pivots
- *   raised to the rank floor (directions the snapshots do not span). */
+ *   info[4] tag of the first failure, info[5] number of sketch directions
+ *   dropped by the Gram orthonormalisations (directions the snapshots do not
+ *   resolve above rounding). */
 #define DMD_INFO_WORDS 8
 
 #define DMD_MODAL_DOUBLES(r, q) ((size_t)(r) * (4 + (size_t)(q)))

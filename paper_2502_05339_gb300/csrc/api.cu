@@ -39,7 +39,7 @@ dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, c
                         double* C, void* ws, cudaStream_t st);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
-dmd_status cholesky_upper(int n, double* G, int ld, int32_t* info, int tag, cudaStream_t st);
+dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st);
 dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st);
 dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y, int ldy, int nvec,
@@ -194,16 +194,24 @@ dmd_status validate_fit(const dmd_fit_desc* d) {
   return DMD_OK;
 }
 
+// Relative pivot floor of the Gram-based orthonormalisations: a direction
+// whose squared residual is below tau * (largest squared column norm) is
+// dropped.  The tall Grams are accurate to ~1e-6 relative (FP32 / split-bf16
+// products summed in FP32 over short stretches, FP64 across), so 1e-10 keeps
+// every direction the data resolve and drops the rounding-noise ones; the
+// small FP64 Grams use 1e-13.
+constexpr double kTauTall = 1e-10, kTauSmall = 1e-13;
+
 // CholeskyQR2 of a tall FP32 matrix Y (n x l): Q1 = Y R1^{-1} is written
 // explicitly; the second factor R2 is kept as T2 = R2^{-1} and folded into the
 // consumers, so Q = Q1 T2.  G must hold Y^T Y (FP64) on entry.
 dmd_status orth_tall(const Tall& tall, FitBufs& b, int32_t* info, int tag, cudaStream_t st) {
   const int l = b.l;
-  DMD_TRY(cholesky_upper(l, b.G, l, info, tag, st));
+  DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
   DMD_TRY(tall.nn(b.n, l, l, b.Y, b.ldY, b.T1, b.Q1, b.ldY, b.gemm_ws, st));
   DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
-  DMD_TRY(cholesky_upper(l, b.G, l, info, tag + 1, st));
+  DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag + 1, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
   return DMD_OK;
 }
@@ -213,7 +221,7 @@ dmd_status orth_small(FitBufs& b, int rows, int32_t* info, int tag, cudaStream_t
   const int l = b.l;
   for (int pass = 0; pass < 2; ++pass) {
     DMD_TRY(dgemm(l, l, rows, 1.0, b.Z, rows, true, b.Z, rows, false, 0.0, b.Gz, l, st));
-    DMD_TRY(cholesky_upper(l, b.Gz, l, info, tag + pass, st));
+    DMD_TRY(cholesky_upper(l, b.Gz, l, kTauSmall, info, tag + pass, st));
     DMD_TRY(tri_inv_upper(l, b.Gz, l, b.Tz, l, st));
     DMD_TRY(dgemm(rows, l, l, 1.0, b.Z, rows, false, b.Tz, l, false, 0.0, b.Zp, rows, st));
     DMD_TRY(fit_glue_copy((int64_t)rows * l, b.Zp, b.Z, st));

@@ -67,40 +67,46 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
 // ------------------------------------------------------------- Cholesky
 
 // In place: the upper triangle of G (n x n, ld) becomes R with R^T R = G; the
-// strict lower triangle is zeroed.  One CTA.  A pivot below 1e-14 of the
-// largest diagonal entry (a direction the data do not span, within rounding)
-// is raised to that floor instead of failing, and counted in info[5]; such
-// directions end up with negligible singular values and are truncated later.
-// Only a non-finite pivot or an all-zero matrix is an error.
-__global__ void k_cholesky_upper(int n, double* G, int ld, int32_t* info, int tag) {
+// strict lower triangle is zeroed.  One CTA.  Column j whose pivot (the
+// squared residual of column j against columns 0..j-1) is not above
+// tau * max_i G_ii is dropped: row j of R is set to zero, so the Gram-based
+// orthonormalisation leaves that (numerically dependent) direction out;
+// k_tri_inv_upper then zeroes row and column j of R^{-1}.  Drops are counted
+// in info[5].  A non-finite pivot is DMD_ENONFINITE, an all-zero matrix
+// DMD_ENUMERIC.
+__global__ void k_cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag) {
   __shared__ double piv;
   __shared__ double red[32];
   const int tid = threadIdx.x, bd = blockDim.x;
   double loc = 0.0;
   for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
   const double dmax = block_max(loc, red);
-  const double floor_ = 1e-14 * dmax;
+  const double floor_ = tau * dmax;
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
-      double d = G[j + (int64_t)j * ld];
+      const double d = G[j + (int64_t)j * ld];
       if (!isfinite(d) || !isfinite(dmax)) {
         raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
         piv = -1.0;
       } else if (!(dmax > 0.0)) {
         raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
         piv = -1.0;
+      } else if (!(d > floor_)) {
+        piv = 0.0;   // dropped direction
+        if (info) atomicAdd(&info[5], 1);
       } else {
-        if (!(d > floor_)) {
-          d = floor_;
-          if (info) atomicAdd(&info[5], 1);
-        }
         piv = sqrt(d);
-        G[j + (int64_t)j * ld] = piv;
       }
+      if (piv >= 0.0) G[j + (int64_t)j * ld] = piv;
     }
     __syncthreads();
     const double p = piv;
     if (p < 0.0) return;
+    if (p == 0.0) {
+      for (int i = j + 1 + tid; i < n; i += bd) G[j + (int64_t)i * ld] = 0.0;
+      __syncthreads();
+      continue;
+    }
     const double ip = 1.0 / p;
     for (int i = j + 1 + tid; i < n; i += bd) G[j + (int64_t)i * ld] *= ip;
     __syncthreads();
@@ -117,18 +123,29 @@ __global__ void k_cholesky_upper(int n, double* G, int ld, int32_t* info, int ta
   }
 }
 
-// T = R^{-1} for upper triangular R; one thread per column.
+// T = R^{-1} for upper triangular R; one thread per column.  A zero diagonal
+// entry marks a dropped direction: its row and column of T are zero.
 __global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T,
                                 int ldt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double* t = T + (int64_t)j * ldt;
   for (int i = j + 1; i < n; ++i) t[i] = 0.0;
-  t[j] = 1.0 / R[j + (int64_t)j * ldr];
+  const double rjj = R[j + (int64_t)j * ldr];
+  if (rjj == 0.0) {
+    for (int i = 0; i <= j; ++i) t[i] = 0.0;
+    return;
+  }
+  t[j] = 1.0 / rjj;
   for (int i = j - 1; i >= 0; --i) {
+    const double rii = R[i + (int64_t)i * ldr];
+    if (rii == 0.0) {
+      t[i] = 0.0;
+      continue;
+    }
     double s = 0.0;
     for (int k = i + 1; k <= j; ++k) s = fma(R[i + (int64_t)k * ldr], t[k], s);
-    t[i] = -s / R[i + (int64_t)i * ldr];
+    t[i] = -s / rii;
   }
 }
 
@@ -844,8 +861,8 @@ dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bo
   return DMD_OK;
 }
 
-dmd_status cholesky_upper(int n, double* G, int ld, int32_t* info, int tag, cudaStream_t st) {
-  k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, info, tag);
+dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
+  k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
