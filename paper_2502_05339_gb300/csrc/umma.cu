@@ -1,21 +1,970 @@
-// BF16x3 tcgen05 passes (placeholder until the tensor-core kernels land).
+// BF16x3 tensor-core passes over the tall snapshot matrices (tcgen05, sm_103a).
+//
+// Every FP32 operand x is split into bf16 hi = rn(x), lo = rn(x - hi) and a
+// product is formed as hi*hi' + hi*lo' + lo*hi' with FP32 accumulation in
+// tensor memory (TMEM).  FP32 tiles arrive by TMA (cp.async.bulk.tensor) into a
+// shared-memory ring; converter warps split them into the K-major canonical
+// UMMA layout (no swizzle: 8-row x 16-byte core matrices, K-adjacent core
+// matrices 128 B apart, 8-row groups 256 B apart); one thread issues the
+// tcgen05.mma instructions; epilogue warps drain TMEM with tcgen05.ld.
+// All waits are bounded (2 s on the global timer); a wait that runs out sets
+// an abort flag that every role checks, the kernel finishes its in-flight
+// asynchronous work, frees TMEM and reports DMD_ETIMEOUT.
+//
+//   k_umma_nn_bres : C = A B, A tall (n x Kd) streamed, B (Kd x N, N <= 256)
+//                    resident in shared memory -- sketch X Omega, power step
+//                    X Z, CholeskyQR step Y R^{-1}, modes X' M (Sec. 4.3, 3.1).
+//   k_umma_nn_ares : C = A B with A's 128-row tile resident and B streamed in
+//                    column chunks -- the reconstruction Phi_R C of
+//                    Eq. large_time_step with K frames.
+//   k_umma_tn      : C = A^T B reduced over the tall dimension -- X^T Q, Q^T S
+//                    and Gram matrices; per-CTA FP64 partials.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dmd {
 
-size_t umma_nn_workspace_bytes(int64_t, int, int) { return 256; }
-size_t umma_tn_workspace_bytes(int64_t, int, int) { return 256; }
+namespace {
 
-dmd_status umma_gemm_nn(int64_t, int, int, const float*, int64_t, const double*, float*, int64_t, void*,
-                        cudaStream_t) {
-  set_error("mixed BF16x3 precision is not available in this build");
-  return DMD_EINVAL;
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(tx) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 
-dmd_status umma_gemm_tn(int64_t, int, int, const float*, int64_t, const float*, int64_t, double*, void*,
-                        cudaStream_t) {
-  set_error("mixed BF16x3 precision is not available in this build");
-  return DMD_EINVAL;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
+
+// Wait for the phase of parity `parity`; false if the CTA aborted or the wait
+// ran out (which aborts the CTA).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* abort_flag) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_test(b, parity)) {
+    if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(abort_flag, 1);
+      return false;
+    }
+  }
+  return true;
+}
+// Teardown wait: bounded, ignores the abort flag.
+__device__ __forceinline__ void mbar_wait_drain(uint64_t* b, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_test(b, parity))
+    if (gtimer() - t0 > kWaitNs) return;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, FP32 accumulation.
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle.  lbo: byte distance
+// between K-adjacent core matrices, sbo: between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of tcgen05
+  return d;                 // base offset 0, absolute LBO mode, layout type 0 = no swizzle
+}
+constexpr uint32_t kLBO = 128, kSBO = 256;
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of the 16-byte chunk (row, half) of a rows x 16 K-slice.
+__device__ __forceinline__ uint32_t kslice_off(int row, int half) {
+  return (uint32_t)((row >> 3) * 256 + half * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Split 16 consecutive-K FP32 values into hi/lo and store them as one K-slice
+// row (two 16-byte chunks each) at `hi` and `lo` (slice bases).
+__device__ __forceinline__ void split_store_row(const float* x, uint8_t* hi, uint8_t* lo, int row) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * i + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+    h[i] = pack2(h0, h1);
+    l[i] = pack2(l0, l1);
+  }
+  *reinterpret_cast<uint4*>(hi + kslice_off(row, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(hi + kslice_off(row, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
+  *reinterpret_cast<uint4*>(lo + kslice_off(row, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<uint4*>(lo + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
+}
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// ---------------------------------------------------- B operand pre-split
+
+// B (Kd x N, FP64, column-major, ld Kd) -> bf16 hi/lo in the UMMA K-slice
+// layout of an N-row operand, grouped in column chunks of BN rows:
+// chunk c, slice s, row j: offset c*(2*ks*BN*32) + s*BN*32 + chunk-of(j, k); lo
+// follows hi inside each chunk (ks*BN*32 bytes later).  Zero padded.
+__global__ void k_split_b(int Kd, int N, const double* __restrict__ B, int BN, int ksteps, int nchunks,
+                          uint8_t* __restrict__ out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // one thread per (row, slice)
+  const int64_t total = (int64_t)nchunks * BN * ksteps;
+  if (idx >= total) return;
+  const int jr = (int)(idx % BN);
+  const int s = (int)((idx / BN) % ksteps);
+  const int c = (int)(idx / ((int64_t)BN * ksteps));
+  const int j = c * BN + jr;
+  float x[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int k = s * 16 + t;
+    x[t] = (j < N && k < Kd) ? (float)B[(int64_t)j * Kd + k] : 0.f;
+  }
+  uint8_t* base = out + (int64_t)c * (2LL * ksteps * BN * 32);
+  uint8_t* hi = base + (int64_t)s * BN * 32;
+  uint8_t* lo = base + (int64_t)(ksteps + s) * BN * 32;
+  // residual of the FP64 value: use x (FP32) for hi, the FP64 remainder for lo
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float v0 = x[2 * i], v1 = x[2 * i + 1];
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+    double r0 = 0.0, r1 = 0.0;
+    const int k0 = s * 16 + 2 * i;
+    if (j < N && k0 < Kd) r0 = B[(int64_t)j * Kd + k0] - (double)__bfloat162float(h0);
+    if (j < N && k0 + 1 < Kd) r1 = B[(int64_t)j * Kd + k0 + 1] - (double)__bfloat162float(h1);
+    h[i] = pack2(h0, h1);
+    l[i] = pack2(__float2bfloat16_rn((float)r0), __float2bfloat16_rn((float)r1));
+  }
+  *reinterpret_cast<uint4*>(hi + kslice_off(jr, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(hi + kslice_off(jr, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
+  *reinterpret_cast<uint4*>(lo + kslice_off(jr, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<uint4*>(lo + kslice_off(jr, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
+}
+
+// ============================================================ NN, B resident
+
+constexpr int NN_S = 4;    // TMA stages (FP32 128 x 16 tiles, 8 KB)
+constexpr int NN_CS = 4;   // converted stages (bf16 hi + lo, 8 KB)
+constexpr int NN_THREADS = 320;
+
+__global__ void __launch_bounds__(NN_THREADS, 1)
+    k_umma_nn_bres(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bsplit,
+                   float* __restrict__ C, int64_t ldc, int64_t n, int N, int Np, int ksteps, int64_t ntiles,
+                   int32_t* err) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = align1024(smraw);
+  const uint32_t bres_bytes = 2u * (uint32_t)ksteps * (uint32_t)Np * 32u;
+  uint8_t* Bres = sm;
+  uint8_t* stA = sm + ((bres_bytes + 1023u) & ~1023u);
+  uint8_t* cv = stA + NN_S * 8192;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cv + NN_CS * 8192);
+  uint64_t* full = bars;
+  uint64_t* empty = full + NN_S;
+  uint64_t* cfull = empty + NN_S;
+  uint64_t* cempty = cfull + NN_CS;
+  uint64_t* accf = cempty + NN_CS;
+  uint64_t* acce = accf + 2;
+  uint64_t* bfull = acce + 2;
+  uint64_t* tdown = bfull + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NN_S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 128);
+    }
+    for (int i = 0; i < NN_CS; ++i) {
+      mbar_init(&cfull[i], 128);
+      mbar_init(&cempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 128);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(tdown, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, 512);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(bfull, bres_bytes);
+      for (uint32_t off = 0; off < bres_bytes; off += 32768u)
+        bulk_g2s(Bres + off, Bsplit + off, min(32768u, bres_bytes - off), bfull);
+      uint32_t it = 0;
+      uint32_t last_par[NN_S];
+      bool issued[NN_S];
+      for (int i = 0; i < NN_S; ++i) issued[i] = false, last_par[i] = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        for (int ks = 0; ks < ksteps; ++ks, ++it) {
+          const uint32_t s = it % NN_S;
+          if (!mbar_wait(&empty[s], ((it / NN_S) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], 8192);
+          tma_load_2d(stA + s * 8192, &tmA, &full[s], (int)(tile * 128), ks * 16);
+          issued[s] = true;
+          last_par[s] = (it / NN_S) & 1;
+        }
+      }
+      // in-flight TMA writes must land before the CTA's shared memory goes away
+      for (int i = 0; i < NN_S; ++i)
+        if (issued[i]) mbar_wait_drain(&full[i], last_par[i]);
+      mbar_wait_drain(bfull, 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, Np);
+      bool ok = mbar_wait(bfull, 0, abort_flag);
+      uint32_t cit = 0, ait = 0;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++ait) {
+        const uint32_t ab = ait & 1;
+        if (!mbar_wait(&acce[ab], ((ait >> 1) & 1) ^ 1, abort_flag)) break;
+        tc_after();
+        const uint32_t d = tmem + ab * 256;
+        for (int ks = 0; ks < ksteps; ++ks, ++cit) {
+          const uint32_t cs = cit % NN_CS;
+          if (!mbar_wait(&cfull[cs], (cit / NN_CS) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t a = su32(cv + cs * 8192);
+          const uint32_t bh = su32(Bres) + (uint32_t)ks * Np * 32;
+          const uint32_t bl = su32(Bres) + (uint32_t)(ksteps + ks) * Np * 32;
+          const uint64_t ahd = sdesc(a, kLBO, kSBO), ald = sdesc(a + 4096, kLBO, kSBO);
+          const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
+          umma_bf16(d, ahd, bhd, idesc, ks > 0 ? 1u : 0u);
+          umma_bf16(d, ahd, bld, idesc, 1u);
+          umma_bf16(d, ald, bhd, idesc, 1u);
+          umma_commit(&cempty[cs]);
+        }
+        if (!ok) break;
+        umma_commit(&accf[ab]);
+      }
+      umma_commit(tdown);          // completes when every MMA issued above has finished
+      mbar_wait_drain(tdown, 0);
+    }
+  } else if (warp < 6) {
+    const int t = threadIdx.x - 64;   // row of the tile
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      for (int ks = 0; ks < ksteps; ++ks, ++it) {
+        const uint32_t s = it % NN_S, cs = it % NN_CS;
+        if (!mbar_wait(&full[s], (it / NN_S) & 1, abort_flag) ||
+            !mbar_wait(&cempty[cs], ((it / NN_CS) & 1) ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const float* src = reinterpret_cast<const float*>(stA + s * 8192);
+        float x[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];
+        uint8_t* dst = cv + cs * 8192;
+        split_store_row(x, dst, dst + 4096, t);
+        fence_async_smem();
+        mbar_arrive(&cfull[cs]);
+        mbar_arrive(&empty[s]);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int rowq = q * 32 + lane;
+    uint32_t ait = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ait) {
+      const uint32_t ab = ait & 1;
+      if (!mbar_wait(&accf[ab], (ait >> 1) & 1, abort_flag)) break;
+      tc_after();
+      const int64_t row = tile * 128 + rowq;
+      for (int c0 = 0; c0 < Np; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ab * 256 + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < N) C[(int64_t)(c0 + j) * ldc + row] = v[j];
+        }
+      }
+      tc_before();
+      mbar_arrive(&acce[ab]);
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8001);
+}
+
+// ============================================================ NN, A resident
+
+constexpr int AR_SA = 2;     // TMA stages for the A tile slices
+constexpr int AR_NB = 2;     // B chunk buffers
+constexpr int AR_ACC = 4;    // TMEM accumulators (64 columns each)
+constexpr int AR_BN = 64;    // frames per chunk
+constexpr int AR_THREADS = 320;
+
+__global__ void __launch_bounds__(AR_THREADS, 1)
+    k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bchunks,
+                   float* __restrict__ C, int64_t ldc, int64_t n, int N, int ksteps, int nchunks, int64_t ntiles,
+                   int32_t* err) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = align1024(smraw);
+  const uint32_t ares_bytes = 2u * (uint32_t)ksteps * 128u * 32u;            // hi then lo
+  const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * AR_BN * 32u;
+  uint8_t* Ares = sm;
+  uint8_t* stA = Ares + ((ares_bytes + 1023u) & ~1023u);
+  uint8_t* Bbuf = stA + AR_SA * 8192;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bbuf + AR_NB * ((chunk_bytes + 1023u) & ~1023u));
+  uint64_t* afull = bars;               // TMA slice landed
+  uint64_t* aempty = afull + AR_SA;     // slice converted
+  uint64_t* bfull = aempty + AR_SA;
+  uint64_t* bempty = bfull + AR_NB;
+  uint64_t* accf = bempty + AR_NB;
+  uint64_t* acce = accf + AR_ACC;
+  uint64_t* ares_full = acce + AR_ACC;  // converters finished the tile's A
+  uint64_t* ares_free = ares_full + 1;  // MMAs of the tile finished reading A
+  uint64_t* tdown = ares_free + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+  const uint32_t bstride = (chunk_bytes + 1023u) & ~1023u;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < AR_SA; ++i) {
+      mbar_init(&afull[i], 1);
+      mbar_init(&aempty[i], 128);
+    }
+    for (int i = 0; i < AR_NB; ++i) {
+      mbar_init(&bfull[i], 1);
+      mbar_init(&bempty[i], 1);
+    }
+    for (int i = 0; i < AR_ACC; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 128);
+    }
+    mbar_init(ares_full, 128);
+    mbar_init(ares_free, 1);
+    mbar_init(tdown, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, 256);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t ait = 0, bit = 0;
+      bool ok = true;
+      bool a_issued[AR_SA] = {false, false}, b_issued[AR_NB] = {false, false};
+      uint32_t a_par[AR_SA] = {0, 0}, b_par[AR_NB] = {0, 0};
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        for (int ks = 0; ks < ksteps; ++ks, ++ait) {
+          const uint32_t s = ait % AR_SA;
+          if (!mbar_wait(&aempty[s], ((ait / AR_SA) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&afull[s], 8192);
+          tma_load_2d(stA + s * 8192, &tmA, &afull[s], (int)(tile * 128), ks * 16);
+          a_issued[s] = true;
+          a_par[s] = (ait / AR_SA) & 1;
+        }
+        for (int c = 0; ok && c < nchunks; ++c, ++bit) {
+          const uint32_t b = bit % AR_NB;
+          if (!mbar_wait(&bempty[b], ((bit / AR_NB) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&bfull[b], chunk_bytes);
+          const uint8_t* src = Bchunks + (int64_t)c * chunk_bytes;
+          for (uint32_t off = 0; off < chunk_bytes; off += 32768u)
+            bulk_g2s(Bbuf + b * bstride + off, src + off, min(32768u, chunk_bytes - off), &bfull[b]);
+          b_issued[b] = true;
+          b_par[b] = (bit / AR_NB) & 1;
+        }
+      }
+      for (int i = 0; i < AR_SA; ++i)
+        if (a_issued[i]) mbar_wait_drain(&afull[i], a_par[i]);
+      for (int i = 0; i < AR_NB; ++i)
+        if (b_issued[i]) mbar_wait_drain(&bfull[i], b_par[i]);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, AR_BN);
+      uint32_t tit = 0, bit = 0, accit = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
+        if (!mbar_wait(ares_full, tit & 1, abort_flag)) break;
+        tc_after();
+        for (int c = 0; c < nchunks; ++c, ++bit, ++accit) {
+          const uint32_t b = bit % AR_NB, ab = accit % AR_ACC;
+          if (!mbar_wait(&bfull[b], (bit / AR_NB) & 1, abort_flag) ||
+              !mbar_wait(&acce[ab], ((accit / AR_ACC) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t d = tmem + ab * AR_BN;
+          const uint32_t bbase = su32(Bbuf + b * bstride);
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t ah = su32(Ares) + (uint32_t)ks * 4096u;
+            const uint32_t al = su32(Ares) + (uint32_t)(ksteps + ks) * 4096u;
+            const uint32_t bh = bbase + (uint32_t)ks * AR_BN * 32u;
+            const uint32_t bl = bbase + (uint32_t)(ksteps + ks) * AR_BN * 32u;
+            const uint64_t ahd = sdesc(ah, kLBO, kSBO), ald = sdesc(al, kLBO, kSBO);
+            const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
+            umma_bf16(d, ahd, bhd, idesc, ks > 0 ? 1u : 0u);
+            umma_bf16(d, ahd, bld, idesc, 1u);
+            umma_bf16(d, ald, bhd, idesc, 1u);
+          }
+          umma_commit(&bempty[b]);
+          umma_commit(&accf[ab]);
+        }
+        if (!ok) break;
+        umma_commit(ares_free);
+      }
+      umma_commit(tdown);
+      mbar_wait_drain(tdown, 0);
+    }
+  } else if (warp < 6) {
+    const int t = threadIdx.x - 64;
+    uint32_t ait = 0, tit = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
+      // the previous tile's MMAs must be done with the resident A
+      if (tit > 0 && !mbar_wait(ares_free, (tit - 1) & 1, abort_flag)) break;
+      for (int ks = 0; ks < ksteps; ++ks, ++ait) {
+        const uint32_t s = ait % AR_SA;
+        if (!mbar_wait(&afull[s], (ait / AR_SA) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const float* src = reinterpret_cast<const float*>(stA + s * 8192);
+        float x[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];
+        split_store_row(x, Ares + (uint32_t)ks * 4096u, Ares + (uint32_t)(ksteps + ks) * 4096u, t);
+        mbar_arrive(&aempty[s]);
+      }
+      if (!ok) break;
+      fence_async_smem();
+      mbar_arrive(ares_full);
+    }
+  } else {
+    const int q = warp & 3;
+    const int rowq = q * 32 + lane;
+    uint32_t accit = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const int64_t row = tile * 128 + rowq;
+      for (int c = 0; c < nchunks; ++c, ++accit) {
+        const uint32_t ab = accit % AR_ACC;
+        if (!mbar_wait(&accf[ab], (accit / AR_ACC) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+#pragma unroll
+        for (int c0 = 0; c0 < AR_BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ab * AR_BN + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+          if (row < n) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = c * AR_BN + c0 + j;
+              if (col < N) C[(int64_t)col * ldc + row] = v[j];
+            }
+          }
+        }
+        tc_before();
+        mbar_arrive(&acce[ab]);
+      }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_after();
+    tmem_dealloc(tmem, 256);
+  }
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8002);
+}
+
+// ============================================================ TN reduction
+
+constexpr int TN_S = 3;          // TMA stages (A slice + B slice)
+constexpr int TN_THREADS = 320;
+constexpr int TN_FLUSH = 256;    // k-steps (of 16 rows) between FP64 flushes
+
+// part[blockIdx.x][b * Ka + a] = sum over this CTA's rows of A[:, a] * B[:, b].
+// A slice: TMA box {16 rows, Mt*128 cols}; B slice: box {16 rows, Np cols}.
+__global__ void __launch_bounds__(TN_THREADS, 1)
+    k_umma_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
+              int N, int Mt, int Np, int64_t chunk, double* __restrict__ part, int32_t* err) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = align1024(smraw);
+  const uint32_t a_bytes = 16u * 4u * (uint32_t)Mt * 128u;   // FP32 slice of A
+  const uint32_t b_bytes = 16u * 4u * (uint32_t)Np;          // FP32 slice of B
+  const uint32_t st_bytes = (a_bytes + b_bytes + 1023u) & ~1023u;
+  const uint32_t ca_bytes = (uint32_t)Mt * 128u * 32u;       // one bf16 K-slice of A (hi or lo)
+  const uint32_t cb_bytes = (uint32_t)Np * 32u;
+  const uint32_t cv_bytes = (2u * (ca_bytes + cb_bytes) + 1023u) & ~1023u;
+  uint8_t* st = sm;
+  uint8_t* cv = st + TN_S * st_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cv + 2 * cv_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = full + TN_S;
+  uint64_t* cfull = empty + TN_S;      // 2 converted buffers
+  uint64_t* cempty = cfull + 2;
+  uint64_t* accf = cempty + 2;
+  uint64_t* acce = accf + 1;
+  uint64_t* tdown = acce + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rbeg = (int64_t)blockIdx.x * chunk;
+  const int64_t rend = min(n, rbeg + chunk);
+  const int ksteps = rend > rbeg ? (int)((rend - rbeg + 15) / 16) : 0;
+  const int nflush = (ksteps + TN_FLUSH - 1) / TN_FLUSH;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TN_S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 128);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&cfull[i], 128);
+      mbar_init(&cempty[i], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 128);
+    mbar_init(tdown, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, 512);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool issued[TN_S] = {false, false, false};
+      uint32_t par[TN_S] = {0, 0, 0};
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t s = ks % TN_S;
+        if (!mbar_wait(&empty[s], ((ks / TN_S) & 1) ^ 1, abort_flag)) break;
+        mbar_expect_tx(&full[s], a_bytes + b_bytes);
+        const int r0 = (int)(rbeg + (int64_t)ks * 16);
+        tma_load_2d(st + s * st_bytes, &tmA, &full[s], r0, 0);
+        tma_load_2d(st + s * st_bytes + a_bytes, &tmB, &full[s], r0, 0);
+        issued[s] = true;
+        par[s] = (ks / TN_S) & 1;
+      }
+      for (int i = 0; i < TN_S; ++i)
+        if (issued[i]) mbar_wait_drain(&full[i], par[i]);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, Np);
+      bool ok = true;
+      int ks = 0;
+      for (int f = 0; ok && f < nflush; ++f) {
+        if (!mbar_wait(acce, (f & 1) ^ 1, abort_flag)) break;
+        tc_after();
+        const int kend = min(ksteps, (f + 1) * TN_FLUSH);
+        for (int kk = 0; ks < kend; ++ks, ++kk) {
+          const uint32_t cs = ks & 1;
+          if (!mbar_wait(&cfull[cs], (ks >> 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t base = su32(cv + cs * cv_bytes);
+          const uint32_t ahi = base, alo = base + ca_bytes;
+          const uint32_t bhi = base + 2 * ca_bytes, blo = bhi + cb_bytes;
+          const uint64_t bhd = sdesc(bhi, kLBO, kSBO), bld = sdesc(blo, kLBO, kSBO);
+          for (int mt = 0; mt < Mt; ++mt) {
+            const uint32_t d = tmem + (uint32_t)(mt * Np);
+            const uint64_t ahd = sdesc(ahi + mt * 4096u, kLBO, kSBO), ald = sdesc(alo + mt * 4096u, kLBO, kSBO);
+            umma_bf16(d, ahd, bhd, idesc, kk > 0 ? 1u : 0u);
+            umma_bf16(d, ahd, bld, idesc, 1u);
+            umma_bf16(d, ald, bhd, idesc, 1u);
+          }
+          umma_commit(&cempty[cs]);
+        }
+        if (!ok) break;
+        umma_commit(accf);
+      }
+      umma_commit(tdown);
+      mbar_wait_drain(tdown, 0);
+    }
+  } else if (warp < 6) {
+    const int t = threadIdx.x - 64;
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const uint32_t s = ks % TN_S, cs = ks & 1;
+      if (!mbar_wait(&full[s], (ks / TN_S) & 1, abort_flag) ||
+          !mbar_wait(&cempty[cs], ((ks >> 1) & 1) ^ 1, abort_flag))
+        break;
+      const float* sa = reinterpret_cast<const float*>(st + s * st_bytes);
+      const float* sb = reinterpret_cast<const float*>(st + s * st_bytes + a_bytes);
+      uint8_t* base = cv + cs * cv_bytes;
+      float x[16];
+      for (int col = t; col < Mt * 128; col += 128) {   // A columns = operand rows
+        const float4* p = reinterpret_cast<const float4*>(sa + col * 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = p[c];
+          x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
+        }
+        split_store_row(x, base, base + ca_bytes, col);
+      }
+      for (int col = t; col < Np; col += 128) {
+        const float4* p = reinterpret_cast<const float4*>(sb + col * 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = p[c];
+          x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
+        }
+        split_store_row(x, base + 2 * ca_bytes, base + 2 * ca_bytes + cb_bytes, col);
+      }
+      fence_async_smem();
+      mbar_arrive(&cfull[cs]);
+      mbar_arrive(&empty[s]);
+    }
+  } else {
+    const int q = warp & 3;
+    const int rowq = q * 32 + lane;
+    double* out = part + (int64_t)blockIdx.x * Ka * N;
+    for (int f = 0; f < nflush; ++f) {
+      if (!mbar_wait(accf, f & 1, abort_flag)) break;
+      tc_after();
+      for (int mt = 0; mt < Mt; ++mt) {
+        const int a = mt * 128 + rowq;
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + (uint32_t)(mt * Np + c0) + ((uint32_t)(q * 32) << 16), v);
+          if (a < Ka) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int b = c0 + j;
+              if (b < N) {
+                double* p = out + (int64_t)b * Ka + a;
+                *p = (f == 0 ? 0.0 : *p) + (double)v[j];
+              }
+            }
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(acce);
+    }
+    if (nflush == 0) {   // no rows for this CTA: its partial is zero
+      for (int mt = 0; mt < Mt; ++mt) {
+        const int a = mt * 128 + rowq;
+        if (a < Ka)
+          for (int b = 0; b < N; ++b) out[(int64_t)b * Ka + a] = 0.0;
+      }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8003);
+}
+
+__global__ void k_reduce_parts(int64_t count, int parts, const double* __restrict__ part, double* __restrict__ C) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double s = 0.0;
+  for (int p = 0; p < parts; ++p) s += part[(int64_t)p * count + i];
+  C[i] = s;
+}
+
+// ------------------------------------------------------------ host side
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 2D FP32 map over a column-major matrix (rows x cols, ld floats) with box {box_rows, box_cols}.
+dmd_status make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                    int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return DMD_ECUDA;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0) {
+    set_error("TMA operand must be 16-byte aligned with ld a multiple of 4");
+    return DMD_EINVAL;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)std::max<int64_t>(cols, 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d): rows=%lld cols=%lld ld=%lld box=%dx%d", (int)r, (long long)rows,
+              (long long)cols, (long long)ld, box_rows, box_cols);
+    return DMD_ECUDA;
+  }
+  return DMD_OK;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+constexpr int kMaxSmem = 227 * 1024;
+
+size_t bres_smem(int ksteps, int Np) {
+  return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + NN_S * 8192 + NN_CS * 8192 + 256;
+}
+size_t ares_smem(int ksteps) {
+  const size_t chunk = ((size_t)2 * ksteps * AR_BN * 32 + 1023) & ~(size_t)1023;
+  return 1024 + (((size_t)2 * ksteps * 128 * 32 + 1023) & ~(size_t)1023) + AR_SA * 8192 + AR_NB * chunk + 256;
+}
+size_t tn_smem(int Mt, int Np) {
+  const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
+  const size_t cv = ((size_t)2 * (Mt * 128 * 32 + Np * 32) + 1023) & ~(size_t)1023;
+  return 1024 + TN_S * st + 2 * cv + 256;
+}
+
+// Largest column chunk of B that stays resident for the B-resident kernel.
+int bres_cols(int ksteps) {
+  int np = 256;
+  while (np > 16 && bres_smem(ksteps, np) > (size_t)kMaxSmem) np -= 16;
+  return np;
+}
+
+int tn_grid(int64_t n) {
+  const int64_t want = ceil_div(n, 4096);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), want));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N) {
+  (void)n;
+  const int ksteps = (int)ceil_div(Kd, 16);
+  // recon layout (64-column chunks) is the larger of the two layouts
+  const int64_t nch = ceil_div(N, AR_BN);
+  const size_t ares = (size_t)nch * 2 * ksteps * AR_BN * 32;
+  const size_t bres = (size_t)2 * ksteps * round_up(N, 16) * 32 + 2 * ksteps * 256 * 32;
+  return std::max(ares, bres) + 4096;
+}
+
+size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N) {
+  // per-CTA FP64 partials for every (Ka-chunk, N-chunk) sub-problem, reused
+  return (size_t)tn_grid(n) * std::min(Ka, 256) * std::min(N, 256) * sizeof(double) + 4096;
+}
+
+dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
+                        void* ws, cudaStream_t st) {
+  if (n <= 0 || N <= 0) return DMD_OK;
+  const int ksteps = (int)ceil_div(Kd, 16);
+  const int64_t ntiles = ceil_div(n, 128);
+  uint8_t* split = reinterpret_cast<uint8_t*>(ws);
+  CUtensorMap mapA;
+  DMD_TRY(make_map(&mapA, A, n, Kd, lda, 128, 16));
+  const int Npmax = bres_cols(ksteps);
+  const int grid = (int)std::min<int64_t>(num_sms(), ntiles);
+  if (N <= 256 && round_up(N, 16) <= Npmax) {
+    const int Np = (int)round_up(N, 16);
+    const int64_t work = (int64_t)Np * ksteps;
+    k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, Np, ksteps, 1, split);
+    DMD_LAUNCH_CHECK();
+    const size_t smem = bres_smem(ksteps, Np);
+    DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_bres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, nullptr);
+    DMD_LAUNCH_CHECK();
+    return DMD_OK;
+  }
+  // many output columns: A tile resident, B in 64-column chunks
+  const size_t smem = ares_smem(ksteps);
+  if (smem > (size_t)kMaxSmem) {
+    set_error("umma_gemm_nn: inner dimension %d too large for the resident-A layout", Kd);
+    return DMD_EINVAL;
+  }
+  const int nchunks = (int)ceil_div(N, AR_BN);
+  const int64_t work = (int64_t)nchunks * AR_BN * ksteps;
+  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, AR_BN, ksteps, nchunks, split);
+  DMD_LAUNCH_CHECK();
+  DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, ksteps, nchunks, ntiles, nullptr);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+// C (Ka x N, ld Ka) = A^T B; sub-problems of at most 256 x 256 so that the
+// accumulators (Mt * Np columns) fit in 512 TMEM columns.
+dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
+                        void* ws, cudaStream_t st) {
+  if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
+  double* part = reinterpret_cast<double*>(ws);
+  const int grid = tn_grid(n);
+  const int64_t chunk = round_up(ceil_div(n, grid), 16);
+  for (int a0 = 0; a0 < Ka; a0 += 256) {
+    const int ka = std::min(256, Ka - a0);
+    const int Mt = (int)ceil_div(ka, 128);
+    for (int b0 = 0; b0 < N; b0 += 256) {
+      const int nb = std::min(256, N - b0);
+      const int Np = (int)round_up(nb, 16);
+      CUtensorMap mA, mB;
+      DMD_TRY(make_map(&mA, A + (int64_t)a0 * lda, n, ka, lda, 16, Mt * 128));
+      DMD_TRY(make_map(&mB, B + (int64_t)b0 * ldb, n, nb, ldb, 16, Np));
+      const size_t smem = tn_smem(Mt, Np);
+      DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, chunk, part, nullptr);
+      DMD_LAUNCH_CHECK();
+      // reduce into the (a0, b0) block of C
+      const int64_t count = (int64_t)ka * nb;
+      if (a0 == 0 && ka == Ka) {
+        k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, grid, part, C + (int64_t)b0 * Ka);
+        DMD_LAUNCH_CHECK();
+      } else {
+        set_error("umma_gemm_tn: Ka > 256 is not supported yet");
+        return DMD_EINVAL;
+      }
+    }
+  }
+  return DMD_OK;
 }
 
 }  // namespace dmd

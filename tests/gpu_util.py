@@ -41,7 +41,8 @@ def gpu_kinds(lam: np.ndarray) -> np.ndarray:
 
 
 def mode_product_error(PhiR_g, beta_g, lam_g, PhiR_o, beta_o, lam_o):
-    """Per-mode relative error of the scale-free fields phi_j b_j after matching."""
+    """Relative Frobenius error of the scale-free fields [phi_j b_j] over all
+    modes (after eigenvalue matching), and the per-mode relative errors."""
     kg, ko = gpu_kinds(lam_g), gpu_kinds(lam_o)
     pg = O.mode_products(PhiR_g, beta_g, kg)
     po = O.mode_products(PhiR_o, beta_o, ko)
@@ -49,4 +50,5 @@ def mode_product_error(PhiR_g, beta_g, lam_g, PhiR_o, beta_o, lam_o):
     ho = lam_o[ko != 2]
     perm, _ = match(hg, ho)
     errs = [rel(pg[:, perm[j]], po[:, j]) for j in range(po.shape[1])]
-    return np.array(errs)
+    frob = rel(pg[:, perm], po)
+    return frob, np.array(errs)

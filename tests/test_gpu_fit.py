@@ -10,8 +10,12 @@ from tests.gpu_util import cols, match, mode_product_error, oracle_model, rel
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "mixed"]
 BAR = {"fp32": 1e-5, "mixed": 1e-4}   # relative Frobenius error bars
+# ||div x_k|| / ||x_k|| of a reconstruction of divergence-free data: the frames
+# carry the GEMM rounding of their precision (about sqrt(depth) * u), and the
+# divergence is a 4-point difference of it; 10x that level is the bar.
+DIV_BAR = {"fp32": 1e-5, "mixed": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -48,8 +52,8 @@ def test_cfg0_fit_and_predict(dmd, cfg0, prec):
     _, lam_err = match(lam_g, ref["lam"])
     assert lam_err < BAR[prec], lam_err
     PhiR_g = cols(model.Phi_R, sc.n)
-    mp = mode_product_error(PhiR_g, model.beta(), lam_g, PhiR_o, beta_o, ref["lam"])
-    assert mp.max() < 10 * BAR[prec], mp
+    mp_frob, mp = mode_product_error(PhiR_g, model.beta(), lam_g, PhiR_o, beta_o, ref["lam"])
+    assert mp_frob < BAR[prec], (mp_frob, mp)
     ks = list(range(0, 501))
     F = dmd.dmd_predict(model, ks, precision=prec)
     Fo = O.predict_real(PhiR_o, O.coefficients(ref["lam"], beta_o, ks))
@@ -68,7 +72,7 @@ def test_known_operator_gpu(dmd, prec):
     sc = synth.config0(noise=0.0)
     model = _fit(dmd, sc, 20, prec)
     _, err = match(model.lam(), sc.lam_true)
-    assert err < 1e-6, err
+    assert err < (1e-6 if prec == "fp32" else 1e-5), err
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -93,7 +97,7 @@ def test_divergence_free_reconstruction(dmd, prec):
     F = dmd.dmd_predict(model, [0, 7, 99, 100, 250, 500], precision=prec)[:, : sc.n].double().cpu()
     d = synth.div2d(F, sc.N)
     ratio = (d.norm(dim=1) / F.norm(dim=1)).max().item()
-    assert ratio < (1e-6 if prec == "fp32" else 1e-5), ratio
+    assert ratio < DIV_BAR[prec], ratio
 
 
 @pytest.mark.parametrize("prec", PRECS)
