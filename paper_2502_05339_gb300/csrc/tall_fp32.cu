@@ -6,9 +6,9 @@
 //    column-major, B is small.
 //  * TN: C[Ka x N] = A^T[Ka x n] * B[n x N] -- power step X^T Q, projection
 //    Q^T S and Gram matrices.  The tall dimension is split across blocks;
-//    each block sums its rows in FP32 over 1024-row stretches and carries the
-//    running total in FP64; the per-block FP64 partials are then added in a
-//    fixed order, so the result does not depend on scheduling.
+//    each block sums 32-row tiles in FP32, adds 32 tiles in FP32 and carries
+//    the running total in FP64; the per-block FP64 partials are then added in
+//    a fixed order, so the result does not depend on scheduling.
 #include "common.cuh"
 
 namespace dmd {
@@ -137,12 +137,13 @@ __global__ void __launch_bounds__(256) k_gemm_tn_f32(int64_t n, int Ka, int N, c
   const int64_t rbeg = (int64_t)split * chunk;
   const int64_t rend = min(n, rbeg + chunk);
 
-  float acc[4][4];
+  // three-level sum: a 32-row tile in FP32, 32 tiles in FP32, then FP64
+  float acc[4][4], mid[4][4];
   double tot[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f, tot[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) mid[i][j] = 0.f, tot[i][j] = 0.0;
 
   int stretch = 0;
   for (int64_t r0 = rbeg; r0 < rend; r0 += TN_BR) {
@@ -157,6 +158,10 @@ __global__ void __launch_bounds__(256) k_gemm_tn_f32(int64_t n, int Ka, int N, c
       Bs[rr][c] = (rok && b0 + c < N) ? B[(int64_t)(b0 + c) * ldb + row] : 0.f;
     }
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 #pragma unroll 8
     for (int rr = 0; rr < TN_BR; ++rr) {
       const float4 a = *reinterpret_cast<const float4*>(&As[rr][tx * 4]);
@@ -167,12 +172,16 @@ __global__ void __launch_bounds__(256) k_gemm_tn_f32(int64_t n, int Ka, int N, c
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (++stretch == 32) {                       // 1024 rows in FP32, then fold into FP64
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mid[i][j] += acc[i][j];
+    if (++stretch == 32) {                       // 1024 rows, then fold into FP64
       stretch = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] += (double)acc[i][j], acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) tot[i][j] += (double)mid[i][j], mid[i][j] = 0.f;
     }
   }
   double* out = part + (int64_t)split * Ka * N;
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn_f32(int64_t n, int Ka, int N, c
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = a0 + tx * 4 + i, b = b0 + ty * 4 + j;
-      if (a < Ka && b < N) out[(int64_t)b * Ka + a] = tot[i][j] + (double)acc[i][j];
+      if (a < Ka && b < N) out[(int64_t)b * Ka + a] = tot[i][j] + (double)mid[i][j];
     }
 }
 
