@@ -36,7 +36,7 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
                         int64_t ldc, void* ws, cudaStream_t st);
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                        double* C, void* ws, cudaStream_t st);
+                        double* C, int nsplit, void* ws, cudaStream_t st);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
@@ -55,7 +55,8 @@ dmd_status eig_layout(int n, const double* wr, const double* wi, const int* head
                       const double* Yre, const double* Yim, double* WR, double* lam_re, double* lam_im,
                       int* order_scratch, int32_t* info, cudaStream_t st);
 dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, double* scratch, cudaStream_t st);
-dmd_status lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info, cudaStream_t st);
+dmd_status lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
+                 int32_t* info, cudaStream_t st);
 dmd_status launch_coefficients(int r, int K, const double* modal, const int32_t* ks, double* C, cudaStream_t st);
 dmd_status launch_rollout(int r, int q, int steps, const double* modal, const float* u, double* Xi,
                           cudaStream_t st);
@@ -76,6 +77,9 @@ dmd_status fit_glue_check_finite(int64_t count, const double* A, int32_t* info, 
 dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStream_t st);
 dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st);
 dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st);
+dmd_status fit_glue_stack(int l, int q, int m, const double* P, const float* Ups, double* Om, cudaStream_t st);
+dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma_or_null, double* inv_sq, int32_t* info,
+                                int tag, cudaStream_t st);
 
 namespace {
 
@@ -102,7 +106,10 @@ struct Tall {
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn(n, Ka, N, A, lda, B, ldb, C, ws, st);
+    // Reductions over the tall dimension decide the accuracy of the fit (the
+    // Gram matrices square the snapshot condition number), so the mixed form
+    // splits their operands three ways; see umma.cu.
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn(n, Ka, N, A, lda, B, ldb, C, 3, ws, st);
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
 };
@@ -118,6 +125,9 @@ struct FitBufs {
       *tauA, *Hq, *wr, *wi, *Yre, *Yim, *invit, *WR, *MR, *LS, *rhs, *hnorm, *invsq;
   float *Y, *Q1;
   int *heads, *nheads, *order;
+  // DMD with control (q > 0): input-space SVD of [Q^T X; Ups] and its products
+  int L, p;
+  double *Omc, *Hc, *tauC, *evC, *YC, *tridC, *VS, *T1c, *T2c, *Tw, *invC, *rhsc, *solc;
   void* gemm_ws;
   size_t gemm_ws_bytes;
 };
@@ -168,6 +178,24 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   b.order = a.take<int>(r);
   b.Y = a.take<float>((size_t)b.ldY * l);
   b.Q1 = a.take<float>((size_t)b.ldY * l);
+  b.L = l + d.q;
+  b.p = std::min(d.r + d.q, std::min(b.L, m));
+  if (d.q > 0) {
+    const int L = b.L, pp = b.p, q = d.q;
+    b.Omc = a.take<double>((size_t)L * m);
+    b.Hc = a.take<double>((size_t)L * L);
+    b.tauC = a.take<double>(L);
+    b.evC = a.take<double>(L);
+    b.YC = a.take<double>((size_t)L * L);
+    b.tridC = a.take<double>((size_t)7 * L * L);
+    b.VS = a.take<double>((size_t)m * pp);
+    b.T1c = a.take<double>((size_t)l * pp);
+    b.T2c = a.take<double>((size_t)pp * r);
+    b.Tw = a.take<double>((size_t)pp * r);
+    b.invC = a.take<double>(L);
+    b.rhsc = a.take<double>((size_t)l * (q + 1));
+    b.solc = a.take<double>((size_t)r * (q + 1));
+  }
   size_t g = 0;
   g = std::max(g, tall.nn_bytes(n, m, l));
   g = std::max(g, tall.nn_bytes(n, l, l));
@@ -229,6 +257,80 @@ dmd_status orth_small(FitBufs& b, int rows, int32_t* info, int tag, cudaStream_t
   return DMD_OK;
 }
 
+// Symmetric eigendecomposition H = Y diag(ev) Y^T (ev descending) of an n x n
+// FP64 matrix: Householder tridiagonalisation, bisection, inverse iteration,
+// back-transformation.  H is overwritten.
+dmd_status sym_eig(int n, double* H, double* tau, double* ev, double* Y, double* scratch, cudaStream_t st) {
+  DMD_TRY(hessenberg(n, H, n, tau, st));
+  DMD_TRY(tridiag_eig(n, H, n, ev, Y, scratch, st));
+  DMD_TRY(apply_q(n, H, n, tau, Y, n, n, st));
+  return DMD_OK;
+}
+
+// Eigendecomposition of the reduced operator A~ (r x r) into the modal layout:
+// lam_re/lam_im (canonical order) and the real-form eigenvectors W_R.
+dmd_status reduced_eig(FitBufs& b, double* modal, int32_t* info, cudaStream_t st) {
+  const int r = b.r;
+  DMD_TRY(fit_glue_copy((int64_t)r * r, b.At, b.Ah, st));
+  DMD_TRY(fit_glue_maxabs((int64_t)r * r, b.At, b.hnorm, st));
+  DMD_TRY(hessenberg(r, b.Ah, r, b.tauA, st));
+  DMD_TRY(hqr(r, b.Ah, r, b.wr, b.wi, b.Hq, info, st));
+  DMD_TRY(fit_glue_fill_int(r, b.heads, -1, st));
+  DMD_TRY(collect_heads(r, b.wi, b.heads, b.nheads, info, st));
+  DMD_CUDA_TRY(cudaMemsetAsync(b.Yre, 0, (size_t)r * r * sizeof(double), st));
+  DMD_CUDA_TRY(cudaMemsetAsync(b.Yim, 0, (size_t)r * r * sizeof(double), st));
+  DMD_TRY(hess_eigvecs(r, b.Ah, r, b.wr, b.wi, b.heads, r, b.Yre, b.Yim, b.invit, b.hnorm, st));
+  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yre, r, r, st));
+  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yim, r, r, st));
+  DMD_TRY(normalize_complex(r, b.Yre, b.Yim, r, st));
+  DMD_TRY(eig_layout(r, b.wr, b.wi, b.heads, b.nheads, b.Yre, b.Yim, b.WR, modal, modal + r, b.order, info, st));
+  return DMD_OK;
+}
+
+// DMD with control (Eq. external_forces, with the unknown-B least-squares fit
+// of [A B] from Omega = [X; Ups]) in the basis Q of the randomized range
+// finder: B0 = Q^T X, B1 = Q^T X'.  Input space: SVD of [B0; Ups] truncated to
+// p = r + q; output space U_hat: leading r left singular vectors of B1.
+// A~ = U_hat^T B1 Vt St^-1 Ut1^T U_hat, modes Phi = X' Vt St^-1 Ut1^T U_hat W,
+// amplitudes and real-form forcing by least squares:
+// (B1 M) [beta | G_R] ~ [Q^T x_0 | B1 Vt St^-1 Ut2^T].
+dmd_status fit_control(const dmd_fit_desc& d, const float* S, const float* Ups, float* PhiR, double* modal,
+                       int32_t* info, const Tall& tall, FitBufs& b, cudaStream_t st) {
+  const int m = b.m, l = b.l, r = b.r, q = b.q, L = b.L, pp = b.p;
+  const double* B0 = b.P;
+  const double* B1 = b.P + l;
+  (void)B0;
+  DMD_TRY(fit_glue_stack(l, q, m, b.P, Ups, b.Omc, st));
+  DMD_TRY(dgemm(L, L, m, 1.0, b.Omc, L, false, b.Omc, L, true, 0.0, b.Hc, L, st));
+  DMD_TRY(sym_eig(L, b.Hc, b.tauC, b.evC, b.YC, b.tridC, st));
+  DMD_TRY(fit_glue_sigma_range(L, pp, b.evC, nullptr, b.invC, info, 7100, st));
+  // Vt St^-1 = Omega_c^T Ut St^-2  (m x p)
+  DMD_TRY(dgemm(m, pp, L, 1.0, b.Omc, L, true, b.YC, L, false, 0.0, b.VS, m, st));
+  DMD_TRY(fit_glue_scale_cols(m, pp, b.VS, m, b.invC, st));
+  // output space from B1 = Q^T X'
+  DMD_TRY(dgemm(l, l, m, 1.0, B1, l, false, B1, l, true, 0.0, b.Hb, l, st));
+  DMD_TRY(sym_eig(l, b.Hb, b.tauB, b.evB, b.YB, b.trid, st));
+  DMD_TRY(fit_glue_sigma(l, r, b.evB, modal + 3 * r, b.invsq, info, st));
+  // T1 = B1 Vt St^-1 (l x p); T2 = Ut1^T U_hat (p x r); Tmp = T1 T2; A~ = U_hat^T Tmp
+  DMD_TRY(dgemm(l, pp, m, 1.0, B1, l, false, b.VS, m, false, 0.0, b.T1c, l, st));
+  DMD_TRY(dgemm(pp, r, l, 1.0, b.YC, L, true, b.YB, l, false, 0.0, b.T2c, pp, st));
+  DMD_TRY(dgemm(l, r, pp, 1.0, b.T1c, l, false, b.T2c, pp, false, 0.0, b.Tmp, l, st));
+  DMD_TRY(dgemm(r, r, l, 1.0, b.YB, l, true, b.Tmp, l, false, 0.0, b.At, r, st));
+  DMD_TRY(reduced_eig(b, modal, info, st));
+  // modes: M_R = Vt St^-1 (T2 W_R)
+  DMD_TRY(dgemm(pp, r, r, 1.0, b.T2c, pp, false, b.WR, r, false, 0.0, b.Tw, pp, st));
+  DMD_TRY(dgemm(m, r, pp, 1.0, b.VS, m, false, b.Tw, pp, false, 0.0, b.MR, m, st));
+  DMD_TRY(tall.nn(b.n, m, r, S + d.ldS, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st));
+  // least squares for beta and G_R in the Q basis
+  DMD_TRY(dgemm(l, r, r, 1.0, b.Tmp, l, false, b.WR, r, false, 0.0, b.LS, l, st));
+  DMD_TRY(fit_glue_copy(l, b.P, b.rhsc, st));
+  DMD_TRY(dgemm(l, q, pp, 1.0, b.T1c, l, false, b.YC + l, L, true, 0.0, b.rhsc + l, l, st));
+  DMD_TRY(lstsq(l, r, b.LS, l, q + 1, b.rhsc, l, b.solc, r, info, st));
+  DMD_TRY(fit_glue_copy(r, b.solc, modal + 2 * r, st));
+  DMD_TRY(fit_glue_copy((int64_t)r * q, b.solc + r, modal + 4 * r, st));
+  return DMD_OK;
+}
+
 dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, const double* Omega, float* PhiR,
                     double* modal, int32_t* info, FitBufs& b, cudaStream_t st) {
   const Tall tall{d.precision};
@@ -261,13 +363,12 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
   DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));
   DMD_TRY(fit_glue_check_finite((int64_t)l * (m + 1), b.P, info, 90, st));
+  if (q > 0) return fit_control(d, S, Ups, PhiR, modal, info, tall, b, st);
   const double* B = b.P;
   const double* Bp = b.P + l;
   // 5. SVD of B via B B^T = U_B Sigma^2 U_B^T (tridiagonalisation, bisection, inverse iteration)
   DMD_TRY(dgemm(l, l, m, 1.0, B, l, false, B, l, true, 0.0, b.Hb, l, st));
-  DMD_TRY(hessenberg(l, b.Hb, l, b.tauB, st));
-  DMD_TRY(tridiag_eig(l, b.Hb, l, b.evB, b.YB, b.trid, st));
-  DMD_TRY(apply_q(l, b.Hb, l, b.tauB, b.YB, l, l, st));
+  DMD_TRY(sym_eig(l, b.Hb, b.tauB, b.evB, b.YB, b.trid, st));
   double* sigma = modal + 3 * r;
   DMD_TRY(fit_glue_sigma(l, r, b.evB, sigma, b.invsq, info, st));
   // 6. V Sigma^{-1} = B^T U_r Sigma^{-2}; reduced operator A~ = U_r^T (Q^T X') V Sigma^{-1} (Sec. 3.1)
@@ -276,28 +377,14 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   DMD_TRY(dgemm(l, r, m, 1.0, Bp, l, false, b.Vs, m, false, 0.0, b.Tmp, l, st));
   DMD_TRY(dgemm(r, r, l, 1.0, b.YB, l, true, b.Tmp, l, false, 0.0, b.At, r, st));
   // 7. eigendecomposition A~ W = W Lambda
-  DMD_TRY(fit_glue_copy((int64_t)r * r, b.At, b.Ah, st));
-  DMD_TRY(fit_glue_maxabs((int64_t)r * r, b.At, b.hnorm, st));
-  DMD_TRY(hessenberg(r, b.Ah, r, b.tauA, st));
-  DMD_TRY(hqr(r, b.Ah, r, b.wr, b.wi, b.Hq, info, st));
-  DMD_TRY(fit_glue_fill_int(r, b.heads, -1, st));
-  DMD_TRY(collect_heads(r, b.wi, b.heads, b.nheads, info, st));
-  DMD_CUDA_TRY(cudaMemsetAsync(b.Yre, 0, (size_t)r * r * sizeof(double), st));
-  DMD_CUDA_TRY(cudaMemsetAsync(b.Yim, 0, (size_t)r * r * sizeof(double), st));
-  DMD_TRY(hess_eigvecs(r, b.Ah, r, b.wr, b.wi, b.heads, r, b.Yre, b.Yim, b.invit, b.hnorm, st));
-  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yre, r, r, st));
-  DMD_TRY(apply_q(r, b.Ah, r, b.tauA, b.Yim, r, r, st));
-  DMD_TRY(normalize_complex(r, b.Yre, b.Yim, r, st));
-  DMD_TRY(eig_layout(r, b.wr, b.wi, b.heads, b.nheads, b.Yre, b.Yim, b.WR, modal, modal + r, b.order, info, st));
+  DMD_TRY(reduced_eig(b, modal, info, st));
   // 8. modes Phi_R = X' M_R with M_R = V Sigma^{-1} W_R
   DMD_TRY(dgemm(m, r, r, 1.0, b.Vs, m, false, b.WR, r, false, 0.0, b.MR, m, st));
   DMD_TRY(tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st));
   // 9. amplitudes: min || (Q^T X') M_R beta - Q^T x_0 ||  (Eq. projection in the Q basis)
   DMD_TRY(dgemm(l, r, r, 1.0, b.Tmp, l, false, b.WR, r, false, 0.0, b.LS, l, st));
   DMD_TRY(fit_glue_copy(l, b.P, b.rhs, st));
-  DMD_TRY(lstsq(l, r, b.LS, l, b.rhs, modal + 2 * r, info, st));
-  (void)Ups;
-  (void)q;
+  DMD_TRY(lstsq(l, r, b.LS, l, 1, b.rhs, l, modal + 2 * r, r, info, st));
   return DMD_OK;
 }
 
@@ -404,7 +491,6 @@ dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const float* Ups, c
   DMD_TRY(validate_fit(desc));
   DMD_REQUIRE(S && Phi_R && modal && info, "dmd_fit: NULL pointer argument");
   DMD_REQUIRE(desc->q == 0 || Ups != nullptr, "dmd_fit: q > 0 needs Ups");
-  DMD_REQUIRE(desc->q == 0, "dmd_fit: control inputs are handled by the DMDc path (q > 0 not enabled in this build)");
   size_t need = 0;
   DMD_TRY(dmd_fit_workspace_bytes(desc, &need));
   return with_arena(workspace, ws_bytes, [&](Arena& a) {

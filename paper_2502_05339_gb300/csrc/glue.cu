@@ -49,6 +49,34 @@ __global__ void k_copy(int64_t count, const double* src, double* dst) {
   if (t < count) dst[t] = src[t];
 }
 
+// Om[:, j] = [P[0:l, j]; Ups[:, j]] (column-major, ld l + q)
+__global__ void k_stack(int l, int q, int m, const double* P, const float* Ups, double* Om) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int L = l + q;
+  if (t >= (int64_t)L * m) return;
+  const int i = (int)(t % L), j = (int)(t / L);
+  Om[t] = (i < l) ? P[(int64_t)j * l + i] : (double)Ups[(int64_t)j * q + (i - l)];
+}
+
+// inv_sq[i] = 1 / ev[i] for the p leading eigenvalues (descending) of a Gram
+// matrix; rank guard sqrt(ev[p-1]) > 1e-6 sqrt(ev[0]); optional sigma output.
+__global__ void k_sigma_range(int L, int p, const double* ev, double* sigma, double* inv_sq, int32_t* info, int tag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double s0 = sqrt(fmax(ev[0], 0.0));
+  for (int i = 0; i < p; ++i) {
+    const double e = fmax(ev[i], 0.0);
+    const double s = sqrt(e);
+    if (sigma) sigma[i] = s;
+    if (!(s > 1e-6 * s0) || !isfinite(s)) {
+      raise_status(info, isfinite(s) ? DMD_ERANK : DMD_ENONFINITE, tag + i);
+      inv_sq[i] = 0.0;
+    } else {
+      inv_sq[i] = 1.0 / e;
+    }
+  }
+  (void)L;
+}
+
 __global__ void k_fill_int(int64_t count, int* dst, int v) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < count) dst[t] = v;
@@ -87,6 +115,20 @@ dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStre
 dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st) {
   if (count == 0) return DMD_OK;
   k_copy<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, src, dst);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_stack(int l, int q, int m, const double* P, const float* Ups, double* Om, cudaStream_t st) {
+  const int64_t tot = (int64_t)(l + q) * m;
+  k_stack<<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(l, q, m, P, Ups, Om);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma, double* inv_sq, int32_t* info, int tag,
+                                cudaStream_t st) {
+  k_sigma_range<<<1, 32, 0, st>>>(L, p, ev, sigma, inv_sq, info, tag);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

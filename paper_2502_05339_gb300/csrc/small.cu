@@ -784,15 +784,19 @@ __global__ void k_cluster_mgs(int n, const double* __restrict__ ev, double* __re
 
 // ------------------------------------------------------ least squares
 
-// min || A x - b || for A (mr x nc, ld, mr >= nc) by Householder QR; A and b
-// are overwritten.  One CTA; shared memory: mr + nc + 32 doubles.
-__global__ void k_lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info) {
+// min || A X - B ||_F for A (mr x nc, ld, mr >= nc) and nrhs right-hand sides
+// B (mr x nrhs, ld ldb) by Householder QR; A and B are overwritten; X is
+// nc x nrhs (ld ldx).  One CTA; shared memory: mr + nc + nrhs + 32 doubles.
+__global__ void k_lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
+                        int32_t* info) {
   extern __shared__ double sm[];
   double* v = sm;
-  double* w = sm + mr;
-  double* red = sm + mr + nc;
+  double* w = sm + mr;              // nc - 1 trailing columns + nrhs right-hand sides
+  double* red = sm + mr + nc + nrhs;
   const int tid = threadIdx.x, bd = blockDim.x;
   double rmax = 0.0;
+  const int ncol = nc + nrhs;       // columns of [A | B]
+  auto colp = [&](int j) -> double* { return j < nc ? A + (int64_t)j * ld : B + (int64_t)(j - nc) * ldb; };
   for (int k = 0; k < nc; ++k) {
     double* col = A + (int64_t)k * ld;
     double loc = 0.0;
@@ -812,20 +816,18 @@ __global__ void k_lstsq(int mr, int nc, double* A, int ld, double* b, double* x,
     __syncthreads();
     rmax = fmax(rmax, fabs(beta));
     if (tau != 0.0) {
-      // w_j = v^T A[k:, j] for the trailing columns and the right-hand side (j = nc)
-      for (int j = k + 1 + tid; j <= nc; j += bd) {
-        const double* cj = (j < nc) ? A + (int64_t)j * ld : b;
+      for (int j = k + 1 + tid; j < ncol; j += bd) {
+        const double* cj = colp(j);
         double s = 0.0;
         for (int i = k; i < mr; ++i) s = fma(v[i], cj[i], s);
         w[j - 1] = s;   // j >= k + 1
       }
       __syncthreads();
-      const int wcols = nc - k;   // trailing columns k+1..nc-1 plus b
+      const int wcols = ncol - k - 1;
       const int hgt = mr - k;
       for (int q = tid; q < wcols * hgt; q += bd) {
         const int i = k + q % hgt, j = k + 1 + q / hgt;
-        double* cj = (j < nc) ? A + (int64_t)j * ld : b;
-        cj[i] -= tau * v[i] * w[j - 1];
+        colp(j)[i] -= tau * v[i] * w[j - 1];
       }
       __syncthreads();
     }
@@ -833,7 +835,9 @@ __global__ void k_lstsq(int mr, int nc, double* A, int ld, double* b, double* x,
     for (int i = k + 1 + tid; i < mr; i += bd) col[i] = 0.0;
     __syncthreads();
   }
-  if (tid == 0) {
+  for (int c = tid; c < nrhs; c += bd) {
+    const double* b = B + (int64_t)c * ldb;
+    double* x = X + (int64_t)c * ldx;
     for (int i = nc - 1; i >= 0; --i) {
       double s = b[i];
       for (int j = i + 1; j < nc; ++j) s -= A[i + (int64_t)j * ld] * x[j];
@@ -945,9 +949,10 @@ dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, d
   return DMD_OK;
 }
 
-dmd_status lstsq(int mr, int nc, double* A, int ld, double* b, double* x, int32_t* info, cudaStream_t st) {
-  const size_t smem = ((size_t)mr + nc + 32) * sizeof(double);
-  k_lstsq<<<1, 256, smem, st>>>(mr, nc, A, ld, b, x, info);
+dmd_status lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
+                 int32_t* info, cudaStream_t st) {
+  const size_t smem = ((size_t)mr + nc + nrhs + 32) * sizeof(double);
+  k_lstsq<<<1, 256, smem, st>>>(mr, nc, A, ld, nrhs, B, ldb, X, ldx, info);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

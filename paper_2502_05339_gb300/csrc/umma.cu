@@ -18,7 +18,8 @@
 //                    column chunks -- the reconstruction Phi_R C of
 //                    Eq. large_time_step with K frames.
 //   k_umma_tn      : C = A^T B reduced over the tall dimension -- X^T Q, Q^T S
-//                    and Gram matrices; per-CTA FP64 partials.
+//                    and Gram matrices; per-CTA FP64 partials; 2- or 3-way
+//                    bf16 split (3 or 6 products).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -181,6 +182,36 @@ __device__ __forceinline__ void split_store_row(const float* x, uint8_t* hi, uin
   *reinterpret_cast<uint4*>(hi + kslice_off(row, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
   *reinterpret_cast<uint4*>(lo + kslice_off(row, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
   *reinterpret_cast<uint4*>(lo + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
+}
+
+// 3-way split x = hi + mid + lo (bf16 each; exact for FP32 x up to the last
+// bit of lo) stored as three K-slice planes spaced `plane` bytes apart.
+__device__ __forceinline__ void split3_store_row(const float* x, uint8_t* base, uint32_t plane, int row) {
+  uint32_t h[8], m[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    __nv_bfloat16 hv[2], mv[2], lv[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float v = x[2 * i + t];
+      hv[t] = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(hv[t]);
+      mv[t] = __float2bfloat16_rn(r1);
+      lv[t] = __float2bfloat16_rn(r1 - __bfloat162float(mv[t]));
+    }
+    h[i] = pack2(hv[0], hv[1]);
+    m[i] = pack2(mv[0], mv[1]);
+    l[i] = pack2(lv[0], lv[1]);
+  }
+  uint8_t* p0 = base;
+  uint8_t* p1 = base + plane;
+  uint8_t* p2 = base + 2 * plane;
+  *reinterpret_cast<uint4*>(p0 + kslice_off(row, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(p0 + kslice_off(row, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
+  *reinterpret_cast<uint4*>(p1 + kslice_off(row, 0)) = make_uint4(m[0], m[1], m[2], m[3]);
+  *reinterpret_cast<uint4*>(p1 + kslice_off(row, 1)) = make_uint4(m[4], m[5], m[6], m[7]);
+  *reinterpret_cast<uint4*>(p2 + kslice_off(row, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<uint4*>(p2 + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
 }
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
@@ -604,17 +635,21 @@ constexpr int TN_FLUSH = 256;    // k-steps (of 16 rows) between FP64 flushes
 
 // part[blockIdx.x][b * Ka + a] = sum over this CTA's rows of A[:, a] * B[:, b].
 // A slice: TMA box {16 rows, Mt*128 cols}; B slice: box {16 rows, Np cols}.
+// nsplit = 2: bf16 hi + lo, products hh + hl + lh (BF16x3).  nsplit = 3:
+// hi + mid + lo, products hh + hm + mh + hl + lh + mm (every term of order
+// <= 2^-16 relative), which resolves Gram directions down to ~1e-8 of the
+// largest -- the reductions whose accuracy decides the fit use it.
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_umma_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
-              int N, int Mt, int Np, int64_t chunk, double* __restrict__ part, int32_t* err) {
+              int N, int Mt, int Np, int nsplit, int64_t chunk, double* __restrict__ part, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t a_bytes = 16u * 4u * (uint32_t)Mt * 128u;   // FP32 slice of A
   const uint32_t b_bytes = 16u * 4u * (uint32_t)Np;          // FP32 slice of B
   const uint32_t st_bytes = (a_bytes + b_bytes + 1023u) & ~1023u;
-  const uint32_t ca_bytes = (uint32_t)Mt * 128u * 32u;       // one bf16 K-slice of A (hi or lo)
+  const uint32_t ca_bytes = (uint32_t)Mt * 128u * 32u;       // one bf16 K-slice plane of A
   const uint32_t cb_bytes = (uint32_t)Np * 32u;
-  const uint32_t cv_bytes = (2u * (ca_bytes + cb_bytes) + 1023u) & ~1023u;
+  const uint32_t cv_bytes = ((uint32_t)nsplit * (ca_bytes + cb_bytes) + 1023u) & ~1023u;
   uint8_t* st = sm;
   uint8_t* cv = st + TN_S * st_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(cv + 2 * cv_bytes);
@@ -689,15 +724,21 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
           }
           tc_after();
           const uint32_t base = su32(cv + cs * cv_bytes);
-          const uint32_t ahi = base, alo = base + ca_bytes;
-          const uint32_t bhi = base + 2 * ca_bytes, blo = bhi + cb_bytes;
-          const uint64_t bhd = sdesc(bhi, kLBO, kSBO), bld = sdesc(blo, kLBO, kSBO);
+          const uint32_t bbase = base + (uint32_t)nsplit * ca_bytes;   // B planes follow the A planes
+          uint64_t bd[3];
+          for (int t = 0; t < nsplit; ++t) bd[t] = sdesc(bbase + t * cb_bytes, kLBO, kSBO);
           for (int mt = 0; mt < Mt; ++mt) {
             const uint32_t d = tmem + (uint32_t)(mt * Np);
-            const uint64_t ahd = sdesc(ahi + mt * 4096u, kLBO, kSBO), ald = sdesc(alo + mt * 4096u, kLBO, kSBO);
-            umma_bf16(d, ahd, bhd, idesc, kk > 0 ? 1u : 0u);
-            umma_bf16(d, ahd, bld, idesc, 1u);
-            umma_bf16(d, ald, bhd, idesc, 1u);
+            uint64_t ad[3];
+            for (int t = 0; t < nsplit; ++t) ad[t] = sdesc(base + t * ca_bytes + mt * 4096u, kLBO, kSBO);
+            umma_bf16(d, ad[0], bd[0], idesc, kk > 0 ? 1u : 0u);
+            umma_bf16(d, ad[0], bd[1], idesc, 1u);
+            umma_bf16(d, ad[1], bd[0], idesc, 1u);
+            if (nsplit == 3) {
+              umma_bf16(d, ad[0], bd[2], idesc, 1u);
+              umma_bf16(d, ad[2], bd[0], idesc, 1u);
+              umma_bf16(d, ad[1], bd[1], idesc, 1u);
+            }
           }
           umma_commit(&cempty[cs]);
         }
@@ -725,8 +766,10 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
           const float4 v = p[c];
           x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
         }
-        split_store_row(x, base, base + ca_bytes, col);
+        if (nsplit == 3) split3_store_row(x, base, ca_bytes, col);
+        else split_store_row(x, base, base + ca_bytes, col);
       }
+      uint8_t* bb = base + (uint32_t)nsplit * ca_bytes;
       for (int col = t; col < Np; col += 128) {
         const float4* p = reinterpret_cast<const float4*>(sb + col * 16);
 #pragma unroll
@@ -734,7 +777,8 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
           const float4 v = p[c];
           x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
         }
-        split_store_row(x, base + 2 * ca_bytes, base + 2 * ca_bytes + cb_bytes, col);
+        if (nsplit == 3) split3_store_row(x, bb, cb_bytes, col);
+        else split_store_row(x, bb, bb + cb_bytes, col);
       }
       fence_async_smem();
       mbar_arrive(&cfull[cs]);
@@ -784,12 +828,16 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8003);
 }
 
-__global__ void k_reduce_parts(int64_t count, int parts, const double* __restrict__ part, double* __restrict__ C) {
+// C[a0 + a, b0 + b] (ld ldc) = sum over the CTAs' partials (ka x nb each), fixed order.
+__global__ void k_reduce_parts(int ka, int nb, int parts, const double* __restrict__ part, double* __restrict__ C,
+                               int64_t ldc) {
+  const int64_t count = (int64_t)ka * nb;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   double s = 0.0;
   for (int p = 0; p < parts; ++p) s += part[(int64_t)p * count + i];
-  C[i] = s;
+  const int a = (int)(i % ka), b = (int)(i / ka);
+  C[(int64_t)b * ldc + a] = s;
 }
 
 // ------------------------------------------------------------ host side
@@ -858,9 +906,9 @@ size_t ares_smem(int ksteps) {
   const size_t chunk = ((size_t)2 * ksteps * AR_BN * 32 + 1023) & ~(size_t)1023;
   return 1024 + (((size_t)2 * ksteps * 128 * 32 + 1023) & ~(size_t)1023) + AR_SA * 8192 + AR_NB * chunk + 256;
 }
-size_t tn_smem(int Mt, int Np) {
+size_t tn_smem(int Mt, int Np, int nsplit) {
   const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
-  const size_t cv = ((size_t)2 * (Mt * 128 * 32 + Np * 32) + 1023) & ~(size_t)1023;
+  const size_t cv = ((size_t)nsplit * (Mt * 128 * 32 + Np * 32) + 1023) & ~(size_t)1023;
   return 1024 + TN_S * st + 2 * cv + 256;
 }
 
@@ -935,7 +983,7 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 // C (Ka x N, ld Ka) = A^T B; sub-problems of at most 256 x 256 so that the
 // accumulators (Mt * Np columns) fit in 512 TMEM columns.
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
-                        void* ws, cudaStream_t st) {
+                        int nsplit, void* ws, cudaStream_t st) {
   if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
   double* part = reinterpret_cast<double*>(ws);
   const int grid = tn_grid(n);
@@ -949,19 +997,15 @@ dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, c
       CUtensorMap mA, mB;
       DMD_TRY(make_map(&mA, A + (int64_t)a0 * lda, n, ka, lda, 16, Mt * 128));
       DMD_TRY(make_map(&mB, B + (int64_t)b0 * ldb, n, nb, ldb, 16, Np));
-      const size_t smem = tn_smem(Mt, Np);
+      const size_t smem = tn_smem(Mt, Np, nsplit);
       DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, chunk, part, nullptr);
+      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, chunk, part, nullptr);
       DMD_LAUNCH_CHECK();
       // reduce into the (a0, b0) block of C
       const int64_t count = (int64_t)ka * nb;
-      if (a0 == 0 && ka == Ka) {
-        k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, grid, part, C + (int64_t)b0 * Ka);
-        DMD_LAUNCH_CHECK();
-      } else {
-        set_error("umma_gemm_tn: Ka > 256 is not supported yet");
-        return DMD_EINVAL;
-      }
+      k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(ka, nb, grid, part,
+                                                                      C + (int64_t)b0 * Ka + a0, Ka);
+      DMD_LAUNCH_CHECK();
     }
   }
   return DMD_OK;

@@ -311,7 +311,7 @@ def piecewise_controls(g: np.random.Generator, q: int, steps: int, hold: int = 2
 
 
 def controlled_scene(N: int, dim: int, npairs: int, m: int, q: int, seed: int,
-                     device="cpu", sigma_lo: float = -0.02) -> Scene:
+                     device="cpu", sigma_lo: float = -0.02, stratified: bool = True) -> Scene:
     """DMDc data (config 2 recipe): latent z_{k+1} = L z_k + P F u_k, x_k = Phi z_k.
 
     Phi are `npairs` conjugate-pair curl modes in real 2x2 form, F are q blob
@@ -322,7 +322,7 @@ def controlled_scene(N: int, dim: int, npairs: int, m: int, q: int, seed: int,
     n = dim * N ** dim
     ld = round_up(n, LD_ALIGN)
     modes = make_modes(N, dim, npairs, seed + 1, device=device)     # (2P, n)
-    sigma, omega, a = draw_spectrum(g, npairs, sigma_lo, math.pi / 4)
+    sigma, omega, a = draw_spectrum(g, npairs, sigma_lo, math.pi / 4, stratified)
     F = blob_forces(N, dim, q, g, device=device)                     # (q, n)
     gram = modes @ modes.T
     PF = torch.linalg.solve(gram, modes @ F.T)                       # (2P, q)

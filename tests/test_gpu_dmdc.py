@@ -1,0 +1,108 @@
+"""DMD with control (Eq. external_forces): GPU fit, controlled rollout and its
+adjoint against the FP64 oracle on seeded blob-forced snapshots."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dmd_oracle as O
+from paper_2502_05339_gb300 import synth
+from tests.gpu_util import cols, match, rel
+
+pytestmark = pytest.mark.gpu
+BAR = {"fp32": 1e-5, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def dmd():
+    from paper_2502_05339_gb300 import build_lib
+    build_lib.build()
+    from paper_2502_05339_gb300 import dmd as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def scene():
+    sc = synth.controlled_scene(24, 2, 5, 80, 3, 2024)
+    ref = O.dmdc(sc.X().numpy(), sc.extra["U"], 10)
+    return sc, ref
+
+
+def _fit(dmd, sc, prec):
+    Ups = torch.as_tensor(sc.extra["U"].T.astype(np.float32)).contiguous().cuda()   # (m, q)
+    model = dmd.dmd_fit(sc.S.cuda(), sc.n, 10, oversample=6, power_iters=1, precision=prec, seed=3, Ups=Ups)
+    torch.cuda.synchronize()
+    model.check()
+    return model
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_dmdc_fit_matches_oracle(dmd, scene, prec):
+    sc, ref = scene
+    model = _fit(dmd, sc, prec)
+    _, err = match(model.lam(), ref["lam"])
+    assert err < BAR[prec], err
+    # a fresh control sequence: the rolled-out frames of both models agree
+    g = np.random.default_rng(5)
+    U2 = synth.piecewise_controls(g, 3, 60)
+    PhiR_o, beta_o, kinds_o = O.to_real_form(ref["Phi"], ref["lam"], ref["b"])
+    L = O.real_block_operator(ref["lam"], kinds_o)
+    GR = O.real_form_control(ref["G"], kinds_o)
+    Xi = O.rollout_real(L, beta_o, GR, U2, 60)
+    Fo = PhiR_o @ Xi
+    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()   # (steps, q)
+    F = cols(dmd.dmd_predict(model, list(range(61)), u=u, precision=prec), sc.n)
+    assert rel(F, Fo) < BAR[prec], rel(F, Fo)
+
+
+def test_dmdc_reproduces_generator(dmd, scene):
+    """Noise-free latent generator: the fitted model's response to a new input
+    sequence matches the generator's own response."""
+    sc, _ = scene
+    model = _fit(dmd, sc, "fp32")
+    g = np.random.default_rng(9)
+    U2 = synth.piecewise_controls(g, 3, 50)
+    z = sc.extra["z"][:, 0].copy()
+    modes = sc.modes_true.numpy()
+    truth = [modes.T @ z]
+    for k in range(50):
+        z = sc.extra["L"] @ z + sc.extra["PF"] @ U2[:, k]
+        truth.append(modes.T @ z)
+    truth = np.stack(truth, axis=1)
+    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()
+    F = cols(dmd.dmd_predict(model, list(range(51)), u=u), sc.n)
+    assert rel(F, truth) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_dmdc_adjoint_matches_oracle(dmd, scene, prec):
+    """Gradient of ||x_T - x_tgt||^2 w.r.t. u_0..u_{T-1} and beta: the device
+    reverse recursion vs the oracle's on the same (device-fitted) model."""
+    sc, _ = scene
+    model = _fit(dmd, sc, prec)
+    T = 40
+    g = np.random.default_rng(4)
+    U2 = synth.piecewise_controls(g, 3, T)
+    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()
+    x_T = dmd.dmd_predict(model, [T], u=u, precision=prec)
+    tgt = torch.zeros_like(x_T)
+    tgt[0, : sc.n] = torch.as_tensor(g.standard_normal(sc.n), dtype=torch.float32)
+    dOut = (2 * (x_T - tgt)).contiguous()
+    dmodal, du = dmd.dmd_predict_backward(model, [T], dOut, u=u, precision=prec)
+    # oracle adjoint on the device model's parameters
+    r = model.r
+    lam = model.lam()
+    beta = model.beta()
+    kinds = O.pair_kinds(lam)
+    GR = model.G()
+    PhiR = cols(model.Phi_R, sc.n)
+    L = O.real_block_operator(lam, kinds)
+    Xi = O.rollout_real(L, beta, GR, U2.astype(np.float64), T)
+    dXi = np.zeros_like(Xi)
+    dXi[:, T] = PhiR.T @ cols(dOut, sc.n)[:, 0]
+    dlr, dli, db, du_o = O.rollout_adjoint(L, GR, Xi, dXi, kinds)
+    tol = 1e-5 if prec == "fp32" else 1e-4
+    assert rel(du.cpu().numpy().T, du_o) < tol
+    dm = dmodal.cpu().numpy()
+    assert rel(dm[2 * r:3 * r], db) < tol
+    assert rel(dm[:r], dlr) < tol

@@ -183,3 +183,22 @@ def test_autograd_function(dmd):
     heads = kinds != 2
     assert rel(gm[:r][heads], dlr[heads]) < 1e-5
     assert np.all(gm[:r][kinds == 2] == 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gram_resolves_weak_directions(dmd, prec):
+    """The Gram of an ill-conditioned tall matrix (singular values 1 .. 1e-4,
+    Gram eigenvalues down to 1e-8) keeps every eigen-direction to 10%: the
+    rank-revealing CholeskyQR of the fit relies on it."""
+    g = np.random.default_rng(0)
+    n, l = 8192 * 8, 30
+    U, _ = np.linalg.qr(g.standard_normal((n, l)))
+    V, _ = np.linalg.qr(g.standard_normal((l, l)))
+    Y = ((U * np.logspace(0, -4, l)) @ V.T).astype(np.float32)
+    Yt = torch.as_tensor(Y.T).contiguous().cuda()
+    Yd = Y.astype(np.float64)
+    Gx = Yd.T @ Yd
+    w, E = np.linalg.eigh(Gx)
+    G = dmd.dmd_gemm_tn(Yt, Yt, n, precision=prec).cpu().numpy().T
+    err = np.abs(np.einsum("ij,ik,kj->j", E, G - Gx, E)) / w
+    assert err.max() < 0.1, err[:5]
