@@ -42,6 +42,7 @@ dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bo
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st);
 dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st);
+dmd_status sytrd(int n, double* A, int ld, double* tau, cudaStream_t st);
 dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y, int ldy, int nvec,
                    cudaStream_t st);
 dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
@@ -261,7 +262,7 @@ dmd_status orth_small(FitBufs& b, int rows, int32_t* info, int tag, cudaStream_t
 // FP64 matrix: Householder tridiagonalisation, bisection, inverse iteration,
 // back-transformation.  H is overwritten.
 dmd_status sym_eig(int n, double* H, double* tau, double* ev, double* Y, double* scratch, cudaStream_t st) {
-  DMD_TRY(hessenberg(n, H, n, tau, st));
+  DMD_TRY(sytrd(n, H, n, tau, st));
   DMD_TRY(tridiag_eig(n, H, n, ev, Y, scratch, st));
   DMD_TRY(apply_q(n, H, n, tau, Y, n, n, st));
   return DMD_OK;

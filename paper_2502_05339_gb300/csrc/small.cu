@@ -123,29 +123,31 @@ __global__ void k_cholesky_upper(int n, double* G, int ld, double tau, int32_t* 
   }
 }
 
-// T = R^{-1} for upper triangular R; one thread per column.  A zero diagonal
+// T = R^{-1} for upper triangular R by back substitution, one warp per
+// column (the dot products are split across the lanes).  A zero diagonal
 // entry marks a dropped direction: its row and column of T are zero.
-__global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T,
-                                int ldt) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T, int ldt) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= n) return;
   double* t = T + (int64_t)j * ldt;
-  for (int i = j + 1; i < n; ++i) t[i] = 0.0;
+  for (int i = j + 1 + lane; i < n; i += 32) t[i] = 0.0;
   const double rjj = R[j + (int64_t)j * ldr];
   if (rjj == 0.0) {
-    for (int i = 0; i <= j; ++i) t[i] = 0.0;
+    for (int i = lane; i <= j; i += 32) t[i] = 0.0;
     return;
   }
-  t[j] = 1.0 / rjj;
+  if (lane == 0) t[j] = 1.0 / rjj;
+  __syncwarp();
   for (int i = j - 1; i >= 0; --i) {
-    const double rii = R[i + (int64_t)i * ldr];
-    if (rii == 0.0) {
-      t[i] = 0.0;
-      continue;
-    }
     double s = 0.0;
-    for (int k = i + 1; k <= j; ++k) s = fma(R[i + (int64_t)k * ldr], t[k], s);
-    t[i] = -s / rii;
+    for (int k = i + 1 + lane; k <= j; k += 32) s = fma(R[i + (int64_t)k * ldr], t[k], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double rii = R[i + (int64_t)i * ldr];
+      t[i] = (rii == 0.0) ? 0.0 : -s / rii;
+    }
+    __syncwarp();
   }
 }
 
@@ -214,6 +216,64 @@ __global__ void k_hessenberg(int n, double* A, int ld, double* tau) {
   }
 }
 
+// Symmetric A (n x n, ld, both triangles stored) <- Q^T A Q tridiagonal, with
+// the same reflector storage as k_hessenberg (v below the subdiagonal of
+// column k, tau[k]).  Per step: p = tau A22 v, w = p - (tau/2)(p.v) v,
+// A22 -= v w^T + w v^T.  One CTA; shared memory 3n + 32 doubles.
+__global__ void k_sytrd(int n, double* A, int ld, double* tau) {
+  extern __shared__ double sm[];
+  double* v = sm;
+  double* w = sm + n;
+  double* red = sm + 2 * n;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = A + (int64_t)k * ld + (k + 1);
+    double loc = 0.0;
+    for (int i = 1 + tid; i < m; i += bd) loc += x[i] * x[i];
+    const double sig = block_sum(loc, red);
+    const double alpha = x[0];
+    if (sig == 0.0) {
+      if (tid == 0) tau[k] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double nrm = sqrt(alpha * alpha + sig);
+    const double beta = alpha <= 0.0 ? nrm : -nrm;
+    const double t = (beta - alpha) / beta;
+    const double sc = 1.0 / (alpha - beta);
+    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : x[i] * sc;
+    __syncthreads();
+    for (int i = 1 + tid; i < m; i += bd) x[i] = v[i];
+    if (tid == 0) {
+      x[0] = beta;
+      A[k + (int64_t)(k + 1) * ld] = beta;
+      tau[k] = t;
+    }
+    // p = tau * A22 v (A22 symmetric: use its columns)
+    for (int j = tid; j < m; j += bd) {
+      const double* col = A + (int64_t)(k + 1 + j) * ld + (k + 1);
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s = fma(col[i], v[i], s);
+      w[j] = t * s;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = tid; i < m; i += bd) pv += w[i] * v[i];
+    pv = block_sum(pv, red);
+    for (int i = tid; i < m; i += bd) w[i] -= 0.5 * t * pv * v[i];
+    __syncthreads();
+    for (int e = tid; e < m * m; e += bd) {
+      const int i = e % m, j = e / m;
+      A[(int64_t)(k + 1 + j) * ld + (k + 1 + i)] -= v[i] * w[j] + w[i] * v[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) tau[k] = 0.0;
+  }
+}
+
 // y <- Q y for every column of Y (n x nvec, ld), Q = H_0 ... H_{n-3} from
 // k_hessenberg's storage in A.  One CTA per column.
 __global__ void k_apply_q(int n, const double* __restrict__ A, int lda, const double* __restrict__ tau,
@@ -236,59 +296,77 @@ __global__ void k_apply_q(int n, const double* __restrict__ A, int lda, const do
 
 // ------------------------------------------------------- Francis QR
 
-__device__ __forceinline__ void two_by_two_eigs(double a, double b, double c, double d, double& r1,
-                                                double& i1, double& r2, double& i2) {
-  const double p = 0.5 * (a - d);
-  const double bc = b * c;
-  const double disc = p * p + bc;
-  if (disc >= 0.0) {
-    const double z = p + copysign(sqrt(disc), p);
-    r1 = d + z;
-    r2 = (z != 0.0) ? d - bc / z : d + z;
+template <class Real>
+__device__ __forceinline__ void two_by_two_eigs(Real a, Real b, Real c, Real d, double& r1, double& i1, double& r2,
+                                                double& i2) {
+  const Real p = Real(0.5) * (a - d);
+  const Real bc = b * c;
+  const Real disc = p * p + bc;
+  if (disc >= Real(0)) {
+    const Real z = p + copysign(sqrt(disc), p);
+    r1 = (double)(d + z);
+    r2 = (z != Real(0)) ? (double)(d - bc / z) : (double)(d + z);
     i1 = i2 = 0.0;
   } else {
-    const double re = d + p, im = sqrt(-disc);
-    r1 = r2 = re;
-    i1 = im;
-    i2 = -im;
+    const Real re = d + p, im = sqrt(-disc);
+    r1 = r2 = (double)re;
+    i1 = (double)im;
+    i2 = -(double)im;
   }
 }
 
-// Eigenvalues of the upper Hessenberg matrix Hin (n x n, ld) by Francis
-// double-shift QR.  One warp; the matrix is copied into shared memory when
-// `in_smem`, otherwise into the global scratch `H` (n x n, ld n).
-__global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi,
-                      double* Hscratch, int in_smem, int32_t* info) {
-  extern __shared__ double smem[];
-  double* H = in_smem ? smem : Hscratch;
+template <class Real>
+struct EpsOf;
+template <>
+struct EpsOf<double> {
+  static constexpr double v = DBL_EPSILON;
+};
+template <>
+struct EpsOf<float> {
+  static constexpr float v = FLT_EPSILON;
+};
+
+// Eigenvalues of the upper Hessenberg matrix Hin (n x n, ld; FP64) by Francis
+// double-shift QR in precision Real.  One warp; the matrix is copied into
+// shared memory (leading dimension ldw, odd so that a warp's row accesses hit
+// distinct banks) when `in_smem`, otherwise into the global scratch.  With
+// Real = float this only supplies starting shifts: every eigenvalue is then
+// refined in FP64 by k_hess_rqi.
+template <class Real>
+__global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi, Real* Hscratch,
+                      int in_smem, int32_t* info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldw = n | 1;
+  Real* H = in_smem ? reinterpret_cast<Real*>(smem_raw) : Hscratch;
   const int lane = threadIdx.x;
+  const Real eps = EpsOf<Real>::v;
   for (int e = lane; e < n * n; e += 32) {
     const int i = e % n, j = e / n;
-    H[e] = (i <= j + 1) ? Hin[i + (int64_t)j * ldh] : 0.0;
+    H[i + (int64_t)j * ldw] = (i <= j + 1) ? (Real)Hin[i + (int64_t)j * ldh] : Real(0);
   }
   __syncwarp();
-#define HH(i, j) H[(i) + (int64_t)(j) * n]
-  double anorm = 0.0;
+#define HH(i, j) H[(i) + (int64_t)(j) * ldw]
+  Real anorm = 0;
   for (int j = 0; j < n; ++j)
     for (int i = 0; i <= min(j + 1, n - 1); ++i) anorm = fmax(anorm, fabs(HH(i, j)));
-  if (anorm == 0.0) anorm = 1.0;
+  if (anorm == Real(0)) anorm = 1;
   int hi = n - 1, its = 0, total = 0;
   while (hi >= 0) {
     int lo = hi;
     while (lo > 0) {
-      double s = fabs(HH(lo - 1, lo - 1)) + fabs(HH(lo, lo));
-      if (s == 0.0) s = anorm;
-      if (fabs(HH(lo, lo - 1)) <= kEps * s) break;
+      Real s = fabs(HH(lo - 1, lo - 1)) + fabs(HH(lo, lo));
+      if (s == Real(0)) s = anorm;
+      if (fabs(HH(lo, lo - 1)) <= eps * s) break;
       --lo;
     }
     if (lo > 0) {
       __syncwarp();
-      if (lane == 0) HH(lo, lo - 1) = 0.0;
+      if (lane == 0) HH(lo, lo - 1) = 0;
       __syncwarp();
     }
     if (lo == hi) {
       if (lane == 0) {
-        wr[hi] = HH(hi, hi);
+        wr[hi] = (double)HH(hi, hi);
         wi[hi] = 0.0;
       }
       --hi;
@@ -297,7 +375,7 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
     }
     if (lo == hi - 1) {
       double r1, i1, r2, i2;
-      two_by_two_eigs(HH(hi - 1, hi - 1), HH(hi - 1, hi), HH(hi, hi - 1), HH(hi, hi), r1, i1, r2, i2);
+      two_by_two_eigs<Real>(HH(hi - 1, hi - 1), HH(hi - 1, hi), HH(hi, hi - 1), HH(hi, hi), r1, i1, r2, i2);
       if (lane == 0) {
         wr[hi - 1] = r1;
         wi[hi - 1] = i1;
@@ -318,42 +396,42 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
     ++its;
     ++total;
     // double shift from the trailing 2x2 block (sum s, product t); exceptional every 10 sweeps
-    double s, t;
+    Real s, t;
     if (its % 10 == 0) {
-      const double w = fabs(HH(hi, hi - 1)) + fabs(HH(hi - 1, hi - 2));
-      const double h = 0.75 * w + HH(hi, hi);
-      s = 2.0 * h;
-      t = h * h + 0.4375 * w * w;
+      const Real w = fabs(HH(hi, hi - 1)) + fabs(HH(hi - 1, hi - 2));
+      const Real h = Real(0.75) * w + HH(hi, hi);
+      s = Real(2) * h;
+      t = h * h + Real(0.4375) * w * w;
     } else {
       s = HH(hi - 1, hi - 1) + HH(hi, hi);
       t = HH(hi - 1, hi - 1) * HH(hi, hi) - HH(hi - 1, hi) * HH(hi, hi - 1);
     }
-    double x = HH(lo, lo) * HH(lo, lo) + HH(lo, lo + 1) * HH(lo + 1, lo) - s * HH(lo, lo) + t;
-    double y = HH(lo + 1, lo) * (HH(lo, lo) + HH(lo + 1, lo + 1) - s);
-    double z = HH(lo + 1, lo) * HH(lo + 2, lo + 1);
+    Real x = HH(lo, lo) * HH(lo, lo) + HH(lo, lo + 1) * HH(lo + 1, lo) - s * HH(lo, lo) + t;
+    Real y = HH(lo + 1, lo) * (HH(lo, lo) + HH(lo + 1, lo + 1) - s);
+    Real z = HH(lo + 1, lo) * HH(lo + 2, lo + 1);
     for (int k = lo; k <= hi - 2; ++k) {
       // reflector P = I - tau v v^T, v = [1, v1, v2], P [x y z]^T = [beta 0 0]^T
-      const double nrm = sqrt(x * x + y * y + z * z);
-      if (nrm != 0.0 && (y != 0.0 || z != 0.0)) {
-        const double beta = x <= 0.0 ? nrm : -nrm;
-        const double tau = (beta - x) / beta;
-        const double sc = 1.0 / (x - beta);
-        const double v1 = y * sc, v2 = z * sc;
+      const Real nrm = sqrt(x * x + y * y + z * z);
+      if (nrm != Real(0) && (y != Real(0) || z != Real(0))) {
+        const Real beta = x <= Real(0) ? nrm : -nrm;
+        const Real tau = (beta - x) / beta;
+        const Real sc = Real(1) / (x - beta);
+        const Real v1 = y * sc, v2 = z * sc;
         const int c0 = max(lo, k - 1);
         for (int c = c0 + lane; c <= hi; c += 32) {
-          const double p = tau * (HH(k, c) + v1 * HH(k + 1, c) + v2 * HH(k + 2, c));
+          const Real p = tau * (HH(k, c) + v1 * HH(k + 1, c) + v2 * HH(k + 2, c));
           HH(k, c) -= p;
           HH(k + 1, c) -= p * v1;
           HH(k + 2, c) -= p * v2;
         }
         __syncwarp();
         if (k > lo && lane == 0) {
-          HH(k + 1, k - 1) = 0.0;
-          HH(k + 2, k - 1) = 0.0;
+          HH(k + 1, k - 1) = 0;
+          HH(k + 2, k - 1) = 0;
         }
         const int rend = min(k + 3, hi);
         for (int rr = lo + lane; rr <= rend; rr += 32) {
-          const double p = tau * (HH(rr, k) + v1 * HH(rr, k + 1) + v2 * HH(rr, k + 2));
+          const Real p = tau * (HH(rr, k) + v1 * HH(rr, k + 1) + v2 * HH(rr, k + 2));
           HH(rr, k) -= p;
           HH(rr, k + 1) -= p * v1;
           HH(rr, k + 2) -= p * v2;
@@ -366,21 +444,21 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
     }
     // final 2-vector reflector on rows/columns hi-1, hi
     {
-      const double nrm = sqrt(x * x + y * y);
-      if (nrm != 0.0 && y != 0.0) {
-        const double beta = x <= 0.0 ? nrm : -nrm;
-        const double tau = (beta - x) / beta;
-        const double v1 = y / (x - beta);
+      const Real nrm = sqrt(x * x + y * y);
+      if (nrm != Real(0) && y != Real(0)) {
+        const Real beta = x <= Real(0) ? nrm : -nrm;
+        const Real tau = (beta - x) / beta;
+        const Real v1 = y / (x - beta);
         const int k = hi - 1;
         for (int c = max(lo, k - 1) + lane; c <= hi; c += 32) {
-          const double p = tau * (HH(k, c) + v1 * HH(k + 1, c));
+          const Real p = tau * (HH(k, c) + v1 * HH(k + 1, c));
           HH(k, c) -= p;
           HH(k + 1, c) -= p * v1;
         }
         __syncwarp();
-        if (k > lo && lane == 0) HH(k + 1, k - 1) = 0.0;
+        if (k > lo && lane == 0) HH(k + 1, k - 1) = 0;
         for (int rr = lo + lane; rr <= hi; rr += 32) {
-          const double p = tau * (HH(rr, k) + v1 * HH(rr, k + 1));
+          const Real p = tau * (HH(rr, k) + v1 * HH(rr, k + 1));
           HH(rr, k) -= p;
           HH(rr, k + 1) -= p * v1;
         }
@@ -394,93 +472,107 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
 
 // ---------------------------------------------- inverse iteration (Hessenberg)
 
-// For each head eigenvalue mu = wr + i wi (wi >= 0), solve (H - mu I) x = rhs
-// three times with an LU factorisation (row pivoting between adjacent rows),
-// giving the eigenvector y of the Hessenberg matrix.  One CTA per eigenvalue.
-// work: per CTA 2 n^2 doubles.  Outputs Yre/Yim (n x nheads, ld n).
-__global__ void k_hess_invit(int n, const double* __restrict__ H, int ldh, const double* __restrict__ wr,
-                             const double* __restrict__ wi, const int* __restrict__ heads,
-                             double* __restrict__ Yre, double* __restrict__ Yim,
-                             double* __restrict__ work, const double* __restrict__ hnorm_ptr) {
+// Rayleigh-quotient inverse iteration on the FP64 Hessenberg matrix for each
+// head eigenvalue estimate mu = wr + i wi (wi >= 0): factor H - mu I (LU with
+// pivoting between adjacent rows, O(n^2)), solve y = (H - mu I)^{-1} x,
+// update mu <- mu + (x^H x) / (x^H y) and x <- y / |y|.  Three iterations
+// take an FP32-accurate estimate to FP64 accuracy (quadratic convergence);
+// a correction larger than 1e-3 |mu| is not applied (the shift then stays
+// put, so the iteration cannot wander to another eigenvalue).  Writes the
+// refined eigenvalue (and its conjugate partner, index e + 1) and the
+// eigenvector y of H.  One CTA per head; work: 2 n^2 doubles per CTA.
+__global__ void k_hess_rqi(int n, const double* __restrict__ H, int ldh, double* __restrict__ wr,
+                           double* __restrict__ wi, const int* __restrict__ heads, double* __restrict__ Yre,
+                           double* __restrict__ Yim, double* __restrict__ work, const double* __restrict__ hnorm_ptr) {
   extern __shared__ double sm[];
   double* mre = sm;                 // multipliers
   double* mim = sm + n;
   double* xre = sm + 2 * n;
   double* xim = sm + 3 * n;
-  int* piv = reinterpret_cast<int*>(sm + 4 * n);
+  double* yre = sm + 4 * n;
+  double* yim = sm + 5 * n;
+  int* piv = reinterpret_cast<int*>(sm + 6 * n);
   __shared__ double red[32];
+  __shared__ double mu_s[2];
   const int tid = threadIdx.x, bd = blockDim.x;
   const int e = heads[blockIdx.x];
   if (e < 0) return;   // padding beyond the actual number of heads
-  const double mur = wr[e], mui = wi[e];
+  double mur = wr[e], mui = wi[e];
+  const bool pair = mui > 0.0;
   double* Ur = work + (int64_t)blockIdx.x * 2 * n * n;
   double* Ui = Ur + (int64_t)n * n;
 #define UR(i, j) Ur[(i) + (int64_t)(j) * n]
 #define UI(i, j) Ui[(i) + (int64_t)(j) * n]
-  for (int q = tid; q < n * n; q += bd) {
-    const int i = q % n, j = q / n;
-    double hr = (i <= j + 1) ? H[i + (int64_t)j * ldh] : 0.0, hi_ = 0.0;
-    if (i == j) {
-      hr -= mur;
-      hi_ = -mui;
-    }
-    UR(i, j) = hr;
-    UI(i, j) = hi_;
-  }
-  __syncthreads();
   const double hnorm = fmax(*hnorm_ptr, DBL_MIN);
   const double tiny = kEps * hnorm;
-  for (int k = 0; k + 1 < n; ++k) {
-    if (tid == 0) {
-      const double ar = UR(k, k), ai = UI(k, k), br = UR(k + 1, k), bi = UI(k + 1, k);
-      const bool sw = (br * br + bi * bi) > (ar * ar + ai * ai);
-      piv[k] = sw ? 1 : 0;
-      double pr = sw ? br : ar, pi = sw ? bi : ai;   // pivot
-      double orr = sw ? ar : br, oi = sw ? ai : bi;  // eliminated entry
-      if (pr == 0.0 && pi == 0.0) pr = tiny;
-      const double den = pr * pr + pi * pi;
-      mre[k] = (orr * pr + oi * pi) / den;          // other / pivot
-      mim[k] = (oi * pr - orr * pi) / den;
-      UR(k, k) = pr;
-      UI(k, k) = pi;
-      UR(k + 1, k) = 0.0;
-      UI(k + 1, k) = 0.0;
-    }
-    __syncthreads();
-    const int sw = piv[k];
-    const double lr = mre[k], li = mim[k];
-    for (int j = k + 1 + tid; j < n; j += bd) {
-      double ar = UR(k, j), ai = UI(k, j), br = UR(k + 1, j), bi = UI(k + 1, j);
-      if (sw) {
-        double tr = ar, ti = ai;
-        ar = br; ai = bi; br = tr; bi = ti;
-      }
-      UR(k, j) = ar;
-      UI(k, j) = ai;
-      UR(k + 1, j) = br - (lr * ar - li * ai);
-      UI(k + 1, j) = bi - (lr * ai + li * ar);
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    if (UR(n - 1, n - 1) == 0.0 && UI(n - 1, n - 1) == 0.0) UR(n - 1, n - 1) = tiny;
-  }
   for (int i = tid; i < n; i += bd) {
-    xre[i] = 1.0;
+    xre[i] = 1.0 / sqrt((double)n);
     xim[i] = 0.0;
   }
-  __syncthreads();
   for (int it = 0; it < 3; ++it) {
+    __syncthreads();
+    for (int q = tid; q < n * n; q += bd) {
+      const int i = q % n, j = q / n;
+      double hr = (i <= j + 1) ? H[i + (int64_t)j * ldh] : 0.0, hi_ = 0.0;
+      if (i == j) {
+        hr -= mur;
+        hi_ = -mui;
+      }
+      UR(i, j) = hr;
+      UI(i, j) = hi_;
+    }
+    __syncthreads();
+    for (int k = 0; k + 1 < n; ++k) {
+      if (tid == 0) {
+        const double ar = UR(k, k), ai = UI(k, k), br = UR(k + 1, k), bi = UI(k + 1, k);
+        const bool sw = (br * br + bi * bi) > (ar * ar + ai * ai);
+        piv[k] = sw ? 1 : 0;
+        double pr = sw ? br : ar, pi = sw ? bi : ai;
+        double orr = sw ? ar : br, oi = sw ? ai : bi;
+        if (pr == 0.0 && pi == 0.0) pr = tiny;
+        const double den = pr * pr + pi * pi;
+        mre[k] = (orr * pr + oi * pi) / den;
+        mim[k] = (oi * pr - orr * pi) / den;
+        UR(k, k) = pr;
+        UI(k, k) = pi;
+      }
+      __syncthreads();
+      const int sw = piv[k];
+      const double lr = mre[k], li = mim[k];
+      for (int j = k + 1 + tid; j < n; j += bd) {
+        double ar = UR(k, j), ai = UI(k, j), br = UR(k + 1, j), bi = UI(k + 1, j);
+        if (sw) {
+          const double tr = ar, ti = ai;
+          ar = br;
+          ai = bi;
+          br = tr;
+          bi = ti;
+        }
+        UR(k, j) = ar;
+        UI(k, j) = ai;
+        UR(k + 1, j) = br - (lr * ar - li * ai);
+        UI(k + 1, j) = bi - (lr * ai + li * ar);
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && UR(n - 1, n - 1) == 0.0 && UI(n - 1, n - 1) == 0.0) UR(n - 1, n - 1) = tiny;
+    // y = P L^{-1} x (forward, sequential), then U y = that (back substitution)
     if (tid == 0) {
+      for (int i = 0; i < n; ++i) {
+        yre[i] = xre[i];
+        yim[i] = xim[i];
+      }
       for (int k = 0; k + 1 < n; ++k) {
         if (piv[k]) {
-          double tr = xre[k], ti = xim[k];
-          xre[k] = xre[k + 1]; xim[k] = xim[k + 1];
-          xre[k + 1] = tr; xim[k + 1] = ti;
+          const double tr = yre[k], ti = yim[k];
+          yre[k] = yre[k + 1];
+          yim[k] = yim[k + 1];
+          yre[k + 1] = tr;
+          yim[k + 1] = ti;
         }
         const double lr = mre[k], li = mim[k];
-        xre[k + 1] -= lr * xre[k] - li * xim[k];
-        xim[k + 1] -= lr * xim[k] + li * xre[k];
+        yre[k + 1] -= lr * yre[k] - li * yim[k];
+        yim[k + 1] -= lr * yim[k] + li * yre[k];
       }
     }
     __syncthreads();
@@ -488,32 +580,65 @@ __global__ void k_hess_invit(int n, const double* __restrict__ H, int ldh, const
       double sr = 0.0, si = 0.0;
       for (int j = i + 1 + tid; j < n; j += bd) {
         const double ur = UR(i, j), ui = UI(i, j);
-        sr += ur * xre[j] - ui * xim[j];
-        si += ur * xim[j] + ui * xre[j];
+        sr += ur * yre[j] - ui * yim[j];
+        si += ur * yim[j] + ui * yre[j];
       }
       sr = block_sum(sr, red);
       si = block_sum(si, red);
       if (tid == 0) {
-        const double br = xre[i] - sr, bi = xim[i] - si;
+        const double br = yre[i] - sr, bi = yim[i] - si;
         const double ur = UR(i, i), ui = UI(i, i), den = ur * ur + ui * ui;
-        xre[i] = (br * ur + bi * ui) / den;
-        xim[i] = (bi * ur - br * ui) / den;
+        yre[i] = (br * ur + bi * ui) / den;
+        yim[i] = (bi * ur - br * ui) / den;
       }
       __syncthreads();
     }
-    double loc = 0.0;
-    for (int i = tid; i < n; i += bd) loc = fmax(loc, fmax(fabs(xre[i]), fabs(xim[i])));
-    const double mx = block_max(loc, red);
-    const double inv = (mx > 0.0 && isfinite(mx)) ? 1.0 / mx : 1.0;
+    // Rayleigh quotient: theta = x^H y (x has unit norm); mu += 1 / theta
+    double tr_ = 0.0, ti_ = 0.0, yy = 0.0;
     for (int i = tid; i < n; i += bd) {
-      xre[i] *= inv;
-      xim[i] *= inv;
+      tr_ += xre[i] * yre[i] + xim[i] * yim[i];
+      ti_ += xre[i] * yim[i] - xim[i] * yre[i];
+      yy += yre[i] * yre[i] + yim[i] * yim[i];
     }
+    tr_ = block_sum(tr_, red);
+    ti_ = block_sum(ti_, red);
+    yy = block_sum(yy, red);
+    if (tid == 0) {
+      const double den = tr_ * tr_ + ti_ * ti_;
+      double dr = 0.0, di = 0.0;
+      if (den > 0.0 && isfinite(den)) {
+        dr = tr_ / den;
+        di = -ti_ / den;
+      }
+      const double mag = hypot(mur, mui);
+      if (hypot(dr, di) < 1e-3 * fmax(mag, 1e-300)) {
+        mur += dr;
+        if (pair) mui += di;   // a real eigenvalue stays real
+      }
+      mu_s[0] = mur;
+      mu_s[1] = mui;
+    }
+    const double inv = (yy > 0.0 && isfinite(yy)) ? 1.0 / sqrt(yy) : 1.0;
     __syncthreads();
+    mur = mu_s[0];
+    mui = mu_s[1];
+    for (int i = tid; i < n; i += bd) {
+      xre[i] = yre[i] * inv;
+      xim[i] = yim[i] * inv;
+    }
   }
+  __syncthreads();
   for (int i = tid; i < n; i += bd) {
     Yre[i + (int64_t)blockIdx.x * n] = xre[i];
     Yim[i + (int64_t)blockIdx.x * n] = xim[i];
+  }
+  if (tid == 0) {
+    wr[e] = mur;
+    wi[e] = pair ? mui : 0.0;
+    if (pair && e + 1 < n) {
+      wr[e + 1] = mur;
+      wi[e + 1] = -mui;
+    }
   }
 #undef UR
 #undef UI
@@ -662,39 +787,55 @@ __device__ int sturm_count(int n, const double* d, const double* e, double x, do
   return cnt;
 }
 
-// Eigenvalue i (descending) of the tridiagonal (d, e) by bisection and its
-// eigenvector by inverse iteration (3 solves, partial pivoting); one thread
-// per eigenvalue.  scratch: 7 n doubles per thread.  Outputs ev[i], Y[:, i].
-__global__ void k_tridiag_eig(int n, const double* __restrict__ A, int lda, double* __restrict__ ev,
-                              double* __restrict__ Y, double* __restrict__ scratch) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Eigenvalue i (descending) of the symmetric tridiagonal (d, e) -- the
+// diagonal and subdiagonal of A after k_sytrd -- by warp multisection: each
+// round the 32 lanes evaluate Sturm counts at 32 interior points and the
+// bracket shrinks 33-fold; then lane 0 runs inverse iteration (3 solves with
+// partial pivoting) for the eigenvector.  One warp per eigenvalue, so the
+// FP64 work spreads over all SMs.  scratch: 7 n doubles per eigenvalue.
+__global__ void k_tridiag_eig_ms(int n, const double* __restrict__ A, int lda, double* __restrict__ ev,
+                                 double* __restrict__ Y, double* __restrict__ scratch) {
   extern __shared__ double sde[];
   double* d = sde;
   double* e = sde + n;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x;
+  for (int t = lane; t < n; t += 32) {
     d[t] = A[t + (int64_t)t * lda];
     e[t] = (t + 1 < n) ? A[(t + 1) + (int64_t)t * lda] : 0.0;
   }
-  __syncthreads();
-  if (i >= n) return;
-  double tnorm = 0.0, lo = 0.0, hi = 0.0;
-  for (int t = 0; t < n; ++t) {
+  __syncwarp();
+  double lo = INFINITY, hi = -INFINITY, tnorm = 0.0;
+  for (int t = lane; t < n; t += 32) {
     const double off = (t > 0 ? fabs(e[t - 1]) : 0.0) + (t + 1 < n ? fabs(e[t]) : 0.0);
-    lo = (t == 0) ? d[t] - off : fmin(lo, d[t] - off);
-    hi = (t == 0) ? d[t] + off : fmax(hi, d[t] + off);
+    lo = fmin(lo, d[t] - off);
+    hi = fmax(hi, d[t] + off);
     tnorm = fmax(tnorm, fabs(d[t]) + off);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    tnorm = fmax(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
   }
   if (tnorm == 0.0) tnorm = 1.0;
   const double pivmin = DBL_MIN * 4.0 + kEps * kEps * tnorm;
   lo -= 2.0 * kEps * tnorm;
   hi += 2.0 * kEps * tnorm;
   const int k = n - 1 - i;   // ascending index
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) break;
-    if (sturm_count(n, d, e, mid, pivmin) > k) hi = mid; else lo = mid;
+  for (int round = 0; round < 14; ++round) {
+    if (hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double step = (hi - lo) / 33.0;
+    const double x = lo + step * (lane + 1);
+    const int cnt = sturm_count(n, d, e, x, pivmin);
+    const unsigned mask = __ballot_sync(0xffffffffu, cnt > k);
+    const int j = mask ? (__ffs(mask) - 1) : 32;   // first point with more than k eigenvalues below
+    const double nlo = (j == 0) ? lo : lo + step * j;
+    const double nhi = (j == 32) ? hi : lo + step * (j + 1);
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double lam = 0.5 * (lo + hi);
   ev[i] = lam;
   double* u0 = scratch + (int64_t)i * 7 * n;
@@ -702,9 +843,8 @@ __global__ void k_tridiag_eig(int n, const double* __restrict__ A, int lda, doub
   double* u2 = u1 + n;
   double* ml = u2 + n;
   double* pv = ml + n;
-  double* x = pv + n;
+  double* xv = pv + n;
   const double tiny = kEps * tnorm;
-  // factorise T - lam I with adjacent-row pivoting; U has two superdiagonals
   double c0 = d[0] - lam, c1 = (n > 1) ? e[0] : 0.0, c2 = 0.0;
   for (int q = 0; q + 1 < n; ++q) {
     const double b0 = e[q], b1 = d[q + 1] - lam, b2 = (q + 2 < n) ? e[q + 1] : 0.0;
@@ -725,29 +865,29 @@ __global__ void k_tridiag_eig(int n, const double* __restrict__ A, int lda, doub
   }
   if (c0 == 0.0) c0 = tiny;
   u0[n - 1] = c0; u1[n - 1] = 0.0; u2[n - 1] = 0.0;
-  for (int t = 0; t < n; ++t) x[t] = 1.0;
+  for (int t = 0; t < n; ++t) xv[t] = 1.0;
   for (int it = 0; it < 3; ++it) {
     for (int q = 0; q + 1 < n; ++q) {
       if (pv[q] != 0.0) {
-        const double tt = x[q];
-        x[q] = x[q + 1];
-        x[q + 1] = tt;
+        const double tt = xv[q];
+        xv[q] = xv[q + 1];
+        xv[q + 1] = tt;
       }
-      x[q + 1] -= ml[q] * x[q];
+      xv[q + 1] -= ml[q] * xv[q];
     }
     for (int t = n - 1; t >= 0; --t) {
-      double s = x[t];
-      if (t + 1 < n) s -= u1[t] * x[t + 1];
-      if (t + 2 < n) s -= u2[t] * x[t + 2];
-      x[t] = s / u0[t];
+      double sacc = xv[t];
+      if (t + 1 < n) sacc -= u1[t] * xv[t + 1];
+      if (t + 2 < n) sacc -= u2[t] * xv[t + 2];
+      xv[t] = sacc / u0[t];
     }
     double nrm = 0.0;
-    for (int t = 0; t < n; ++t) nrm += x[t] * x[t];
+    for (int t = 0; t < n; ++t) nrm += xv[t] * xv[t];
     nrm = sqrt(nrm);
     const double inv = (nrm > 0.0 && isfinite(nrm)) ? 1.0 / nrm : 1.0;
-    for (int t = 0; t < n; ++t) x[t] *= inv;
+    for (int t = 0; t < n; ++t) xv[t] *= inv;
   }
-  for (int t = 0; t < n; ++t) Y[t + (int64_t)i * n] = x[t];
+  for (int t = 0; t < n; ++t) Y[t + (int64_t)i * n] = xv[t];
 }
 
 // Modified Gram-Schmidt inside clusters of (nearly) equal eigenvalues, in
@@ -872,7 +1012,7 @@ dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, i
 }
 
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st) {
-  k_tri_inv_upper<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, R, ldr, T, ldt);
+  k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -892,16 +1032,17 @@ dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y
   return DMD_OK;
 }
 
-size_t hqr_smem_bytes(int n) { return (size_t)n * n * sizeof(double); }
+size_t hqr_smem_bytes(int n) { return (size_t)n * (n | 1) * sizeof(float); }
 bool hqr_fits_smem(int n) { return hqr_smem_bytes(n) <= 200 * 1024; }
 
+// FP32 Francis QR for the eigenvalue estimates (refined in FP64 by hess_eigvecs).
 dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
                cudaStream_t st) {
   const bool in_smem = hqr_fits_smem(n);
   const size_t smem = in_smem ? hqr_smem_bytes(n) : 0;
   if (smem > 48 * 1024)
-    DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_hqr<<<1, 32, smem, st>>>(n, H, ldh, wr, wi, scratch, in_smem ? 1 : 0, info);
+    DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_hqr<float><<<1, 32, smem, st>>>(n, H, ldh, wr, wi, reinterpret_cast<float*>(scratch), in_smem ? 1 : 0, info);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -917,8 +1058,9 @@ dmd_status collect_heads(int n, const double* wi, int* heads, int* nheads, int32
 dmd_status hess_eigvecs(int n, const double* H, int ldh, const double* wr, const double* wi,
                         const int* heads, int nheads_max, double* Yre, double* Yim, double* work,
                         const double* hnorm, cudaStream_t st) {
-  const size_t smem = (4 * (size_t)n) * sizeof(double) + (size_t)n * sizeof(int) + 16;
-  k_hess_invit<<<(unsigned)nheads_max, 256, smem, st>>>(n, H, ldh, wr, wi, heads, Yre, Yim, work, hnorm);
+  const size_t smem = (6 * (size_t)n) * sizeof(double) + (size_t)n * sizeof(int) + 16;
+  k_hess_rqi<<<(unsigned)nheads_max, 256, smem, st>>>(n, H, ldh, const_cast<double*>(wr), const_cast<double*>(wi),
+                                                       heads, Yre, Yim, work, hnorm);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -939,10 +1081,17 @@ dmd_status eig_layout(int n, const double* wr, const double* wi, const int* head
   return DMD_OK;
 }
 
+dmd_status sytrd(int n, double* A, int ld, double* tau, cudaStream_t st) {
+  const size_t smem = (3 * (size_t)n + 32) * sizeof(double);
+  k_sytrd<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
 dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, double* scratch,
                        cudaStream_t st) {
   const size_t smem = 2 * (size_t)n * sizeof(double);
-  k_tridiag_eig<<<(unsigned)ceil_div(n, 128), 128, smem, st>>>(n, A, lda, ev, Y, scratch);
+  k_tridiag_eig_ms<<<(unsigned)n, 32, smem, st>>>(n, A, lda, ev, Y, scratch);
   DMD_LAUNCH_CHECK();
   k_cluster_mgs<<<1, 256, 0, st>>>(n, ev, Y, 1e-11);
   DMD_LAUNCH_CHECK();

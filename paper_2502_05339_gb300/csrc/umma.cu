@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
 
 constexpr int TN_S = 3;          // TMA stages (A slice + B slice)
 constexpr int TN_THREADS = 320;
-constexpr int TN_FLUSH = 256;    // k-steps (of 16 rows) between FP64 flushes
+constexpr int TN_FLUSH = 256;    // default k-steps (of 16 rows) between FP64 flushes
 
 // part[blockIdx.x][b * Ka + a] = sum over this CTA's rows of A[:, a] * B[:, b].
 // A slice: TMA box {16 rows, Mt*128 cols}; B slice: box {16 rows, Np cols}.
@@ -641,7 +641,7 @@ constexpr int TN_FLUSH = 256;    // k-steps (of 16 rows) between FP64 flushes
 // largest -- the reductions whose accuracy decides the fit use it.
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_umma_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
-              int N, int Mt, int Np, int nsplit, int64_t chunk, double* __restrict__ part, int32_t* err) {
+              int N, int Mt, int Np, int nsplit, int flush, int64_t chunk, double* __restrict__ part, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t a_bytes = 16u * 4u * (uint32_t)Mt * 128u;   // FP32 slice of A
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   const int64_t rbeg = (int64_t)blockIdx.x * chunk;
   const int64_t rend = min(n, rbeg + chunk);
   const int ksteps = rend > rbeg ? (int)((rend - rbeg + 15) / 16) : 0;
-  const int nflush = (ksteps + TN_FLUSH - 1) / TN_FLUSH;
+  const int nflush = (ksteps + flush - 1) / flush;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < TN_S; ++i) {
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       for (int f = 0; ok && f < nflush; ++f) {
         if (!mbar_wait(acce, (f & 1) ^ 1, abort_flag)) break;
         tc_after();
-        const int kend = min(ksteps, (f + 1) * TN_FLUSH);
+        const int kend = min(ksteps, (f + 1) * flush);
         for (int kk = 0; ks < kend; ++ks, ++kk) {
           const uint32_t cs = ks & 1;
           if (!mbar_wait(&cfull[cs], (ks >> 1) & 1, abort_flag)) {
@@ -982,8 +982,8 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 
 // C (Ka x N, ld Ka) = A^T B; sub-problems of at most 256 x 256 so that the
 // accumulators (Mt * Np columns) fit in 512 TMEM columns.
-dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
-                        int nsplit, void* ws, cudaStream_t st) {
+dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                              double* C, int nsplit, int flush, void* ws, cudaStream_t st) {
   if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
   double* part = reinterpret_cast<double*>(ws);
   const int grid = tn_grid(n);
@@ -999,7 +999,7 @@ dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, c
       DMD_TRY(make_map(&mB, B + (int64_t)b0 * ldb, n, nb, ldb, 16, Np));
       const size_t smem = tn_smem(Mt, Np, nsplit);
       DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, chunk, part, nullptr);
+      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, flush, chunk, part, nullptr);
       DMD_LAUNCH_CHECK();
       // reduce into the (a0, b0) block of C
       const int64_t count = (int64_t)ka * nb;
@@ -1009,6 +1009,11 @@ dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, c
     }
   }
   return DMD_OK;
+}
+
+dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
+                        int nsplit, void* ws, cudaStream_t st) {
+  return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, nsplit, TN_FLUSH, ws, st);
 }
 
 }  // namespace dmd
