@@ -37,6 +37,8 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                         double* C, int nsplit, void* ws, cudaStream_t st);
+dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                              double* C, int nsplit, int flush, void* ws, cudaStream_t st);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
@@ -107,10 +109,12 @@ struct Tall {
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
-    // Reductions over the tall dimension decide the accuracy of the fit (the
-    // Gram matrices square the snapshot condition number), so the mixed form
-    // splits their operands three ways; see umma.cu.
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn(n, Ka, N, A, lda, B, ldb, C, 3, ws, st);
+    // Reductions over the tall dimension decide the accuracy of the fit, so
+    // the mixed form splits their operands three ways and moves the TMEM
+    // partial sums into FP64 every 16 k-steps (256 rows): the tensor core's
+    // FP32 accumulation error grows with the number of k-steps summed in TMEM
+    // (measured), the split error is then below it.
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 3, 16, ws, st);
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
 };
@@ -127,6 +131,7 @@ struct FitBufs {
   float *Y, *Q1;
   int *heads, *nheads, *order;
   // DMD with control (q > 0): input-space SVD of [Q^T X; Ups] and its products
+  double *W, *WB;   // snapshot Gram S^T S ((m+1) x (m+1)) and W_X B (m x l)
   int L, p;
   double *Omc, *Hc, *tauC, *evC, *YC, *tridC, *VS, *T1c, *T2c, *Tw, *invC, *rhsc, *solc;
   void* gemm_ws;
@@ -143,6 +148,8 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   const int m = b.m, l = b.l, r = b.r;
   const int64_t n = b.n;
   b.Om = a.take<double>((size_t)m * l);
+  b.W = a.take<double>((size_t)(m + 1) * (m + 1));
+  b.WB = a.take<double>((size_t)m * l);
   b.G = a.take<double>((size_t)l * l);
   b.T1 = a.take<double>((size_t)l * l);
   b.T2 = a.take<double>((size_t)l * l);
@@ -204,6 +211,7 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   g = std::max(g, tall.tn_bytes(n, l, l));
   g = std::max(g, tall.tn_bytes(n, m, l));
   g = std::max(g, tall.tn_bytes(n, l, m + 1));
+  g = std::max(g, tall.tn_bytes(n, m + 1, m + 1));
   b.gemm_ws_bytes = g;
   b.gemm_ws = a.take<char>(g, 1024);
 }
@@ -231,11 +239,17 @@ dmd_status validate_fit(const dmd_fit_desc* d) {
 // small FP64 Grams use 1e-13.
 constexpr double kTauTall = 1e-10, kTauSmall = 1e-13;
 
-// CholeskyQR2 of a tall FP32 matrix Y (n x l): Q1 = Y R1^{-1} is written
-// explicitly; the second factor R2 is kept as T2 = R2^{-1} and folded into the
-// consumers, so Q = Q1 T2.  G must hold Y^T Y (FP64) on entry.
-dmd_status orth_tall(const Tall& tall, FitBufs& b, int32_t* info, int tag, cudaStream_t st) {
-  const int l = b.l;
+// CholeskyQR2 of the tall sketch Y = X Bs (n x l, Bs = Omega or Z, m x l):
+// the first Gram is formed in the small space as Bs^T (X^T X) Bs from the
+// snapshot Gram W (one accurate pass over S per fit), so it carries FP64
+// accuracy whatever the condition of Y; Q1 = Y R1^{-1} is written explicitly;
+// the second Gram Q1^T Q1 (of a well-conditioned matrix) is a tall reduction;
+// the second factor is kept as T2 = R2^{-1} and folded into the consumers
+// (Q = Q1 T2).
+dmd_status orth_tall(const Tall& tall, FitBufs& b, const double* Bs, int32_t* info, int tag, cudaStream_t st) {
+  const int l = b.l, m = b.m;
+  DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
+  DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
   DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
   DMD_TRY(tall.nn(b.n, l, l, b.Y, b.ldY, b.T1, b.Q1, b.ldY, b.gemm_ws, st));
@@ -347,20 +361,21 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   } else {
     DMD_TRY(launch_sketch(m, l, d.seed, b.Om, st));
   }
-  // 2. Y = X Omega, G = Y^T Y, Q = orth(Y)
+  // 2. snapshot Gram W = S^T S (one pass; also screens the input for NaN/Inf)
+  DMD_TRY(tall.tn(n, m + 1, m + 1, S, d.ldS, S, d.ldS, b.W, b.gemm_ws, st));
+  DMD_TRY(fit_glue_check_finite((int64_t)(m + 1) * (m + 1), b.W, info, 91, st));
+  // 3. Y = X Omega, Q = orth(Y)
   DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Om, b.Y, b.ldY, b.gemm_ws, st));
-  DMD_TRY(tall.tn(n, l, l, b.Y, b.ldY, b.Y, b.ldY, b.G, b.gemm_ws, st));
-  DMD_TRY(orth_tall(tall, b, info, 1, st));
-  // 3. power iterations: Z = orth(X^T Q), Y = X Z, Q = orth(Y)
+  DMD_TRY(orth_tall(tall, b, b.Om, info, 1, st));
+  // 4. power iterations: Z = orth(X^T Q), Y = X Z, Q = orth(Y)
   for (int it = 0; it < d.power_iters; ++it) {
     DMD_TRY(tall.tn(n, m, l, X, d.ldS, b.Q1, b.ldY, b.Zp, b.gemm_ws, st));
     DMD_TRY(dgemm(m, l, l, 1.0, b.Zp, m, false, b.T2, l, false, 0.0, b.Z, m, st));
     DMD_TRY(orth_small(b, m, info, 10 + 4 * it, st));
     DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Z, b.Y, b.ldY, b.gemm_ws, st));
-    DMD_TRY(tall.tn(n, l, l, b.Y, b.ldY, b.Y, b.ldY, b.G, b.gemm_ws, st));
-    DMD_TRY(orth_tall(tall, b, info, 12 + 4 * it, st));
+    DMD_TRY(orth_tall(tall, b, b.Z, info, 12 + 4 * it, st));
   }
-  // 4. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
+  // 5. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
   DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
   DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));
   DMD_TRY(fit_glue_check_finite((int64_t)l * (m + 1), b.P, info, 90, st));
