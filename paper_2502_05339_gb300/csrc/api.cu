@@ -107,6 +107,19 @@ struct Tall {
     DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st));
     return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st);
   }
+  // The snapshot Gram W = S^T S on the CUDA cores in both forms: the first
+  // CholeskyQR Gram of every sketch is derived from it, and a random sketch
+  // of the leading subspace can be conditioned far worse than the snapshots
+  // (cond(Y)^2 up to ~1e10 was seen for l = r); FP32 products summed in
+  // 32-row tiles and carried in FP64 resolve that, the tensor-core
+  // accumulation does not (measured: ~2e-8 of the largest eigenvalue).
+  size_t tn_accurate_bytes(int64_t n, int Ka, int N) const {
+    return tn_partial_doubles(n, Ka, N) * sizeof(double) + 256;
+  }
+  dmd_status tn_accurate(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                         double* C, void* ws, cudaStream_t st) const {
+    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
+  }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
     // Reductions over the tall dimension decide the accuracy of the fit, so
@@ -211,7 +224,7 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   g = std::max(g, tall.tn_bytes(n, l, l));
   g = std::max(g, tall.tn_bytes(n, m, l));
   g = std::max(g, tall.tn_bytes(n, l, m + 1));
-  g = std::max(g, tall.tn_bytes(n, m + 1, m + 1));
+  g = std::max(g, tall.tn_accurate_bytes(n, m + 1, m + 1));
   b.gemm_ws_bytes = g;
   b.gemm_ws = a.take<char>(g, 1024);
 }
@@ -362,7 +375,7 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
     DMD_TRY(launch_sketch(m, l, d.seed, b.Om, st));
   }
   // 2. snapshot Gram W = S^T S (one pass; also screens the input for NaN/Inf)
-  DMD_TRY(tall.tn(n, m + 1, m + 1, S, d.ldS, S, d.ldS, b.W, b.gemm_ws, st));
+  DMD_TRY(tall.tn_accurate(n, m + 1, m + 1, S, d.ldS, S, d.ldS, b.W, b.gemm_ws, st));
   DMD_TRY(fit_glue_check_finite((int64_t)(m + 1) * (m + 1), b.W, info, 91, st));
   // 3. Y = X Omega, Q = orth(Y)
   DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Om, b.Y, b.ldY, b.gemm_ws, st));
