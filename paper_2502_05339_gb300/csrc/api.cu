@@ -122,12 +122,10 @@ struct Tall {
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
-    // Reductions over the tall dimension decide the accuracy of the fit, so
-    // the mixed form splits their operands three ways and moves the TMEM
-    // partial sums into FP64 every 16 k-steps (256 rows): the tensor core's
-    // FP32 accumulation error grows with the number of k-steps summed in TMEM
-    // (measured), the split error is then below it.
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 3, 16, ws, st);
+    // BF16x3 (hi/lo split, 3 products), TMEM flushed to FP64 every 256
+    // k-steps.  The reductions that see the snapshots' full dynamic range
+    // (the snapshot Gram) run on the CUDA cores instead (tn_accurate).
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 2, 256, ws, st);
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
 };

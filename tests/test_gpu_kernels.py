@@ -185,14 +185,14 @@ def test_autograd_function(dmd):
     assert np.all(gm[:r][kinds == 2] == 0)
 
 
-@pytest.mark.parametrize("prec,decades", [("fp32", 4.0), ("mixed", 2.5)])
+@pytest.mark.parametrize("prec,decades", [("fp32", 4.0), ("mixed", 1.5)])
 def test_gram_resolves_weak_directions(dmd, prec, decades):
     """The Gram of an ill-conditioned tall matrix keeps every eigen-direction
-    to 10%.  FP32: singular values 1 .. 1e-4 (Gram eigenvalues to 1e-8).
-    Mixed (3-way bf16 split, TMEM flushed to FP64 every 16 k-steps, measured
-    error ~6e-8 of the largest eigenvalue): singular values 1 .. 3e-3.  The
-    snapshot Gram of the fit is formed this way; the first CholeskyQR Gram of
-    every sketch is derived from it in FP64."""
+    to 10%.  FP32: singular values 1 .. 1e-4 (Gram eigenvalues to 1e-8); the
+    snapshot Gram of the fit is formed this way and the first CholeskyQR Gram
+    of every sketch is derived from it in FP64.  Mixed (BF16x3, measured error
+    ~2e-7 of the largest eigenvalue): singular values 1 .. 3e-2, the range of
+    the second CholeskyQR Gram, which sees an already orthonormalised basis."""
     g = np.random.default_rng(0)
     n, l = 8192 * 8, 30
     U, _ = np.linalg.qr(g.standard_normal((n, l)))
