@@ -97,6 +97,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// shared -> global tiled store (bulk-group completion); rows/cols past the
+// tensor's extent are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(su32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
                "l"(src), "r"(bytes), "r"(su32(bar))
@@ -433,22 +445,27 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
 
 constexpr int AR_SA = 2;     // TMA stages for the A tile slices
 constexpr int AR_NB = 2;     // B chunk buffers
-constexpr int AR_ACC = 4;    // TMEM accumulators (64 columns each)
-constexpr int AR_BN = 64;    // frames per chunk
+constexpr int AR_ACC = 4;    // TMEM accumulators (bn columns each)
 constexpr int AR_THREADS = 320;
 
+// bn: frames per chunk (multiple of 16, <= 64).  Each epilogue warp stages its
+// 32-row x bn accumulator slice in shared memory and writes it with one TMA
+// store (box {32 rows, bn cols} of C).
 __global__ void __launch_bounds__(AR_THREADS, 1)
-    k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bchunks,
-                   float* __restrict__ C, int64_t ldc, int64_t n, int N, int ksteps, int nchunks, int64_t ntiles,
-                   int32_t* err) {
+    k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
+                   const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int nchunks,
+                   int64_t ntiles, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t ares_bytes = 2u * (uint32_t)ksteps * 128u * 32u;            // hi then lo
-  const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * AR_BN * 32u;
+  const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * (uint32_t)bn * 32u;
+  const uint32_t bstride = (chunk_bytes + 1023u) & ~1023u;
+  const uint32_t stg_bytes = 32u * (uint32_t)bn * 4u;                        // per epilogue warp
   uint8_t* Ares = sm;
   uint8_t* stA = Ares + ((ares_bytes + 1023u) & ~1023u);
   uint8_t* Bbuf = stA + AR_SA * 8192;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bbuf + AR_NB * ((chunk_bytes + 1023u) & ~1023u));
+  uint8_t* stg = Bbuf + AR_NB * bstride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * stg_bytes);
   uint64_t* afull = bars;               // TMA slice landed
   uint64_t* aempty = afull + AR_SA;     // slice converted
   uint64_t* bfull = aempty + AR_SA;
@@ -460,7 +477,6 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   uint64_t* tdown = ares_free + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
-  const uint32_t bstride = (chunk_bytes + 1023u) & ~1023u;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -527,7 +543,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, AR_BN);
+      const uint32_t idesc = idesc_bf16(128, bn);
       uint32_t tit = 0, bit = 0, accit = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
@@ -541,13 +557,13 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
             break;
           }
           tc_after();
-          const uint32_t d = tmem + ab * AR_BN;
+          const uint32_t d = tmem + ab * (uint32_t)bn;
           const uint32_t bbase = su32(Bbuf + b * bstride);
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ah = su32(Ares) + (uint32_t)ks * 4096u;
             const uint32_t al = su32(Ares) + (uint32_t)(ksteps + ks) * 4096u;
-            const uint32_t bh = bbase + (uint32_t)ks * AR_BN * 32u;
-            const uint32_t bl = bbase + (uint32_t)(ksteps + ks) * AR_BN * 32u;
+            const uint32_t bh = bbase + (uint32_t)ks * (uint32_t)bn * 32u;
+            const uint32_t bl = bbase + (uint32_t)(ksteps + ks) * (uint32_t)bn * 32u;
             const uint64_t ahd = sdesc(ah, kLBO, kSBO), ald = sdesc(al, kLBO, kSBO);
             const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
             umma_bf16(d, ahd, bhd, idesc, ks > 0 ? 1u : 0u);
@@ -589,11 +605,11 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     }
   } else {
     const int q = warp & 3;
-    const int rowq = q * 32 + lane;
+    float* mystg = reinterpret_cast<float*>(stg + (uint32_t)(warp - 6) * stg_bytes);
     uint32_t accit = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-      const int64_t row = tile * 128 + rowq;
+      const int row0 = (int)(tile * 128) + q * 32;
       for (int c = 0; c < nchunks; ++c, ++accit) {
         const uint32_t ab = accit % AR_ACC;
         if (!mbar_wait(&accf[ab], (accit / AR_ACC) & 1, abort_flag)) {
@@ -601,22 +617,26 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           break;
         }
         tc_after();
-#pragma unroll
-        for (int c0 = 0; c0 < AR_BN; c0 += 16) {
+        // the previous store from this warp's staging buffer must have read it
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        for (int c0 = 0; c0 < bn; c0 += 16) {
           float v[16];
-          tmem_ld16(tmem + ab * AR_BN + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
-          if (row < n) {
+          tmem_ld16(tmem + ab * (uint32_t)bn + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int col = c * AR_BN + c0 + j;
-              if (col < N) C[(int64_t)col * ldc + row] = v[j];
-            }
-          }
+          for (int j = 0; j < 16; ++j) mystg[(c0 + j) * 32 + lane] = v[j];
         }
         tc_before();
-        mbar_arrive(&acce[ab]);
+        mbar_arrive(&acce[ab]);   // TMEM slot free: the values are in shared memory
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmC, mystg, row0, c * bn);
+          bulk_commit();
+        }
       }
     }
+    if (lane == 0) bulk_wait0();
   }
   tc_before();
   __syncthreads();
@@ -902,9 +922,17 @@ constexpr int kMaxSmem = 227 * 1024;
 size_t bres_smem(int ksteps, int Np) {
   return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + NN_S * 8192 + NN_CS * 8192 + 256;
 }
-size_t ares_smem(int ksteps) {
-  const size_t chunk = ((size_t)2 * ksteps * AR_BN * 32 + 1023) & ~(size_t)1023;
-  return 1024 + (((size_t)2 * ksteps * 128 * 32 + 1023) & ~(size_t)1023) + AR_SA * 8192 + AR_NB * chunk + 256;
+size_t ares_smem(int ksteps, int bn) {
+  const size_t chunk = ((size_t)2 * ksteps * bn * 32 + 1023) & ~(size_t)1023;
+  return 1024 + (((size_t)2 * ksteps * 128 * 32 + 1023) & ~(size_t)1023) + AR_SA * 8192 + AR_NB * chunk +
+         4 * (size_t)32 * bn * 4 + 256;
+}
+
+// Widest frame chunk (64, 48, 32 or 16 columns) whose buffers fit in shared memory; 0 if none.
+int ares_bn(int ksteps) {
+  for (int bn = 64; bn >= 16; bn -= 16)
+    if (ares_smem(ksteps, bn) <= (size_t)kMaxSmem) return bn;
+  return 0;
 }
 size_t tn_smem(int Mt, int Np, int nsplit) {
   const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
@@ -932,8 +960,8 @@ size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N) {
   (void)n;
   const int ksteps = (int)ceil_div(Kd, 16);
   // recon layout (64-column chunks) is the larger of the two layouts
-  const int64_t nch = ceil_div(N, AR_BN);
-  const size_t ares = (size_t)nch * 2 * ksteps * AR_BN * 32;
+  const int64_t nch = ceil_div(N, 16);   // smallest chunk width gives the largest padding
+  const size_t ares = (size_t)nch * 2 * ksteps * 16 * 32 + (size_t)2 * ksteps * 64 * 32;
   const size_t bres = (size_t)2 * ksteps * round_up(N, 16) * 32 + 2 * ksteps * 256 * 32;
   return std::max(ares, bres) + 4096;
 }
@@ -964,18 +992,21 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
     DMD_LAUNCH_CHECK();
     return DMD_OK;
   }
-  // many output columns: A tile resident, B in 64-column chunks
-  const size_t smem = ares_smem(ksteps);
-  if (smem > (size_t)kMaxSmem) {
+  // many output columns: A tile resident, B streamed in bn-column chunks
+  const int bn = ares_bn(ksteps);
+  if (bn == 0) {
     set_error("umma_gemm_nn: inner dimension %d too large for the resident-A layout", Kd);
     return DMD_EINVAL;
   }
-  const int nchunks = (int)ceil_div(N, AR_BN);
-  const int64_t work = (int64_t)nchunks * AR_BN * ksteps;
-  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, AR_BN, ksteps, nchunks, split);
+  const size_t smem = ares_smem(ksteps, bn);
+  const int nchunks = (int)ceil_div(N, bn);
+  const int64_t work = (int64_t)nchunks * bn * ksteps;
+  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split);
   DMD_LAUNCH_CHECK();
+  CUtensorMap mapC;
+  DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, bn));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, ksteps, nchunks, ntiles, nullptr);
+  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, nchunks, ntiles, nullptr);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
