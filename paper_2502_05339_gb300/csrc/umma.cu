@@ -14,7 +14,7 @@
 //   k_umma_nn_bres : C = A B, A tall (n x Kd) streamed, B (Kd x N, N <= 256)
 //                    resident in shared memory -- sketch X Omega, power step
 //                    X Z, CholeskyQR step Y R^{-1}, modes X' M (Sec. 4.3, 3.1).
-//   k_umma_nn_ares : C = A B with A's 128-row tile resident and B streamed in
+//   k_umma_nn_ares : C = A B with A's 128-row tile resident in TMEM and B streamed in
 //                    column chunks -- the reconstruction Phi_R C of
 //                    Eq. large_time_step with K frames.
 //   k_umma_tn      : C = A^T B reduced over the tall dimension -- X^T Q, Q^T S
@@ -134,6 +134,21 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t adesc, uint64_t b
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
+// D[tmem] (+)= A[tmem] * B[smem]^T (A: 128 lanes = rows, 8 columns per 16-wide K-slice)
+__device__ __forceinline__ void umma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -443,48 +458,52 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
 
 // ============================================================ NN, A resident
 
-constexpr int AR_SA = 2;     // TMA stages for the A tile slices
-constexpr int AR_NB = 2;     // B chunk buffers
-constexpr int AR_ACC = 4;    // TMEM accumulators (bn columns each)
+constexpr int AR_MAXSA = 4;  // TMA stages for the A tile slices (runtime sa <= 4)
+constexpr int AR_MAXNB = 4;  // B chunk buffers (runtime nb <= 4)
+constexpr int AR_MAXKS = 16; // K-slices of the resident A tile (Kd <= 256)
+constexpr int AR_ACC = 2;    // TMEM accumulators (bn <= 128 columns each)
+constexpr int AR_ACOL = 256; // first TMEM column of the resident A (hi, then lo)
 constexpr int AR_THREADS = 320;
 
-// bn: frames per chunk (multiple of 16, <= 64).  Each epilogue warp stages its
-// 32-row x bn accumulator slice in shared memory and writes it with one TMA
-// store (box {32 rows, bn cols} of C).
+// C = A B with the 128-row tile of A resident in TENSOR memory (split into
+// bf16 hi / lo by the converter warps and written with tcgen05.st: lane =
+// row, 8 columns per 16-wide K-slice), the coefficient matrix B streamed in
+// bn-column chunks (bn <= 128) through a shared-memory ring.  Keeping A in
+// TMEM leaves shared memory for wide chunks: the MMA count per output column
+// is what bounds this kernel (measured: ~2.4 us per 30 MMAs whatever N).
+// Each epilogue warp writes its 32 rows in 16-column TMA stores through a
+// double-buffered 2 KB staging area.
 __global__ void __launch_bounds__(AR_THREADS, 1)
     k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
-                   const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int nchunks,
-                   int64_t ntiles, int32_t* err) {
+                   const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int sa, int nb,
+                   int nchunks, int64_t ntiles, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
-  const uint32_t ares_bytes = 2u * (uint32_t)ksteps * 128u * 32u;            // hi then lo
   const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * (uint32_t)bn * 32u;
   const uint32_t bstride = (chunk_bytes + 1023u) & ~1023u;
-  const uint32_t stg_bytes = 32u * (uint32_t)bn * 4u;                        // per epilogue warp
-  uint8_t* Ares = sm;
-  uint8_t* stA = Ares + ((ares_bytes + 1023u) & ~1023u);
-  uint8_t* Bbuf = stA + AR_SA * 8192;
-  uint8_t* stg = Bbuf + AR_NB * bstride;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * stg_bytes);
+  uint8_t* stA = sm;
+  uint8_t* Bbuf = stA + sa * 8192;
+  uint8_t* stg = Bbuf + nb * bstride;            // 4 warps x 2 buffers x 2 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * 2 * 2048);
   uint64_t* afull = bars;               // TMA slice landed
-  uint64_t* aempty = afull + AR_SA;     // slice converted
-  uint64_t* bfull = aempty + AR_SA;
-  uint64_t* bempty = bfull + AR_NB;
-  uint64_t* accf = bempty + AR_NB;
+  uint64_t* aempty = afull + AR_MAXSA;  // slice converted
+  uint64_t* bfull = aempty + AR_MAXSA;
+  uint64_t* bempty = bfull + AR_MAXNB;
+  uint64_t* accf = bempty + AR_MAXNB;
   uint64_t* acce = accf + AR_ACC;
-  uint64_t* ares_full = acce + AR_ACC;  // converters finished the tile's A
-  uint64_t* ares_free = ares_full + 1;  // MMAs of the tile finished reading A
+  uint64_t* ares_full = acce + AR_ACC;  // [AR_MAXKS]: slice ks of the tile's A is in TMEM
+  uint64_t* ares_free = ares_full + AR_MAXKS;  // MMAs of the tile finished reading A
   uint64_t* tdown = ares_free + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < AR_SA; ++i) {
+    for (int i = 0; i < AR_MAXSA; ++i) {
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 128);
     }
-    for (int i = 0; i < AR_NB; ++i) {
+    for (int i = 0; i < AR_MAXNB; ++i) {
       mbar_init(&bfull[i], 1);
       mbar_init(&bempty[i], 1);
     }
@@ -492,13 +511,13 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
       mbar_init(&accf[i], 1);
       mbar_init(&acce[i], 128);
     }
-    mbar_init(ares_full, 128);
+    for (int i = 0; i < AR_MAXKS; ++i) mbar_init(&ares_full[i], 128);
     mbar_init(ares_free, 1);
     mbar_init(tdown, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(tslot, 256);
+  if (warp == 1) tmem_alloc(tslot, 512);
   tc_before();
   __syncthreads();
   tc_after();
@@ -508,23 +527,23 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     if (lane == 0) {
       uint32_t ait = 0, bit = 0;
       bool ok = true;
-      bool a_issued[AR_SA] = {false, false}, b_issued[AR_NB] = {false, false};
-      uint32_t a_par[AR_SA] = {0, 0}, b_par[AR_NB] = {0, 0};
+      bool a_issued[AR_MAXSA] = {false, false, false, false}, b_issued[AR_MAXNB] = {false, false, false, false};
+      uint32_t a_par[AR_MAXSA] = {0, 0, 0, 0}, b_par[AR_MAXNB] = {0, 0, 0, 0};
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         for (int ks = 0; ks < ksteps; ++ks, ++ait) {
-          const uint32_t s = ait % AR_SA;
-          if (!mbar_wait(&aempty[s], ((ait / AR_SA) & 1) ^ 1, abort_flag)) {
+          const uint32_t s = ait % sa;
+          if (!mbar_wait(&aempty[s], ((ait / sa) & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           mbar_expect_tx(&afull[s], 8192);
           tma_load_2d(stA + s * 8192, &tmA, &afull[s], (int)(tile * 128), ks * 16);
           a_issued[s] = true;
-          a_par[s] = (ait / AR_SA) & 1;
+          a_par[s] = (ait / sa) & 1;
         }
         for (int c = 0; ok && c < nchunks; ++c, ++bit) {
-          const uint32_t b = bit % AR_NB;
-          if (!mbar_wait(&bempty[b], ((bit / AR_NB) & 1) ^ 1, abort_flag)) {
+          const uint32_t b = bit % nb;
+          if (!mbar_wait(&bempty[b], ((bit / nb) & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
@@ -533,43 +552,47 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           for (uint32_t off = 0; off < chunk_bytes; off += 32768u)
             bulk_g2s(Bbuf + b * bstride + off, src + off, min(32768u, chunk_bytes - off), &bfull[b]);
           b_issued[b] = true;
-          b_par[b] = (bit / AR_NB) & 1;
+          b_par[b] = (bit / nb) & 1;
         }
       }
-      for (int i = 0; i < AR_SA; ++i)
+      for (int i = 0; i < sa; ++i)
         if (a_issued[i]) mbar_wait_drain(&afull[i], a_par[i]);
-      for (int i = 0; i < AR_NB; ++i)
+      for (int i = 0; i < nb; ++i)
         if (b_issued[i]) mbar_wait_drain(&bfull[i], b_par[i]);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, bn);
+      const uint32_t a_hi = tmem + AR_ACOL, a_lo = tmem + AR_ACOL + (uint32_t)ksteps * 8u;
       uint32_t tit = 0, bit = 0, accit = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
-        if (!mbar_wait(ares_full, tit & 1, abort_flag)) break;
-        tc_after();
         for (int c = 0; c < nchunks; ++c, ++bit, ++accit) {
-          const uint32_t b = bit % AR_NB, ab = accit % AR_ACC;
-          if (!mbar_wait(&bfull[b], (bit / AR_NB) & 1, abort_flag) ||
+          const uint32_t b = bit % nb, ab = accit % AR_ACC;
+          if (!mbar_wait(&bfull[b], (bit / nb) & 1, abort_flag) ||
               !mbar_wait(&acce[ab], ((accit / AR_ACC) & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           tc_after();
-          const uint32_t d = tmem + ab * (uint32_t)bn;
+          const uint32_t d = tmem + ab * 128u;
           const uint32_t bbase = su32(Bbuf + b * bstride);
           for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t ah = su32(Ares) + (uint32_t)ks * 4096u;
-            const uint32_t al = su32(Ares) + (uint32_t)(ksteps + ks) * 4096u;
+            if (c == 0) {   // the tile's first chunk follows the conversion slice by slice
+              if (!mbar_wait(&ares_full[ks], tit & 1, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_after();
+            }
             const uint32_t bh = bbase + (uint32_t)ks * (uint32_t)bn * 32u;
             const uint32_t bl = bbase + (uint32_t)(ksteps + ks) * (uint32_t)bn * 32u;
-            const uint64_t ahd = sdesc(ah, kLBO, kSBO), ald = sdesc(al, kLBO, kSBO);
             const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
-            umma_bf16(d, ahd, bhd, idesc, ks > 0 ? 1u : 0u);
-            umma_bf16(d, ahd, bld, idesc, 1u);
-            umma_bf16(d, ald, bhd, idesc, 1u);
+            umma_bf16_ta(d, a_hi + (uint32_t)ks * 8u, bhd, idesc, ks > 0 ? 1u : 0u);
+            umma_bf16_ta(d, a_hi + (uint32_t)ks * 8u, bld, idesc, 1u);
+            umma_bf16_ta(d, a_lo + (uint32_t)ks * 8u, bhd, idesc, 1u);
           }
+          if (!ok) break;
           umma_commit(&bempty[b]);
           umma_commit(&accf[ab]);
         }
@@ -580,33 +603,45 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
       mbar_wait_drain(tdown, 0);
     }
   } else if (warp < 6) {
-    const int t = threadIdx.x - 64;
+    // converters: warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. those rows of the tile
+    const int q = warp & 3;
+    const int t = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     uint32_t ait = 0, tit = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
       // the previous tile's MMAs must be done with the resident A
       if (tit > 0 && !mbar_wait(ares_free, (tit - 1) & 1, abort_flag)) break;
+      tc_after();
       for (int ks = 0; ks < ksteps; ++ks, ++ait) {
-        const uint32_t s = ait % AR_SA;
-        if (!mbar_wait(&afull[s], (ait / AR_SA) & 1, abort_flag)) {
+        const uint32_t s = ait % sa;
+        if (!mbar_wait(&afull[s], (ait / sa) & 1, abort_flag)) {
           ok = false;
           break;
         }
         const float* src = reinterpret_cast<const float*>(stA + s * 8192);
-        float x[16];
+        uint32_t h[8], l[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];
-        split_store_row(x, Ares + (uint32_t)ks * 4096u, Ares + (uint32_t)(ksteps + ks) * 4096u, t);
+        for (int i = 0; i < 8; ++i) {
+          const float x0 = src[(2 * i) * 128 + t], x1 = src[(2 * i + 1) * 128 + t];
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+          h[i] = pack2(h0, h1);
+          l[i] = pack2(__float2bfloat16_rn(x0 - __bfloat162float(h0)), __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+        }
+        tmem_st8(tmem + AR_ACOL + (uint32_t)ks * 8u + lane_base, h);
+        tmem_st8(tmem + AR_ACOL + (uint32_t)(ksteps + ks) * 8u + lane_base, l);
+        tmem_st_wait();
         mbar_arrive(&aempty[s]);
+        tc_before();
+        mbar_arrive(&ares_full[ks]);
       }
       if (!ok) break;
-      fence_async_smem();
-      mbar_arrive(ares_full);
     }
   } else {
     const int q = warp & 3;
-    float* mystg = reinterpret_cast<float*>(stg + (uint32_t)(warp - 6) * stg_bytes);
+    float* mystg = reinterpret_cast<float*>(stg + (uint32_t)(warp - 6) * 2u * 2048u);
     uint32_t accit = 0;
+    int sbuf = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const int row0 = (int)(tile * 128) + q * 32;
@@ -617,23 +652,26 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           break;
         }
         tc_after();
-        // the previous store from this warp's staging buffer must have read it
-        if (lane == 0) bulk_wait_read0();
-        __syncwarp();
-        for (int c0 = 0; c0 < bn; c0 += 16) {
+        const int cend = min(bn, N - c * bn);   // the last chunk may be ragged
+        for (int c0 = 0; c0 < cend; c0 += 16) {
           float v[16];
-          tmem_ld16(tmem + ab * (uint32_t)bn + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+          tmem_ld16(tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+          // the store issued two rounds ago from this buffer must have read it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+          float* buf = mystg + sbuf * 512;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) mystg[(c0 + j) * 32 + lane] = v[j];
+          for (int j = 0; j < 16; ++j) buf[j * 32 + lane] = v[j];
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmC, buf, row0, c * bn + c0);
+            bulk_commit();
+          }
+          sbuf ^= 1;
         }
         tc_before();
-        mbar_arrive(&acce[ab]);   // TMEM slot free: the values are in shared memory
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          tma_store_2d(&tmC, mystg, row0, c * bn);
-          bulk_commit();
-        }
+        mbar_arrive(&acce[ab]);
       }
     }
     if (lane == 0) bulk_wait0();
@@ -642,7 +680,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8002);
 }
@@ -922,17 +960,25 @@ constexpr int kMaxSmem = 227 * 1024;
 size_t bres_smem(int ksteps, int Np) {
   return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + NN_S * 8192 + NN_CS * 8192 + 256;
 }
-size_t ares_smem(int ksteps, int bn) {
+size_t ares_smem(int ksteps, int bn, int sa, int nb) {
   const size_t chunk = ((size_t)2 * ksteps * bn * 32 + 1023) & ~(size_t)1023;
-  return 1024 + (((size_t)2 * ksteps * 128 * 32 + 1023) & ~(size_t)1023) + AR_SA * 8192 + AR_NB * chunk +
-         4 * (size_t)32 * bn * 4 + 256;
+  return 1024 + (size_t)sa * 8192 + (size_t)nb * chunk + 4 * 2 * 2048 + 512;
 }
 
-// Widest frame chunk (64, 48, 32 or 16 columns) whose buffers fit in shared memory; 0 if none.
-int ares_bn(int ksteps) {
-  for (int bn = 64; bn >= 16; bn -= 16)
-    if (ares_smem(ksteps, bn) <= (size_t)kMaxSmem) return bn;
-  return 0;
+struct AresCfg {
+  int bn, sa, nb;
+};
+// Configuration override for tuning sweeps (bn = 0: automatic).
+AresCfg g_ares_override = {0, 0, 0};
+
+// Widest frame chunk (64, 48, 32 or 16 columns), then the deepest rings, that fit in shared memory.
+AresCfg ares_cfg(int ksteps) {
+  if (g_ares_override.bn) return g_ares_override;
+  for (int bn = 128; bn >= 16; bn -= 16)
+    for (int nb = 3; nb >= 2; --nb)
+      for (int sa = 3; sa >= 2; --sa)
+        if (ares_smem(ksteps, bn, sa, nb) <= (size_t)kMaxSmem) return {bn, sa, nb};
+  return {0, 0, 0};
 }
 size_t tn_smem(int Mt, int Np, int nsplit) {
   const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
@@ -961,7 +1007,7 @@ size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N) {
   const int ksteps = (int)ceil_div(Kd, 16);
   // recon layout (64-column chunks) is the larger of the two layouts
   const int64_t nch = ceil_div(N, 16);   // smallest chunk width gives the largest padding
-  const size_t ares = (size_t)nch * 2 * ksteps * 16 * 32 + (size_t)2 * ksteps * 64 * 32;
+  const size_t ares = (size_t)nch * 2 * ksteps * 16 * 32 + (size_t)2 * ksteps * 128 * 32;
   const size_t bres = (size_t)2 * ksteps * round_up(N, 16) * 32 + 2 * ksteps * 256 * 32;
   return std::max(ares, bres) + 4096;
 }
@@ -993,20 +1039,22 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
     return DMD_OK;
   }
   // many output columns: A tile resident, B streamed in bn-column chunks
-  const int bn = ares_bn(ksteps);
-  if (bn == 0) {
+  const AresCfg cfg = ares_cfg(ksteps);
+  const int bn = cfg.bn;
+  if (bn == 0 || ksteps > AR_MAXKS || ares_smem(ksteps, bn, cfg.sa, cfg.nb) > (size_t)kMaxSmem) {
     set_error("umma_gemm_nn: inner dimension %d too large for the resident-A layout", Kd);
     return DMD_EINVAL;
   }
-  const size_t smem = ares_smem(ksteps, bn);
+  const size_t smem = ares_smem(ksteps, bn, cfg.sa, cfg.nb);
   const int nchunks = (int)ceil_div(N, bn);
   const int64_t work = (int64_t)nchunks * bn * ksteps;
   k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split);
   DMD_LAUNCH_CHECK();
   CUtensorMap mapC;
-  DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, bn));
+  DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, 16));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, nchunks, ntiles, nullptr);
+  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks, ntiles,
+                                                  nullptr);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
