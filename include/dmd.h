@@ -189,6 +189,37 @@ DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float
                             double* d_modal, float* d_u, void* workspace, size_t ws_bytes,
                             void* stream);
 
+/* ---- prediction without allocation --------------------------------------- */
+
+/* Size of the library's fixed device scratch array used by dmd_predict_noalloc
+ * (held on every GPU that loads the library until the process exits). */
+#define DMD_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+
+/* dmd_predict for callers that cannot allocate GPU memory.  The paper has no
+ * counterpart: it is an interface for applications that drive the prediction
+ * from an interactive frame loop, reserve their GPU memory once under their
+ * own allocator and forbid cudaMalloc / cudaFree afterwards (those calls can
+ * synchronise the device and stall a frame), or that host this library as a
+ * plug-in without giving it an allocator.
+ * Arguments, layouts and results are those of dmd_predict: the caller owns
+ * and passes every input and the output frames; the workspace comes from a
+ * fixed DMD_NOALLOC_SCRATCH_BYTES array inside the library instead.  Nothing
+ * is allocated: no cudaMalloc, no cudaFree, no allocating library routine.
+ * Limits and errors: DMD_EINVAL (with a message naming the bytes needed) when
+ * the forward pass's workspace (the r x K FP64 coefficients, the control
+ * rollout and the product's scratch) exceeds DMD_NOALLOC_SCRATCH_BYTES; for
+ * r = 150 without control that is about K = 9000 frames.  Otherwise the
+ * errors of dmd_predict.
+ * Set-up: the first call on each device looks up the array's device address
+ * on that (current) device; make that first call before any stream capture.
+ * Sharing: every call on a device uses the same array, and the array keeps
+ * the previous call's contents (each call clears the part it uses before
+ * use).  Calls whose GPU work overlaps -- on different streams, or from
+ * different host threads -- race on the array and give wrong frames; order
+ * them on one stream or with events. */
+DMD_EXPORT dmd_status dmd_predict_noalloc(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                               const int32_t* k, const float* u, float* out, void* stream);
+
 /* ---- component entry points (the building blocks, exposed for tests) ------ */
 
 /* Omega (m x l FP64, ld m) ~ N(0, 1) from Philox4x32-10 (Salmon et al. 2011):

@@ -661,3 +661,36 @@ dmd_status dmd_gemm_tn(int32_t precision, int64_t n, int32_t Ka, int32_t N, cons
 }
 
 }  // extern "C"
+
+namespace dmd {
+
+// Forward prediction with a workspace sized for the forward pass alone (the
+// coefficient matrix, the control rollout and the tall product's scratch);
+// dmd_predict_workspace_bytes covers the backward and loss passes as well.
+// Used by dmd_predict_noalloc, whose workspace is a fixed device array.
+dmd_status predict_forward_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_predict(desc, true));
+  Arena a;
+  PredBufs b;
+  carve_predict(a, *desc, 0, b);
+  *bytes = a.used + 256;
+  return DMD_OK;
+}
+
+dmd_status predict_forward(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
+                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st) {
+  DMD_TRY(validate_predict(desc, true));
+  DMD_REQUIRE(Phi_R && modal && k && out, "dmd_predict_noalloc: NULL pointer argument");
+  DMD_REQUIRE(desc->q == 0 || u != nullptr || desc->steps == 0, "dmd_predict_noalloc: q > 0 needs u");
+  size_t need = 0;
+  DMD_TRY(predict_forward_workspace_bytes(desc, &need));
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    PredBufs b;
+    carve_predict(a, *desc, 0, b);
+    DMD_TRY(form_coefficients(*desc, modal, k, u, b, st));
+    const Tall tall{desc->precision};
+    return tall.nn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, out, desc->ldOut, b.gemm_ws, st);
+  }, need);
+}
+
+}  // namespace dmd

@@ -57,6 +57,7 @@ SIGNATURES = {
     "dmd_fit": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "dmd_predict_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _SZ]),
     "dmd_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_predict_noalloc": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P]),
     "dmd_predict_backward": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, _P, _P,
                                               ctypes.c_size_t, _P]),
     "dmd_predict_loss": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_int32,
@@ -231,6 +232,23 @@ def dmd_predict(model: DmdModel, ks, *, u: torch.Tensor | None = None, precision
     md = model.modal if modal is None else modal
     _check(lib().dmd_predict(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(out),
                              _ptr(ws), ws.numel(), _stream(dev)), "dmd_predict")
+    return out
+
+
+def dmd_predict_noalloc(model: DmdModel, ks, out: torch.Tensor, *, u: torch.Tensor | None = None,
+                        precision="fp32", modal: torch.Tensor | None = None) -> torch.Tensor:
+    """dmd_predict into a caller-provided `out` (K, ldOut) float32 without any
+    workspace: the library uses its fixed device scratch array
+    (DMD_NOALLOC_SCRATCH_BYTES) instead of allocating.  `ks` should already be
+    an int32 CUDA tensor if the caller must not allocate at all."""
+    dev = model.Phi_R.device
+    kt = _ks_tensor(ks, dev)
+    _need_cuda(out, "out", torch.float32)
+    steps = 0 if u is None else u.shape[0]
+    d = _pdesc(model, kt.numel(), out.shape[1], precision, steps)
+    md = model.modal if modal is None else modal
+    _check(lib().dmd_predict_noalloc(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(out),
+                                     _stream(dev)), "dmd_predict_noalloc")
     return out
 
 
