@@ -122,6 +122,42 @@ def exact_dmd(S: np.ndarray, r: int) -> dict:
     return dict(U=U, s=s, V=V, Atilde=At, lam=lam, W=W, M=M, Phi=Phi, b=b)
 
 
+def gram_blocks(Wg: np.ndarray):
+    """From Wg = S^T S with S = [x_0 .. x_m] (Eq. reduced_koopman):
+    X^T X, X^T X', X'^T X' and X'^T x_0."""
+    Wg = np.asarray(Wg, dtype=np.float64)
+    return Wg[:-1, :-1], Wg[:-1, 1:], Wg[1:, 1:], Wg[1:, 0]
+
+
+def exact_dmd_from_gram(Wg: np.ndarray, r: int, Xp_rows: np.ndarray) -> dict:
+    """Exact DMD at rank r (same definition as exact_dmd, Sec. 3.1) evaluated
+    from inner products, for snapshot matrices too tall to decompose in FP64.
+
+    Inputs: the Gram matrix Wg = S^T S of S = [x_0 .. x_m] ((m+1) x (m+1),
+    FP64) and some rows of X' (the modes are returned at those rows only).
+    The truncated SVD X = U Sigma V^T is taken from X^T X = V Sigma^2 V^T
+    (method of snapshots; U = X V Sigma^{-1} is never formed), so
+      A~  = U^T X' V Sigma^{-1} = Sigma^{-1} V^T (X^T X') V Sigma^{-1}
+      Phi = X' M with M = V Sigma^{-1} W           (rows of X' only)
+      b   solves (M^H X'^T X' M) b = M^H X'^T x_0   (normal equations of Eq. projection).
+    Rounding: relative errors grow like eps * (sigma_1 / sigma_r)^2."""
+    XtX, XtXp, XptXp, Xptx0 = gram_blocks(Wg)
+    ev, V = np.linalg.eigh(XtX)
+    idx = np.argsort(ev)[::-1][:r]
+    s, V = np.sqrt(ev[idx]), V[:, idx]
+    piv = np.argmax(np.abs(V), axis=0)
+    sgn = np.sign(V[piv, np.arange(r)])
+    sgn[sgn == 0] = 1.0
+    V = V * sgn
+    At = (V.T @ XtXp @ V) / s[:, None] / s[None, :]
+    lam, W = eig_canonical(At)
+    M = (V / s[None, :]) @ W
+    G = M.conj().T @ XptXp @ M
+    b = np.linalg.solve(G, M.conj().T @ Xptx0)
+    Phi_rows = np.asarray(Xp_rows, dtype=np.float64) @ M
+    return dict(s=s, V=V, Atilde=At, lam=lam, W=W, M=M, Phi_rows=Phi_rows, b=b)
+
+
 # ----------------------------------------------------------------------------
 # prediction (Eq. large_time_step) and its real 2x2-block form
 # ----------------------------------------------------------------------------

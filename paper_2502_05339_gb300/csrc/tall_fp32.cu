@@ -10,6 +10,7 @@
 //    the running total in FP64; the per-block FP64 partials are then added in
 //    a fixed order, so the result does not depend on scheduling.
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace dmd {
 
@@ -121,85 +122,177 @@ __global__ void __launch_bounds__(256) k_gemm_nn_f32(int64_t n, int Kd, int N, c
   }
 }
 
-constexpr int TN_BT = 64, TN_BR = 32, TN_PAD = 68;
+constexpr int TN_BT = 64, TN_BR = 32, TN_STAGES = 4, TN_THREADS = 128;
+constexpr uint32_t TN_BOX_BYTES = TN_BT * TN_BR * 4;        // one 32-row x 64-column box: 8 KB
+constexpr uint32_t TN_STAGE_BYTES = 2 * TN_BOX_BYTES;        // A and B boxes
+constexpr size_t TN_SMEM = 1024 + TN_STAGES * TN_STAGE_BYTES + 64;
 
-// C partial for one (Ka-tile, N-tile, split): 256 threads, 4x4 outputs each.
-__global__ void __launch_bounds__(256) k_gemm_tn_f32(int64_t n, int Ka, int N, const float* __restrict__ A,
-                                                     int64_t lda, const float* __restrict__ B,
-                                                     int64_t ldb, double* __restrict__ part,
-                                                     int nta, int ntb, int64_t chunk) {
-  __shared__ __align__(16) float As[TN_BR][TN_PAD];
-  __shared__ __align__(16) float Bs[TN_BR][TN_PAD];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int tile = blockIdx.x % (nta * ntb);
-  const int split = blockIdx.x / (nta * ntb);
-  const int a0 = (tile % nta) * TN_BT, b0 = (tile / nta) * TN_BT;
-  const int64_t rbeg = (int64_t)split * chunk;
-  const int64_t rend = min(n, rbeg + chunk);
-
-  // three-level sum: a 32-row tile in FP32, 32 tiles in FP32, then FP64
-  float acc[4][4], mid[4][4];
-  double tot[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) mid[i][j] = 0.f, tot[i][j] = 0.0;
-
-  int stretch = 0;
-  for (int64_t r0 = rbeg; r0 < rend; r0 += TN_BR) {
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int idx = tid + t * 256;             // 2048 = 64 cols x 32 rows
-      const int rr = idx & 31, c = idx >> 5;
-      const int64_t row = r0 + rr;
-      const bool rok = row < rend;
-      As[rr][c] = (rok && a0 + c < Ka) ? A[(int64_t)(a0 + c) * lda + row] : 0.f;
-      Bs[rr][c] = (rok && b0 + c < N) ? B[(int64_t)(b0 + c) * ldb + row] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 8
-    for (int rr = 0; rr < TN_BR; ++rr) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[rr][tx * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[rr][ty * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) mid[i][j] += acc[i][j];
-    if (++stretch == 32) {                       // 1024 rows, then fold into FP64
-      stretch = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] += (double)mid[i][j], mid[i][j] = 0.f;
-    }
+// Upper-triangle tile t of an nt x nt tile grid -> (ti, tj), ti <= tj.
+__device__ __forceinline__ void sym_tile(int t, int nt, int& ti, int& tj) {
+  ti = 0;
+  while (t >= nt - ti) {
+    t -= nt - ti;
+    ++ti;
   }
-  double* out = part + (int64_t)split * Ka * N;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int a = a0 + tx * 4 + i, b = b0 + ty * 4 + j;
-      if (a < Ka && b < N) out[(int64_t)b * Ka + a] = tot[i][j] + (double)mid[i][j];
-    }
+  tj = ti + t;
 }
 
-__global__ void k_reduce_splits(int64_t count, int splits, const double* __restrict__ part,
-                                double* __restrict__ C) {
+// Float4 of rows 4q..4q+3 of box column c in a 128-byte-swizzled box
+// (each column is one 128-byte line; its 16-byte chunks are XOR-permuted by
+// the line index mod 8, which makes the column-strided reads conflict-free).
+__device__ __forceinline__ float4 box_ld4(const uint8_t* box, int c, int q) {
+  return *reinterpret_cast<const float4*>(box + c * 128 + ((q ^ (c & 7)) << 4));
+}
+
+// Partial C = A^T B of one (64 x 64 tile, row split).  A box column c is
+// A[:, a0 + c] over 32 consecutive rows; TMA streams the boxes through a
+// 4-stage ring.  128 threads: warp w owns tile columns 16w .. 16w+15 (and
+// skips its work where they are all past N); lane (ta, tb) = (lane % 16,
+// lane / 16) owns the outputs (a0 + ta + 16 i, b0 + 16 w + tb + 2 j),
+// i < 4, j < 8.  Sums: 32 rows in FP32 (acc), 32 such tiles in FP32 (mid),
+// then FP64 in the per-split partial, which this CTA owns alone.  With
+// sym != 0 (A = B) only tiles ti <= tj are formed.
+__global__ void __launch_bounds__(TN_THREADS, 3)
+    k_gemm_tn_f32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
+                  int N, double* __restrict__ part, int nta, int ntb, int ntiles, int sym, int64_t chunk,
+                  int32_t* err) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + TN_STAGES * TN_STAGE_BYTES);
+  int* abort_flag = reinterpret_cast<int*>(full + TN_STAGES);
+
+  const int tile = blockIdx.x % ntiles;
+  const int split = blockIdx.x / ntiles;
+  int ti, tj;
+  if (sym) {
+    sym_tile(tile, nta, ti, tj);
+  } else {
+    ti = tile % nta;
+    tj = tile / nta;
+  }
+  const int a0 = ti * TN_BT, b0 = tj * TN_BT;
+  const int64_t rbeg = (int64_t)split * chunk;
+  const int64_t rend = min(n, rbeg + chunk);
+  const int nq = rbeg < rend ? (int)((rend - rbeg + TN_BR - 1) / TN_BR) : 0;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ta = lane & 15, tb = lane >> 4;
+  const bool active = b0 + 16 * warp < N;
+
+  if (tid == 0) {
+    for (int i = 0; i < TN_STAGES; ++i) mbar_init(&full[i], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0) {
+    for (; issued < min(nq, TN_STAGES); ++issued) {
+      uint8_t* buf = sm + issued * TN_STAGE_BYTES;
+      mbar_expect_tx(&full[issued], TN_STAGE_BYTES);
+      const int x = (int)(rbeg + (int64_t)issued * TN_BR);
+      tma_load_2d(buf, &tmA, &full[issued], x, a0);
+      tma_load_2d(buf + TN_BOX_BYTES, &tmB, &full[issued], x, b0);
+    }
+  }
+
+  float acc[4][8], mid[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mid[i][j] = 0.f;
+  double* out = part + (int64_t)split * Ka * N;
+  bool first = true;
+  auto flush = [&]() {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + 16 * warp + tb + 2 * j;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int a = a0 + ta + 16 * i;
+        if (a < Ka && b < N) {
+          double* o = out + (int64_t)b * Ka + a;
+          *o = first ? (double)mid[i][j] : *o + (double)mid[i][j];
+        }
+        mid[i][j] = 0.f;
+      }
+    }
+    first = false;
+  };
+
+  int stretch = 0;
+  for (int q = 0; q < nq; ++q) {
+    const int s = q % TN_STAGES;
+    const bool ok = mbar_wait(&full[s], (uint32_t)(q / TN_STAGES) & 1u, abort_flag);
+    if (ok && active) {
+      const uint8_t* Ab = sm + s * TN_STAGE_BYTES;
+      const uint8_t* Bb = Ab + TN_BOX_BYTES;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 1
+      for (int kq = 0; kq < TN_BR / 4; ++kq) {
+        float4 av[4], bv[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = box_ld4(Ab, ta + 16 * i, kq);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bv[j] = box_ld4(Bb, 16 * warp + tb + 2 * j, kq);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            acc[i][j] = fmaf(av[i].x, bv[j].x, acc[i][j]);
+            acc[i][j] = fmaf(av[i].y, bv[j].y, acc[i][j]);
+            acc[i][j] = fmaf(av[i].z, bv[j].z, acc[i][j]);
+            acc[i][j] = fmaf(av[i].w, bv[j].w, acc[i][j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mid[i][j] += acc[i][j];
+      if (++stretch == 32) {   // 1024 rows, then fold into FP64
+        stretch = 0;
+        flush();
+      }
+    }
+    // every thread has finished with stage s (or the CTA gives up)
+    if (__syncthreads_or(!ok)) break;
+    if (tid == 0 && issued < nq) {
+      uint8_t* buf = sm + s * TN_STAGE_BYTES;
+      mbar_expect_tx(&full[s], TN_STAGE_BYTES);
+      const int x = (int)(rbeg + (int64_t)issued * TN_BR);
+      tma_load_2d(buf, &tmA, &full[s], x, a0);
+      tma_load_2d(buf + TN_BOX_BYTES, &tmB, &full[s], x, b0);
+      ++issued;
+    }
+  }
+  if (active && (stretch > 0 || first)) flush();
+  // on an abort, let the loads still in flight land before the CTA exits
+  if (tid == 0 && *reinterpret_cast<volatile int*>(abort_flag)) {
+    for (int q = max(0, issued - TN_STAGES); q < issued; ++q)
+      mbar_wait_drain(&full[q % TN_STAGES], (uint32_t)(q / TN_STAGES) & 1u);
+    raise_status(err, DMD_ETIMEOUT, 8101);
+  }
+}
+
+// C = sum over splits, in split order.  With sym, entries below the diagonal
+// tiles come from their mirror.
+__global__ void k_reduce_splits(int Ka, int N, int splits, const double* __restrict__ part, double* __restrict__ C,
+                                int sym) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t count = (int64_t)Ka * N;
   if (i >= count) return;
+  int a = (int)(i % Ka), b = (int)(i / Ka);
+  if (sym && a / TN_BT > b / TN_BT) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  const int64_t src = (int64_t)b * Ka + a;
   double s = 0.0;
-  for (int p = 0; p < splits; ++p) s += part[(int64_t)p * count + i];
+  for (int p = 0; p < splits; ++p) s += part[(int64_t)p * count + src];
   C[i] = s;
 }
 
@@ -221,11 +314,11 @@ int sm_count() {
 
 }  // namespace
 
-// Number of row splits for the TN reduction: enough blocks to fill the GPU
-// about four times over, each split at least 1024 rows.
+// Row splits of the TN reduction: about four resident waves of CTAs (three
+// per SM), each split at least 1024 rows.
 int tn_splits(int64_t n, int Ka, int N) {
   const int tiles = (int)(ceil_div(Ka, TN_BT) * ceil_div(N, TN_BT));
-  int64_t want = ceil_div(4LL * 152, tiles);
+  int64_t want = ceil_div(4LL * 3 * sm_count(), tiles);
   const int64_t maxs = std::max<int64_t>(1, ceil_div(n, 1024));
   if (want > maxs) want = maxs;
   if (want > 1024) want = 1024;
@@ -248,14 +341,26 @@ dmd_status f32_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, co
 
 dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B,
                        int64_t ldb, double* C, double* part, cudaStream_t st) {
-  const int splits = tn_splits(n, Ka, N);
+  if (Ka <= 0 || N <= 0) return DMD_OK;
+  if (n <= 0) {
+    DMD_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)Ka * N * sizeof(double), st));
+    return DMD_OK;
+  }
+  int splits = tn_splits(n, Ka, N);
   const int64_t chunk = round_up(ceil_div(n, splits), TN_BR);
+  splits = (int)ceil_div(n, chunk);   // every split owns rows
   const int nta = (int)ceil_div(Ka, TN_BT), ntb = (int)ceil_div(N, TN_BT);
-  k_gemm_tn_f32<<<(unsigned)(nta * ntb * splits), 256, 0, st>>>(n, Ka, N, A, lda, B, ldb, part,
-                                                                 nta, ntb, chunk);
+  const bool sym = A == B && Ka == N && lda == ldb;
+  const int ntiles = sym ? nta * (nta + 1) / 2 : nta * ntb;
+  CUtensorMap mA, mB;
+  DMD_TRY(make_map(&mA, A, n, Ka, lda, TN_BR, TN_BT, true));
+  DMD_TRY(make_map(&mB, B, n, N, ldb, TN_BR, TN_BT, true));
+  DMD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TN_SMEM));
+  k_gemm_tn_f32<<<(unsigned)(ntiles * splits), TN_THREADS, TN_SMEM, st>>>(mA, mB, n, Ka, N, part, nta, ntb, ntiles,
+                                                                         sym ? 1 : 0, chunk, nullptr);
   DMD_LAUNCH_CHECK();
   const int64_t count = (int64_t)Ka * N;
-  k_reduce_splits<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, splits, part, C);
+  k_reduce_splits<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(Ka, N, splits, part, C, sym ? 1 : 0);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

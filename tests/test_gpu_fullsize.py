@@ -1,0 +1,72 @@
+"""Parity at the full 128^3 x 3 size (n = 6,291,456 values per snapshot,
+m = 200, rank 150, oversampling 10, two power iterations, frames k = 0..999):
+the launch configuration the benchmark times, in both precision forms.
+
+The FP64 oracle cannot decompose the 6.3M x 200 snapshot matrix directly in a
+test, so it evaluates the same exact-DMD definition from inner products: the
+snapshot Gram S^T S is formed on the host in FP64 (column blocks of the same
+FP32 snapshots the GPU sees), and modes and frames are evaluated at 4,098
+sampled rows (random rows plus the first and the last, ragged-tail, row)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dmd_oracle as O
+from paper_2502_05339_gb300 import synth
+from tests.gpu_util import match, mode_product_error, rel
+
+pytestmark = pytest.mark.gpu
+
+BAR = {"fp32": 1e-5, "mixed": 1e-4}
+R, OVERSAMPLE, POWER, FRAMES, SEED = 150, 10, 2, 1000, 1001
+
+
+@pytest.fixture(scope="module")
+def dmd():
+    from paper_2502_05339_gb300 import build_lib
+    build_lib.build()
+    from paper_2502_05339_gb300 import dmd as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def scene_and_oracle():
+    sc = synth.config1(seed=SEED, device="cuda")
+    S, n = sc.S, sc.n
+    mp1 = S.shape[0]
+    Wg = np.zeros((mp1, mp1))
+    step = 1 << 20
+    for a in range(0, n, step):
+        blk = S[:, a:min(n, a + step)].cpu().numpy().astype(np.float64)
+        Wg += blk @ blk.T
+    g = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, n - 1], g.choice(n, 4096, replace=False)]))
+    Srows = S[:, torch.as_tensor(rows, device=S.device)].cpu().numpy().astype(np.float64).T   # rows x (m+1)
+    ref = O.exact_dmd_from_gram(Wg, R, Srows[:, 1:])
+    PhiR, beta, kinds = O.to_real_form(ref["Phi_rows"], ref["lam"], ref["b"])
+    frames = O.predict_real(PhiR, O.coefficients(ref["lam"], beta, range(FRAMES)))
+    return sc, rows, ref, PhiR, beta, frames
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_config1_full_size(dmd, scene_and_oracle, prec):
+    sc, rows, ref, PhiR_o, beta_o, frames_o = scene_and_oracle
+    model = dmd.dmd_fit(sc.S, sc.n, R, oversample=OVERSAMPLE, power_iters=POWER, precision=prec, seed=SEED)
+    model.check()
+    out = dmd.dmd_predict(model, torch.arange(FRAMES, dtype=torch.int32, device="cuda"), precision=prec)
+    ridx = torch.as_tensor(rows, device=out.device)
+    frames_g = out[:, ridx].double().cpu().numpy().T                 # rows x frames
+    PhiR_g = model.Phi_R[:, ridx].double().cpu().numpy().T
+    del out
+    torch.cuda.empty_cache()
+    lam_g, beta_g = model.lam(), model.beta()
+    # eigenvalues (matched), scale-free mode fields phi_j b_j and the frames at the sampled rows
+    _, worst = match(lam_g, ref["lam"])
+    frob, per_mode = mode_product_error(PhiR_g, beta_g, lam_g, PhiR_o, beta_o, ref["lam"])
+    err = rel(frames_g, frames_o)
+    print(f"[{prec}] eigenvalues max rel {worst:.3e}; mode products rel Frobenius {frob:.3e} "
+          f"(worst mode {per_mode.max():.3e}); frames rel Frobenius {err:.3e}")
+    assert worst < BAR[prec], ("eigenvalues", worst)
+    assert frob < BAR[prec], ("mode products", frob)
+    assert err < BAR[prec], ("frames", err)

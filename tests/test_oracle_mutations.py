@@ -34,6 +34,8 @@ def _pins():
     yield P.test_rsvd_exact_when_rank_le_sketch
     yield P.test_philox_published_vectors
     yield P.test_adjoint_matches_central_differences
+    yield P.test_gram_route_known_operator
+    yield P.test_gram_route_equals_svd_route
 
 
 def _count_failures():
@@ -128,6 +130,19 @@ def _mut_mode_products(PhiR, beta, kinds):
     return 2.0 * _orig_mode_products(PhiR, beta, kinds)   # dropped the 1/2
 
 
+_orig_gram_blocks = O.gram_blocks
+
+
+def _mut_gram_cross(Wg):
+    a, b, c, d = _orig_gram_blocks(Wg)
+    return a, b.T.copy(), c, d                 # X'^T X instead of X^T X'
+
+
+def _mut_gram_rhs(Wg):
+    a, b, c, d = _orig_gram_blocks(Wg)
+    return a, b, c, np.asarray(Wg, dtype=np.float64)[:-1, 0]   # X^T x_0 instead of X'^T x_0
+
+
 MUTATIONS = [
     ("split_snapshots", _mut_split, O),
     ("reduced_operator", _mut_reduced_scale, O),
@@ -141,6 +156,8 @@ MUTATIONS = [
     ("predict_adjoint", _mut_adjoint, O),
     ("philox4x32_10", _mut_philox, philox),
     ("mode_products", _mut_mode_products, O),
+    ("gram_blocks", _mut_gram_cross, O),
+    ("gram_blocks", _mut_gram_rhs, O),
 ]
 
 

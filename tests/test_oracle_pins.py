@@ -427,3 +427,45 @@ def test_mode_products_match_ground_truth(exact_cfg0):
         c = int(np.argmin(np.abs(lam_heads - lt)))
         truth = sc.amps_true[j] * (modes[2 * j] + 1j * modes[2 * j + 1])
         assert np.linalg.norm(got[:, c] - truth) < 1e-10 * np.linalg.norm(truth)
+
+
+# ------------------------------------------- exact DMD from inner products
+
+
+def test_gram_route_known_operator():
+    """The inner-product evaluation of exact DMD returns the generating
+    spectrum of a noise-free scene, and its mode fields phi_j b_j at sampled
+    rows equal the generator's a_j phi_true_j there."""
+    sc = synth.linear_modes_scene(12, 3, 5, 30, 78, keep_fp64=True)
+    S = sc.extra["S64"]
+    rows = np.array([0, 5, 1000, 3001, S.shape[0] - 1])
+    res = O.exact_dmd_from_gram(S.T @ S, 10, S[rows, 1:])
+    assert match_eigs(res["lam"], sc.lam_true) < 1e-9
+    PhiR, beta, kinds = O.to_real_form(res["Phi_rows"], res["lam"], res["b"])
+    got = O.mode_products(PhiR, beta, kinds)
+    heads = [c for c in range(len(kinds)) if kinds[c] != 2]
+    modes = sc.modes_true.numpy()
+    for j, lt in enumerate(sc.lam_true[0::2]):
+        c = int(np.argmin(np.abs(res["lam"][heads] - lt)))
+        truth = sc.amps_true[j] * (modes[2 * j, rows] + 1j * modes[2 * j + 1, rows])
+        assert np.linalg.norm(got[:, c] - truth) < 1e-8 * np.linalg.norm(truth)
+
+
+def test_gram_route_equals_svd_route():
+    """On noisy data (full-rank X, truncated at r) the inner-product
+    evaluation and the SVD evaluation of the same definition agree."""
+    sc = synth.linear_modes_scene(16, 2, 6, 40, 79, noise=1e-3, keep_fp64=True)
+    S = sc.extra["S64"]
+    r = 12
+    ref = O.exact_dmd(S, r)
+    rows = np.arange(0, S.shape[0], 7)
+    res = O.exact_dmd_from_gram(S.T @ S, r, S[rows, 1:])
+    # the inner-product route loses accuracy like eps (sigma_1 / sigma_r)^2
+    tol = 100 * np.finfo(float).eps * (ref["s"][0] / ref["s"][-1]) ** 2
+    np.testing.assert_allclose(res["s"], ref["s"], rtol=tol)
+    assert match_eigs(res["lam"], ref["lam"]) < tol
+    k1 = O.pair_kinds(ref["lam"])
+    k2 = O.pair_kinds(res["lam"])
+    p1 = O.mode_products(*O.to_real_form(ref["Phi"][rows], ref["lam"], ref["b"])[:2], k1)
+    p2 = O.mode_products(*O.to_real_form(res["Phi_rows"], res["lam"], res["b"])[:2], k2)
+    assert np.linalg.norm(p1 - p2) < tol * np.linalg.norm(p1)
