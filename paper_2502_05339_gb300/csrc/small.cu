@@ -692,26 +692,27 @@ __global__ void k_eig_layout(int n, const double* __restrict__ wr, const double*
                              double* __restrict__ lam_re, double* __restrict__ lam_im,
                              int* __restrict__ order_scratch, int32_t* info) {
   __shared__ int colstart[1024];
-  const int tid = threadIdx.x;
-  const int nheads = *nheads_ptr;
-  if (tid == 0) {
-    int* ord = order_scratch;
-    for (int h = 0; h < nheads; ++h) ord[h] = h;
-    for (int a = 1; a < nheads; ++a) {   // insertion sort: few hundred entries
-      const int key = ord[a];
-      const int ek = heads[key];
-      const double mk = hypot(wr[ek], wi[ek]), ik = wi[ek];
-      int b = a - 1;
-      while (b >= 0) {
-        const int eb = heads[ord[b]];
-        const double mb = hypot(wr[eb], wi[eb]), ib = wi[eb];
-        const bool before = (mk > mb) || (mk == mb && ik > ib);
-        if (!before) break;
-        ord[b + 1] = ord[b];
-        --b;
-      }
-      ord[b + 1] = key;
+  __shared__ double mag[1024];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nheads = min(*nheads_ptr, 1024);
+  int* ord = order_scratch;
+  for (int h = tid; h < nheads; h += bd) {
+    const int e = heads[h];
+    mag[h] = hypot(wr[e], wi[e]);
+  }
+  __syncthreads();
+  // stable rank sort: |lambda| descending, then Im descending, then head index
+  for (int h = tid; h < nheads; h += bd) {
+    const double mh = mag[h], ih = wi[heads[h]];
+    int rank = 0;
+    for (int g = 0; g < nheads; ++g) {
+      const double mg = mag[g], ig = wi[heads[g]];
+      rank += (mg > mh) || (mg == mh && (ig > ih || (ig == ih && g < h)));
     }
+    ord[rank] = h;
+  }
+  __syncthreads();
+  if (tid == 0) {
     int c = 0, pairs = 0, reals = 0;
     for (int h = 0; h < nheads; ++h) {
       colstart[h] = c;
@@ -739,13 +740,14 @@ __global__ void k_eig_layout(int n, const double* __restrict__ wr, const double*
     }
   }
   __syncthreads();
-  for (int h = 0; h < nheads; ++h) {
-    const int src = order_scratch[h];
+  const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  for (int h = warp; h < nheads; h += nw) {
+    const int src = ord[h];
     const int e = heads[src];
     const int c = colstart[h];
     if (c < 0) continue;
     const bool pair = wi[e] > 0.0;
-    for (int i = tid; i < n; i += blockDim.x) {
+    for (int i = lane; i < n; i += 32) {
       WR[i + (int64_t)c * n] = Yre[i + (int64_t)src * n];
       if (pair) WR[i + (int64_t)(c + 1) * n] = Yim[i + (int64_t)src * n];
     }
@@ -992,6 +994,322 @@ __global__ void k_lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, 
   }
 }
 
+// ------------------------------------------- shared-memory resident variants
+//
+// The same algorithms with the matrix held in shared memory (leading dimension
+// n | 1, odd, so that a warp reading a row touches distinct banks): the
+// global-memory versions above stream every column through L2 with strided,
+// uncoalesced accesses, which dominates their run time.  Loops are arranged
+// warp-per-column / lane-per-row (contiguous in shared memory), with no
+// integer division.  Used whenever the matrix fits (n up to ~160).
+
+constexpr size_t kSmallSmemMax = 220 * 1024;
+
+__device__ __forceinline__ void load_square(double* S, int ldw, const double* G, int ld, int rows, int cols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = warp; b < cols; b += nw)
+    for (int a = lane; a < rows; a += 32) S[a + b * ldw] = G[a + (int64_t)b * ld];
+}
+__device__ __forceinline__ void store_square(double* G, int ld, const double* S, int ldw, int rows, int cols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = warp; b < cols; b += nw)
+    for (int a = lane; a < rows; a += 32) G[a + (int64_t)b * ld] = S[a + b * ldw];
+}
+
+// Cholesky as k_cholesky_upper (same pivot / drop rule), matrix in shared memory.
+__global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+  extern __shared__ double sm[];
+  const int ldw = n | 1;
+  double* S = sm;
+  double* r = S + n * ldw;      // row j of R, contiguous
+  double* red = r + n;
+  __shared__ double piv;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = G[a + (int64_t)b * ld];
+  double loc = 0.0;
+  for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
+  const double dmax = block_max(loc, red);
+  const double floor_ = tau * dmax;
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double d = S[j + j * ldw];
+      if (!isfinite(d) || !isfinite(dmax)) {
+        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+        piv = -1.0;
+      } else if (!(dmax > 0.0)) {
+        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+        piv = -1.0;
+      } else if (!(d > floor_)) {
+        piv = 0.0;   // dropped direction
+        if (info) atomicAdd(&info[5], 1);
+      } else {
+        piv = sqrt(d);
+      }
+      if (piv >= 0.0) S[j + j * ldw] = piv;
+    }
+    __syncthreads();
+    const double p = piv;
+    if (p < 0.0) return;
+    const double ip = p == 0.0 ? 0.0 : 1.0 / p;
+    for (int i = j + 1 + tid; i < n; i += bd) {
+      const double v = p == 0.0 ? 0.0 : S[j + i * ldw] * ip;
+      S[j + i * ldw] = v;
+      r[i] = v;
+    }
+    __syncthreads();
+    if (p == 0.0) continue;
+    for (int b = j + 1 + warp; b < n; b += nw) {
+      const double rb = r[b];
+      double* col = S + b * ldw;
+      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fma(-r[a], rb, col[a]);
+    }
+    __syncthreads();
+  }
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? S[a + b * ldw] : 0.0;
+}
+
+// T = R^{-1} as k_tri_inv_upper; every CTA first copies the columns it needs
+// (0 .. its last column) of R into shared memory.  One warp per column.
+__global__ void k_tri_inv_smem(int n, const double* __restrict__ R, int ldr, double* __restrict__ T, int ldt) {
+  extern __shared__ double sm[];
+  const int ldw = n | 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int jfirst = blockIdx.x * nw;
+  const int jlast = min(n - 1, jfirst + nw - 1);
+  double* S = sm;
+  double* tv = S + (jlast + 1) * ldw;   // nw vectors of n
+  for (int b = warp; b <= jlast; b += nw)
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = R[a + (int64_t)b * ldr];
+  __syncthreads();
+  const int j = jfirst + warp;
+  if (j > jlast) return;
+  double* t = tv + warp * n;
+  double* out = T + (int64_t)j * ldt;
+  for (int i = j + 1 + lane; i < n; i += 32) out[i] = 0.0;
+  const double rjj = S[j + j * ldw];
+  if (rjj == 0.0) {
+    for (int i = lane; i <= j; i += 32) out[i] = 0.0;
+    return;
+  }
+  if (lane == 0) t[j] = 1.0 / rjj;
+  __syncwarp();
+  for (int i = j - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1 + lane; k <= j; k += 32) s = fma(S[i + k * ldw], t[k], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double rii = S[i + i * ldw];
+      t[i] = (rii == 0.0) ? 0.0 : -s / rii;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i <= j; i += 32) out[i] = t[i];
+}
+
+// Householder reflector of x[0..m) (x[0] = alpha): v (v[0] = 1) into v[],
+// returns tau and beta; x itself is not modified.  Block-wide.
+__device__ __forceinline__ void house(const double* x, int m, double* v, double* red, double& tau, double& beta) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double loc = 0.0;
+  for (int i = 1 + tid; i < m; i += bd) loc += x[i] * x[i];
+  const double sig = block_sum(loc, red);
+  const double alpha = x[0];
+  if (sig == 0.0) {
+    tau = 0.0;
+    beta = alpha;
+    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : 0.0;
+  } else {
+    const double nrm = sqrt(alpha * alpha + sig);
+    beta = alpha <= 0.0 ? nrm : -nrm;
+    tau = (beta - alpha) / beta;
+    const double sc = 1.0 / (alpha - beta);
+    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : x[i] * sc;
+  }
+  __syncthreads();
+}
+
+// Tridiagonalisation as k_sytrd (same reflector storage), A in shared memory.
+__global__ void k_sytrd_smem(int n, double* A, int ld, double* tau) {
+  extern __shared__ double sm[];
+  const int ldw = n | 1;
+  double* S = sm;
+  double* v = S + n * ldw;
+  double* w = v + n;
+  double* red = w + n;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  load_square(S, ldw, A, ld, n, n);
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = S + k * ldw + (k + 1);
+    double t, beta;
+    house(x, m, v, red, t, beta);
+    if (t == 0.0) {
+      if (tid == 0) tau[k] = 0.0;
+      continue;
+    }
+    for (int i = 1 + tid; i < m; i += bd) x[i] = v[i];
+    if (tid == 0) {
+      x[0] = beta;
+      S[k + (k + 1) * ldw] = beta;
+      tau[k] = t;
+    }
+    double* A22 = S + (k + 1) * ldw + (k + 1);
+    // p = t * A22 v: row j of the symmetric A22 (contiguous across lanes = rows)
+    for (int j = tid; j < m; j += bd) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s = fma(A22[j + i * ldw], v[i], s);
+      w[j] = t * s;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = tid; i < m; i += bd) pv += w[i] * v[i];
+    pv = block_sum(pv, red);
+    for (int i = tid; i < m; i += bd) w[i] -= 0.5 * t * pv * v[i];
+    __syncthreads();
+    for (int j = warp; j < m; j += nw) {
+      const double vj = v[j], wj = w[j];
+      double* col = A22 + j * ldw;
+      for (int i = lane; i < m; i += 32) col[i] -= v[i] * wj + w[i] * vj;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) tau[k] = 0.0;
+  }
+  __syncthreads();
+  store_square(A, ld, S, ldw, n, n);
+}
+
+// Hessenberg reduction as k_hessenberg (same reflector storage), A in shared memory.
+__global__ void k_hessenberg_smem(int n, double* A, int ld, double* tau) {
+  extern __shared__ double sm[];
+  const int ldw = n | 1;
+  double* S = sm;
+  double* v = S + n * ldw;
+  double* w = v + n;
+  double* red = w + n;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  load_square(S, ldw, A, ld, n, n);
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double* x = S + k * ldw + (k + 1);
+    double t, beta;
+    house(x, m, v, red, t, beta);
+    if (t == 0.0) {
+      if (tid == 0) tau[k] = 0.0;
+      continue;
+    }
+    for (int i = 1 + tid; i < m; i += bd) x[i] = v[i];
+    if (tid == 0) {
+      x[0] = beta;
+      tau[k] = t;
+    }
+    // left: w_j = v . A[k+1.., j] for columns j = k+1..; then A -= t v w^T
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      const double* col = S + j * ldw + (k + 1);
+      double s = 0.0;
+      for (int i = lane; i < m; i += 32) s = fma(v[i], col[i], s);
+      s = warp_sum(s);
+      if (lane == 0) w[j] = s;
+    }
+    __syncthreads();
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      const double tw = t * w[j];
+      double* col = S + j * ldw + (k + 1);
+      for (int i = lane; i < m; i += 32) col[i] = fma(-v[i], tw, col[i]);
+    }
+    __syncthreads();
+    // right: w_i = A[i, k+1..] . v for all rows i; then A -= t w v^T
+    for (int i = tid; i < n; i += bd) {
+      const double* row = S + (k + 1) * ldw + i;
+      double s = 0.0;
+      for (int jj = 0; jj < m; ++jj) s = fma(row[jj * ldw], v[jj], s);
+      w[i] = s;
+    }
+    __syncthreads();
+    for (int jj = warp; jj < m; jj += nw) {
+      const double tv = t * v[jj];
+      double* col = S + (k + 1 + jj) * ldw;
+      for (int i = lane; i < n; i += 32) col[i] = fma(-w[i], tv, col[i]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) tau[k] = 0.0;
+  }
+  __syncthreads();
+  store_square(A, ld, S, ldw, n, n);
+}
+
+// Least squares as k_lstsq, [A | B] in shared memory (mr x (nc + nrhs)).
+__global__ void k_lstsq_smem(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
+                             int32_t* info) {
+  extern __shared__ double sm[];
+  const int ldw = mr | 1;
+  const int ncol = nc + nrhs;
+  double* S = sm;
+  double* v = S + ncol * ldw;
+  double* w = v + mr;
+  double* red = w + ncol;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  load_square(S, ldw, A, ld, mr, nc);
+  load_square(S + nc * ldw, ldw, B, ldb, mr, nrhs);
+  __syncthreads();
+  double rmax = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    double* col = S + k * ldw;
+    const int hgt = mr - k;
+    double t, beta;
+    house(col + k, hgt, v + k, red, t, beta);
+    rmax = fmax(rmax, fabs(beta));
+    if (t != 0.0) {
+      for (int j = k + 1 + warp; j < ncol; j += nw) {
+        const double* cj = S + j * ldw;
+        double s = 0.0;
+        for (int i = k + lane; i < mr; i += 32) s = fma(v[i], cj[i], s);
+        s = warp_sum(s);
+        if (lane == 0) w[j] = s;
+      }
+      __syncthreads();
+      for (int j = k + 1 + warp; j < ncol; j += nw) {
+        const double tw = t * w[j];
+        double* cj = S + j * ldw;
+        for (int i = k + lane; i < mr; i += 32) cj[i] = fma(-v[i], tw, cj[i]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) col[k] = beta;
+    for (int i = k + 1 + tid; i < mr; i += bd) col[i] = 0.0;
+    __syncthreads();
+  }
+  // back substitution, one warp per right-hand side (solution in shared memory)
+  double* xsm = red + 32;
+  for (int c = warp; c < nrhs; c += nw) {
+    const double* b = S + (nc + c) * ldw;
+    double* x = xsm + c * nc;
+    for (int i = nc - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int j = i + 1 + lane; j < nc; j += 32) s = fma(S[i + j * ldw], x[j], s);
+      s = b[i] - warp_sum(s);
+      const double piv = S[i + i * ldw];
+      if (lane == 0) {
+        if (fabs(piv) <= 1e-14 * rmax || !isfinite(piv)) {
+          raise_status(info, DMD_ENUMERIC, 5000 + i);
+          x[i] = 0.0;
+        } else {
+          x[i] = s / piv;
+        }
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < nc; i += 32) X[(int64_t)c * ldx + i] = x[i];
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
@@ -1005,21 +1323,50 @@ dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bo
   return DMD_OK;
 }
 
+// Shared-memory bytes of an n x n FP64 matrix with leading dimension n | 1
+// plus `extra` doubles.
+static size_t square_smem(int rows, int cols, size_t extra) {
+  return ((size_t)(rows | 1) * cols + extra) * sizeof(double);
+}
+
+static dmd_status set_smem(const void* fn, size_t bytes) {
+  DMD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return DMD_OK;
+}
+
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
-  k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
+  const size_t smem = square_smem(n, n, (size_t)n + 32);
+  if (smem <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_cholesky_smem, smem));
+    k_cholesky_smem<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+  } else {
+    k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
 
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st) {
-  k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
+  const size_t smem = square_smem(n, n, 8 * (size_t)n);
+  if (smem <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_tri_inv_smem, smem));
+    k_tri_inv_smem<<<(unsigned)ceil_div(n, 8), 256, smem, st>>>(n, R, ldr, T, ldt);
+  } else {
+    k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
 
 dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st) {
-  const size_t smem = (2 * (size_t)n + 32) * sizeof(double);
-  k_hessenberg<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  const size_t smem_s = square_smem(n, n, 2 * (size_t)n + 32);
+  if (smem_s <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_hessenberg_smem, smem_s));
+    k_hessenberg_smem<<<1, 512, smem_s, st>>>(n, A, ld, tau);
+  } else {
+    const size_t smem = (2 * (size_t)n + 32) * sizeof(double);
+    k_hessenberg<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -1082,8 +1429,14 @@ dmd_status eig_layout(int n, const double* wr, const double* wi, const int* head
 }
 
 dmd_status sytrd(int n, double* A, int ld, double* tau, cudaStream_t st) {
-  const size_t smem = (3 * (size_t)n + 32) * sizeof(double);
-  k_sytrd<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  const size_t smem_s = square_smem(n, n, 2 * (size_t)n + 32);
+  if (smem_s <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_sytrd_smem, smem_s));
+    k_sytrd_smem<<<1, 512, smem_s, st>>>(n, A, ld, tau);
+  } else {
+    const size_t smem = (3 * (size_t)n + 32) * sizeof(double);
+    k_sytrd<<<1, 1024, smem, st>>>(n, A, ld, tau);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -1100,8 +1453,14 @@ dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, d
 
 dmd_status lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
                  int32_t* info, cudaStream_t st) {
-  const size_t smem = ((size_t)mr + nc + nrhs + 32) * sizeof(double);
-  k_lstsq<<<1, 256, smem, st>>>(mr, nc, A, ld, nrhs, B, ldb, X, ldx, info);
+  const size_t smem_s = square_smem(mr, nc + nrhs, (size_t)mr + nc + nrhs + 32 + (size_t)nrhs * nc);
+  if (smem_s <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_lstsq_smem, smem_s));
+    k_lstsq_smem<<<1, 512, smem_s, st>>>(mr, nc, A, ld, nrhs, B, ldb, X, ldx, info);
+  } else {
+    const size_t smem = ((size_t)mr + nc + nrhs + 32) * sizeof(double);
+    k_lstsq<<<1, 256, smem, st>>>(mr, nc, A, ld, nrhs, B, ldb, X, ldx, info);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

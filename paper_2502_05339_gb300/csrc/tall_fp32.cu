@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn_f32(int64_t n, int Kd, int N, c
 constexpr int TN_BT = 64, TN_BR = 32, TN_STAGES = 4, TN_THREADS = 128;
 constexpr uint32_t TN_BOX_BYTES = TN_BT * TN_BR * 4;        // one 32-row x 64-column box: 8 KB
 constexpr uint32_t TN_STAGE_BYTES = 2 * TN_BOX_BYTES;        // A and B boxes
-constexpr size_t TN_SMEM = 1024 + TN_STAGES * TN_STAGE_BYTES + 64;
+constexpr size_t TN_SMEM = 1024 + TN_STAGES * TN_STAGE_BYTES + 128;
 
 // Upper-triangle tile t of an nt x nt tile grid -> (ti, tj), ti <= tj.
 __device__ __forceinline__ void sym_tile(int t, int nt, int& ti, int& tj) {
@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + TN_STAGES * TN_STAGE_BYTES);
-  int* abort_flag = reinterpret_cast<int*>(full + TN_STAGES);
+  uint64_t* empty = full + TN_STAGES;
+  int* abort_flag = reinterpret_cast<int*>(empty + TN_STAGES);
 
   const int tile = blockIdx.x % ntiles;
   const int split = blockIdx.x / ntiles;
@@ -180,21 +181,32 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
   const bool active = b0 + 16 * warp < N;
 
   if (tid == 0) {
-    for (int i = 0; i < TN_STAGES; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < TN_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], TN_THREADS / 32);   // one arrival per warp
+    }
     *abort_flag = 0;
     fence_barrier_init();
   }
   __syncthreads();
+
+  // Thread 0 keeps up to TN_STAGES boxes in flight; a stage is refilled once
+  // every warp has released it, so the warps never wait for one another.
   int issued = 0;
-  if (tid == 0) {
-    for (; issued < min(nq, TN_STAGES); ++issued) {
-      uint8_t* buf = sm + issued * TN_STAGE_BYTES;
-      mbar_expect_tx(&full[issued], TN_STAGE_BYTES);
+  auto produce = [&](int upto) -> bool {
+    for (; issued < min(nq, upto); ++issued) {
+      const int s = issued % TN_STAGES;
+      if (issued >= TN_STAGES &&
+          !mbar_wait(&empty[s], (uint32_t)(issued / TN_STAGES - 1) & 1u, abort_flag))
+        return false;
+      uint8_t* buf = sm + s * TN_STAGE_BYTES;
+      mbar_expect_tx(&full[s], TN_STAGE_BYTES);
       const int x = (int)(rbeg + (int64_t)issued * TN_BR);
-      tma_load_2d(buf, &tmA, &full[issued], x, a0);
-      tma_load_2d(buf + TN_BOX_BYTES, &tmB, &full[issued], x, b0);
+      tma_load_2d(buf, &tmA, &full[s], x, a0);
+      tma_load_2d(buf + TN_BOX_BYTES, &tmB, &full[s], x, b0);
     }
-  }
+    return true;
+  };
 
   float acc[4][8], mid[4][8];
 #pragma unroll
@@ -222,9 +234,12 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
 
   int stretch = 0;
   for (int q = 0; q < nq; ++q) {
+    bool ok = true;
+    if (tid == 0) ok = produce(q + TN_STAGES);
     const int s = q % TN_STAGES;
-    const bool ok = mbar_wait(&full[s], (uint32_t)(q / TN_STAGES) & 1u, abort_flag);
-    if (ok && active) {
+    ok = ok && mbar_wait(&full[s], (uint32_t)(q / TN_STAGES) & 1u, abort_flag);
+    if (!__all_sync(0xffffffffu, ok)) break;
+    if (active) {
       const uint8_t* Ab = sm + s * TN_STAGE_BYTES;
       const uint8_t* Bb = Ab + TN_BOX_BYTES;
 #pragma unroll
@@ -248,6 +263,10 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
             acc[i][j] = fmaf(av[i].w, bv[j].w, acc[i][j]);
           }
       }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
+    if (active) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -256,16 +275,6 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
         stretch = 0;
         flush();
       }
-    }
-    // every thread has finished with stage s (or the CTA gives up)
-    if (__syncthreads_or(!ok)) break;
-    if (tid == 0 && issued < nq) {
-      uint8_t* buf = sm + s * TN_STAGE_BYTES;
-      mbar_expect_tx(&full[s], TN_STAGE_BYTES);
-      const int x = (int)(rbeg + (int64_t)issued * TN_BR);
-      tma_load_2d(buf, &tmA, &full[s], x, a0);
-      tma_load_2d(buf + TN_BOX_BYTES, &tmB, &full[s], x, b0);
-      ++issued;
     }
   }
   if (active && (stretch > 0 || first)) flush();

@@ -109,6 +109,8 @@ __device__ __forceinline__ uint32_t kslice_off(int row, int half) {
   return (uint32_t)((row >> 3) * 256 + half * 128 + (row & 7) * 16);
 }
 
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
@@ -608,29 +610,62 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
 
 // ============================================================ TN reduction
 
-constexpr int TN_S = 3;          // TMA stages (A slice + B slice)
-constexpr int TN_THREADS = 320;
-constexpr int TN_FLUSH = 256;    // default k-steps (of 16 rows) between FP64 flushes
+constexpr int TN_S = 4;            // TMA stages (A slice + B slice)
+constexpr int TN_CONV = 8;         // converter warps
+constexpr int TN_THREADS = 32 * (2 + TN_CONV + 4);
+constexpr int TN_FLUSH = 256;      // default k-steps (of 16 rows) between FP64 flushes
+
+// Split 4 consecutive-K FP32 values of operand row `row` (K offset 4*qd in
+// the 16-wide slice) into NS bf16 planes `plane` bytes apart (hi, then the
+// rounded remainders).
+template <int NS>
+__device__ __forceinline__ void split_store4(float4 v, uint8_t* base, uint32_t plane, int row, int qd) {
+  const uint32_t off = kslice_off(row, qd >> 1) + (uint32_t)(qd & 1) * 8u;
+  const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+  const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+  const float r0 = v.x - f01.x, r1 = v.y - f01.y, r2 = v.z - f23.x, r3 = v.w - f23.y;
+  const __nv_bfloat162 m01 = __floats2bfloat162_rn(r0, r1), m23 = __floats2bfloat162_rn(r2, r3);
+  *reinterpret_cast<uint2*>(base + off) = make_uint2(bf2_bits(h01), bf2_bits(h23));
+  *reinterpret_cast<uint2*>(base + plane + off) = make_uint2(bf2_bits(m01), bf2_bits(m23));
+  if (NS == 3) {
+    const float2 g01 = __bfloat1622float2(m01), g23 = __bfloat1622float2(m23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(r0 - g01.x, r1 - g01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(r2 - g23.x, r3 - g23.y);
+    *reinterpret_cast<uint2*>(base + 2 * plane + off) = make_uint2(bf2_bits(l01), bf2_bits(l23));
+  }
+}
+
+// Converter loop: `units` float4 of a TMA slice (operand row u / 4, K offset
+// 4 * (u % 4): the box stores 16 rows of n per column) into NS planes.
+template <int NS>
+__device__ __forceinline__ void split_slice(const float4* src, int units, uint8_t* base, uint32_t plane, int t,
+                                            int nthreads) {
+#pragma unroll 4
+  for (int u = t; u < units; u += nthreads) split_store4<NS>(src[u], base, plane, u >> 2, u & 3);
+}
 
 // part[blockIdx.x][b * Ka + a] = sum over this CTA's rows of A[:, a] * B[:, b].
 // A slice: TMA box {16 rows, Mt*128 cols}; B slice: box {16 rows, Np cols}.
 // nsplit = 2: bf16 hi + lo, products hh + hl + lh (BF16x3).  nsplit = 3:
-// hi + mid + lo, products hh + hm + mh + hl + lh + mm (every term of order
-// <= 2^-16 relative), which resolves Gram directions down to ~1e-8 of the
-// largest -- the reductions whose accuracy decides the fit use it.
+// hi + mid + lo, products hh + hm + mh + hl + lh + mm.  sym != 0: B is A
+// (a Gram matrix), loaded and split once.  Roles: warp 0 TMA producer, warp 1
+// MMA issuer, TN_CONV converter warps (FP32 slice -> bf16 planes; each warp
+// reads 512 contiguous bytes per step, four lanes per operand row), four
+// epilogue warps (TMEM -> FP64 partial every `flush` k-steps).
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_umma_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
-              int N, int Mt, int Np, int nsplit, int flush, int64_t chunk, double* __restrict__ part, int32_t* err) {
+              int N, int Mt, int Np, int nsplit, int flush, int sym, int ns, int64_t chunk,
+              double* __restrict__ part, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t a_bytes = 16u * 4u * (uint32_t)Mt * 128u;   // FP32 slice of A
-  const uint32_t b_bytes = 16u * 4u * (uint32_t)Np;          // FP32 slice of B
-  const uint32_t st_bytes = (a_bytes + b_bytes + 1023u) & ~1023u;
+  const uint32_t b_bytes = sym ? 0u : 16u * 4u * (uint32_t)Np;   // FP32 slice of B
+  const uint32_t st_bytes = (16u * 4u * (uint32_t)Mt * 128u + 16u * 4u * (uint32_t)Np + 1023u) & ~1023u;
   const uint32_t ca_bytes = (uint32_t)Mt * 128u * 32u;       // one bf16 K-slice plane of A
   const uint32_t cb_bytes = (uint32_t)Np * 32u;
   const uint32_t cv_bytes = ((uint32_t)nsplit * (ca_bytes + cb_bytes) + 1023u) & ~1023u;
   uint8_t* st = sm;
-  uint8_t* cv = st + TN_S * st_bytes;
+  uint8_t* cv = st + ns * st_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(cv + 2 * cv_bytes);
   uint64_t* full = bars;
   uint64_t* empty = full + TN_S;
@@ -647,14 +682,15 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   const int64_t rend = min(n, rbeg + chunk);
   const int ksteps = rend > rbeg ? (int)((rend - rbeg + 15) / 16) : 0;
   const int nflush = (ksteps + flush - 1) / flush;
+  constexpr int kConvThreads = 32 * TN_CONV;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < TN_S; ++i) {
+    for (int i = 0; i < ns; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 128);
+      mbar_init(&empty[i], kConvThreads);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&cfull[i], 128);
+      mbar_init(&cfull[i], kConvThreads);
       mbar_init(&cempty[i], 1);
     }
     mbar_init(accf, 1);
@@ -671,19 +707,19 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      bool issued[TN_S] = {false, false, false};
-      uint32_t par[TN_S] = {0, 0, 0};
+      bool issued[TN_S] = {false, false, false, false};
+      uint32_t par[TN_S] = {0, 0, 0, 0};
       for (int ks = 0; ks < ksteps; ++ks) {
-        const uint32_t s = ks % TN_S;
-        if (!mbar_wait(&empty[s], ((ks / TN_S) & 1) ^ 1, abort_flag)) break;
+        const uint32_t s = ks % ns;
+        if (!mbar_wait(&empty[s], ((ks / ns) & 1) ^ 1, abort_flag)) break;
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
         const int r0 = (int)(rbeg + (int64_t)ks * 16);
         tma_load_2d(st + s * st_bytes, &tmA, &full[s], r0, 0);
-        tma_load_2d(st + s * st_bytes + a_bytes, &tmB, &full[s], r0, 0);
+        if (!sym) tma_load_2d(st + s * st_bytes + a_bytes, &tmB, &full[s], r0, 0);
         issued[s] = true;
-        par[s] = (ks / TN_S) & 1;
+        par[s] = (ks / ns) & 1;
       }
-      for (int i = 0; i < TN_S; ++i)
+      for (int i = 0; i < ns; ++i)
         if (issued[i]) mbar_wait_drain(&full[i], par[i]);
     }
   } else if (warp == 1) {
@@ -703,9 +739,11 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
           }
           tc_after();
           const uint32_t base = su32(cv + cs * cv_bytes);
-          const uint32_t bbase = base + (uint32_t)nsplit * ca_bytes;   // B planes follow the A planes
+          // B planes follow the A planes; a Gram reads A's planes twice
+          const uint32_t bbase = sym ? base : base + (uint32_t)nsplit * ca_bytes;
+          const uint32_t bstride = sym ? ca_bytes : cb_bytes;
           uint64_t bd[3];
-          for (int t = 0; t < nsplit; ++t) bd[t] = sdesc(bbase + t * cb_bytes, kLBO, kSBO);
+          for (int t = 0; t < nsplit; ++t) bd[t] = sdesc(bbase + t * bstride, kLBO, kSBO);
           for (int mt = 0; mt < Mt; ++mt) {
             const uint32_t d = tmem + (uint32_t)(mt * Np);
             uint64_t ad[3];
@@ -727,37 +765,24 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       umma_commit(tdown);
       mbar_wait_drain(tdown, 0);
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + TN_CONV) {
     const int t = threadIdx.x - 64;
+    const int na4 = Mt * 128 * 4, nb4 = sym ? 0 : Np * 4;   // float4 units per slice
     for (int ks = 0; ks < ksteps; ++ks) {
-      const uint32_t s = ks % TN_S, cs = ks & 1;
-      if (!mbar_wait(&full[s], (ks / TN_S) & 1, abort_flag) ||
+      const uint32_t s = ks % ns, cs = ks & 1;
+      if (!mbar_wait(&full[s], (ks / ns) & 1, abort_flag) ||
           !mbar_wait(&cempty[cs], ((ks >> 1) & 1) ^ 1, abort_flag))
         break;
-      const float* sa = reinterpret_cast<const float*>(st + s * st_bytes);
-      const float* sb = reinterpret_cast<const float*>(st + s * st_bytes + a_bytes);
+      const float4* sa = reinterpret_cast<const float4*>(st + s * st_bytes);
+      const float4* sb = reinterpret_cast<const float4*>(st + s * st_bytes + a_bytes);
       uint8_t* base = cv + cs * cv_bytes;
-      float x[16];
-      for (int col = t; col < Mt * 128; col += 128) {   // A columns = operand rows
-        const float4* p = reinterpret_cast<const float4*>(sa + col * 16);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float4 v = p[c];
-          x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
-        }
-        if (nsplit == 3) split3_store_row(x, base, ca_bytes, col);
-        else split_store_row(x, base, base + ca_bytes, col);
-      }
       uint8_t* bb = base + (uint32_t)nsplit * ca_bytes;
-      for (int col = t; col < Np; col += 128) {
-        const float4* p = reinterpret_cast<const float4*>(sb + col * 16);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float4 v = p[c];
-          x[4 * c] = v.x, x[4 * c + 1] = v.y, x[4 * c + 2] = v.z, x[4 * c + 3] = v.w;
-        }
-        if (nsplit == 3) split3_store_row(x, bb, cb_bytes, col);
-        else split_store_row(x, bb, bb + cb_bytes, col);
+      if (nsplit == 3) {
+        split_slice<3>(sa, na4, base, ca_bytes, t, kConvThreads);
+        split_slice<3>(sb, nb4, bb, cb_bytes, t, kConvThreads);
+      } else {
+        split_slice<2>(sa, na4, base, ca_bytes, t, kConvThreads);
+        split_slice<2>(sb, nb4, bb, cb_bytes, t, kConvThreads);
       }
       fence_async_smem();
       mbar_arrive(&cfull[cs]);
@@ -775,13 +800,16 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
         for (int c0 = 0; c0 < Np; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + (uint32_t)(mt * Np + c0) + ((uint32_t)(q * 32) << 16), v);
+          // Each partial entry has one owner thread, so its additions land in
+          // program order (deterministic); a reduction needs no round trip.
           if (a < Ka) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int b = c0 + j;
               if (b < N) {
                 double* p = out + (int64_t)b * Ka + a;
-                *p = (f == 0 ? 0.0 : *p) + (double)v[j];
+                if (f == 0) *p = (double)v[j];
+                else atomicAdd(p, (double)v[j]);
               }
             }
           }
@@ -808,15 +836,17 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
 }
 
 // C[a0 + a, b0 + b] (ld ldc) = sum over the CTAs' partials (ka x nb each), fixed order.
+// With trans != 0 the block is written transposed: C[a, b] goes to C[b + a * ldc].
 __global__ void k_reduce_parts(int ka, int nb, int parts, const double* __restrict__ part, double* __restrict__ C,
-                               int64_t ldc) {
+                               int64_t ldc, int trans) {
   const int64_t count = (int64_t)ka * nb;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   double s = 0.0;
   for (int p = 0; p < parts; ++p) s += part[(int64_t)p * count + i];
   const int a = (int)(i % ka), b = (int)(i / ka);
-  C[(int64_t)b * ldc + a] = s;
+  if (trans) C[(int64_t)a * ldc + b] = s;
+  else C[(int64_t)b * ldc + a] = s;
 }
 
 // ------------------------------------------------------------ host side
@@ -857,10 +887,16 @@ AresCfg ares_cfg(int ksteps) {
         if (ares_smem(ksteps, bn, sa, nb) <= (size_t)kMaxSmem) return {bn, sa, nb};
   return {0, 0, 0};
 }
-size_t tn_smem(int Mt, int Np, int nsplit) {
+size_t tn_smem(int Mt, int Np, int nsplit, int ns) {
   const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
   const size_t cv = ((size_t)nsplit * (Mt * 128 * 32 + Np * 32) + 1023) & ~(size_t)1023;
-  return 1024 + TN_S * st + 2 * cv + 256;
+  return 1024 + ns * st + 2 * cv + 256;
+}
+// Deepest TMA ring (2 .. TN_S stages) that fits in shared memory (0: none does).
+int tn_stages(int Mt, int Np, int nsplit) {
+  for (int ns = TN_S; ns >= 2; --ns)
+    if (tn_smem(Mt, Np, nsplit, ns) <= (size_t)kMaxSmem) return ns;
+  return 0;
 }
 
 // Largest column chunk of B that stays resident for the B-resident kernel.
@@ -944,23 +980,38 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
   double* part = reinterpret_cast<double*>(ws);
   const int grid = tn_grid(n);
   const int64_t chunk = round_up(ceil_div(n, grid), 16);
-  for (int a0 = 0; a0 < Ka; a0 += 256) {
-    const int ka = std::min(256, Ka - a0);
+  const bool sym = A == B && Ka == N && lda == ldb && Ka <= 256;
+  // The MMA's M side is padded to 128 rows, its N side to 16 columns: put the
+  // operand that pads less on the M side (then reduce into C transposed).
+  const bool swap = !sym && Ka <= 256 && N <= 256 &&
+                    round_up(N, 128) * round_up(Ka, 16) < round_up(Ka, 128) * round_up(N, 16);
+  const float* Am = swap ? B : A;
+  const float* Bm = swap ? A : B;
+  const int64_t ldam = swap ? ldb : lda, ldbm = swap ? lda : ldb;
+  const int Km = swap ? N : Ka, Nm = swap ? Ka : N;
+  for (int a0 = 0; a0 < Km; a0 += 256) {
+    const int ka = std::min(256, Km - a0);
     const int Mt = (int)ceil_div(ka, 128);
-    for (int b0 = 0; b0 < N; b0 += 256) {
-      const int nb = std::min(256, N - b0);
+    for (int b0 = 0; b0 < Nm; b0 += 256) {
+      const int nb = std::min(256, Nm - b0);
       const int Np = (int)round_up(nb, 16);
       CUtensorMap mA, mB;
-      DMD_TRY(make_map(&mA, A + (int64_t)a0 * lda, n, ka, lda, 16, Mt * 128));
-      DMD_TRY(make_map(&mB, B + (int64_t)b0 * ldb, n, nb, ldb, 16, Np));
-      const size_t smem = tn_smem(Mt, Np, nsplit);
+      DMD_TRY(make_map(&mA, Am + (int64_t)a0 * ldam, n, ka, ldam, 16, Mt * 128));
+      DMD_TRY(make_map(&mB, Bm + (int64_t)b0 * ldbm, n, nb, ldbm, 16, Np));
+      const int ns = tn_stages(Mt, Np, nsplit);
+      if (ns == 0) {
+        set_error("umma_gemm_tn: %d x %d block with %d-way split does not fit in shared memory", ka, nb, nsplit);
+        return DMD_EINVAL;
+      }
+      const size_t smem = tn_smem(Mt, Np, nsplit, ns);
       DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, flush, chunk, part, nullptr);
+      k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, flush, sym ? 1 : 0, ns, chunk,
+                                                part, nullptr);
       DMD_LAUNCH_CHECK();
-      // reduce into the (a0, b0) block of C
+      // reduce into the (a0, b0) block of C (of C^T when swapped)
       const int64_t count = (int64_t)ka * nb;
-      k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(ka, nb, grid, part,
-                                                                      C + (int64_t)b0 * Ka + a0, Ka);
+      double* dst = swap ? C + (int64_t)a0 * Ka + b0 : C + (int64_t)b0 * Ka + a0;
+      k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(ka, nb, grid, part, dst, Ka, swap ? 1 : 0);
       DMD_LAUNCH_CHECK();
     }
   }
