@@ -42,6 +42,7 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
+dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st);
 dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st);
 dmd_status sytrd(int n, double* A, int ld, double* tau, cudaStream_t st);
@@ -139,7 +140,7 @@ struct FitBufs {
   int m, r, l, q, lo;   // lo = rows of the "input" sketch (m); control stacks q extra rows
   double *Om, *G, *T1, *T2, *Zp, *Z, *Gz, *Tz, *P, *Pp, *Hb, *tauB, *evB, *YB, *trid, *Vs, *Tmp, *At, *Ah,
       *tauA, *Hq, *wr, *wi, *Yre, *Yim, *invit, *WR, *MR, *LS, *rhs, *hnorm, *invsq;
-  float *Y, *Q1;
+  float* Q1;
   int *heads, *nheads, *order;
   // DMD with control (q > 0): input-space SVD of [Q^T X; Ups] and its products
   double *W, *WB;   // snapshot Gram S^T S ((m+1) x (m+1)) and W_X B (m x l)
@@ -195,7 +196,6 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   b.heads = a.take<int>(r);
   b.nheads = a.take<int>(1);
   b.order = a.take<int>(r);
-  b.Y = a.take<float>((size_t)b.ldY * l);
   b.Q1 = a.take<float>((size_t)b.ldY * l);
   b.L = l + d.q;
   b.p = std::min(d.r + d.q, std::min(b.L, m));
@@ -253,29 +253,34 @@ constexpr double kTauTall = 1e-10, kTauSmall = 1e-13;
 // CholeskyQR2 of the tall sketch Y = X Bs (n x l, Bs = Omega or Z, m x l):
 // the first Gram is formed in the small space as Bs^T (X^T X) Bs from the
 // snapshot Gram W (one accurate pass over S per fit), so it carries FP64
-// accuracy whatever the condition of Y; Q1 = Y R1^{-1} is written explicitly;
-// the second Gram Q1^T Q1 (of a well-conditioned matrix) is a tall reduction;
-// the second factor is kept as T2 = R2^{-1} and folded into the consumers
-// (Q = Q1 T2).
-dmd_status orth_tall(const Tall& tall, FitBufs& b, const double* Bs, int32_t* info, int tag, cudaStream_t st) {
+// accuracy whatever the condition of Y.  Y itself is never stored: the first
+// orthonormal factor is one tall product Q1 = Y R1^{-1} = X (Bs R1^{-1}).
+// The second Gram Q1^T Q1 (of a well-conditioned matrix, close to I) is a
+// tall reduction and its Cholesky factor is taken in FP32; the second factor
+// is kept as T2 = R2^{-1} and folded into the consumers (Q = Q1 T2).
+dmd_status orth_tall(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, const double* Bs, int32_t* info,
+                     int tag, cudaStream_t st) {
   const int l = b.l, m = b.m;
   DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
   DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
   DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
-  DMD_TRY(tall.nn(b.n, l, l, b.Y, b.ldY, b.T1, b.Q1, b.ldY, b.gemm_ws, st));
+  DMD_TRY(dgemm(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, st));   // Bs R1^{-1}
+  DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st));
   DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
-  DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag + 1, st));
+  DMD_TRY(cholesky_upper_f32(l, b.G, l, kTauTall, info, tag + 1, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
   return DMD_OK;
 }
 
-// CholeskyQR2 of a small FP64 matrix Z (rows x l) in place.
+// CholeskyQR2 of a small FP64 matrix Z (rows x l) in place (second factor in
+// FP32, as for the tall sketch).
 dmd_status orth_small(FitBufs& b, int rows, int32_t* info, int tag, cudaStream_t st) {
   const int l = b.l;
   for (int pass = 0; pass < 2; ++pass) {
     DMD_TRY(dgemm(l, l, rows, 1.0, b.Z, rows, true, b.Z, rows, false, 0.0, b.Gz, l, st));
-    DMD_TRY(cholesky_upper(l, b.Gz, l, kTauSmall, info, tag + pass, st));
+    if (pass == 0) DMD_TRY(cholesky_upper(l, b.Gz, l, kTauSmall, info, tag + pass, st));
+    else DMD_TRY(cholesky_upper_f32(l, b.Gz, l, kTauSmall, info, tag + pass, st));
     DMD_TRY(tri_inv_upper(l, b.Gz, l, b.Tz, l, st));
     DMD_TRY(dgemm(rows, l, l, 1.0, b.Z, rows, false, b.Tz, l, false, 0.0, b.Zp, rows, st));
     DMD_TRY(fit_glue_copy((int64_t)rows * l, b.Zp, b.Z, st));
@@ -376,15 +381,13 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   DMD_TRY(tall.tn_accurate(n, m + 1, m + 1, S, d.ldS, S, d.ldS, b.W, b.gemm_ws, st));
   DMD_TRY(fit_glue_check_finite((int64_t)(m + 1) * (m + 1), b.W, info, 91, st));
   // 3. Y = X Omega, Q = orth(Y)
-  DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Om, b.Y, b.ldY, b.gemm_ws, st));
-  DMD_TRY(orth_tall(tall, b, b.Om, info, 1, st));
+  DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Om, info, 1, st));
   // 4. power iterations: Z = orth(X^T Q), Y = X Z, Q = orth(Y)
   for (int it = 0; it < d.power_iters; ++it) {
     DMD_TRY(tall.tn(n, m, l, X, d.ldS, b.Q1, b.ldY, b.Zp, b.gemm_ws, st));
     DMD_TRY(dgemm(m, l, l, 1.0, b.Zp, m, false, b.T2, l, false, 0.0, b.Z, m, st));
     DMD_TRY(orth_small(b, m, info, 10 + 4 * it, st));
-    DMD_TRY(tall.nn(n, m, l, X, d.ldS, b.Z, b.Y, b.ldY, b.gemm_ws, st));
-    DMD_TRY(orth_tall(tall, b, b.Z, info, 12 + 4 * it, st));
+    DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Z, info, 12 + 4 * it, st));
   }
   // 5. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
   DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));

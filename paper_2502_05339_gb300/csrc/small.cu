@@ -1108,6 +1108,103 @@ __global__ void k_tri_inv_smem(int n, const double* __restrict__ R, int ldr, dou
   for (int i = lane; i <= j; i += 32) out[i] = t[i];
 }
 
+// T = R^{-1}, one CTA (one warp) per column j, column-oriented back
+// substitution: b = e_j; for i = j .. 0: t_i = b_i / r_ii, b[0..i) -= t_i
+// R[0..i, i].  No reductions: each step is one scaled column update spread
+// over the lanes, so the FP64 work of the n columns runs on n SMs at once.
+// R's columns 0..j (upper part) are staged in shared memory, packed.
+__global__ void __launch_bounds__(32) k_tri_inv_col(int n, const double* __restrict__ R, int ldr,
+                                                    double* __restrict__ T, int ldt) {
+  extern __shared__ double sm[];
+  const int j = blockIdx.x, lane = threadIdx.x;
+  double* Rp = sm;                        // column i at offset i (i + 1) / 2
+  double* b = Rp + (j + 1) * (j + 2) / 2;  // j + 1
+  double* inv = b + (j + 1);               // j + 1
+  for (int i = 0; i <= j; ++i) {
+    const int off = i * (i + 1) / 2;
+    for (int a = lane; a <= i; a += 32) Rp[off + a] = R[a + (int64_t)i * ldr];
+  }
+  __syncwarp();
+  for (int i = lane; i <= j; i += 32) {
+    const double d = Rp[i * (i + 1) / 2 + i];
+    inv[i] = d == 0.0 ? 0.0 : 1.0 / d;
+    b[i] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  double* out = T + (int64_t)j * ldt;
+  for (int i = j + 1 + lane; i < n; i += 32) out[i] = 0.0;
+  if (inv[j] == 0.0) {   // dropped direction: zero column
+    for (int i = lane; i <= j; i += 32) out[i] = 0.0;
+    return;
+  }
+  for (int i = j; i >= 0; --i) {
+    const double ti = b[i] * inv[i];
+    const double* col = Rp + i * (i + 1) / 2;
+    __syncwarp();
+    if (lane == 0) b[i] = ti;
+    for (int a = lane; a < i; a += 32) b[a] = fma(-ti, col[a], b[a]);
+    __syncwarp();
+  }
+  for (int i = lane; i <= j; i += 32) out[i] = b[i];
+}
+
+// Cholesky as k_cholesky_smem in FP32 (input and output FP64).  For Gram
+// matrices that are already close to the identity (the second pass of
+// CholeskyQR2), where FP32 rounding (~1e-7) is far below the accuracy the
+// basis is stored with.
+__global__ void k_cholesky_f32(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+  extern __shared__ float smf[];
+  const int ldw = n | 1;
+  float* S = smf;
+  float* r = S + n * ldw;
+  __shared__ double red[32];
+  __shared__ float piv;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = (float)G[a + (int64_t)b * ld];
+  double loc = 0.0;
+  for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
+  const double dmax = block_max(loc, red);
+  const float floor_ = (float)(tau * dmax);
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float d = S[j + j * ldw];
+      if (!isfinite(d) || !isfinite(dmax)) {
+        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+        piv = -1.f;
+      } else if (!(dmax > 0.0)) {
+        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+        piv = -1.f;
+      } else if (!(d > floor_)) {
+        piv = 0.f;
+        if (info) atomicAdd(&info[5], 1);
+      } else {
+        piv = sqrtf(d);
+      }
+      if (piv >= 0.f) S[j + j * ldw] = piv;
+    }
+    __syncthreads();
+    const float p = piv;
+    if (p < 0.f) return;
+    const float ip = p == 0.f ? 0.f : 1.f / p;
+    for (int i = j + 1 + tid; i < n; i += bd) {
+      const float v = p == 0.f ? 0.f : S[j + i * ldw] * ip;
+      S[j + i * ldw] = v;
+      r[i] = v;
+    }
+    __syncthreads();
+    if (p == 0.f) continue;
+    for (int b = j + 1 + warp; b < n; b += nw) {
+      const float rb = r[b];
+      float* col = S + b * ldw;
+      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fmaf(-r[a], rb, col[a]);
+    }
+    __syncthreads();
+  }
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? (double)S[a + b * ldw] : 0.0;
+}
+
 // Householder reflector of x[0..m) (x[0] = alpha): v (v[0] = 1) into v[],
 // returns tau and beta; x itself is not modified.  Block-wide.
 __device__ __forceinline__ void house(const double* x, int m, double* v, double* red, double& tau, double& beta) {
@@ -1347,13 +1444,22 @@ dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, i
 }
 
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st) {
-  const size_t smem = square_smem(n, n, 8 * (size_t)n);
+  const size_t smem = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(double);
   if (smem <= kSmallSmemMax) {
-    DMD_TRY(set_smem((const void*)k_tri_inv_smem, smem));
-    k_tri_inv_smem<<<(unsigned)ceil_div(n, 8), 256, smem, st>>>(n, R, ldr, T, ldt);
+    DMD_TRY(set_smem((const void*)k_tri_inv_col, smem));
+    k_tri_inv_col<<<(unsigned)n, 32, smem, st>>>(n, R, ldr, T, ldt);
   } else {
     k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
   }
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
+  const size_t smem = ((size_t)(n | 1) * n + n) * sizeof(float);
+  if (smem > kSmallSmemMax) return cholesky_upper(n, G, ld, tau, info, tag, st);
+  DMD_TRY(set_smem((const void*)k_cholesky_f32, smem));
+  k_cholesky_f32<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

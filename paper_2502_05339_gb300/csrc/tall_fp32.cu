@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
                   int N, double* __restrict__ part, int nta, int ntb, int ntiles, int sym, int64_t chunk,
                   int32_t* err) {
   extern __shared__ uint8_t smraw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte alignment by pointer arithmetic keeps the shared address space
+  uint8_t* sm = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + TN_STAGES * TN_STAGE_BYTES);
   uint64_t* empty = full + TN_STAGES;
   int* abort_flag = reinterpret_cast<int*>(empty + TN_STAGES);

@@ -164,8 +164,11 @@ __device__ __forceinline__ void split3_store_row(const float* x, uint8_t* base, 
   *reinterpret_cast<uint4*>(p2 + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
 }
 
+// Round a dynamic shared-memory pointer up to 1024 bytes by pointer
+// arithmetic (an integer round trip would lose the shared address space and
+// turn every later access into a generic one).
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+  return p + ((1024u - (su32(p) & 1023u)) & 1023u);
 }
 
 // ---------------------------------------------------- B operand pre-split
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
 // ============================================================ TN reduction
 
 constexpr int TN_S = 4;            // TMA stages (A slice + B slice)
-constexpr int TN_CONV = 8;         // converter warps
+constexpr int TN_CONV = 16;        // converter warps
 constexpr int TN_THREADS = 32 * (2 + TN_CONV + 4);
 constexpr int TN_FLUSH = 256;      // default k-steps (of 16 rows) between FP64 flushes
 
@@ -635,13 +638,19 @@ __device__ __forceinline__ void split_store4(float4 v, uint8_t* base, uint32_t p
   }
 }
 
-// Converter loop: `units` float4 of a TMA slice (operand row u / 4, K offset
-// 4 * (u % 4): the box stores 16 rows of n per column) into NS planes.
+// Converter loop over one k-step (half h of a 32-row stage): unit u is
+// operand row u / 4 (a column of the box: one 128-byte line, 16-byte chunks
+// XOR-swizzled by the line index mod 8), K offset 4 * (u % 4), read from
+// chunk 4 h + u % 4 of that line; written into NS planes.
 template <int NS>
-__device__ __forceinline__ void split_slice(const float4* src, int units, uint8_t* base, uint32_t plane, int t,
+__device__ __forceinline__ void split_slice(const float4* src, int units, int h, uint8_t* base, uint32_t plane, int t,
                                             int nthreads) {
 #pragma unroll 4
-  for (int u = t; u < units; u += nthreads) split_store4<NS>(src[u], base, plane, u >> 2, u & 3);
+  for (int u = t; u < units; u += nthreads) {
+    const int col = u >> 2, q = u & 3;
+    const float4 v = src[col * 8 + ((h * 4 + q) ^ (col & 7))];
+    split_store4<NS>(v, base, plane, col, q);
+  }
 }
 
 // part[blockIdx.x][b * Ka + a] = sum over this CTA's rows of A[:, a] * B[:, b].
@@ -658,9 +667,11 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
               double* __restrict__ part, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
-  const uint32_t a_bytes = 16u * 4u * (uint32_t)Mt * 128u;   // FP32 slice of A
-  const uint32_t b_bytes = sym ? 0u : 16u * 4u * (uint32_t)Np;   // FP32 slice of B
-  const uint32_t st_bytes = (16u * 4u * (uint32_t)Mt * 128u + 16u * 4u * (uint32_t)Np + 1023u) & ~1023u;
+  // a TMA stage holds 32 rows of n (two k-steps): 128 contiguous bytes per
+  // column, laid out with the 128-byte swizzle
+  const uint32_t a_bytes = 32u * 4u * (uint32_t)Mt * 128u;        // FP32 rows of A
+  const uint32_t b_bytes = sym ? 0u : 32u * 4u * (uint32_t)Np;   // FP32 rows of B
+  const uint32_t st_bytes = (32u * 4u * (uint32_t)Mt * 128u + 32u * 4u * (uint32_t)Np + 1023u) & ~1023u;
   const uint32_t ca_bytes = (uint32_t)Mt * 128u * 32u;       // one bf16 K-slice plane of A
   const uint32_t cb_bytes = (uint32_t)Np * 32u;
   const uint32_t cv_bytes = ((uint32_t)nsplit * (ca_bytes + cb_bytes) + 1023u) & ~1023u;
@@ -680,7 +691,10 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t rbeg = (int64_t)blockIdx.x * chunk;
   const int64_t rend = min(n, rbeg + chunk);
-  const int ksteps = rend > rbeg ? (int)((rend - rbeg + 15) / 16) : 0;
+  // k-steps of 16 rows, rounded up to whole stages (rows past this CTA's
+  // range are past n: chunk is a multiple of 32, and TMA fills zeros there)
+  const int ksteps = rend > rbeg ? 2 * (int)((rend - rbeg + 31) / 32) : 0;
+  const int nstage = ksteps / 2;
   const int nflush = (ksteps + flush - 1) / flush;
   constexpr int kConvThreads = 32 * TN_CONV;
 
@@ -709,15 +723,15 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
     if (lane == 0) {
       bool issued[TN_S] = {false, false, false, false};
       uint32_t par[TN_S] = {0, 0, 0, 0};
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const uint32_t s = ks % ns;
-        if (!mbar_wait(&empty[s], ((ks / ns) & 1) ^ 1, abort_flag)) break;
+      for (int g = 0; g < nstage; ++g) {
+        const uint32_t s = g % ns;
+        if (!mbar_wait(&empty[s], ((g / ns) & 1) ^ 1, abort_flag)) break;
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
-        const int r0 = (int)(rbeg + (int64_t)ks * 16);
+        const int r0 = (int)(rbeg + (int64_t)g * 32);
         tma_load_2d(st + s * st_bytes, &tmA, &full[s], r0, 0);
         if (!sym) tma_load_2d(st + s * st_bytes + a_bytes, &tmB, &full[s], r0, 0);
         issued[s] = true;
-        par[s] = (ks / ns) & 1;
+        par[s] = (g / ns) & 1;
       }
       for (int i = 0; i < ns; ++i)
         if (issued[i]) mbar_wait_drain(&full[i], par[i]);
@@ -767,10 +781,30 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
     }
   } else if (warp < 2 + TN_CONV) {
     const int t = threadIdx.x - 64;
-    const int na4 = Mt * 128 * 4, nb4 = sym ? 0 : Np * 4;   // float4 units per slice
+    // float4 units per k-step: valid operand rows only.  The padding rows of
+    // the converted planes (A rows Ka .. Mt*128, B rows N .. Np) are zeroed
+    // once here and never written again.
+    const int na4 = Ka * 4, nb4 = sym ? 0 : N * 4;
+    {
+      const int pa = Mt * 128 - Ka, pb = sym ? 0 : Np - N;
+      const int per_plane = 2 * (pa + pb);   // 16-byte chunks: 2 per row
+      const int total = 2 * nsplit * per_plane;
+      for (int i = t; i < total; i += kConvThreads) {
+        const int buf = i / (nsplit * per_plane);
+        const int rem = i % (nsplit * per_plane);
+        const int plane = rem / per_plane;
+        const int c = rem % per_plane;
+        const int row = c >> 1, half = c & 1;
+        uint8_t* base = cv + buf * cv_bytes;
+        uint8_t* dst = row < pa ? base + plane * ca_bytes + kslice_off(Ka + row, half)
+                                : base + nsplit * ca_bytes + plane * cb_bytes + kslice_off(N + row - pa, half);
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
     for (int ks = 0; ks < ksteps; ++ks) {
-      const uint32_t s = ks % ns, cs = ks & 1;
-      if (!mbar_wait(&full[s], (ks / ns) & 1, abort_flag) ||
+      const int g = ks >> 1, h = ks & 1;
+      const uint32_t s = g % ns, cs = ks & 1;
+      if ((h == 0 && !mbar_wait(&full[s], (g / ns) & 1, abort_flag)) ||
           !mbar_wait(&cempty[cs], ((ks >> 1) & 1) ^ 1, abort_flag))
         break;
       const float4* sa = reinterpret_cast<const float4*>(st + s * st_bytes);
@@ -778,15 +812,15 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
       uint8_t* base = cv + cs * cv_bytes;
       uint8_t* bb = base + (uint32_t)nsplit * ca_bytes;
       if (nsplit == 3) {
-        split_slice<3>(sa, na4, base, ca_bytes, t, kConvThreads);
-        split_slice<3>(sb, nb4, bb, cb_bytes, t, kConvThreads);
+        split_slice<3>(sa, na4, h, base, ca_bytes, t, kConvThreads);
+        split_slice<3>(sb, nb4, h, bb, cb_bytes, t, kConvThreads);
       } else {
-        split_slice<2>(sa, na4, base, ca_bytes, t, kConvThreads);
-        split_slice<2>(sb, nb4, bb, cb_bytes, t, kConvThreads);
+        split_slice<2>(sa, na4, h, base, ca_bytes, t, kConvThreads);
+        split_slice<2>(sb, nb4, h, bb, cb_bytes, t, kConvThreads);
       }
       fence_async_smem();
       mbar_arrive(&cfull[cs]);
-      mbar_arrive(&empty[s]);
+      if (h == 1) mbar_arrive(&empty[s]);
     }
   } else {
     const int q = warp & 3;
@@ -888,7 +922,7 @@ AresCfg ares_cfg(int ksteps) {
   return {0, 0, 0};
 }
 size_t tn_smem(int Mt, int Np, int nsplit, int ns) {
-  const size_t st = ((size_t)64 * Mt * 128 + (size_t)64 * Np + 1023) & ~(size_t)1023;
+  const size_t st = ((size_t)128 * Mt * 128 + (size_t)128 * Np + 1023) & ~(size_t)1023;
   const size_t cv = ((size_t)nsplit * (Mt * 128 * 32 + Np * 32) + 1023) & ~(size_t)1023;
   return 1024 + ns * st + 2 * cv + 256;
 }
@@ -979,7 +1013,7 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
   if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
   double* part = reinterpret_cast<double*>(ws);
   const int grid = tn_grid(n);
-  const int64_t chunk = round_up(ceil_div(n, grid), 16);
+  const int64_t chunk = round_up(ceil_div(n, grid), 32);
   const bool sym = A == B && Ka == N && lda == ldb && Ka <= 256;
   // The MMA's M side is padded to 128 rows, its N side to 16 columns: put the
   // operand that pads less on the M side (then reduce into C transposed).
@@ -996,8 +1030,8 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
       const int nb = std::min(256, Nm - b0);
       const int Np = (int)round_up(nb, 16);
       CUtensorMap mA, mB;
-      DMD_TRY(make_map(&mA, Am + (int64_t)a0 * ldam, n, ka, ldam, 16, Mt * 128));
-      DMD_TRY(make_map(&mB, Bm + (int64_t)b0 * ldbm, n, nb, ldbm, 16, Np));
+      DMD_TRY(make_map(&mA, Am + (int64_t)a0 * ldam, n, ka, ldam, 32, Mt * 128, true));
+      DMD_TRY(make_map(&mB, Bm + (int64_t)b0 * ldbm, n, nb, ldbm, 32, Np, true));
       const int ns = tn_stages(Mt, Np, nsplit);
       if (ns == 0) {
         set_error("umma_gemm_tn: %d x %d block with %d-way split does not fit in shared memory", ka, nb, nsplit);
