@@ -4,8 +4,12 @@ One step = the whole hot path on one synthetic snapshot matrix: dmd_fit
 (rSVD at r = 150, oversample 10, 2 power iterations, modes, amplitudes) of the
 n = 6,291,456 x 201 FP32 snapshots, then dmd_predict of 1000 frames (k = 0..999)
 written as FP32.  `value` is frames per second of whole steps (1000 frames per
-step over fit + reconstruction); the fit seconds and the reconstruction-only
-frames/s are reported beside it.
+step over fit + reconstruction) in the mixed (BF16x3 tensor-core) form by
+default; the fit seconds and the reconstruction-only frames/s are reported
+beside it, and `forms` gives the same three numbers for both the mixed and the
+plain FP32 form side by side.  `kernels` holds a roofline entry per tall pass
+of the step (each timed alone on the step's shapes); `roofline` is the entry
+with the largest share of the step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32]
                   [--impl ours|reference] [--config cfg1|cfg0]
@@ -208,7 +212,13 @@ def run_ours(args):
 
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
-    roof = roofline(n, r, K, rec_s, prec, peaks, peak_kind)
+    kernels = [] if args.no_kernels else kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind)
+    kernels.insert(0, roofline(n, r, K, rec_s, prec, peaks, peak_kind))
+    roof = max(kernels, key=lambda e: e["step_ms"])
+    forms = {prec: {"frames_per_s": value, "fit_s": fit_s, "recon_frames_per_s": K / rec_s}}
+    if not args.no_forms:
+        other = "fp32" if prec == "mixed" else "mixed"
+        forms[other] = time_form(sc, c, dmd, dev, st, other, out, ks)
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
@@ -218,6 +228,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}", "l2": "inputs (5.06 GB) and outputs (25.2 GB) exceed L2"},
         "fit_s": fit_s, "recon_frames_per_s": K / rec_s, "recon_s": rec_s,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+        "forms": forms, "kernels": kernels,
         "parity": {"status": model.status()},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -262,21 +273,105 @@ def run_e2e(args, sc, c, dmd, dev, st, out, ks):
             "d2h_bytes_per_step": int(F_host.numel() * 4), "steps": steps}
 
 
+def alu_peak(peaks):
+    """FP32 FFMA peak: 152 SMs x 128 lanes x 2 flops x maximum SM clock."""
+    return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def hbm_entry(name, bytes_, sec, launches, peaks, peak_kind, what):
+    achieved = bytes_ / sec / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind, "launch_ms": 1e3 * sec,
+            "launches_per_step": launches, "step_ms": 1e3 * sec * launches, "algorithmic": what}
+
+
+def alu_entry(name, flops, sec, launches, peaks, what):
+    achieved = flops / sec / 1e12
+    peak = alu_peak(peaks)
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock", "launch_ms": 1e3 * sec,
+            "launches_per_step": launches, "step_ms": 1e3 * sec * launches, "algorithmic": what}
+
+
 def roofline(n, r, K, rec_s, prec, peaks, peak_kind):
-    """Reconstruction launch F = Phi_R C (the largest single launch of a step)."""
+    """Reconstruction launch F = Phi_R C (timed with events around dmd_predict)."""
     if prec == "mixed":
-        bytes_ = 4.0 * n * (r + K)                 # read Phi_R once, write K frames
-        achieved = bytes_ / rec_s / 1e9
-        peak = float(peaks["hbm_gbs"])
-        return {"kernel": "umma_nn (reconstruction)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind}
-    flops = 2.0 * n * r * K
-    achieved = flops / rec_s / 1e12
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # FP32 FFMA: 152 SMs x 128 lanes x 2 flops x clock
-    return {"kernel": "k_gemm_nn_f32 (reconstruction)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        return hbm_entry("k_umma_nn_ares (reconstruction Phi_R C)", 4.0 * n * (r + K), rec_s, 1, peaks, peak_kind,
+                         "4 n (r + K) bytes: Phi_R read once, K frames written")
+    return alu_entry("k_gemm_nn_f32 (reconstruction Phi_R C)", 2.0 * n * r * K, rec_s, 1, peaks,
+                     "2 n r K flops")
+
+
+def event_time(fn, st, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind):
+    """The fit's tall passes, each launched alone on the step's own shapes
+    (same kernels, same sizes) and timed with CUDA events on the launching
+    stream: the snapshot Gram W = S^T S, the sketch product Q1 = X M, the
+    tensor-core reductions Q1^T Q1 and Q1^T S (mixed form; the FP32 form runs
+    them on the CUDA cores)."""
+    n, m, r = sc.n, sc.m, c["r"]
+    l = min(r + c["oversample"], m)
+    S, ld = sc.S, sc.S.shape[1]
+    X = S[:m]
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    Q = torch.randn((l, ld), device=dev, generator=g)
+    M = torch.randn((l, m), dtype=torch.float64, device=dev, generator=g)
+    out = []
+    sec = event_time(lambda: dmd.dmd_gemm_tn(S, S, n, precision="fp32"), st)
+    out.append(alu_entry("k_gemm_tn_f32 (snapshot Gram W = S^T S)", float(n) * (m + 1) * (m + 2), sec, 1, peaks,
+                         "n (m+1)(m+2) flops: 2n per distinct entry of the symmetric W"))
+    npass = 1 + c["power_iters"]
+    sec = event_time(lambda: dmd.dmd_gemm_tall(X, n, M, precision=prec, out=Q), st)
+    name = "k_umma_nn_bres (sketch Q1 = X M)" if prec == "mixed" else "k_gemm_nn_f32 (sketch Q1 = X M)"
+    if prec == "mixed":
+        out.append(hbm_entry(name, 4.0 * n * (m + l), sec, npass + 1, peaks, peak_kind,
+                             "4 n (m + l) bytes: X read, Q1 written (also the modes X' M_R)"))
+    else:
+        out.append(alu_entry(name, 2.0 * n * m * l, sec, npass + 1, peaks, "2 n m l flops"))
+    sec = event_time(lambda: dmd.dmd_gemm_tn(Q, Q, n, precision=prec), st)
+    name = "k_umma_tn (Gram Q1^T Q1)" if prec == "mixed" else "k_gemm_tn_f32 (Gram Q1^T Q1)"
+    if prec == "mixed":
+        out.append(hbm_entry(name, 4.0 * n * l, sec, npass, peaks, peak_kind, "4 n l bytes: Q1 read once"))
+    else:
+        out.append(alu_entry(name, float(n) * l * (l + 1), sec, npass, peaks, "n l (l+1) flops"))
+    sec = event_time(lambda: dmd.dmd_gemm_tn(Q, S, n, precision=prec), st)
+    name = "k_umma_tn (X^T Q1, Q1^T S)" if prec == "mixed" else "k_gemm_tn_f32 (X^T Q1, Q1^T S)"
+    if prec == "mixed":
+        out.append(hbm_entry(name, 4.0 * n * (l + m + 1), sec, npass, peaks, peak_kind,
+                             "4 n (l + m + 1) bytes: Q1 and S read once"))
+    else:
+        out.append(alu_entry(name, 2.0 * n * l * (m + 1), sec, npass, peaks, "2 n l (m+1) flops"))
+    del Q, M
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_form(sc, c, dmd, dev, st, prec, out, ks):
+    """Fit seconds, reconstruction frames/s and whole-step frames/s of one form."""
+    n, K = sc.n, c["frames"]
+    fit = lambda: dmd.dmd_fit(sc.S, n, c["r"], oversample=c["oversample"], power_iters=c["power_iters"],
+                              precision=prec, seed=c["seed"])
+    model = fit()
+    torch.cuda.synchronize()
+    model.check()
+    fit_s = event_time(fit, st)
+    rec_s = event_time(lambda: dmd.dmd_predict(model, ks, precision=prec, out=out), st)
+    return {"frames_per_s": K / (fit_s + rec_s), "fit_s": fit_s, "recon_frames_per_s": K / rec_s}
 
 
 def cpu_baseline(cfg, sample_rows=None):
@@ -342,7 +437,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("DMD_BENCH_PRECISION", "fp32"), choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default=os.environ.get("DMD_BENCH_PRECISION", "mixed"), choices=["fp32", "mixed"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side timing of the other form")
+    ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel roofline timings")
     ap.add_argument("--config", default="cfg1", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=None)

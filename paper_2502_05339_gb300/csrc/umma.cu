@@ -298,6 +298,8 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, Np);
+      const uint64_t a0d = sdesc(su32(cv), kLBO, kSBO), b0d = sdesc(su32(Bres), kLBO, kSBO);
+      const uint32_t b_step = ((uint32_t)Np * 32u) >> 4, b_lo = ((uint32_t)ksteps * (uint32_t)Np * 32u) >> 4;
       bool ok = mbar_wait(bfull, 0, abort_flag);
       uint32_t cit = 0, ait = 0;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++ait) {
@@ -312,11 +314,9 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
             break;
           }
           tc_after();
-          const uint32_t a = su32(cv + cs * 8192);
-          const uint32_t bh = su32(Bres) + (uint32_t)ks * Np * 32;
-          const uint32_t bl = su32(Bres) + (uint32_t)(ksteps + ks) * Np * 32;
-          const uint64_t ahd = sdesc(a, kLBO, kSBO), ald = sdesc(a + 4096, kLBO, kSBO);
-          const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
+          // descriptors by offset from precomputed bases (16-byte units)
+          const uint64_t ahd = a0d + (uint64_t)(cs * 512u), ald = ahd + 256u;
+          const uint64_t bhd = b0d + (uint64_t)((uint32_t)ks * b_step), bld = bhd + b_lo;
           umma_bf16(d, ahd, bhd, idesc, ks > 0 ? 1u : 0u);
           umma_bf16(d, ahd, bld, idesc, 1u);
           umma_bf16(d, ald, bhd, idesc, 1u);
@@ -502,21 +502,36 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           }
           tc_after();
           const uint32_t d = tmem + ab * 128u;
-          const uint32_t bbase = su32(Bbuf + b * bstride);
-          for (int ks = 0; ks < ksteps; ++ks) {
-            if (c == 0) {   // the tile's first chunk follows the conversion slice by slice
+          // descriptors advance by offsets (address field in 16-byte units)
+          uint64_t bhd = sdesc(su32(Bbuf + b * bstride), kLBO, kSBO);
+          uint64_t bld = bhd + (uint64_t)(((uint32_t)ksteps * (uint32_t)bn * 32u) >> 4);
+          const uint64_t bstep = (uint64_t)(((uint32_t)bn * 32u) >> 4);
+          if (c == 0) {   // the tile's first chunk follows the conversion slice by slice
+            for (int ks = 0; ks < ksteps; ++ks, bhd += bstep, bld += bstep) {
               if (!mbar_wait(&ares_full[ks], tit & 1, abort_flag)) {
                 ok = false;
                 break;
               }
               tc_after();
+              const uint32_t ah = a_hi + (uint32_t)ks * 8u, al = a_lo + (uint32_t)ks * 8u;
+              umma_bf16_ta(d, ah, bhd, idesc, ks > 0 ? 1u : 0u);
+              umma_bf16_ta(d, ah, bld, idesc, 1u);
+              umma_bf16_ta(d, al, bhd, idesc, 1u);
             }
-            const uint32_t bh = bbase + (uint32_t)ks * (uint32_t)bn * 32u;
-            const uint32_t bl = bbase + (uint32_t)(ksteps + ks) * (uint32_t)bn * 32u;
-            const uint64_t bhd = sdesc(bh, kLBO, kSBO), bld = sdesc(bl, kLBO, kSBO);
-            umma_bf16_ta(d, a_hi + (uint32_t)ks * 8u, bhd, idesc, ks > 0 ? 1u : 0u);
-            umma_bf16_ta(d, a_hi + (uint32_t)ks * 8u, bld, idesc, 1u);
-            umma_bf16_ta(d, a_lo + (uint32_t)ks * 8u, bhd, idesc, 1u);
+          } else {
+            uint32_t ah = a_hi, al = a_lo;
+            umma_bf16_ta(d, ah, bhd, idesc, 0u);
+            umma_bf16_ta(d, ah, bld, idesc, 1u);
+            umma_bf16_ta(d, al, bhd, idesc, 1u);
+            for (int ks = 1; ks < ksteps; ++ks) {
+              bhd += bstep;
+              bld += bstep;
+              ah += 8u;
+              al += 8u;
+              umma_bf16_ta(d, ah, bhd, idesc, 1u);
+              umma_bf16_ta(d, ah, bld, idesc, 1u);
+              umma_bf16_ta(d, al, bhd, idesc, 1u);
+            }
           }
           if (!ok) break;
           umma_commit(&bempty[b]);
@@ -739,6 +754,10 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, Np);
+      const uint64_t dbase = sdesc(su32(cv), kLBO, kSBO);
+      const uint32_t cv_off = cv_bytes >> 4, a_plane = ca_bytes >> 4;
+      const uint32_t b_off = sym ? 0u : ((uint32_t)nsplit * ca_bytes) >> 4;
+      const uint32_t b_plane = (sym ? ca_bytes : cb_bytes) >> 4;
       bool ok = true;
       int ks = 0;
       for (int f = 0; ok && f < nflush; ++f) {
@@ -752,23 +771,24 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
             break;
           }
           tc_after();
-          const uint32_t base = su32(cv + cs * cv_bytes);
-          // B planes follow the A planes; a Gram reads A's planes twice
-          const uint32_t bbase = sym ? base : base + (uint32_t)nsplit * ca_bytes;
-          const uint32_t bstride = sym ? ca_bytes : cb_bytes;
-          uint64_t bd[3];
-          for (int t = 0; t < nsplit; ++t) bd[t] = sdesc(bbase + t * bstride, kLBO, kSBO);
-          for (int mt = 0; mt < Mt; ++mt) {
+          // descriptors by offset from the first buffer's (address field in
+          // 16-byte units, far from overflowing): B planes follow the A
+          // planes; a Gram reads A's planes twice
+          const uint64_t base = dbase + (uint64_t)(cs * cv_off);
+          const uint64_t b0 = base + b_off, b1 = b0 + b_plane, b2 = b1 + b_plane;
+          const uint32_t acc = kk > 0 ? 1u : 0u;
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            if (mt >= Mt) break;
             const uint32_t d = tmem + (uint32_t)(mt * Np);
-            uint64_t ad[3];
-            for (int t = 0; t < nsplit; ++t) ad[t] = sdesc(base + t * ca_bytes + mt * 4096u, kLBO, kSBO);
-            umma_bf16(d, ad[0], bd[0], idesc, kk > 0 ? 1u : 0u);
-            umma_bf16(d, ad[0], bd[1], idesc, 1u);
-            umma_bf16(d, ad[1], bd[0], idesc, 1u);
+            const uint64_t a0 = base + (uint64_t)(mt * 256), a1 = a0 + a_plane, a2 = a1 + a_plane;
+            umma_bf16(d, a0, b0, idesc, acc);
+            umma_bf16(d, a0, b1, idesc, 1u);
+            umma_bf16(d, a1, b0, idesc, 1u);
             if (nsplit == 3) {
-              umma_bf16(d, ad[0], bd[2], idesc, 1u);
-              umma_bf16(d, ad[2], bd[0], idesc, 1u);
-              umma_bf16(d, ad[1], bd[1], idesc, 1u);
+              umma_bf16(d, a0, b2, idesc, 1u);
+              umma_bf16(d, a2, b0, idesc, 1u);
+              umma_bf16(d, a1, b1, idesc, 1u);
             }
           }
           umma_commit(&cempty[cs]);
