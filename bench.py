@@ -214,6 +214,9 @@ def run_ours(args):
     clocks = clk.summary()
     kernels = [] if args.no_kernels else kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind)
     kernels.insert(0, roofline(n, r, K, rec_s, prec, peaks, peak_kind))
+    for e in kernels:
+        if e["kernel"] in TRAFFIC_PER_ROW and c["N"] == 128:
+            e["traffic"] = TRAFFIC_PER_ROW[e["kernel"]] * n
     roof = max(kernels, key=lambda e: e["step_ms"])
     forms = {prec: {"frames_per_s": value, "fit_s": fit_s, "recon_frames_per_s": K / rec_s}}
     if not args.no_forms:
@@ -271,6 +274,19 @@ def run_e2e(args, sc, c, dmd, dev, st, out, ks):
     sec = a.elapsed_time(b) / 1e3
     return {"value": K * steps / sec, "unit": "frames/s", "h2d_bytes_per_step": int(S_host.numel() * 4),
             "d2h_bytes_per_step": int(F_host.numel() * 4), "steps": steps}
+
+
+# DRAM bytes per row of n (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch divided by its rows) from the ncu captures of the 1,048,576-row cases
+# summarised in profiles/tall_kernels_cfg1_1M_rows.md; traffic grows in
+# proportion to the rows, so a full launch moves these x n bytes.
+TRAFFIC_PER_ROW = {
+    "k_gemm_tn_f32 (snapshot Gram W = S^T S)": 1.441e9 / 1048576,
+    "k_umma_tn (X^T Q1, Q1^T S)": 1.596e9 / 1048576,
+    "k_umma_tn (Gram Q1^T Q1)": 0.737e9 / 1048576,
+    "k_umma_nn_bres (sketch Q1 = X M)": 1.463e9 / 1048576,
+    "k_umma_nn_ares (reconstruction Phi_R C)": 4.786e9 / 1048576,
+}
 
 
 def alu_peak(peaks):
