@@ -318,10 +318,6 @@ __device__ __forceinline__ void two_by_two_eigs(Real a, Real b, Real c, Real d, 
 template <class Real>
 struct EpsOf;
 template <>
-struct EpsOf<double> {
-  static constexpr double v = DBL_EPSILON;
-};
-template <>
 struct EpsOf<float> {
   static constexpr float v = FLT_EPSILON;
 };
@@ -645,6 +641,201 @@ __global__ void k_hess_rqi(int n, const double* __restrict__ H, int ldh, double*
 }
 
 // Unit 2-norm, largest-magnitude entry real positive.  One CTA per column.
+// The same Rayleigh-quotient inverse iteration (same shift rule, same
+// outputs) with one warp per head and U in shared memory: no block barriers,
+// no global round trips.  LU of the Hessenberg H - mu I row by row: an active
+// row a (U's row k once the adjacent-row pivot is taken) and the next matrix
+// row h; U is stored row-packed (row k holds columns k..n-1 at offset
+// k n - k (k - 1) / 2).  The back substitution is column-oriented (no
+// reductions).  Shared memory: n (n + 1) + 8 n doubles + n ints.
+__global__ void __launch_bounds__(32) k_hess_rqi_w(int n, const double* __restrict__ H, int ldh,
+                                                   double* __restrict__ wr, double* __restrict__ wi,
+                                                   const int* __restrict__ heads, double* __restrict__ Yre,
+                                                   double* __restrict__ Yim, const double* __restrict__ hnorm_ptr) {
+  extern __shared__ double sm[];
+  const int np = n * (n + 1) / 2;
+  double* Ur = sm;
+  double* Ui = Ur + np;
+  double* ar = Ui + np;     // active row (columns k..)
+  double* ai = ar + n;
+  double* mre = ai + n;     // multipliers
+  double* mim = mre + n;
+  double* xre = mim + n;
+  double* xim = xre + n;
+  double* yre = xim + n;
+  double* yim = yre + n;
+  int* piv = reinterpret_cast<int*>(yim + n);
+  const int lane = threadIdx.x;
+  const int e = heads[blockIdx.x];
+  if (e < 0) return;
+  double mur = wr[e], mui = wi[e];
+  const bool pair = mui > 0.0;
+  const double tiny = kEps * fmax(*hnorm_ptr, DBL_MIN);
+  auto off = [n](int k) { return k * n - k * (k - 1) / 2; };
+  for (int i = lane; i < n; i += 32) {
+    xre[i] = 1.0 / sqrt((double)n);
+    xim[i] = 0.0;
+  }
+  for (int it = 0; it < 3; ++it) {
+    // active row = row 0 of H - mu I
+    for (int j = lane; j < n; j += 32) {
+      ar[j] = H[(int64_t)j * ldh] - (j == 0 ? mur : 0.0);
+      ai[j] = j == 0 ? -mui : 0.0;
+    }
+    __syncwarp();
+    // row k + 1 of H at columns k + lane + 32 t, loaded one step ahead
+    constexpr int kMaxT = 5;   // n <= 160
+    double hrow[kMaxT];
+#pragma unroll
+    for (int t = 0; t < kMaxT; ++t) {
+      const int j = lane + 32 * t;
+      hrow[t] = (n > 1 && j < n) ? H[1 + (int64_t)j * ldh] : 0.0;
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+      // next row of H - mu I (columns k.. ; Hessenberg: zero left of k)
+      const double hkr = __shfl_sync(0xffffffffu, hrow[0], 0);
+      const double pa = ar[k] * ar[k] + ai[k] * ai[k];
+      const bool sw = hkr * hkr > pa;
+      // pivot p and the other entry o of column k; multiplier l = o / p
+      double pr = sw ? hkr : ar[k], pim = sw ? 0.0 : ai[k];
+      const double orr = sw ? ar[k] : hkr, oi = sw ? ai[k] : 0.0;
+      if (pr == 0.0 && pim == 0.0) pr = tiny;
+      const double den = pr * pr + pim * pim;
+      const double lr = (orr * pr + oi * pim) / den, li = (oi * pr - orr * pim) / den;
+      double* ur = Ur + off(k) - k;   // ur[j] = U(k, j)
+      double* ui = Ui + off(k) - k;
+      double hnext[kMaxT];
+#pragma unroll
+      for (int t = 0; t < kMaxT; ++t) {
+        const int j = k + 1 + lane + 32 * t;
+        hnext[t] = (k + 2 < n && j < n) ? H[(k + 2) + (int64_t)j * ldh] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxT; ++t) {
+        const int j = k + lane + 32 * t;
+        if (j >= n) break;
+        double hr = hrow[t], hi = 0.0;
+        if (j == k + 1) {
+          hr -= mur;
+          hi = -mui;
+        }
+        double a_r = ar[j], a_i = ai[j];
+        if (sw) {
+          const double tr = a_r, ti = a_i;
+          a_r = hr;
+          a_i = hi;
+          hr = tr;
+          hi = ti;
+        }
+        if (j == k) {
+          ur[j] = pr;
+          ui[j] = pim;
+        } else {
+          ur[j] = a_r;
+          ui[j] = a_i;
+          ar[j] = hr - (lr * a_r - li * a_i);   // new active row
+          ai[j] = hi - (lr * a_i + li * a_r);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxT; ++t) hrow[t] = hnext[t];
+      if (lane == 0) {
+        piv[k] = sw ? 1 : 0;
+        mre[k] = lr;
+        mim[k] = li;
+      }
+      __syncwarp();
+    }
+    {
+      double* ur = Ur + off(n - 1) - (n - 1);
+      double* ui = Ui + off(n - 1) - (n - 1);
+      if (lane == 0) {
+        double r_ = ar[n - 1], i_ = ai[n - 1];
+        if (r_ == 0.0 && i_ == 0.0) r_ = tiny;
+        ur[n - 1] = r_;
+        ui[n - 1] = i_;
+      }
+    }
+    __syncwarp();
+    // y = L^{-1} P x (sequential, lane 0), then U y = that (column-oriented)
+    if (lane == 0) {
+      for (int i = 0; i < n; ++i) {
+        yre[i] = xre[i];
+        yim[i] = xim[i];
+      }
+      for (int k = 0; k + 1 < n; ++k) {
+        if (piv[k]) {
+          const double tr = yre[k], ti = yim[k];
+          yre[k] = yre[k + 1];
+          yim[k] = yim[k + 1];
+          yre[k + 1] = tr;
+          yim[k + 1] = ti;
+        }
+        const double lr = mre[k], li = mim[k];
+        yre[k + 1] -= lr * yre[k] - li * yim[k];
+        yim[k + 1] -= lr * yim[k] + li * yre[k];
+      }
+    }
+    __syncwarp();
+    for (int i = n - 1; i >= 0; --i) {
+      const double uir = Ur[off(i)], uii = Ui[off(i)];
+      const double den = uir * uir + uii * uii;
+      const double br = yre[i], bi = yim[i];
+      const double tr = (br * uir + bi * uii) / den, ti = (bi * uir - br * uii) / den;
+      __syncwarp();
+      if (lane == 0) {
+        yre[i] = tr;
+        yim[i] = ti;
+      }
+      for (int j = lane; j < i; j += 32) {   // y[j] -= U(j, i) y[i]
+        const double cr = Ur[off(j) + (i - j)], ci = Ui[off(j) + (i - j)];
+        yre[j] -= cr * tr - ci * ti;
+        yim[j] -= cr * ti + ci * tr;
+      }
+      __syncwarp();
+    }
+    // Rayleigh quotient: theta = x^H y (x has unit norm); mu += 1 / theta
+    double tr_ = 0.0, ti_ = 0.0, yy = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      tr_ += xre[i] * yre[i] + xim[i] * yim[i];
+      ti_ += xre[i] * yim[i] - xim[i] * yre[i];
+      yy += yre[i] * yre[i] + yim[i] * yim[i];
+    }
+    tr_ = warp_sum(tr_);
+    ti_ = warp_sum(ti_);
+    yy = warp_sum(yy);
+    const double den = tr_ * tr_ + ti_ * ti_;
+    double dr = 0.0, di = 0.0;
+    if (den > 0.0 && isfinite(den)) {
+      dr = tr_ / den;
+      di = -ti_ / den;
+    }
+    const double mag = hypot(mur, mui);
+    if (hypot(dr, di) < 1e-3 * fmax(mag, 1e-300)) {
+      mur += dr;
+      if (pair) mui += di;   // a real eigenvalue stays real
+    }
+    const double inv = (yy > 0.0 && isfinite(yy)) ? 1.0 / sqrt(yy) : 1.0;
+    for (int i = lane; i < n; i += 32) {
+      xre[i] = yre[i] * inv;
+      xim[i] = yim[i] * inv;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) {
+    Yre[i + (int64_t)blockIdx.x * n] = xre[i];
+    Yim[i + (int64_t)blockIdx.x * n] = xim[i];
+  }
+  if (lane == 0) {
+    wr[e] = mur;
+    wi[e] = pair ? mui : 0.0;
+    if (pair && e + 1 < n) {
+      wr[e + 1] = mur;
+      wi[e + 1] = -mui;
+    }
+  }
+}
+
 __global__ void k_normalize_complex(int n, double* Yre, double* Yim) {
   __shared__ double red[32];
   __shared__ int argmax;
@@ -1016,115 +1207,101 @@ __device__ __forceinline__ void store_square(double* G, int ld, const double* S,
     for (int a = lane; a < rows; a += 32) G[a + (int64_t)b * ld] = S[a + b * ldw];
 }
 
-// Cholesky as k_cholesky_upper (same pivot / drop rule), matrix in shared memory.
-__global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* info, int tag) {
-  extern __shared__ double sm[];
+// Cholesky in shared memory with one barrier per column (same pivot / drop
+// rule as k_cholesky_upper), in precision Real.  Column j's step: the warp
+// owning column b > j parks R[j][b] = S[j][b] / p_j in the unused lower
+// triangle (S[b][j]) and updates S[a][b] -= S[j][a] S[j][b] / d_j for
+// j < a <= b -- row j is only read, so no second barrier is needed; the warp
+// owning column j + 1 finishes first and its lane 0 takes the next pivot.
+template <class Real>
+__global__ void k_chol_1s(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+  extern __shared__ __align__(16) unsigned char smc[];
+  Real* S = reinterpret_cast<Real*>(smc);
   const int ldw = n | 1;
-  double* S = sm;
-  double* r = S + n * ldw;      // row j of R, contiguous
-  double* red = r + n;
-  __shared__ double piv;
+  __shared__ Real piv_s[2], invd_s[2], ip_s[2];
+  __shared__ int stop;
+  __shared__ double red[32];
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
   for (int b = warp; b < n; b += nw)
-    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = G[a + (int64_t)b * ld];
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = (Real)G[a + (int64_t)b * ld];
   double loc = 0.0;
   for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
   const double dmax = block_max(loc, red);
-  const double floor_ = tau * dmax;
+  const Real floor_ = (Real)(tau * dmax);
+  // pivot of column j from the (final) S[j][j]: p, 1/p^2; 0 = dropped direction
+  auto pivot = [&](int j) {
+    const Real d = S[j + j * ldw];
+    Real p = 0, invd = 0, ip = 0;
+    int st = 0;
+    if (!isfinite((double)d) || !isfinite(dmax)) {
+      raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+      st = 1;
+    } else if (!(dmax > 0.0)) {
+      raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+      st = 1;
+    } else if (!(d > floor_)) {
+      if (info) atomicAdd(&info[5], 1);
+    } else {
+      p = sqrt(d);
+      ip = Real(1) / p;
+      invd = ip * ip;
+    }
+    S[j + j * ldw] = p;
+    piv_s[j & 1] = p;
+    invd_s[j & 1] = invd;
+    ip_s[j & 1] = ip;
+    if (st) stop = 1;
+  };
+  if (tid == 0) {
+    stop = 0;
+    if (n > 0) pivot(0);
+  }
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const double d = S[j + j * ldw];
-      if (!isfinite(d) || !isfinite(dmax)) {
-        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
-        piv = -1.0;
-      } else if (!(dmax > 0.0)) {
-        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
-        piv = -1.0;
-      } else if (!(d > floor_)) {
-        piv = 0.0;   // dropped direction
-        if (info) atomicAdd(&info[5], 1);
-      } else {
-        piv = sqrt(d);
-      }
-      if (piv >= 0.0) S[j + j * ldw] = piv;
-    }
-    __syncthreads();
-    const double p = piv;
-    if (p < 0.0) return;
-    const double ip = p == 0.0 ? 0.0 : 1.0 / p;
-    for (int i = j + 1 + tid; i < n; i += bd) {
-      const double v = p == 0.0 ? 0.0 : S[j + i * ldw] * ip;
-      S[j + i * ldw] = v;
-      r[i] = v;
-    }
-    __syncthreads();
-    if (p == 0.0) continue;
+    if (stop) return;
+    // the pivot's square root and reciprocals come from one lane: on the
+    // slow FP64 pipe a redundant per-thread division would cost more than
+    // the column's update
+    const Real p = piv_s[j & 1], invd = invd_s[j & 1], ip = ip_s[j & 1];
     for (int b = j + 1 + warp; b < n; b += nw) {
-      const double rb = r[b];
-      double* col = S + b * ldw;
-      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fma(-r[a], rb, col[a]);
+      const Real sjb = S[j + b * ldw];
+      if (lane == 0) S[b + j * ldw] = p == Real(0) ? Real(0) : sjb * ip;   // R[j][b], parked
+      if (p != Real(0)) {
+        const Real tb = sjb * invd;
+        Real* col = S + b * ldw;
+        for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fma(-S[j + a * ldw], tb, col[a]);
+      }
+      if (b == j + 1) {
+        __syncwarp();
+        if (lane == 0) pivot(j + 1);
+      }
     }
     __syncthreads();
   }
   for (int b = warp; b < n; b += nw)
-    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? S[a + b * ldw] : 0.0;
+    for (int a = lane; a < n; a += 32)
+      G[a + (int64_t)b * ld] = (a < b) ? (double)S[b + a * ldw] : (a == b ? (double)S[a + a * ldw] : 0.0);
 }
 
-// T = R^{-1} as k_tri_inv_upper; every CTA first copies the columns it needs
-// (0 .. its last column) of R into shared memory.  One warp per column.
-__global__ void k_tri_inv_smem(int n, const double* __restrict__ R, int ldr, double* __restrict__ T, int ldt) {
+// T = R^{-1}, one CTA per column j, column-oriented back substitution:
+// b = e_j; for i = j .. 0: t_i = b_i / r_ii, b[0..i) -= t_i R[0..i, i].  No
+// reductions: each step is one scaled column update spread over the lanes of
+// one warp, so the FP64 work of the n columns runs on n SMs at once.  All
+// warps of the CTA stage R's columns 0..j (upper part, packed) in shared
+// memory first.
+__global__ void __launch_bounds__(128) k_tri_inv_col(int n, const double* __restrict__ R, int ldr,
+                                                     double* __restrict__ T, int ldt) {
   extern __shared__ double sm[];
-  const int ldw = n | 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int jfirst = blockIdx.x * nw;
-  const int jlast = min(n - 1, jfirst + nw - 1);
-  double* S = sm;
-  double* tv = S + (jlast + 1) * ldw;   // nw vectors of n
-  for (int b = warp; b <= jlast; b += nw)
-    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = R[a + (int64_t)b * ldr];
-  __syncthreads();
-  const int j = jfirst + warp;
-  if (j > jlast) return;
-  double* t = tv + warp * n;
-  double* out = T + (int64_t)j * ldt;
-  for (int i = j + 1 + lane; i < n; i += 32) out[i] = 0.0;
-  const double rjj = S[j + j * ldw];
-  if (rjj == 0.0) {
-    for (int i = lane; i <= j; i += 32) out[i] = 0.0;
-    return;
-  }
-  if (lane == 0) t[j] = 1.0 / rjj;
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int k = i + 1 + lane; k <= j; k += 32) s = fma(S[i + k * ldw], t[k], s);
-    s = warp_sum(s);
-    if (lane == 0) {
-      const double rii = S[i + i * ldw];
-      t[i] = (rii == 0.0) ? 0.0 : -s / rii;
-    }
-    __syncwarp();
-  }
-  for (int i = lane; i <= j; i += 32) out[i] = t[i];
-}
-
-// T = R^{-1}, one CTA (one warp) per column j, column-oriented back
-// substitution: b = e_j; for i = j .. 0: t_i = b_i / r_ii, b[0..i) -= t_i
-// R[0..i, i].  No reductions: each step is one scaled column update spread
-// over the lanes, so the FP64 work of the n columns runs on n SMs at once.
-// R's columns 0..j (upper part) are staged in shared memory, packed.
-__global__ void __launch_bounds__(32) k_tri_inv_col(int n, const double* __restrict__ R, int ldr,
-                                                    double* __restrict__ T, int ldt) {
-  extern __shared__ double sm[];
-  const int j = blockIdx.x, lane = threadIdx.x;
+  const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   double* Rp = sm;                        // column i at offset i (i + 1) / 2
   double* b = Rp + (j + 1) * (j + 2) / 2;  // j + 1
   double* inv = b + (j + 1);               // j + 1
-  for (int i = 0; i <= j; ++i) {
+  for (int i = warp; i <= j; i += nw) {
     const int off = i * (i + 1) / 2;
     for (int a = lane; a <= i; a += 32) Rp[off + a] = R[a + (int64_t)i * ldr];
   }
-  __syncwarp();
+  __syncthreads();
+  if (warp != 0) return;
   for (int i = lane; i <= j; i += 32) {
     const double d = Rp[i * (i + 1) / 2 + i];
     inv[i] = d == 0.0 ? 0.0 : 1.0 / d;
@@ -1148,82 +1325,36 @@ __global__ void __launch_bounds__(32) k_tri_inv_col(int n, const double* __restr
   for (int i = lane; i <= j; i += 32) out[i] = b[i];
 }
 
-// Cholesky as k_cholesky_smem in FP32 (input and output FP64).  For Gram
-// matrices that are already close to the identity (the second pass of
-// CholeskyQR2), where FP32 rounding (~1e-7) is far below the accuracy the
-// basis is stored with.
-__global__ void k_cholesky_f32(int n, double* G, int ld, double tau, int32_t* info, int tag) {
-  extern __shared__ float smf[];
-  const int ldw = n | 1;
-  float* S = smf;
-  float* r = S + n * ldw;
-  __shared__ double red[32];
-  __shared__ float piv;
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-  for (int b = warp; b < n; b += nw)
-    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = (float)G[a + (int64_t)b * ld];
-  double loc = 0.0;
-  for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
-  const double dmax = block_max(loc, red);
-  const float floor_ = (float)(tau * dmax);
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const float d = S[j + j * ldw];
-      if (!isfinite(d) || !isfinite(dmax)) {
-        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
-        piv = -1.f;
-      } else if (!(dmax > 0.0)) {
-        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
-        piv = -1.f;
-      } else if (!(d > floor_)) {
-        piv = 0.f;
-        if (info) atomicAdd(&info[5], 1);
-      } else {
-        piv = sqrtf(d);
-      }
-      if (piv >= 0.f) S[j + j * ldw] = piv;
-    }
-    __syncthreads();
-    const float p = piv;
-    if (p < 0.f) return;
-    const float ip = p == 0.f ? 0.f : 1.f / p;
-    for (int i = j + 1 + tid; i < n; i += bd) {
-      const float v = p == 0.f ? 0.f : S[j + i * ldw] * ip;
-      S[j + i * ldw] = v;
-      r[i] = v;
-    }
-    __syncthreads();
-    if (p == 0.f) continue;
-    for (int b = j + 1 + warp; b < n; b += nw) {
-      const float rb = r[b];
-      float* col = S + b * ldw;
-      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fmaf(-r[a], rb, col[a]);
-    }
-    __syncthreads();
-  }
-  for (int b = warp; b < n; b += nw)
-    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? (double)S[a + b * ldw] : 0.0;
-}
-
 // Householder reflector of x[0..m) (x[0] = alpha): v (v[0] = 1) into v[],
-// returns tau and beta; x itself is not modified.  Block-wide.
+// returns tau and beta; x itself is not modified.  Block-wide.  The scalar
+// square root and divisions are taken by one thread and broadcast: on GB300's
+// FP64 pipe (~2 DFMA/clk per SM) a block-wide redundant evaluation costs more
+// than the reflector's vector work.
 __device__ __forceinline__ void house(const double* x, int m, double* v, double* red, double& tau, double& beta) {
+  __shared__ double hs[3];
   const int tid = threadIdx.x, bd = blockDim.x;
   double loc = 0.0;
   for (int i = 1 + tid; i < m; i += bd) loc += x[i] * x[i];
   const double sig = block_sum(loc, red);
-  const double alpha = x[0];
-  if (sig == 0.0) {
-    tau = 0.0;
-    beta = alpha;
-    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : 0.0;
-  } else {
-    const double nrm = sqrt(alpha * alpha + sig);
-    beta = alpha <= 0.0 ? nrm : -nrm;
-    tau = (beta - alpha) / beta;
-    const double sc = 1.0 / (alpha - beta);
-    for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : x[i] * sc;
+  if (tid == 0) {
+    const double alpha = x[0];
+    if (sig == 0.0) {
+      hs[0] = 0.0;
+      hs[1] = alpha;
+      hs[2] = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      const double bt = alpha <= 0.0 ? nrm : -nrm;
+      hs[0] = (bt - alpha) / bt;
+      hs[1] = bt;
+      hs[2] = 1.0 / (alpha - bt);
+    }
   }
+  __syncthreads();
+  tau = hs[0];
+  beta = hs[1];
+  const double sc = hs[2];
+  for (int i = tid; i < m; i += bd) v[i] = (i == 0) ? 1.0 : x[i] * sc;
   __syncthreads();
 }
 
@@ -1305,13 +1436,13 @@ __global__ void k_hessenberg_smem(int n, double* A, int ld, double* tau) {
       x[0] = beta;
       tau[k] = t;
     }
-    // left: w_j = v . A[k+1.., j] for columns j = k+1..; then A -= t v w^T
-    for (int j = k + 1 + warp; j < n; j += nw) {
+    // left: w_j = v . A[k+1.., j] for columns j = k+1.. (one thread per
+    // column: no FP64 reductions); then A -= t v w^T
+    for (int j = k + 1 + tid; j < n; j += bd) {
       const double* col = S + j * ldw + (k + 1);
       double s = 0.0;
-      for (int i = lane; i < m; i += 32) s = fma(v[i], col[i], s);
-      s = warp_sum(s);
-      if (lane == 0) w[j] = s;
+      for (int i = 0; i < m; ++i) s = fma(v[i], col[i], s);
+      w[j] = s;
     }
     __syncthreads();
     for (int j = k + 1 + warp; j < n; j += nw) {
@@ -1364,12 +1495,11 @@ __global__ void k_lstsq_smem(int mr, int nc, double* A, int ld, int nrhs, double
     house(col + k, hgt, v + k, red, t, beta);
     rmax = fmax(rmax, fabs(beta));
     if (t != 0.0) {
-      for (int j = k + 1 + warp; j < ncol; j += nw) {
+      for (int j = k + 1 + tid; j < ncol; j += bd) {   // one thread per column
         const double* cj = S + j * ldw;
         double s = 0.0;
-        for (int i = k + lane; i < mr; i += 32) s = fma(v[i], cj[i], s);
-        s = warp_sum(s);
-        if (lane == 0) w[j] = s;
+        for (int i = k; i < mr; ++i) s = fma(v[i], cj[i], s);
+        w[j] = s;
       }
       __syncthreads();
       for (int j = k + 1 + warp; j < ncol; j += nw) {
@@ -1432,10 +1562,10 @@ static dmd_status set_smem(const void* fn, size_t bytes) {
 }
 
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
-  const size_t smem = square_smem(n, n, (size_t)n + 32);
+  const size_t smem = square_smem(n, n, 0);
   if (smem <= kSmallSmemMax) {
-    DMD_TRY(set_smem((const void*)k_cholesky_smem, smem));
-    k_cholesky_smem<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+    DMD_TRY(set_smem((const void*)k_chol_1s<double>, smem));
+    k_chol_1s<double><<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
   } else {
     k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
   }
@@ -1447,7 +1577,7 @@ dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cu
   const size_t smem = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(double);
   if (smem <= kSmallSmemMax) {
     DMD_TRY(set_smem((const void*)k_tri_inv_col, smem));
-    k_tri_inv_col<<<(unsigned)n, 32, smem, st>>>(n, R, ldr, T, ldt);
+    k_tri_inv_col<<<(unsigned)n, 128, smem, st>>>(n, R, ldr, T, ldt);
   } else {
     k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
   }
@@ -1456,10 +1586,10 @@ dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cu
 }
 
 dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
-  const size_t smem = ((size_t)(n | 1) * n + n) * sizeof(float);
+  const size_t smem = (size_t)(n | 1) * n * sizeof(float);
   if (smem > kSmallSmemMax) return cholesky_upper(n, G, ld, tau, info, tag, st);
-  DMD_TRY(set_smem((const void*)k_cholesky_f32, smem));
-  k_cholesky_f32<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+  DMD_TRY(set_smem((const void*)k_chol_1s<float>, smem));
+  k_chol_1s<float><<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -1511,6 +1641,14 @@ dmd_status collect_heads(int n, const double* wi, int* heads, int* nheads, int32
 dmd_status hess_eigvecs(int n, const double* H, int ldh, const double* wr, const double* wi,
                         const int* heads, int nheads_max, double* Yre, double* Yim, double* work,
                         const double* hnorm, cudaStream_t st) {
+  const size_t smem_w = ((size_t)n * (n + 1) + 8 * (size_t)n) * sizeof(double) + (size_t)n * sizeof(int) + 16;
+  if (n <= 160 && smem_w <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_hess_rqi_w, smem_w));
+    k_hess_rqi_w<<<(unsigned)nheads_max, 32, smem_w, st>>>(n, H, ldh, const_cast<double*>(wr),
+                                                            const_cast<double*>(wi), heads, Yre, Yim, hnorm);
+    DMD_LAUNCH_CHECK();
+    return DMD_OK;
+  }
   const size_t smem = (6 * (size_t)n) * sizeof(double) + (size_t)n * sizeof(int) + 16;
   k_hess_rqi<<<(unsigned)nheads_max, 256, smem, st>>>(n, H, ldh, const_cast<double*>(wr), const_cast<double*>(wi),
                                                        heads, Yre, Yim, work, hnorm);

@@ -324,11 +324,12 @@ int sm_count() {
 
 }  // namespace
 
-// Row splits of the TN reduction: about four resident waves of CTAs (three
-// per SM), each split at least 1024 rows.
+// Row splits of the TN reduction: about eight resident waves of CTAs (three
+// per SM; short CTAs keep the last wave's tail small), each split at least
+// 1024 rows.
 int tn_splits(int64_t n, int Ka, int N) {
   const int tiles = (int)(ceil_div(Ka, TN_BT) * ceil_div(N, TN_BT));
-  int64_t want = ceil_div(4LL * 3 * sm_count(), tiles);
+  int64_t want = ceil_div(8LL * 3 * sm_count(), tiles);
   const int64_t maxs = std::max<int64_t>(1, ceil_div(n, 1024));
   if (want > maxs) want = maxs;
   if (want > 1024) want = 1024;
