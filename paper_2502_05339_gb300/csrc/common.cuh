@@ -91,15 +91,16 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // Block-wide sum; `red` must hold blockDim.x / 32 doubles.  All threads get the result.
+// The cross-warp step is a butterfly over the warps' partials (fixed order,
+// so reproducible) rather than a running sum: FP64 adds have ~64 cycles of
+// latency on GB300, and a chain of 16-32 of them would dominate.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += red[i];  // fixed order: reproducible
-  return t;
+  return warp_sum(lane < nw ? red[lane] : 0.0);
 }
 
 __device__ __forceinline__ double block_max(double v, double* red) {

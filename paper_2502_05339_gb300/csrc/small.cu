@@ -28,6 +28,24 @@ namespace {
 
 constexpr double kEps = DBL_EPSILON;
 
+// ------------------------------------------------------ FP64 reciprocal
+
+// 1 / x for finite, nonzero, normal x: the hardware's approximate reciprocal
+// (about 20 correct bits) refined by two Newton-Raphson steps
+// y <- y + y (1 - x y), each of which roughly doubles the correct bits.  An
+// IEEE FP64 division is a long dependent sequence on GB300 (measured ~560
+// cycles); this is one approximation and four FMAs.  Used inside sequential
+// recurrences (Sturm counts, the Hessenberg LU of the eigenvector
+// refinement), where that latency is the critical path.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // ------------------------------------------------------------------ GEMM
 
 // C[M x N] = alpha op(A) op(B) + beta C (column-major; op = transpose when t* != 0).
@@ -335,16 +353,26 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
   const int ldw = n | 1;
   Real* H = in_smem ? reinterpret_cast<Real*>(smem_raw) : Hscratch;
   const int lane = threadIdx.x;
-  const Real eps = EpsOf<Real>::v;
-  for (int e = lane; e < n * n; e += 32) {
-    const int i = e % n, j = e / n;
-    H[i + (int64_t)j * ldw] = (i <= j + 1) ? (Real)Hin[i + (int64_t)j * ldh] : Real(0);
+  // Deflation threshold.  These eigenvalues only seed the FP64
+  // Rayleigh-quotient refinement: an eigenvalue deflated at a subdiagonal of
+  // 1e-5 (relative) is already accurate to about its square, which the
+  // refinement takes to FP64 accuracy in its first step; waiting for FP32
+  // roundoff would cost about one more QR sweep per eigenvalue.
+  const Real deflate = fmax(EpsOf<Real>::v, Real(1e-5));
+  // copy (Hessenberg part, zeros below) and the max-abs norm, lanes over rows
+  Real amax = 0;
+#pragma unroll 4
+  for (int j = 0; j < n; ++j) {
+    for (int i = lane; i < n; i += 32) {
+      const Real v = (i <= j + 1) ? (Real)Hin[i + (int64_t)j * ldh] : Real(0);
+      H[i + (int64_t)j * ldw] = v;
+      amax = fmax(amax, fabs(v));
+    }
   }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   __syncwarp();
 #define HH(i, j) H[(i) + (int64_t)(j) * ldw]
-  Real anorm = 0;
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i <= min(j + 1, n - 1); ++i) anorm = fmax(anorm, fabs(HH(i, j)));
+  Real anorm = amax;
   if (anorm == Real(0)) anorm = 1;
   int hi = n - 1, its = 0, total = 0;
   while (hi >= 0) {
@@ -352,7 +380,7 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
     while (lo > 0) {
       Real s = fabs(HH(lo - 1, lo - 1)) + fabs(HH(lo, lo));
       if (s == Real(0)) s = anorm;
-      if (fabs(HH(lo, lo - 1)) <= eps * s) break;
+      if (fabs(HH(lo, lo - 1)) <= deflate * s) break;
       --lo;
     }
     if (lo > 0) {
@@ -700,8 +728,8 @@ __global__ void __launch_bounds__(32) k_hess_rqi_w(int n, const double* __restri
       double pr = sw ? hkr : ar[k], pim = sw ? 0.0 : ai[k];
       const double orr = sw ? ar[k] : hkr, oi = sw ? ai[k] : 0.0;
       if (pr == 0.0 && pim == 0.0) pr = tiny;
-      const double den = pr * pr + pim * pim;
-      const double lr = (orr * pr + oi * pim) / den, li = (oi * pr - orr * pim) / den;
+      const double iden = rcp_nr(pr * pr + pim * pim);
+      const double lr = (orr * pr + oi * pim) * iden, li = (oi * pr - orr * pim) * iden;
       double* ur = Ur + off(k) - k;   // ur[j] = U(k, j)
       double* ui = Ui + off(k) - k;
       double hnext[kMaxT];
@@ -779,9 +807,9 @@ __global__ void __launch_bounds__(32) k_hess_rqi_w(int n, const double* __restri
     __syncwarp();
     for (int i = n - 1; i >= 0; --i) {
       const double uir = Ur[off(i)], uii = Ui[off(i)];
-      const double den = uir * uir + uii * uii;
+      const double iden = rcp_nr(uir * uir + uii * uii);
       const double br = yre[i], bi = yim[i];
-      const double tr = (br * uir + bi * uii) / den, ti = (bi * uir - br * uii) / den;
+      const double tr = (br * uir + bi * uii) * iden, ti = (bi * uir - br * uii) * iden;
       __syncwarp();
       if (lane == 0) {
         yre[i] = tr;
@@ -973,7 +1001,7 @@ __device__ int sturm_count(int n, const double* d, const double* e, double x, do
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0.0) ++cnt;
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    q = (d[i] - x) - e[i - 1] * e[i - 1] * rcp_nr(q);   // |q| >= pivmin: normal
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0.0) ++cnt;
   }
@@ -1196,6 +1224,21 @@ __global__ void k_lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, 
 
 constexpr size_t kSmallSmemMax = 220 * 1024;
 
+// sum_i x[i * sx] y[i] with four independent accumulators: an FP64 FMA has
+// ~64 cycles of latency on GB300, so a single chain would serialise on it.
+__device__ __forceinline__ double dot4(const double* x, int sx, const double* y, int m) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = 0;
+  for (; i + 3 < m; i += 4) {
+    s0 = fma(x[i * sx], y[i], s0);
+    s1 = fma(x[(i + 1) * sx], y[i + 1], s1);
+    s2 = fma(x[(i + 2) * sx], y[i + 2], s2);
+    s3 = fma(x[(i + 3) * sx], y[i + 3], s3);
+  }
+  for (; i < m; ++i) s0 = fma(x[i * sx], y[i], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
 __device__ __forceinline__ void load_square(double* S, int ldw, const double* G, int ld, int rows, int cols) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = warp; b < cols; b += nw)
@@ -1207,80 +1250,116 @@ __device__ __forceinline__ void store_square(double* G, int ld, const double* S,
     for (int a = lane; a < rows; a += 32) G[a + (int64_t)b * ld] = S[a + b * ldw];
 }
 
-// Cholesky in shared memory with one barrier per column (same pivot / drop
-// rule as k_cholesky_upper), in precision Real.  Column j's step: the warp
-// owning column b > j parks R[j][b] = S[j][b] / p_j in the unused lower
-// triangle (S[b][j]) and updates S[a][b] -= S[j][a] S[j][b] / d_j for
-// j < a <= b -- row j is only read, so no second barrier is needed; the warp
-// owning column j + 1 finishes first and its lane 0 takes the next pivot.
-template <class Real>
-__global__ void k_chol_1s(int n, double* G, int ld, double tau, int32_t* info, int tag) {
-  extern __shared__ __align__(16) unsigned char smc[];
-  Real* S = reinterpret_cast<Real*>(smc);
+// Cholesky as k_cholesky_upper (same pivot / drop rule), matrix in shared memory.
+__global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+  extern __shared__ double sm[];
   const int ldw = n | 1;
-  __shared__ Real piv_s[2], invd_s[2], ip_s[2];
-  __shared__ int stop;
-  __shared__ double red[32];
+  double* S = sm;
+  double* r = S + n * ldw;      // row j of R, contiguous
+  double* red = r + n;
+  __shared__ double piv, ipiv;
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
   for (int b = warp; b < n; b += nw)
-    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = (Real)G[a + (int64_t)b * ld];
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = G[a + (int64_t)b * ld];
   double loc = 0.0;
   for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
   const double dmax = block_max(loc, red);
-  const Real floor_ = (Real)(tau * dmax);
-  // pivot of column j from the (final) S[j][j]: p, 1/p^2; 0 = dropped direction
-  auto pivot = [&](int j) {
-    const Real d = S[j + j * ldw];
-    Real p = 0, invd = 0, ip = 0;
-    int st = 0;
-    if (!isfinite((double)d) || !isfinite(dmax)) {
-      raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
-      st = 1;
-    } else if (!(dmax > 0.0)) {
-      raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
-      st = 1;
-    } else if (!(d > floor_)) {
-      if (info) atomicAdd(&info[5], 1);
-    } else {
-      p = sqrt(d);
-      ip = Real(1) / p;
-      invd = ip * ip;
-    }
-    S[j + j * ldw] = p;
-    piv_s[j & 1] = p;
-    invd_s[j & 1] = invd;
-    ip_s[j & 1] = ip;
-    if (st) stop = 1;
-  };
-  if (tid == 0) {
-    stop = 0;
-    if (n > 0) pivot(0);
-  }
-  __syncthreads();
+  const double floor_ = tau * dmax;
   for (int j = 0; j < n; ++j) {
-    if (stop) return;
-    // the pivot's square root and reciprocals come from one lane: on the
-    // slow FP64 pipe a redundant per-thread division would cost more than
-    // the column's update
-    const Real p = piv_s[j & 1], invd = invd_s[j & 1], ip = ip_s[j & 1];
+    if (tid == 0) {
+      const double d = S[j + j * ldw];
+      if (!isfinite(d) || !isfinite(dmax)) {
+        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+        piv = -1.0;
+      } else if (!(dmax > 0.0)) {
+        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+        piv = -1.0;
+      } else if (!(d > floor_)) {
+        piv = 0.0;   // dropped direction
+        if (info) atomicAdd(&info[5], 1);
+      } else {
+        piv = sqrt(d);
+      }
+      if (piv >= 0.0) S[j + j * ldw] = piv;
+      ipiv = piv > 0.0 ? 1.0 / piv : 0.0;   // one lane: FP64 division is slow
+    }
+    __syncthreads();
+    const double p = piv;
+    if (p < 0.0) return;
+    const double ip = ipiv;
+    for (int i = j + 1 + tid; i < n; i += bd) {
+      const double v = p == 0.0 ? 0.0 : S[j + i * ldw] * ip;
+      S[j + i * ldw] = v;
+      r[i] = v;
+    }
+    __syncthreads();
+    if (p == 0.0) continue;
     for (int b = j + 1 + warp; b < n; b += nw) {
-      const Real sjb = S[j + b * ldw];
-      if (lane == 0) S[b + j * ldw] = p == Real(0) ? Real(0) : sjb * ip;   // R[j][b], parked
-      if (p != Real(0)) {
-        const Real tb = sjb * invd;
-        Real* col = S + b * ldw;
-        for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fma(-S[j + a * ldw], tb, col[a]);
-      }
-      if (b == j + 1) {
-        __syncwarp();
-        if (lane == 0) pivot(j + 1);
-      }
+      const double rb = r[b];
+      double* col = S + b * ldw;
+      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fma(-r[a], rb, col[a]);
     }
     __syncthreads();
   }
   for (int b = warp; b < n; b += nw)
-    for (int a = lane; a < n; a += 32)
-      G[a + (int64_t)b * ld] = (a < b) ? (double)S[b + a * ldw] : (a == b ? (double)S[a + a * ldw] : 0.0);
+    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? S[a + b * ldw] : 0.0;
+}
+
+// Cholesky as k_cholesky_smem in FP32 (input and output FP64).  For Gram
+// matrices that are already close to the identity (the second pass of
+// CholeskyQR2), where FP32 rounding (~1e-7) is far below the accuracy the
+// basis is stored with.
+__global__ void k_cholesky_f32(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+  extern __shared__ float smf[];
+  const int ldw = n | 1;
+  float* S = smf;
+  float* r = S + n * ldw;
+  __shared__ double red[32];
+  __shared__ float piv;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a <= b; a += 32) S[a + b * ldw] = (float)G[a + (int64_t)b * ld];
+  double loc = 0.0;
+  for (int j = tid; j < n; j += bd) loc = fmax(loc, G[j + (int64_t)j * ld]);
+  const double dmax = block_max(loc, red);
+  const float floor_ = (float)(tau * dmax);
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float d = S[j + j * ldw];
+      if (!isfinite(d) || !isfinite(dmax)) {
+        raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+        piv = -1.f;
+      } else if (!(dmax > 0.0)) {
+        raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+        piv = -1.f;
+      } else if (!(d > floor_)) {
+        piv = 0.f;
+        if (info) atomicAdd(&info[5], 1);
+      } else {
+        piv = sqrtf(d);
+      }
+      if (piv >= 0.f) S[j + j * ldw] = piv;
+    }
+    __syncthreads();
+    const float p = piv;
+    if (p < 0.f) return;
+    const float ip = p == 0.f ? 0.f : 1.f / p;
+    for (int i = j + 1 + tid; i < n; i += bd) {
+      const float v = p == 0.f ? 0.f : S[j + i * ldw] * ip;
+      S[j + i * ldw] = v;
+      r[i] = v;
+    }
+    __syncthreads();
+    if (p == 0.f) continue;
+    for (int b = j + 1 + warp; b < n; b += nw) {
+      const float rb = r[b];
+      float* col = S + b * ldw;
+      for (int a = j + 1 + lane; a <= b; a += 32) col[a] = fmaf(-r[a], rb, col[a]);
+    }
+    __syncthreads();
+  }
+  for (int b = warp; b < n; b += nw)
+    for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = (a <= b) ? (double)S[a + b * ldw] : 0.0;
 }
 
 // T = R^{-1}, one CTA per column j, column-oriented back substitution:
@@ -1388,7 +1467,7 @@ __global__ void k_sytrd_smem(int n, double* A, int ld, double* tau) {
     // p = t * A22 v: row j of the symmetric A22 (contiguous across lanes = rows)
     for (int j = tid; j < m; j += bd) {
       double s = 0.0;
-      for (int i = 0; i < m; ++i) s = fma(A22[j + i * ldw], v[i], s);
+      s = dot4(A22 + j, ldw, v, m);
       w[j] = t * s;
     }
     __syncthreads();
@@ -1441,7 +1520,7 @@ __global__ void k_hessenberg_smem(int n, double* A, int ld, double* tau) {
     for (int j = k + 1 + tid; j < n; j += bd) {
       const double* col = S + j * ldw + (k + 1);
       double s = 0.0;
-      for (int i = 0; i < m; ++i) s = fma(v[i], col[i], s);
+      s = dot4(col, 1, v, m);
       w[j] = s;
     }
     __syncthreads();
@@ -1455,7 +1534,7 @@ __global__ void k_hessenberg_smem(int n, double* A, int ld, double* tau) {
     for (int i = tid; i < n; i += bd) {
       const double* row = S + (k + 1) * ldw + i;
       double s = 0.0;
-      for (int jj = 0; jj < m; ++jj) s = fma(row[jj * ldw], v[jj], s);
+      s = dot4(row, ldw, v, m);
       w[i] = s;
     }
     __syncthreads();
@@ -1498,7 +1577,7 @@ __global__ void k_lstsq_smem(int mr, int nc, double* A, int ld, int nrhs, double
       for (int j = k + 1 + tid; j < ncol; j += bd) {   // one thread per column
         const double* cj = S + j * ldw;
         double s = 0.0;
-        for (int i = k; i < mr; ++i) s = fma(v[i], cj[i], s);
+        s = dot4(cj + k, 1, v + k, mr - k);
         w[j] = s;
       }
       __syncthreads();
@@ -1562,10 +1641,10 @@ static dmd_status set_smem(const void* fn, size_t bytes) {
 }
 
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
-  const size_t smem = square_smem(n, n, 0);
+  const size_t smem = square_smem(n, n, (size_t)n + 32);
   if (smem <= kSmallSmemMax) {
-    DMD_TRY(set_smem((const void*)k_chol_1s<double>, smem));
-    k_chol_1s<double><<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+    DMD_TRY(set_smem((const void*)k_cholesky_smem, smem));
+    k_cholesky_smem<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
   } else {
     k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
   }
@@ -1586,10 +1665,10 @@ dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cu
 }
 
 dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
-  const size_t smem = (size_t)(n | 1) * n * sizeof(float);
+  const size_t smem = ((size_t)(n | 1) * n + n) * sizeof(float);
   if (smem > kSmallSmemMax) return cholesky_upper(n, G, ld, tau, info, tag, st);
-  DMD_TRY(set_smem((const void*)k_chol_1s<float>, smem));
-  k_chol_1s<float><<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+  DMD_TRY(set_smem((const void*)k_cholesky_f32, smem));
+  k_cholesky_f32<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
