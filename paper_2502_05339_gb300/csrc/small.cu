@@ -346,6 +346,8 @@ struct EpsOf<float> {
 // distinct banks) when `in_smem`, otherwise into the global scratch.  With
 // Real = float this only supplies starting shifts: every eigenvalue is then
 // refined in FP64 by k_hess_rqi.
+constexpr int kHqrT = 5;   // rows per lane per batch of the column update (160 per warp)
+
 template <class Real>
 __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi, Real* Hscratch,
                       int in_smem, int32_t* info) {
@@ -454,11 +456,28 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
           HH(k + 2, k - 1) = 0;
         }
         const int rend = min(k + 3, hi);
-        for (int rr = lo + lane; rr <= rend; rr += 32) {
-          const Real p = tau * (HH(rr, k) + v1 * HH(rr, k + 1) + v2 * HH(rr, k + 2));
-          HH(rr, k) -= p;
-          HH(rr, k + 1) -= p * v1;
-          HH(rr, k + 2) -= p * v2;
+        // column update: every lane loads all of its rows first (their
+        // shared-memory latencies overlap); rows lo..k+3 usually span most
+        // of the window, so five per lane are rarely wasted
+        for (int rb = lo; rb <= rend; rb += 32 * kHqrT) {
+          Real q0[kHqrT], q1[kHqrT], q2[kHqrT];
+#pragma unroll
+          for (int t = 0; t < kHqrT; ++t) {
+            const int rr = rb + lane + 32 * t;
+            q0[t] = rr <= rend ? HH(rr, k) : Real(0);
+            q1[t] = rr <= rend ? HH(rr, k + 1) : Real(0);
+            q2[t] = rr <= rend ? HH(rr, k + 2) : Real(0);
+          }
+#pragma unroll
+          for (int t = 0; t < kHqrT; ++t) {
+            const int rr = rb + lane + 32 * t;
+            const Real p = tau * (q0[t] + v1 * q1[t] + v2 * q2[t]);
+            if (rr <= rend) {
+              HH(rr, k) = q0[t] - p;
+              HH(rr, k + 1) = q1[t] - p * v1;
+              HH(rr, k + 2) = q2[t] - p * v2;
+            }
+          }
         }
         __syncwarp();
       }

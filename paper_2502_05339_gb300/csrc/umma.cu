@@ -216,24 +216,24 @@ __global__ void k_split_b(int Kd, int N, const double* __restrict__ B, int BN, i
 
 // ============================================================ NN, B resident
 
-constexpr int NN_S = 4;    // TMA stages (FP32 128 x 16 tiles, 8 KB)
+constexpr int NN_SMAX = 12; // TMA stages (FP32 128 x 16 tiles, 8 KB): as many as fit, up to 12
 constexpr int NN_CS = 4;   // converted stages (bf16 hi + lo, 8 KB)
 constexpr int NN_THREADS = 320;
 
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_umma_nn_bres(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bsplit,
                    float* __restrict__ C, int64_t ldc, int64_t n, int N, int Np, int ksteps, int64_t ntiles,
-                   int32_t* err) {
+                   int ns, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t bres_bytes = 2u * (uint32_t)ksteps * (uint32_t)Np * 32u;
   uint8_t* Bres = sm;
   uint8_t* stA = sm + ((bres_bytes + 1023u) & ~1023u);
-  uint8_t* cv = stA + NN_S * 8192;
+  uint8_t* cv = stA + ns * 8192;
   uint64_t* bars = reinterpret_cast<uint64_t*>(cv + NN_CS * 8192);
   uint64_t* full = bars;
-  uint64_t* empty = full + NN_S;
-  uint64_t* cfull = empty + NN_S;
+  uint64_t* empty = full + NN_SMAX;
+  uint64_t* cfull = empty + NN_SMAX;
   uint64_t* cempty = cfull + NN_CS;
   uint64_t* accf = cempty + NN_CS;
   uint64_t* acce = accf + 2;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NN_S; ++i) {
+    for (int i = 0; i < ns; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 128);
     }
@@ -273,25 +273,25 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
       for (uint32_t off = 0; off < bres_bytes; off += 32768u)
         bulk_g2s(Bres + off, Bsplit + off, min(32768u, bres_bytes - off), bfull);
       uint32_t it = 0;
-      uint32_t last_par[NN_S];
-      bool issued[NN_S];
-      for (int i = 0; i < NN_S; ++i) issued[i] = false, last_par[i] = 0;
+      uint32_t last_par[NN_SMAX];
+      bool issued[NN_SMAX];
+      for (int i = 0; i < NN_SMAX; ++i) issued[i] = false, last_par[i] = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         for (int ks = 0; ks < ksteps; ++ks, ++it) {
-          const uint32_t s = it % NN_S;
-          if (!mbar_wait(&empty[s], ((it / NN_S) & 1) ^ 1, abort_flag)) {
+          const uint32_t s = it % ns;
+          if (!mbar_wait(&empty[s], ((it / ns) & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           mbar_expect_tx(&full[s], 8192);
           tma_load_2d(stA + s * 8192, &tmA, &full[s], (int)(tile * 128), ks * 16);
           issued[s] = true;
-          last_par[s] = (it / NN_S) & 1;
+          last_par[s] = (it / ns) & 1;
         }
       }
       // in-flight TMA writes must land before the CTA's shared memory goes away
-      for (int i = 0; i < NN_S; ++i)
+      for (int i = 0; i < ns; ++i)
         if (issued[i]) mbar_wait_drain(&full[i], last_par[i]);
       mbar_wait_drain(bfull, 0);
     }
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       for (int ks = 0; ks < ksteps; ++ks, ++it) {
-        const uint32_t s = it % NN_S, cs = it % NN_CS;
-        if (!mbar_wait(&full[s], (it / NN_S) & 1, abort_flag) ||
+        const uint32_t s = it % ns, cs = it % NN_CS;
+        if (!mbar_wait(&full[s], (it / ns) & 1, abort_flag) ||
             !mbar_wait(&cempty[cs], ((it / NN_CS) & 1) ^ 1, abort_flag)) {
           ok = false;
           break;
@@ -918,8 +918,15 @@ int num_sms() {
 
 constexpr int kMaxSmem = 227 * 1024;
 
-size_t bres_smem(int ksteps, int Np) {
-  return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + NN_S * 8192 + NN_CS * 8192 + 256;
+size_t bres_smem(int ksteps, int Np, int ns) {
+  return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + (size_t)ns * 8192 + NN_CS * 8192 + 512;
+}
+// TMA stages of the B-resident kernel: as many as fit (more bytes in flight
+// per SM to cover DRAM latency), at least 4.
+int bres_stages(int ksteps, int Np) {
+  int ns = 4;   // measured: deeper rings (up to 7 fit) were slower
+  while (ns > 4 && bres_smem(ksteps, Np, ns) > (size_t)kMaxSmem) --ns;
+  return ns;
 }
 size_t ares_smem(int ksteps, int bn, int sa, int nb) {
   const size_t chunk = ((size_t)2 * ksteps * bn * 32 + 1023) & ~(size_t)1023;
@@ -956,7 +963,7 @@ int tn_stages(int Mt, int Np, int nsplit) {
 // Largest column chunk of B that stays resident for the B-resident kernel.
 int bres_cols(int ksteps) {
   int np = 256;
-  while (np > 16 && bres_smem(ksteps, np) > (size_t)kMaxSmem) np -= 16;
+  while (np > 16 && bres_smem(ksteps, np, 4) > (size_t)kMaxSmem) np -= 16;
   return np;
 }
 
@@ -999,9 +1006,10 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
     const int64_t work = (int64_t)Np * ksteps;
     k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, Np, ksteps, 1, split);
     DMD_LAUNCH_CHECK();
-    const size_t smem = bres_smem(ksteps, Np);
+    const int ns = bres_stages(ksteps, Np);
+    const size_t smem = bres_smem(ksteps, Np, ns);
     DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_bres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, nullptr);
+    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, ns, nullptr);
     DMD_LAUNCH_CHECK();
     return DMD_OK;
   }
