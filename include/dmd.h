@@ -220,6 +220,55 @@ DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float
 DMD_EXPORT dmd_status dmd_predict_noalloc(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                                const int32_t* k, const float* u, float* out, void* stream);
 
+/* Autotuner of the reconstruction (no counterpart in the paper: it picks the
+ * tensor-core tile configuration of Phi_R C for this GPU).  With the
+ * operands of a dmd_predict call (desc->q must be 0; mixed precision; K > 256
+ * frames), every (frame-chunk width, A stages, B buffers) configuration that
+ * fits in shared memory is launched and timed with CUDA events on `stream`,
+ * and the fastest is kept for all later predictions with the same number of
+ * modes (per process).  chosen (3 int32, may be NULL) receives (chunk width,
+ * A stages, B buffers), zeros when nothing was tuned.  `out` is overwritten
+ * with the frames.  Synchronises `stream`: call it before any capture. */
+DMD_EXPORT dmd_status dmd_autotune_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                                const int32_t* k, float* out, void* workspace, size_t ws_bytes,
+                                void* stream, int32_t* chosen);
+
+/* ---- many scenes at once ----------------------------------------------- */
+
+/* One scene of a batch: its fit (no control inputs: fit.q must be 0) and,
+ * with K > 0, the prediction of K frames k[0..K) into out (n x K FP32,
+ * ld ldOut).  Pointers are device pointers owned by the caller. */
+typedef struct dmd_scene {
+  dmd_fit_desc fit;
+  const float* S;       /* (m+1) snapshots, n x (m+1), ld fit.ldS           */
+  float* Phi_R;         /* n x r, ld fit.ldPhi                               */
+  double* modal;        /* DMD_MODAL_DOUBLES(r, 0)                           */
+  int32_t* info;        /* DMD_INFO_WORDS                                    */
+  int32_t K;            /* frames to predict (0: fit only)                   */
+  const int32_t* k;     /* K time indices                                    */
+  float* out;           /* n x K frames, ld ldOut                            */
+  int64_t ldOut;
+} dmd_scene;
+
+/* Workspace bytes of dmd_fit_predict_batch for these scenes and lanes. */
+DMD_EXPORT dmd_status dmd_batch_workspace_bytes(int32_t count, const dmd_scene* scenes, int32_t lanes,
+                                     size_t* bytes);
+
+/* Fit (Sec. 3.1, Sec. 4.3) and predict (Eq. large_time_step) `count`
+ * independent scenes of any sizes.  The scenes run concurrently on `lanes`
+ * internal streams (0 = 16, at most 32), assigned longest first (by n (m+1))
+ * to the least-loaded lane; each lane reuses one slice of the workspace,
+ * sized for its largest scene.  The lanes fork from and join back into
+ * `stream` through events, so the whole batch is ordered on `stream` and, when
+ * `stream` is being captured, is captured (a batch then replays as one graph
+ * launch).  Every scene's results equal those of dmd_fit + dmd_predict on the
+ * same inputs.  The first call on a device creates the lanes: make it before
+ * any capture.  Calls on one device share the lanes: do not overlap them.
+ * Errors: EINVAL for a bad scene (NULL pointers, q > 0, bad ldOut) or any
+ * argument error of dmd_fit; ENOMEM if ws_bytes is below the query. */
+DMD_EXPORT dmd_status dmd_fit_predict_batch(int32_t count, const dmd_scene* scenes, int32_t lanes,
+                                 void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- component entry points (the building blocks, exposed for tests) ------ */
 
 /* Omega (m x l FP64, ld m) ~ N(0, 1) from Philox4x32-10 (Salmon et al. 2011):

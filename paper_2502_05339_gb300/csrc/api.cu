@@ -37,6 +37,8 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                         double* C, int nsplit, void* ws, cudaStream_t st);
+dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
+                        void* ws, cudaStream_t st, int32_t* chosen);
 dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                               double* C, int nsplit, int flush, void* ws, cudaStream_t st);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
@@ -93,8 +95,12 @@ struct Tall {
   int prec;
   // scratch for the small FP64 operand rounded to FP32 / split (NN), and the
   // split partials (TN); carved once per call site.
+  // The tensor-core NN kernels keep up to 256 inner-dimension columns
+  // resident; a longer inner dimension (more than 256 snapshots) takes the
+  // FP32 CUDA-core product in either form.
+  bool nn_tensor(int Kd) const { return prec == DMD_MIXED_BF16X3 && Kd <= 256; }
   size_t nn_bytes(int64_t n, int Kd, int N) const {
-    if (prec == DMD_MIXED_BF16X3) return umma_nn_workspace_bytes(n, Kd, N);
+    if (nn_tensor(Kd)) return umma_nn_workspace_bytes(n, Kd, N);
     return (size_t)Kd * N * sizeof(float) + 256;
   }
   size_t tn_bytes(int64_t n, int Ka, int N) const {
@@ -103,7 +109,7 @@ struct Tall {
   }
   dmd_status nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
                 void* ws, cudaStream_t st) const {
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+    if (nn_tensor(Kd)) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
     float* B32 = reinterpret_cast<float*>(ws);
     DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st));
     return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st);
@@ -664,6 +670,27 @@ dmd_status dmd_gemm_tn(int32_t precision, int64_t n, int32_t Ka, int32_t N, cons
 }
 
 }  // extern "C"
+
+extern "C" dmd_status dmd_autotune_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
+                                           const int32_t* k, float* out, void* workspace, size_t ws_bytes,
+                                           void* stream, int32_t* chosen) {
+  DMD_TRY(validate_predict(desc, true));
+  DMD_REQUIRE(Phi_R && modal && k && out, "dmd_autotune_predict: NULL pointer argument");
+  DMD_REQUIRE(desc->q == 0, "dmd_autotune_predict: tune without control inputs");
+  size_t need = 0;
+  DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    PredBufs b;
+    carve_predict(a, *desc, 0, b);
+    DMD_TRY(form_coefficients(*desc, modal, k, nullptr, b, st));
+    if (desc->precision != DMD_MIXED_BF16X3) {
+      if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+      return DMD_OK;
+    }
+    return umma_tune_nn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, out, desc->ldOut, b.gemm_ws, st, chosen);
+  }, need);
+}
 
 namespace dmd {
 

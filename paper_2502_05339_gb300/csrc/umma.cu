@@ -938,10 +938,18 @@ struct AresCfg {
 };
 // Configuration override for tuning sweeps (bn = 0: automatic).
 AresCfg g_ares_override = {0, 0, 0};
+// Configurations chosen by the autotuner, per number of 16-wide k-slices.
+AresCfg g_ares_tuned[AR_MAXKS + 1] = {};
+std::mutex g_ares_mu;
 
-// Widest frame chunk (64, 48, 32 or 16 columns), then the deepest rings, that fit in shared memory.
+// Tuned configuration if any, else the widest frame chunk (128 .. 16
+// columns), then the deepest rings, that fit in shared memory.
 AresCfg ares_cfg(int ksteps) {
   if (g_ares_override.bn) return g_ares_override;
+  if (ksteps >= 1 && ksteps <= AR_MAXKS) {
+    std::lock_guard<std::mutex> lock(g_ares_mu);
+    if (g_ares_tuned[ksteps].bn) return g_ares_tuned[ksteps];
+  }
   for (int bn = 128; bn >= 16; bn -= 16)
     for (int nb = 3; nb >= 2; --nb)
       for (int sa = 3; sa >= 2; --sa)
@@ -1031,6 +1039,62 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks, ntiles,
                                                   nullptr);
   DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+// Autotuner of the resident-A (many output columns) product: every
+// (frame chunk, A stages, B buffers) configuration that fits in shared memory
+// is launched on the caller's operands -- one warm-up and two timed launches,
+// CUDA events on `st` -- and the fastest is kept for this number of k-slices;
+// later products with the same inner dimension use it.  Synchronises `st`.
+dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
+                        void* ws, cudaStream_t st, int32_t* chosen) {
+  const int ksteps = (int)ceil_div(Kd, 16);
+  if (n <= 0 || N <= 256 || ksteps < 1 || ksteps > AR_MAXKS) {   // not a resident-A product
+    if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+    return DMD_OK;
+  }
+  cudaEvent_t e0, e1;
+  DMD_CUDA_TRY(cudaEventCreate(&e0));
+  DMD_CUDA_TRY(cudaEventCreate(&e1));
+  AresCfg best = {0, 0, 0};
+  float best_ms = 0.f;
+  dmd_status status = DMD_OK;
+  for (int bn = 128; bn >= 32 && status == DMD_OK; bn -= 16)
+    for (int nb = 2; nb <= 3 && status == DMD_OK; ++nb)
+      for (int sa = 2; sa <= 3 && status == DMD_OK; ++sa) {
+        if (ares_smem(ksteps, bn, sa, nb) > (size_t)kMaxSmem) continue;
+        g_ares_override = {bn, sa, nb};
+        status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+        if (status != DMD_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) status = DMD_ECUDA;
+        for (int r = 0; r < 2 && status == DMD_OK; ++r) status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+        if (status != DMD_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          set_error("umma_tune_nn: event timing failed");
+          status = DMD_ECUDA;
+          break;
+        }
+        if (best.bn == 0 || ms < best_ms) {
+          best = {bn, sa, nb};
+          best_ms = ms;
+        }
+      }
+  g_ares_override = {0, 0, 0};
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DMD_TRY(status);
+  {
+    std::lock_guard<std::mutex> lock(g_ares_mu);
+    g_ares_tuned[ksteps] = best;
+  }
+  if (chosen) {
+    chosen[0] = best.bn;
+    chosen[1] = best.sa;
+    chosen[2] = best.nb;
+  }
   return DMD_OK;
 }
 

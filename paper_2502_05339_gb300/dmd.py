@@ -49,6 +49,12 @@ class PredictDesc(ctypes.Structure):
 
 _P = ctypes.c_void_p
 _SZ = ctypes.POINTER(ctypes.c_size_t)
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("fit", FitDesc), ("S", _P), ("Phi_R", _P), ("modal", _P), ("info", _P), ("K", ctypes.c_int32),
+                ("k", _P), ("out", _P), ("ldOut", ctypes.c_int64)]
+
 SIGNATURES = {
     "dmd_last_error": (ctypes.c_char_p, []),
     "dmd_version": (ctypes.c_char_p, []),
@@ -62,6 +68,11 @@ SIGNATURES = {
                                               ctypes.c_size_t, _P]),
     "dmd_predict_loss": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_int32,
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_autotune_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P,
+                                              _P]),
+    "dmd_batch_workspace_bytes": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(Scene), ctypes.c_int32, _SZ]),
+    "dmd_fit_predict_batch": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(Scene), ctypes.c_int32, _P,
+                                               ctypes.c_size_t, _P]),
     "dmd_sketch_matrix": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P]),
     "dmd_philox_blocks": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, _P, _P]),
     "dmd_gemm_tall_workspace_bytes": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
@@ -252,6 +263,21 @@ def dmd_predict_noalloc(model: DmdModel, ks, out: torch.Tensor, *, u: torch.Tens
     return out
 
 
+def dmd_autotune_predict(model: DmdModel, ks, *, precision="mixed") -> tuple:
+    """Tune the reconstruction kernel for this model's mode count on these
+    frames; returns the chosen (chunk width, A stages, B buffers)."""
+    dev = model.Phi_R.device
+    kt = _ks_tensor(ks, dev)
+    K = kt.numel()
+    out = torch.empty((K, round_up(model.n, 32)), dtype=torch.float32, device=dev)
+    d = _pdesc(model, K, out.shape[1], precision, 0)
+    ws = _pred_ws(d, dev)
+    chosen = torch.zeros(3, dtype=torch.int32)
+    _check(lib().dmd_autotune_predict(ctypes.byref(d), _ptr(model.Phi_R), _ptr(model.modal), _ptr(kt), _ptr(out),
+                                      _ptr(ws), ws.numel(), _stream(dev), chosen.data_ptr()), "dmd_autotune_predict")
+    return tuple(int(v) for v in chosen)
+
+
 def dmd_predict_backward(model: DmdModel, ks, dOut: torch.Tensor, *, u: torch.Tensor | None = None,
                          precision="fp32", modal: torch.Tensor | None = None):
     """(d_modal, d_u) for dL/d(frames) = dOut (tensor (K, ldOut) float32)."""
@@ -345,6 +371,50 @@ def dmd_gemm_tn(A: torch.Tensor, B: torch.Tensor, n: int, *, precision="fp32") -
     _check(lib().dmd_gemm_tn(p, n, Ka, N, _ptr(A), lda, _ptr(B), ldb, _ptr(C), _ptr(ws), ws.numel(), _stream(dev)),
            "dmd_gemm_tn")
     return C
+
+
+class Batch:
+    """Many scenes fitted and predicted in one call (dmd_fit_predict_batch).
+
+    items: sequence of (S, n, r, seed, ks) with S a (m+1, ldS) float32 CUDA
+    tensor of snapshots and ks the frame indices (or None for fit only).
+    Outputs (models, frames) are allocated once; `run()` (re)executes the
+    batch on the current stream and may be captured in a CUDA graph after the
+    first call."""
+
+    def __init__(self, items, *, lanes: int = 16, precision="fp32", oversample: int = 10, power_iters: int = 2):
+        self.lanes = lanes
+        self.models, self.frames, self._keep = [], [], []
+        arr = (Scene * len(items))()
+        for i, (S, n, r, seed, ks) in enumerate(items):
+            _need_cuda(S, "S", torch.float32)
+            dev = S.device
+            m = S.shape[0] - 1
+            ldPhi = round_up(n, 32)
+            model = DmdModel(torch.empty((r, ldPhi), dtype=torch.float32, device=dev),
+                             torch.empty(r * 4, dtype=torch.float64, device=dev),
+                             torch.empty(INFO_WORDS, dtype=torch.int32, device=dev), n, r, 0)
+            kt = None if ks is None else _ks_tensor(ks, dev)
+            K = 0 if kt is None else kt.numel()
+            out = torch.empty((K, ldPhi), dtype=torch.float32, device=dev) if K else None
+            arr[i].fit = FitDesc(n=n, ldS=S.shape[1], ldPhi=ldPhi, m=m, r=r, oversample=min(oversample, m - r),
+                                 power_iters=power_iters, q=0, precision=_prec(precision), seed=seed)
+            arr[i].S, arr[i].Phi_R, arr[i].modal, arr[i].info = (_ptr(S), _ptr(model.Phi_R), _ptr(model.modal),
+                                                                 _ptr(model.info))
+            arr[i].K, arr[i].k, arr[i].out, arr[i].ldOut = K, _ptr(kt), _ptr(out), ldPhi
+            self.models.append(model)
+            self.frames.append(out)
+            self._keep += [S, kt]
+        self._arr = arr
+        nb = ctypes.c_size_t(0)
+        _check(lib().dmd_batch_workspace_bytes(len(items), arr, lanes, ctypes.byref(nb)), "dmd_batch_workspace_bytes")
+        self._ws = _workspace(nb.value, items[0][0].device if items else torch.device("cuda"))
+
+    def run(self):
+        dev = self._ws.device
+        _check(lib().dmd_fit_predict_batch(len(self.models), self._arr, self.lanes, _ptr(self._ws), self._ws.numel(),
+                                           _stream(dev)), "dmd_fit_predict_batch")
+        return self.models, self.frames
 
 
 # ----------------------------------------------------------------- autograd

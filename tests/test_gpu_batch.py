@@ -1,0 +1,110 @@
+"""Many scenes of uneven size fitted and predicted in one batched call
+(dmd_fit_predict_batch): every scene's model and frames must equal those of
+its own dmd_fit + dmd_predict (the same kernels on the same inputs), with the
+scenes spread over several concurrent lanes, and a batch captured in a CUDA
+graph must replay to the same results."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_05339_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# (grid N, pairs, snapshots m, seed): 2D scenes of uneven sizes, as in the
+# many-scene workload (sizes, snapshot counts and ranks all differ)
+SCENES = [(16, 3, 30, 11), (48, 8, 90, 12), (24, 5, 60, 13), (64, 10, 120, 14),
+          (20, 4, 40, 15), (56, 9, 100, 16), (32, 6, 70, 17), (40, 7, 80, 18)]
+FRAMES = 64
+
+
+@pytest.fixture(scope="module")
+def dmd():
+    from paper_2502_05339_gb300 import build_lib
+    build_lib.build()
+    from paper_2502_05339_gb300 import dmd as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    out = []
+    for N, pairs, m, seed in SCENES:
+        sc = synth.linear_modes_scene(N, 2, pairs, m, seed, noise=1e-5, device="cuda")
+        out.append((sc.S, sc.n, 2 * pairs, seed, list(range(FRAMES))))
+    return out
+
+
+def _single(dmd, item, prec):
+    S, n, r, seed, ks = item
+    model = dmd.dmd_fit(S, n, r, oversample=10, power_iters=2, precision=prec, seed=seed)
+    frames = dmd.dmd_predict(model, ks, precision=prec)
+    return model, frames
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_batch_equals_single_scene_calls(dmd, scenes, prec):
+    batch = dmd.Batch(scenes, lanes=4, precision=prec)
+    models, frames = batch.run()
+    torch.cuda.synchronize()
+    for item, mb, fb in zip(scenes, models, frames):
+        mb.check()
+        ms, fs = _single(dmd, item, prec)
+        torch.cuda.synchronize()
+        n = item[1]
+        assert torch.equal(mb.modal, ms.modal)
+        assert torch.equal(mb.Phi_R[:, :n], ms.Phi_R[:, :n])
+        assert torch.equal(fb[:, :n], fs[:, :n])
+
+
+def test_batch_graph_replay(dmd, scenes):
+    batch = dmd.Batch(scenes, lanes=8, precision="mixed")
+    models, frames = batch.run()            # first call: lanes created, kernels set up
+    torch.cuda.synchronize()
+    ref = [(m.modal.clone(), f.clone()) for m, f in zip(models, frames)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        batch.run()
+    for m, f in zip(models, frames):
+        m.modal.zero_()
+        f.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for (rm, rf), m, f in zip(ref, models, frames):
+        assert torch.equal(m.modal, rm)
+        assert torch.equal(f, rf)
+
+
+def test_batch_rejects_bad_scenes(dmd, scenes):
+    S, n, r, seed, ks = scenes[0]
+    bad = [(S, n, r, seed, ks)]
+    b = dmd.Batch(bad, lanes=2)
+    b._arr[0].ldOut = 3   # not a multiple of 4
+    with pytest.raises(dmd.DmdError):
+        b.run()
+
+
+def test_autotuned_reconstruction_is_unchanged(dmd):
+    """The autotuner only changes how the frame columns are chunked; every
+    frame is the same sequence of tensor-core products, so the frames after
+    tuning equal those before, bit for bit."""
+    g = np.random.default_rng(3)
+    n, r, K = 100_000 + 7, 150, 700
+    ld = (n + 31) // 32 * 32
+    P = torch.zeros((r, ld), dtype=torch.float32)
+    P[:, :n] = torch.as_tensor(g.standard_normal((r, n)), dtype=torch.float32)
+    lam = np.exp(g.uniform(-0.02, 0, r // 2) + 1j * g.uniform(0.05, 3.0, r // 2))
+    modal = np.zeros(4 * r)
+    modal[0:r:2], modal[1:r:2] = lam.real, lam.real
+    modal[r:2 * r:2], modal[r + 1:2 * r:2] = lam.imag, -lam.imag
+    modal[2 * r:3 * r] = g.standard_normal(r)
+    model = dmd.DmdModel(P.cuda(), torch.as_tensor(modal).cuda(), torch.zeros(8, dtype=torch.int32, device="cuda"),
+                         n, r, 0)
+    ks = list(range(K))
+    before = dmd.dmd_predict(model, ks, precision="mixed")
+    bn, sa, nb = dmd.dmd_autotune_predict(model, ks, precision="mixed")
+    assert bn % 16 == 0 and 32 <= bn <= 128 and sa in (2, 3) and nb in (2, 3)
+    after = dmd.dmd_predict(model, ks, precision="mixed")
+    torch.cuda.synchronize()
+    assert torch.equal(before[:, :n], after[:, :n])

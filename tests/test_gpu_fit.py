@@ -151,3 +151,22 @@ def test_host_argument_errors(dmd):
     with pytest.raises(dmd.DmdError) as e:
         dmd.dmd_fit(sc.S.cuda(), sc.n, 25)          # r > m
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,pairs,m", [(32, 20, 300), (24, 12, 260)])
+def test_more_than_256_snapshots(dmd, prec, N, pairs, m):
+    """Snapshot counts above 256 (the many-scene workload draws m up to 400):
+    the snapshot Gram, the reductions and the sketch products then span more
+    than one 256-wide block.  Eigenvalues, mode fields and frames within the bar."""
+    import math
+    sc = synth.linear_modes_scene(N, 2, pairs, m, 31 + m, sigma_lo=-0.05, omega_hi=math.pi, stratified=True,
+                                  noise=1e-5, keep_fp64=False)
+    r = 2 * pairs
+    ref, PhiR_o, beta_o, _ = oracle_model(sc.X().numpy(), r)
+    model = _fit(dmd, sc, r, prec)
+    lam_g = model.lam()
+    _, lam_err = match(lam_g, ref["lam"])
+    assert lam_err < BAR[prec], lam_err
+    mp_frob, _ = mode_product_error(cols(model.Phi_R, sc.n), model.beta(), lam_g, PhiR_o, beta_o, ref["lam"])
+    assert mp_frob < BAR[prec], mp_frob
