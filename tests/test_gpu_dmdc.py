@@ -106,3 +106,51 @@ def test_dmdc_adjoint_matches_oracle(dmd, scene, prec):
     dm = dmodal.cpu().numpy()
     assert rel(dm[2 * r:3 * r], db) < tol
     assert rel(dm[:r], dlr) < tol
+
+
+def test_dmdc_adjoint_central_differences(dmd, scene):
+    """The device gradient of L(u, beta) = 0.5 ||x_T - x_tgt||^2 against
+    central differences with h = 1e-3 of the same loss evaluated in FP64 for
+    the same (device-fitted) model: rollout of the real 2x2-block latent
+    recursion, lift by Phi_R.  The loss is quadratic in u and in beta, so the
+    differences are exact up to FP64 rounding; the device gradient carries the
+    FP32 rounding of its frames (~1e-5 relative), hence 1e-3."""
+    sc, _ = scene
+    model = _fit(dmd, sc, "fp32")
+    T, h = 40, 1e-3
+    g = np.random.default_rng(6)
+    U2 = synth.piecewise_controls(g, 3, T)                              # (q, T)
+    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()
+    x_T = dmd.dmd_predict(model, [T], u=u, precision="fp32")[0]
+    tgt = x_T.clone()
+    tgt[: sc.n] += torch.as_tensor(1e-2 * g.standard_normal(sc.n), dtype=torch.float32, device="cuda")
+    w = torch.ones(1, dtype=torch.float64, device="cuda")
+    _, dmodal, du = dmd.dmd_predict_loss(model, [T], tgt, w, want_grad=True, u=u, precision="fp32")
+    du = du.cpu().numpy()                                                # (T, q)
+    r = model.r
+    dm = dmodal.cpu().numpy()
+    lam, beta, GR = model.lam(), model.beta(), model.G()
+    kinds = O.pair_kinds(lam)
+    L = O.real_block_operator(lam, kinds)
+    PhiR = cols(model.Phi_R, sc.n)
+    tgt64 = tgt[: sc.n].double().cpu().numpy()
+    U64 = U2.astype(np.float32).astype(np.float64)
+
+    def loss(UU, bb):
+        Xi = O.rollout_real(L, bb, GR, UU, T)
+        res = PhiR @ Xi[:, T] - tgt64
+        return 0.5 * float(res @ res)
+
+    for (t, ch) in [(0, 0), (7, 1), (19, 2), (33, 0), (39, 1)]:
+        up, um = U64.copy(), U64.copy()
+        up[ch, t] += h
+        um[ch, t] -= h
+        fd = (loss(up, beta) - loss(um, beta)) / (2 * h)
+        assert abs(fd - du[t, ch]) <= 1e-3 * max(abs(fd), 1e-2 * np.abs(du).max()), (t, ch, fd, du[t, ch])
+    for c in [0, 3, r - 1]:
+        bp, bm = beta.copy(), beta.copy()
+        bp[c] += h
+        bm[c] -= h
+        fd = (loss(U64, bp) - loss(U64, bm)) / (2 * h)
+        gd = dm[2 * r + c]
+        assert abs(fd - gd) <= 1e-3 * max(abs(fd), 1e-2 * np.abs(dm[2 * r:3 * r]).max()), (c, fd, gd)
