@@ -220,6 +220,19 @@ DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float
 DMD_EXPORT dmd_status dmd_predict_noalloc(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                                const int32_t* k, const float* u, float* out, void* stream);
 
+/* Temporal editing of a fitted model (Eq. edit_temporal): with
+ * Omega = log(lambda) / dt, every mode with |Im Omega| < threshold belongs to
+ * the low-frequency cluster (the paper uses 0.01), the others to the
+ * high-frequency cluster; each cluster's edit {w, s_re, s_im} (host arrays of
+ * 3 doubles: low, high) gives lambda' = exp((s_re Re Omega + i s_im Im Omega) dt)
+ * and beta' = w beta (the mode's weight).  Conjugate partners get conjugate
+ * edits; a negative real eigenvalue keeps its sign.  modal_out (a separate
+ * DMD_MODAL_DOUBLES(r, q) buffer) then feeds dmd_predict like a fitted model;
+ * sigma and G are copied.  Errors: EINVAL for bad sizes, dt <= 0, negative
+ * threshold or aliasing buffers. */
+DMD_EXPORT dmd_status dmd_edit_modes(int32_t r, int32_t q, const double* modal_in, double* modal_out,
+                          double threshold, const double* low, const double* high, double dt, void* stream);
+
 /* Autotuner of the reconstruction (no counterpart in the paper: it picks the
  * tensor-core tile configuration of Phi_R C for this GPU).  With the
  * operands of a dmd_predict call (desc->q must be 0; mixed precision; K > 256

@@ -236,6 +236,36 @@ def coefficients(lam: np.ndarray, beta: np.ndarray, ks, kinds=None) -> np.ndarra
     return C
 
 
+def edit_modes(lam: np.ndarray, beta: np.ndarray, threshold: float, low, high, dt: float = 1.0):
+    """Temporal editing of Eq. edit_temporal.  Omega = log(lambda) / dt; a
+    mode belongs to the low-frequency cluster when |Im Omega| < threshold,
+    else to the high-frequency one.  Each cluster's edit (w, s_re, s_im)
+    gives Omega' = s_re Re Omega + i s_im Im Omega, lambda' = exp(Omega' dt)
+    and amplitude w b (beta scales with it in the real form).  Readings: the
+    edit is a scale of Re Omega and Im Omega (the paper's factors 0.5 .. 1.5);
+    a negative real eigenvalue keeps its sign (only its modulus is edited), so
+    the real form stays real.  Conjugate partners get conjugate edits."""
+    lam = np.asarray(lam, dtype=complex)
+    kinds = pair_kinds(lam)
+    out_lam = lam.copy()
+    out_beta = np.asarray(beta, dtype=np.float64).copy()
+    for c in range(len(lam)):
+        if kinds[c] == 2:
+            continue
+        om = np.log(lam[c]) / dt
+        w, sre, sim = low if abs(om.imag) < threshold else high
+        if kinds[c] == 0:
+            mod = np.exp(sre * om.real * dt)
+            out_lam[c] = mod if lam[c].real >= 0 else -mod
+            out_beta[c] *= w
+            continue
+        new = np.exp((sre * om.real + 1j * sim * om.imag) * dt)
+        out_lam[c], out_lam[c + 1] = new, np.conj(new)
+        out_beta[c] *= w
+        out_beta[c + 1] *= w
+    return out_lam, out_beta
+
+
 def predict_real(PhiR: np.ndarray, C: np.ndarray) -> np.ndarray:
     """Reconstruction as one real product F = Phi_R C."""
     return PhiR @ C

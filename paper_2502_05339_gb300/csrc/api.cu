@@ -37,6 +37,8 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                         double* C, int nsplit, void* ws, cudaStream_t st);
+dmd_status launch_edit_modes(int r, int q, const double* in, double* out, double thr, const double* low,
+                             const double* high, double dt, cudaStream_t st);
 dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
                         void* ws, cudaStream_t st, int32_t* chosen);
 dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
@@ -670,6 +672,15 @@ dmd_status dmd_gemm_tn(int32_t precision, int64_t n, int32_t Ka, int32_t N, cons
 }
 
 }  // extern "C"
+
+extern "C" dmd_status dmd_edit_modes(int32_t r, int32_t q, const double* modal_in, double* modal_out,
+                                     double threshold, const double* low, const double* high, double dt,
+                                     void* stream) {
+  DMD_REQUIRE(r >= 1 && q >= 0 && modal_in && modal_out && low && high, "dmd_edit_modes: bad arguments");
+  DMD_REQUIRE(dt > 0.0 && threshold >= 0.0, "dmd_edit_modes: need dt > 0 and threshold >= 0");
+  DMD_REQUIRE(modal_in != modal_out, "dmd_edit_modes: modal_out must not alias modal_in");
+  return launch_edit_modes(r, q, modal_in, modal_out, threshold, low, high, dt, (cudaStream_t)stream);
+}
 
 extern "C" dmd_status dmd_autotune_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                                            const int32_t* k, float* out, void* workspace, size_t ws_bytes,

@@ -64,6 +64,39 @@ __global__ void k_coefficients(int r, int K, const double* __restrict__ modal, c
 // DMD with control: xi_0 = beta, xi_{t+1} = L xi_t + G_R u_t with L the real
 // 2x2-block operator of lambda; writes Xi (r x (steps+1)).  One thread per
 // head column; the time loop is sequential, the modes are independent.
+// Temporal editing (Eq. edit_temporal): Omega = log(lambda) / dt, cluster by
+// |Im Omega| < thr (low) or not (high); lambda' = exp((s_re Re Omega + i s_im
+// Im Omega) dt), beta' = w beta; a real eigenvalue keeps its sign.  One
+// thread per column; a pair's head writes both columns; sigma and G are
+// copied unchanged.
+__global__ void k_edit_modes(int r, int q, const double* __restrict__ in, double* __restrict__ out, double thr,
+                             double lw, double lre, double lim, double hw, double hre, double him, double dt) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= r) return;
+  out[3 * r + c] = in[3 * r + c];
+  for (int j = 0; j < q; ++j) out[4 * r + (int64_t)j * r + c] = in[4 * r + (int64_t)j * r + c];
+  const double lr = in[c], li = in[r + c], b = in[2 * r + c];
+  if (li < 0.0) return;   // second column of a pair: written by the head
+  const double om_re = log(hypot(lr, li)) / dt, om_im = atan2(li, lr) / dt;
+  const bool low = fabs(om_im) < thr;
+  const double w = low ? lw : hw, sre = low ? lre : hre, sim = low ? lim : him;
+  const double mod = exp(sre * om_re * dt);
+  if (li > 0.0 && c + 1 < r) {
+    double sn, cs;
+    sincos(sim * om_im * dt, &sn, &cs);
+    out[c] = mod * cs;
+    out[r + c] = mod * sn;
+    out[c + 1] = mod * cs;
+    out[r + c + 1] = -mod * sn;
+    out[2 * r + c] = w * b;
+    out[2 * r + c + 1] = w * in[2 * r + c + 1];
+  } else {
+    out[c] = lr >= 0.0 ? mod : -mod;
+    out[r + c] = 0.0;
+    out[2 * r + c] = w * b;
+  }
+}
+
 __global__ void k_rollout(int r, int q, int steps, const double* __restrict__ modal,
                           const float* __restrict__ u, double* __restrict__ Xi) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,16 +299,22 @@ __global__ void k_scatter_frames(int r, int K, int steps, const int32_t* __restr
 // sum_j w_j 0.5 (F_ij - tgt_i)^2; if grad, F <- w_j (F - tgt) in place.
 __global__ void k_loss_chunk(int64_t n, int nf, float* __restrict__ F, int64_t ldf, const float* __restrict__ tgt,
                              const double* __restrict__ w, int grad, double* __restrict__ partial) {
+  // Each thread sums its elements of one frame in FP32 (a few dozen terms)
+  // and carries the frame sums in FP64: FP64 arithmetic per element would be
+  // bound by GB300's FP64 pipe (~64x slower than FP32).
   __shared__ double red[32];
   double loc = 0.0;
   for (int j = 0; j < nf; ++j) {
-    const double wj = w[j];
+    const float wj = (float)w[j];
     float* f = F + (int64_t)j * ldf;
+    float acc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      const double d = (double)f[i] - (double)tgt[i];
-      loc += 0.5 * wj * d * d;
-      if (grad) f[i] = (float)(wj * d);
+      const float d = f[i] - tgt[i];
+      const float wd = wj * d;
+      acc = fmaf(wd, d, acc);
+      if (grad) f[i] = wd;
     }
+    loc += 0.5 * (double)acc;
   }
   const double s = block_sum(loc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -290,6 +329,14 @@ __global__ void k_sum_partials(int count, const double* __restrict__ partial, do
 }
 
 }  // namespace
+
+dmd_status launch_edit_modes(int r, int q, const double* in, double* out, double thr, const double* low,
+                             const double* high, double dt, cudaStream_t st) {
+  k_edit_modes<<<(unsigned)ceil_div(r, 128), 128, 0, st>>>(r, q, in, out, thr, low[0], low[1], low[2], high[0],
+                                                            high[1], high[2], dt);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
 
 dmd_status launch_coefficients(int r, int K, const double* modal, const int32_t* ks, double* C, cudaStream_t st) {
   const int64_t total = (int64_t)r * K;

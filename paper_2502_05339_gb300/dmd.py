@@ -68,6 +68,8 @@ SIGNATURES = {
                                               ctypes.c_size_t, _P]),
     "dmd_predict_loss": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_int32,
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_edit_modes": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_double, _P, _P,
+                                        ctypes.c_double, _P]),
     "dmd_autotune_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P,
                                               _P]),
     "dmd_batch_workspace_bytes": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(Scene), ctypes.c_int32, _SZ]),
@@ -260,6 +262,18 @@ def dmd_predict_noalloc(model: DmdModel, ks, out: torch.Tensor, *, u: torch.Tens
     md = model.modal if modal is None else modal
     _check(lib().dmd_predict_noalloc(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(out),
                                      _stream(dev)), "dmd_predict_noalloc")
+    return out
+
+
+def dmd_edit_modes(model: DmdModel, threshold: float = 0.01, low=(1.0, 1.0, 1.0), high=(1.0, 1.0, 1.0),
+                   dt: float = 1.0) -> torch.Tensor:
+    """Edited modal buffer (Eq. edit_temporal) for dmd_predict(..., modal=...):
+    per cluster (w, s_re, s_im) = (weight, scale of Re Omega, scale of Im Omega)."""
+    out = torch.empty_like(model.modal)
+    lo = (ctypes.c_double * 3)(*low)
+    hi = (ctypes.c_double * 3)(*high)
+    _check(lib().dmd_edit_modes(model.r, model.q, _ptr(model.modal), _ptr(out), float(threshold), lo, hi,
+                                float(dt), _stream(model.modal.device)), "dmd_edit_modes")
     return out
 
 

@@ -469,3 +469,44 @@ def test_gram_route_equals_svd_route():
     p1 = O.mode_products(*O.to_real_form(ref["Phi"][rows], ref["lam"], ref["b"])[:2], k1)
     p2 = O.mode_products(*O.to_real_form(res["Phi_rows"], res["lam"], res["b"])[:2], k2)
     assert np.linalg.norm(p1 - p2) < tol * np.linalg.norm(p1)
+
+
+# ----------------------------------------------------------- temporal editing
+
+
+def test_edit_modes_identity_and_inverse(exact_cfg0):
+    """Identity edits return the model; an edit followed by its inverse
+    (1/w, 1/s_re, 1/s_im) returns it too."""
+    sc, res = exact_cfg0
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    lam = res["lam"]
+    l1, b1 = O.edit_modes(lam, beta, 0.3, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0))
+    np.testing.assert_allclose(l1, lam, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(b1, beta, rtol=1e-15)
+    l2, b2 = O.edit_modes(lam, beta, 0.3, (0.5, 1.5, 0.5), (2.0, 0.5, 1.5))
+    l3, b3 = O.edit_modes(l2, b2, 0.3 * 0.5, (2.0, 1 / 1.5, 2.0), (0.5, 2.0, 1 / 1.5))
+    np.testing.assert_allclose(l3, lam, rtol=1e-12)
+    np.testing.assert_allclose(b3, beta, rtol=1e-14)
+
+
+def test_edit_modes_closed_forms(exact_cfg0):
+    """s_re = 0 removes growth and decay (|lambda'| = 1); s_im = 0 removes the
+    oscillation (lambda' real positive); w scales every frame of its cluster
+    linearly; the cluster split follows |Im log(lambda)| < threshold."""
+    sc, res = exact_cfg0
+    PhiR, beta, kinds = O.to_real_form(res["Phi"], res["lam"], res["b"])
+    lam = res["lam"]
+    l1, _ = O.edit_modes(lam, beta, 1e9, (1.0, 0.0, 1.0), (1.0, 1.0, 1.0))      # everything is "low"
+    np.testing.assert_allclose(np.abs(l1), 1.0, rtol=1e-14)
+    np.testing.assert_allclose(np.angle(l1), np.angle(lam), rtol=1e-12, atol=1e-14)
+    l2, _ = O.edit_modes(lam, beta, 1e9, (1.0, 1.0, 0.0), (1.0, 1.0, 1.0))
+    assert np.all(l2.real > 0) and np.all(np.abs(l2.imag) < 1e-15)
+    np.testing.assert_allclose(np.abs(l2), np.abs(lam), rtol=1e-14)
+    thr = float(np.median(np.abs(np.angle(lam))))
+    ks = [0, 3, 17]
+    l3, b3 = O.edit_modes(lam, beta, thr, (1.0, 1.0, 1.0), (3.0, 1.0, 1.0))
+    high = np.abs(np.angle(lam)) >= thr
+    F0 = O.predict_real(PhiR, O.coefficients(lam, beta, ks))
+    Fl = O.predict_real(PhiR[:, ~high], O.coefficients(lam[~high], beta[~high], ks))
+    F3 = O.predict_real(PhiR, O.coefficients(l3, b3, ks))
+    np.testing.assert_allclose(F3, Fl + 3.0 * (F0 - Fl), rtol=1e-10, atol=1e-12 * np.abs(F0).max())
