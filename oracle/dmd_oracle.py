@@ -288,6 +288,167 @@ def mode_products(PhiR: np.ndarray, beta: np.ndarray, kinds) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# OptDMD by variable projection (Sec. 4.2, Eqs. variable_projection, phi_optdmd)
+# ----------------------------------------------------------------------------
+
+
+def vandermonde(alpha: np.ndarray, T: int) -> np.ndarray:
+    """Phi(alpha) in C^{T x r} with entry (i, j) = alpha_j^(i-1), i = 1..T
+    (Eq. variable_projection): row i is time t = i - 1."""
+    alpha = np.asarray(alpha, dtype=complex)
+    t = np.arange(T)[:, None]
+    return alpha[None, :] ** t
+
+
+def optdmd_params(lam: np.ndarray, kinds) -> np.ndarray:
+    """Real parameters p of a conjugate-closed eigenvalue set (canonical
+    order): a pair (alpha, conj alpha) in columns c, c+1 is (Re alpha, Im alpha),
+    a real eigenvalue is itself.  Reading: for real snapshots the fit keeps
+    the eigenvalues closed under conjugation, so B and the modes stay those of
+    real data."""
+    lam = np.asarray(lam, dtype=complex)
+    p = np.zeros(len(lam))
+    for c in range(len(lam)):
+        if kinds[c] == 1:
+            p[c], p[c + 1] = lam[c].real, lam[c].imag
+        elif kinds[c] == 0:
+            p[c] = lam[c].real
+    return p
+
+
+def optdmd_alphas(p: np.ndarray, kinds) -> np.ndarray:
+    """alpha(p): inverse of optdmd_params."""
+    alpha = np.zeros(len(p), dtype=complex)
+    for c in range(len(p)):
+        if kinds[c] == 1:
+            alpha[c] = p[c] + 1j * p[c + 1]
+            alpha[c + 1] = p[c] - 1j * p[c + 1]
+        elif kinds[c] == 0:
+            alpha[c] = p[c]
+    return alpha
+
+
+def vandermonde_dparams(p: np.ndarray, kinds, T: int) -> list:
+    """d Phi(alpha(p)) / d p_k for every real parameter k (T x r complex each).
+    d alpha^t / d alpha = t alpha^(t-1); d alpha / d Re = 1, d alpha / d Im = i
+    for the Im > 0 member and -i for its conjugate."""
+    alpha = optdmd_alphas(p, kinds)
+    t = np.arange(T)[:, None]
+    dcol = t * alpha[None, :] ** np.maximum(t - 1, 0)
+    out = []
+    for k in range(len(p)):
+        D = np.zeros((T, len(p)), dtype=complex)
+        if kinds[k] == 0:
+            D[:, k] = dcol[:, k]
+        elif kinds[k] == 1:                      # Re alpha of the pair (k, k+1)
+            D[:, k], D[:, k + 1] = dcol[:, k], dcol[:, k + 1]
+        else:                                    # Im alpha of the pair (k-1, k)
+            D[:, k - 1], D[:, k] = 1j * dcol[:, k - 1], -1j * dcol[:, k]
+        out.append(D)
+    return out
+
+
+def varpro_residual(p: np.ndarray, kinds, Y: np.ndarray):
+    """For fixed alpha the best B of Eq. variable_projection is the least-squares
+    solution B = Phi(alpha)^+ Y; the projected residual is rho = Y - Phi B.
+    Returns (rho, Phi, B)."""
+    Phi = vandermonde(optdmd_alphas(p, kinds), Y.shape[0])
+    B, *_ = np.linalg.lstsq(Phi, Y.astype(complex), rcond=None)
+    return Y - Phi @ B, Phi, B
+
+
+def varpro_objective(p: np.ndarray, kinds, Y: np.ndarray) -> float:
+    """||Y - Phi(alpha) B||_F^2 at the best B (Eq. variable_projection, squared)."""
+    rho, _, _ = varpro_residual(p, kinds, Y)
+    return float(np.sum(np.abs(rho) ** 2))
+
+
+def varpro_jacobian(p: np.ndarray, kinds, Y: np.ndarray):
+    """Residual vector and Jacobian of the projected problem, complex parts
+    stacked as real rows.  Column k is -(I - P)(d Phi / d p_k) B with
+    P = Phi Phi^+ (Kaufman's form of the variable-projection Jacobian: the
+    term it drops is orthogonal to rho, so J^T rho is the exact gradient)."""
+    rho, Phi, B = varpro_residual(p, kinds, Y)
+    cols = []
+    for D in vandermonde_dparams(p, kinds, Y.shape[0]):
+        M = D @ B
+        C, *_ = np.linalg.lstsq(Phi, M, rcond=None)
+        Jk = -(M - Phi @ C)
+        cols.append(np.concatenate([Jk.real.ravel(), Jk.imag.ravel()]))
+    res = np.concatenate([rho.real.ravel(), rho.imag.ravel()])
+    return res, np.stack(cols, axis=1)
+
+
+def optdmd_alpha(Y: np.ndarray, lam0: np.ndarray, max_iter: int = 50, tol: float = 1e-10,
+                 mu0: float = 1e-3):
+    """Levenberg-Marquardt on the projected problem, from the eigenvalues lam0
+    (canonical order) of a standard DMD solve.  Each iteration solves
+    (J^T J + mu diag(J^T J)) delta = -J^T res; a trial point that lowers the
+    objective is taken and mu /= 4, otherwise mu *= 4 and the step is
+    re-solved.  Stops when the objective falls by no more than tol of itself,
+    when the step is below 1e-12 of max |p|, when mu exceeds 1e12 (no
+    decrease left at rounding level), or after max_iter iterations.
+    Returns (p, kinds, info dict)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    kinds = pair_kinds(np.asarray(lam0, dtype=complex))
+    p = optdmd_params(lam0, kinds)
+    res, J = varpro_jacobian(p, kinds, Y)
+    f = float(res @ res)
+    f0, mu, it = f, mu0, 0
+    for it in range(1, max_iter + 1):
+        A = J.T @ J
+        g = J.T @ res
+        dA = np.diag(np.diag(A))
+        taken = False
+        while mu <= 1e12:
+            delta = np.linalg.solve(A + mu * dA, -g)
+            p_new = p + delta
+            f_new = varpro_objective(p_new, kinds, Y)
+            if f_new < f:
+                taken = True
+                break
+            mu *= 4.0
+        if not taken:
+            break
+        small_step = np.max(np.abs(delta)) <= 1e-12 * max(1.0, np.max(np.abs(p)))
+        small_fall = (f - f_new) <= tol * f
+        p, f, mu = p_new, f_new, mu / 4.0
+        if small_step or small_fall:
+            break
+        res, J = varpro_jacobian(p, kinds, Y)
+    return p, kinds, dict(f0=f0, f=f, iters=it, mu=mu)
+
+
+def optdmd(S: np.ndarray, r: int, lam0: np.ndarray | None = None, **lm) -> dict:
+    """OptDMD of S = [x_0 .. x_m] at rank r (Sec. 4.2).  X = U Sigma V^T is the
+    rank-r SVD of X = [x_0 .. x_{m-1}] (T = m snapshots); alpha starts from the
+    exact-DMD eigenvalues (or lam0) and minimises ||conj(V) Sigma - Phi(alpha) B||_F.
+    Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2 (Eq. phi_optdmd) and, as the
+    reading for prediction, amplitudes b_i = ||U B^T(:, i)||_2, so that
+    x_t ~ sum_i phi_i b_i alpha_i^t.  Returned in canonical order."""
+    X, _ = split_snapshots(S)
+    U, s, V = svd_truncated(X, r)
+    if lam0 is None:
+        lam0 = exact_dmd(S, r)["lam"]
+    Y = np.conj(V) * s[None, :]
+    p, kinds, info = optdmd_alpha(Y, lam0, **lm)
+    return optdmd_modes(U, Y, p, kinds, info)
+
+
+def optdmd_modes(U: np.ndarray, Y: np.ndarray, p: np.ndarray, kinds, info: dict) -> dict:
+    """B = Phi(alpha)^+ Y at the fitted alpha, then Eq. phi_optdmd's modes and
+    their norms as amplitudes, in canonical order."""
+    alpha = optdmd_alphas(p, kinds)
+    B, *_ = np.linalg.lstsq(vandermonde(alpha, Y.shape[0]), np.asarray(Y, dtype=complex), rcond=None)
+    L = U @ B.T
+    b = np.linalg.norm(L, axis=0)
+    Phi = L / b[None, :]
+    order = canonical_order(alpha)
+    return dict(lam=alpha[order], Phi=Phi[:, order], b=b[order].astype(complex), B=B[order],
+                Y=Y, U=U, **info)
+
+
+# ----------------------------------------------------------------------------
 # randomized SVD (Sec. 4.3)
 # ----------------------------------------------------------------------------
 

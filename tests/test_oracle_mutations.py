@@ -36,6 +36,9 @@ def _pins():
     yield P.test_adjoint_matches_central_differences
     yield P.test_gram_route_known_operator
     yield P.test_gram_route_equals_svd_route
+    yield lambda: P.pin_optdmd_noise_free(0)
+    yield P.test_optdmd_matches_unreduced_least_squares
+    yield P.test_optdmd_beats_exact_dmd_on_noisy_data
 
 
 def _count_failures():
@@ -143,6 +146,41 @@ def _mut_gram_rhs(Wg):
     return a, b, c, np.asarray(Wg, dtype=np.float64)[:-1, 0]   # X^T x_0 instead of X'^T x_0
 
 
+def _mut_vandermonde(alpha, T):
+    alpha = np.asarray(alpha, dtype=complex)
+    return alpha[None, :] ** np.arange(1, T + 1)[:, None]      # alpha^i instead of alpha^(i-1)
+
+
+_orig_dparams = O.vandermonde_dparams
+
+
+def _mut_dparams(p, kinds, T):
+    out = _orig_dparams(p, kinds, T)
+    for k, D in enumerate(out):
+        if kinds[k] == 2:
+            out[k] = np.conj(D)                                    # d/d Im with the signs of i swapped
+    return out
+
+
+_orig_optdmd_modes = O.optdmd_modes
+
+
+def _mut_modes_untransposed(U, Y, p, kinds, info):
+    alpha = O.optdmd_alphas(p, kinds)
+    B, *_ = np.linalg.lstsq(O.vandermonde(alpha, Y.shape[0]), np.asarray(Y, dtype=complex), rcond=None)
+    L = U @ B                                                      # U B instead of U B^T
+    b = np.linalg.norm(L, axis=0)
+    order = O.canonical_order(alpha)
+    return dict(lam=alpha[order], Phi=(L / b[None, :])[:, order], b=b[order].astype(complex), B=B[order],
+                Y=Y, U=U, **info)
+
+
+def _mut_modes_unit_amplitude(U, Y, p, kinds, info):
+    out = _orig_optdmd_modes(U, Y, p, kinds, info)
+    out["b"] = np.ones_like(out["b"])                              # amplitudes dropped
+    return out
+
+
 MUTATIONS = [
     ("split_snapshots", _mut_split, O),
     ("reduced_operator", _mut_reduced_scale, O),
@@ -158,6 +196,10 @@ MUTATIONS = [
     ("mode_products", _mut_mode_products, O),
     ("gram_blocks", _mut_gram_cross, O),
     ("gram_blocks", _mut_gram_rhs, O),
+    ("vandermonde", _mut_vandermonde, O),
+    ("vandermonde_dparams", _mut_dparams, O),
+    ("optdmd_modes", _mut_modes_untransposed, O),
+    ("optdmd_modes", _mut_modes_unit_amplitude, O),
 ]
 
 

@@ -510,3 +510,99 @@ def test_edit_modes_closed_forms(exact_cfg0):
     Fl = O.predict_real(PhiR[:, ~high], O.coefficients(lam[~high], beta[~high], ks))
     F3 = O.predict_real(PhiR, O.coefficients(l3, b3, ks))
     np.testing.assert_allclose(F3, Fl + 3.0 * (F0 - Fl), rtol=1e-10, atol=1e-12 * np.abs(F0).max())
+
+
+# ------------------------------------------------------------------ OptDMD (Sec. 4.2)
+
+def _exp_data(n=40, T=30, npairs=3, real_eigs=(0.97,), noise=0.0, seed=0):
+    """Snapshots x_t = sum_j g_j lambda_j^t (t = 0..T) from known conjugate-closed
+    eigenvalues and fields g_j, plus optional Gaussian noise; returns
+    (S, lambda, g) with g in the same column order as lambda."""
+    g = np.random.default_rng(seed)
+    lam_p = np.exp(g.uniform(-0.05, 0.0, npairs) + 1j * g.uniform(0.2, 2.8, npairs))
+    fp = g.standard_normal((n, npairs)) + 1j * g.standard_normal((n, npairs))
+    lam, fields = [], []
+    for j in range(npairs):
+        lam += [lam_p[j], np.conj(lam_p[j])]
+        fields += [fp[:, j], np.conj(fp[:, j])]
+    for a in real_eigs:
+        lam.append(complex(a))
+        fields.append(g.standard_normal(n) + 0j)
+    lam, fields = np.array(lam), np.stack(fields, axis=1)
+    t = np.arange(T + 1)
+    S = (fields @ (lam[:, None] ** t[None, :])).real
+    if noise:
+        S = S + noise * np.linalg.norm(S) / math.sqrt(S.size) * g.standard_normal(S.shape)
+    return S, lam, fields
+
+
+def pin_optdmd_noise_free(seed=0):
+    """Exponential snapshots are fitted exactly: from eigenvalues perturbed by
+    1e-3 the fit returns the generating eigenvalues and the fields
+    phi_j b_j = g_j (so that x_t = sum_j phi_j b_j alpha_j^t, t from 0)."""
+    S, lam, fields = _exp_data(seed=seed)
+    r = len(lam)
+    ex = O.exact_dmd(S, r)
+    kinds = O.pair_kinds(ex["lam"])
+    g = np.random.default_rng(seed + 100)
+    lam0 = O.optdmd_alphas(O.optdmd_params(ex["lam"], kinds) + 1e-3 * g.standard_normal(r), kinds)
+    res = O.optdmd(S, r, lam0=lam0)
+    assert match_eigs(res["lam"], lam) < 1e-9
+    prod = res["Phi"] * res["b"][None, :]
+    for j in range(r):
+        i = int(np.argmin(np.abs(res["lam"] - lam[j])))
+        assert np.linalg.norm(prod[:, i] - fields[:, j]) < 1e-8 * np.linalg.norm(fields[:, j]), j
+    assert res["f"] < 1e-20 * np.sum(np.abs(res["Y"]) ** 2)
+
+
+def test_optdmd_noise_free_recovery():
+    pin_optdmd_noise_free(0)
+    pin_optdmd_noise_free(1)
+
+
+def test_optdmd_matches_unreduced_least_squares():
+    """Variable projection solves the same problem as the unreduced fit over
+    (alpha, B) jointly: a general-purpose least-squares solver on
+    ||Y - Phi(alpha) B||_F (Vandermonde from numpy.vander, B free complex),
+    started from the same eigenvalues, reaches the same alpha and objective."""
+    from scipy.optimize import least_squares
+    S, lam, _ = _exp_data(n=10, T=25, npairs=2, real_eigs=(), noise=3e-2, seed=5)
+    r = 4
+    X = S[:, :-1]
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    Y = Vt[:r].T * s[:r][None, :]
+    lam0 = O.exact_dmd(S, r)["lam"]
+    p_opt, kinds, info = O.optdmd_alpha(Y, lam0, max_iter=200, tol=1e-15)
+    assert list(kinds) == [1, 2, 1, 2]
+    T = Y.shape[0]
+
+    def alphas(p):
+        return np.array([p[0] + 1j * p[1], p[0] - 1j * p[1], p[2] + 1j * p[3], p[2] - 1j * p[3]])
+
+    def resid(x):
+        Phi = np.vander(alphas(x[:4]), T, increasing=True).T
+        B = (x[4:4 + r * r] + 1j * x[4 + r * r:]).reshape(r, r)
+        R = Y - Phi @ B
+        return np.concatenate([R.real.ravel(), R.imag.ravel()])
+
+    p0 = np.array([lam0[0].real, lam0[0].imag, lam0[2].real, lam0[2].imag])
+    B0 = np.linalg.pinv(np.vander(alphas(p0), T, increasing=True).T) @ Y
+    x0 = np.concatenate([p0, B0.real.ravel(), B0.imag.ravel()])
+    sol = least_squares(resid, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+    f_full = float(sol.fun @ sol.fun)
+    assert abs(f_full - info["f"]) <= 1e-8 * info["f"]
+    assert np.max(np.abs(sol.x[:4] - p_opt)) < 1e-6
+    assert info["f"] < O.varpro_objective(O.optdmd_params(lam0, kinds), kinds, Y)
+
+
+def test_optdmd_beats_exact_dmd_on_noisy_data():
+    """Sec. 4.2's motivation: with noisy snapshots the fit over the whole
+    trajectory places the eigenvalues closer to the generating ones than the
+    one-step fit of exact DMD (mean over seeds)."""
+    e_ex, e_opt = [], []
+    for seed in range(6):
+        S, lam, _ = _exp_data(n=60, T=80, npairs=3, noise=5e-2, seed=20 + seed)
+        r = len(lam)
+        e_ex.append(match_eigs(O.exact_dmd(S, r)["lam"], lam))
+        e_opt.append(match_eigs(O.optdmd(S, r)["lam"], lam))
+    assert np.mean(e_opt) < 0.5 * np.mean(e_ex), (e_opt, e_ex)
