@@ -152,6 +152,40 @@ DMD_EXPORT dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const fl
                    const double* Omega, float* Phi_R, double* modal, int32_t* info,
                    void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- OptDMD (Sec. 4.2, Eqs. variable_projection and phi_optdmd) -------- */
+
+/* Options of dmd_fit_optdmd; zero fields take the defaults. */
+typedef struct dmd_optdmd_opts {
+  int32_t max_evals;   /* objective evaluations of the Levenberg-Marquardt loop (0 = 40) */
+  int32_t reserved;
+  double tol;          /* stop when an accepted step lowers the objective by <= tol of it (0 = 1e-10) */
+  double mu0;          /* initial Marquardt damping, relative to diag(J^T J) (0 = 1e-3) */
+} dmd_optdmd_opts;
+
+DMD_EXPORT dmd_status dmd_fit_optdmd_workspace_bytes(const dmd_fit_desc* desc, size_t* bytes);
+
+/* OptDMD fit of S (desc->q must be 0).  Runs dmd_fit's randomized SVD
+ * X ~ U Sigma V^T (U = Q U_B) and exact-DMD eigenvalues, then fits the
+ * eigenvalues alpha over all T = m snapshots at once:
+ *   min_{alpha, B} || V Sigma - Phi(alpha) B ||_F,  Phi(alpha)_{t, j} = alpha_j^t (t = 0..T-1),
+ * by variable projection (B = Phi^+ V Sigma) and Levenberg-Marquardt on alpha
+ * (FP64, conjugate pairs kept, Kaufman's Jacobian, Marquardt damping mu
+ * diag(J^T J): an accepted step divides mu by 4, a rejected one multiplies
+ * it by 4), starting from the exact-DMD eigenvalues.  The loop stops when an
+ * accepted step lowers the objective by at most tol of it, when the step is
+ * below 1e-12 of max |p|, when mu exceeds 1e12, or after max_evals
+ * evaluations; the decisions are taken on the device (no host
+ * synchronisation).  Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2 and
+ * amplitudes b_i = ||U B^T(:, i)||_2 (so x_t ~ sum_i phi_i b_i alpha_i^t),
+ * written in the real form and canonical order of dmd_fit; sigma as dmd_fit.
+ * stats (device, 4 doubles, may be NULL): objective at the exact-DMD
+ * eigenvalues, final objective, evaluations, accepted steps.  info as
+ * dmd_fit (DMD_ENUMERIC if not even the starting point gave a finite
+ * objective).  Errors: those of dmd_fit; EINVAL for q > 0. */
+DMD_EXPORT dmd_status dmd_fit_optdmd(const dmd_fit_desc* desc, const dmd_optdmd_opts* opts, const float* S,
+                          const double* Omega, float* Phi_R, double* modal, int32_t* info,
+                          double* stats, void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- prediction (Eq. large_time_step, Eq. reverse_simulation, Eq. external_forces) */
 
 DMD_EXPORT dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);

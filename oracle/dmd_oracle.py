@@ -419,17 +419,25 @@ def optdmd_alpha(Y: np.ndarray, lam0: np.ndarray, max_iter: int = 50, tol: float
     return p, kinds, dict(f0=f0, f=f, iters=it, mu=mu)
 
 
-def optdmd(S: np.ndarray, r: int, lam0: np.ndarray | None = None, **lm) -> dict:
+def optdmd(S: np.ndarray, r: int, lam0: np.ndarray | None = None, Omega: np.ndarray | None = None,
+           power_iters: int = 2, **lm) -> dict:
     """OptDMD of S = [x_0 .. x_m] at rank r (Sec. 4.2).  X = U Sigma V^T is the
-    rank-r SVD of X = [x_0 .. x_{m-1}] (T = m snapshots); alpha starts from the
-    exact-DMD eigenvalues (or lam0) and minimises ||conj(V) Sigma - Phi(alpha) B||_F.
-    Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2 (Eq. phi_optdmd) and, as the
-    reading for prediction, amplitudes b_i = ||U B^T(:, i)||_2, so that
-    x_t ~ sum_i phi_i b_i alpha_i^t.  Returned in canonical order."""
+    rank-r SVD of X = [x_0 .. x_{m-1}] (T = m snapshots; the randomized SVD of
+    Sec. 4.3 when a test matrix Omega is given); alpha starts from the
+    exact-DMD eigenvalues of that SVD (or lam0) and minimises
+    ||conj(V) Sigma - Phi(alpha) B||_F.  Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2
+    (Eq. phi_optdmd) and, as the reading for prediction, amplitudes
+    b_i = ||U B^T(:, i)||_2, so that x_t ~ sum_i phi_i b_i alpha_i^t.
+    Returned in canonical order."""
     X, _ = split_snapshots(S)
-    U, s, V = svd_truncated(X, r)
-    if lam0 is None:
-        lam0 = exact_dmd(S, r)["lam"]
+    if Omega is None:
+        U, s, V = svd_truncated(X, r)
+        if lam0 is None:
+            lam0 = exact_dmd(S, r)["lam"]
+    else:
+        U, s, V, _ = rsvd(X, Omega, r, power_iters)
+        if lam0 is None:
+            lam0 = rsvd_dmd(S, Omega, r, power_iters)["lam"]
     Y = np.conj(V) * s[None, :]
     p, kinds, info = optdmd_alpha(Y, lam0, **lm)
     return optdmd_modes(U, Y, p, kinds, info)

@@ -7,6 +7,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "optdmd.cuh"
 
 namespace dmd {
 
@@ -370,8 +371,15 @@ dmd_status fit_control(const dmd_fit_desc& d, const float* S, const float* Ups, 
   return DMD_OK;
 }
 
+// OptDMD request of fit_impl: options, stats output and its small-space buffers.
+struct OptRequest {
+  const dmd_optdmd_opts* opts;
+  double* stats;
+  OptBufs* bufs;
+};
+
 dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, const double* Omega, float* PhiR,
-                    double* modal, int32_t* info, FitBufs& b, cudaStream_t st) {
+                    double* modal, int32_t* info, FitBufs& b, cudaStream_t st, const OptRequest* opt = nullptr) {
   const Tall tall{d.precision};
   const int64_t n = b.n;
   const int m = b.m, l = b.l, r = b.r, q = b.q;
@@ -416,6 +424,11 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   DMD_TRY(dgemm(r, r, l, 1.0, b.YB, l, true, b.Tmp, l, false, 0.0, b.At, r, st));
   // 7. eigendecomposition A~ W = W Lambda
   DMD_TRY(reduced_eig(b, modal, info, st));
+  if (opt) {
+    // OptDMD (Sec. 4.2) from these eigenvalues; modes Phi_R = Q1 (T2 U_B,r Wt)
+    DMD_TRY(optdmd_small(m, r, l, B, b.YB, b.T2, modal, info, opt->stats, *opt->opts, *opt->bufs, st));
+    return tall.nn(n, l, r, b.Q1, b.ldY, opt->bufs->Mlift, PhiR, d.ldPhi, b.gemm_ws, st);
+  }
   // 8. modes Phi_R = X' M_R with M_R = V Sigma^{-1} W_R
   DMD_TRY(dgemm(m, r, r, 1.0, b.Vs, m, false, b.WR, r, false, 0.0, b.MR, m, st));
   DMD_TRY(tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st));
@@ -535,6 +548,39 @@ dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const float* Ups, c
     FitBufs b;
     carve_fit(a, *desc, Tall{desc->precision}, b);
     return fit_impl(*desc, S, Ups, Omega, Phi_R, modal, info, b, (cudaStream_t)stream);
+  }, need);
+}
+
+dmd_status dmd_fit_optdmd_workspace_bytes(const dmd_fit_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_fit(desc));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  DMD_REQUIRE(desc->q == 0, "dmd_fit_optdmd: control inputs (q > 0) are not supported");
+  Arena a;
+  FitBufs b;
+  carve_fit(a, *desc, Tall{desc->precision}, b);
+  OptBufs o;
+  carve_optdmd(a, desc->m, desc->r, b.l, o);
+  *bytes = a.used + 256;
+  return DMD_OK;
+}
+
+dmd_status dmd_fit_optdmd(const dmd_fit_desc* desc, const dmd_optdmd_opts* opts, const float* S,
+                          const double* Omega, float* Phi_R, double* modal, int32_t* info, double* stats,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  DMD_TRY(dmd_fit_optdmd_workspace_bytes(desc, &need));
+  DMD_REQUIRE(S && Phi_R && modal && info, "dmd_fit_optdmd: NULL pointer argument");
+  dmd_optdmd_opts o{};
+  if (opts) o = *opts;
+  DMD_REQUIRE(o.max_evals >= 0 && o.tol >= 0.0 && o.mu0 >= 0.0 && o.max_evals <= 10000,
+              "dmd_fit_optdmd: bad options (max_evals %d, tol %g, mu0 %g)", o.max_evals, o.tol, o.mu0);
+  return with_arena(workspace, ws_bytes, [&](Arena& a) {
+    FitBufs b;
+    carve_fit(a, *desc, Tall{desc->precision}, b);
+    OptBufs ob;
+    carve_optdmd(a, desc->m, desc->r, b.l, ob);
+    OptRequest req{&o, stats, &ob};
+    return fit_impl(*desc, S, nullptr, Omega, Phi_R, modal, info, b, (cudaStream_t)stream, &req);
   }, need);
 }
 

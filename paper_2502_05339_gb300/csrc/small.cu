@@ -49,9 +49,13 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // ------------------------------------------------------------------ GEMM
 
 // C[M x N] = alpha op(A) op(B) + beta C (column-major; op = transpose when t* != 0).
+// Kernels that take `skip` return at once when it is non-NULL and *skip != 0
+// (a device-side flag: iterative solvers stop without a host round trip).
 __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                int lda, int ta, const double* __restrict__ B, int ldb,
-                                               int tb, double beta, double* __restrict__ C, int ldc) {
+                                               int tb, double beta, double* __restrict__ C, int ldc,
+                                               const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -92,7 +96,9 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
 // k_tri_inv_upper then zeroes row and column j of R^{-1}.  Drops are counted
 // in info[5].  A non-finite pivot is DMD_ENONFINITE, an all-zero matrix
 // DMD_ENUMERIC.
-__global__ void k_cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+__global__ void k_cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag,
+                                 const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   __shared__ double piv;
   __shared__ double red[32];
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -144,7 +150,9 @@ __global__ void k_cholesky_upper(int n, double* G, int ld, double tau, int32_t* 
 // T = R^{-1} for upper triangular R by back substitution, one warp per
 // column (the dot products are split across the lanes).  A zero diagonal
 // entry marks a dropped direction: its row and column of T are zero.
-__global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T, int ldt) {
+__global__ void k_tri_inv_upper(int n, const double* __restrict__ R, int ldr, double* __restrict__ T, int ldt,
+                                const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= n) return;
@@ -1270,7 +1278,9 @@ __device__ __forceinline__ void store_square(double* G, int ld, const double* S,
 }
 
 // Cholesky as k_cholesky_upper (same pivot / drop rule), matrix in shared memory.
-__global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* info, int tag) {
+__global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* info, int tag,
+                                const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   extern __shared__ double sm[];
   const int ldw = n | 1;
   double* S = sm;
@@ -1388,7 +1398,9 @@ __global__ void k_cholesky_f32(int n, double* G, int ld, double tau, int32_t* in
 // warps of the CTA stage R's columns 0..j (upper part, packed) in shared
 // memory first.
 __global__ void __launch_bounds__(128) k_tri_inv_col(int n, const double* __restrict__ R, int ldr,
-                                                     double* __restrict__ T, int ldt) {
+                                                     double* __restrict__ T, int ldt,
+                                                     const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   extern __shared__ double sm[];
   const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   double* Rp = sm;                        // column i at offset i (i + 1) / 2
@@ -1639,13 +1651,18 @@ __global__ void k_lstsq_smem(int mr, int nc, double* A, int ld, int nrhs, double
 
 // ------------------------------------------------------------ launchers
 
-dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
-                 int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st) {
+dmd_status dgemm_gated(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
+                       int ldb, bool tb, double beta, double* C, int ldc, const int32_t* skip, cudaStream_t st) {
   if (M <= 0 || N <= 0) return DMD_OK;
   dim3 grid((unsigned)ceil_div(M, 16), (unsigned)ceil_div(N, 16));
-  k_dgemm<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc);
+  k_dgemm<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
+}
+
+dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
+                 int ldb, bool tb, double beta, double* C, int ldc, cudaStream_t st) {
+  return dgemm_gated(M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, nullptr, st);
 }
 
 // Shared-memory bytes of an n x n FP64 matrix with leading dimension n | 1
@@ -1659,28 +1676,38 @@ static dmd_status set_smem(const void* fn, size_t bytes) {
   return DMD_OK;
 }
 
-dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
+dmd_status cholesky_upper_gated(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
+                                cudaStream_t st) {
   const size_t smem = square_smem(n, n, (size_t)n + 32);
   if (smem <= kSmallSmemMax) {
     DMD_TRY(set_smem((const void*)k_cholesky_smem, smem));
-    k_cholesky_smem<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag);
+    k_cholesky_smem<<<1, 512, smem, st>>>(n, G, ld, tau, info, tag, skip);
   } else {
-    k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag);
+    k_cholesky_upper<<<1, 1024, 0, st>>>(n, G, ld, tau, info, tag, skip);
+  }
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
+  return cholesky_upper_gated(n, G, ld, tau, info, tag, nullptr, st);
+}
+
+dmd_status tri_inv_upper_gated(int n, const double* R, int ldr, double* T, int ldt, const int32_t* skip,
+                               cudaStream_t st) {
+  const size_t smem = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(double);
+  if (smem <= kSmallSmemMax) {
+    DMD_TRY(set_smem((const void*)k_tri_inv_col, smem));
+    k_tri_inv_col<<<(unsigned)n, 128, smem, st>>>(n, R, ldr, T, ldt, skip);
+  } else {
+    k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt, skip);
   }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
 
 dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cudaStream_t st) {
-  const size_t smem = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(double);
-  if (smem <= kSmallSmemMax) {
-    DMD_TRY(set_smem((const void*)k_tri_inv_col, smem));
-    k_tri_inv_col<<<(unsigned)n, 128, smem, st>>>(n, R, ldr, T, ldt);
-  } else {
-    k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt);
-  }
-  DMD_LAUNCH_CHECK();
-  return DMD_OK;
+  return tri_inv_upper_gated(n, R, ldr, T, ldt, nullptr, st);
 }
 
 dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {

@@ -41,6 +41,11 @@ class FitDesc(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class OptDmdOpts(ctypes.Structure):
+    _fields_ = [("max_evals", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("mu0", ctypes.c_double)]
+
+
 class PredictDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ldPhi", ctypes.c_int64), ("ldOut", ctypes.c_int64),
                 ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("q", ctypes.c_int32),
@@ -61,6 +66,9 @@ SIGNATURES = {
     "dmd_launch_count": (ctypes.c_uint64, []),
     "dmd_fit_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _SZ]),
     "dmd_fit": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_fit_optdmd_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), ctypes.POINTER(ctypes.c_size_t)]),
+    "dmd_fit_optdmd": (ctypes.c_int32, [ctypes.POINTER(FitDesc), ctypes.POINTER(OptDmdOpts), _P, _P, _P, _P, _P,
+                                        _P, _P, ctypes.c_size_t, _P]),
     "dmd_predict_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _SZ]),
     "dmd_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "dmd_predict_noalloc": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P]),
@@ -207,6 +215,38 @@ def dmd_fit(S: torch.Tensor, n: int, r: int, *, oversample: int = 10, power_iter
     _check(lib().dmd_fit(ctypes.byref(d), _ptr(S), _ptr(Ups), _ptr(Omega), _ptr(Phi), _ptr(modal), _ptr(info),
                          _ptr(ws), ws.numel(), _stream(dev)), "dmd_fit")
     return DmdModel(Phi, modal, info, n, r, q)
+
+
+def dmd_fit_optdmd(S: torch.Tensor, n: int, r: int, *, oversample: int = 10, power_iters: int = 2,
+                   precision="fp32", seed: int = 0, Omega: torch.Tensor | None = None, max_evals: int = 0,
+                   tol: float = 0.0, mu0: float = 0.0, stats: torch.Tensor | None = None) -> DmdModel:
+    """OptDMD fit (Sec. 4.2) of S = [x_0..x_m] (tensor (m+1, ldS) float32), started
+    from the exact-DMD eigenvalues of the same randomized SVD.  `stats` (4 float64
+    on the device, optional) receives the objective at the start, the final
+    objective, the evaluations and the accepted steps."""
+    _need_cuda(S, "S", torch.float32)
+    m = S.shape[0] - 1
+    ldS = S.shape[1]
+    if Omega is not None:
+        _need_cuda(Omega, "Omega", torch.float64)
+    if stats is not None:
+        _need_cuda(stats, "stats", torch.float64)
+    dev = S.device
+    ldPhi = round_up(n, 32)
+    d = FitDesc(n=n, ldS=ldS, ldPhi=ldPhi, m=m, r=r, oversample=oversample, power_iters=power_iters,
+                q=0, precision=_prec(precision), seed=seed)
+    o = OptDmdOpts(max_evals=max_evals, reserved=0, tol=tol, mu0=mu0)
+    nb = ctypes.c_size_t(0)
+    _check(lib().dmd_fit_optdmd_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)), "dmd_fit_optdmd_workspace_bytes")
+    ws = _workspace(nb.value, dev)
+    Phi = torch.empty((r, ldPhi), dtype=torch.float32, device=dev)
+    if ldPhi > n:
+        Phi[:, n:].zero_()
+    modal = torch.empty(modal_doubles(r, 0), dtype=torch.float64, device=dev)
+    info = torch.zeros(INFO_WORDS, dtype=torch.int32, device=dev)
+    _check(lib().dmd_fit_optdmd(ctypes.byref(d), ctypes.byref(o), _ptr(S), _ptr(Omega), _ptr(Phi), _ptr(modal),
+                                _ptr(info), _ptr(stats), _ptr(ws), ws.numel(), _stream(dev)), "dmd_fit_optdmd")
+    return DmdModel(Phi, modal, info, n, r, 0)
 
 
 def _ks_tensor(ks, dev) -> torch.Tensor:
