@@ -220,6 +220,7 @@ def run_ours(args):
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = run_e2e(args, sc, c, dmd, dev, st, out, ks)
     adjoint = adjoint_timing(model, ks, out, dmd, st, prec, rec_s)
+    optdmd = None if args.no_optdmd else optdmd_timing(S, n, c, dmd, st, prec, fit_s)
 
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
@@ -242,7 +243,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}", "l2": "inputs (5.06 GB) and outputs (25.2 GB) exceed L2"},
         "fit_s": fit_s, "recon_frames_per_s": K / rec_s, "recon_s": rec_s,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-        "forms": forms, "kernels": kernels, "adjoint": adjoint, "device": device_info(dev),
+        "forms": forms, "kernels": kernels, "adjoint": adjoint, "optdmd": optdmd, "device": device_info(dev),
         "parity": {"status": model.status()},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -399,6 +400,23 @@ def adjoint_timing(model, ks, out, dmd, st, prec, rec_s):
     grad = event_time(lambda: dmd.dmd_predict_loss(model, ks, target, w, want_grad=True, precision=prec), st)
     return {"forward_s": rec_s, "backward_s": bwd, "backward_over_forward": bwd / rec_s,
             "streamed_loss_s": loss, "streamed_loss_and_grad_s": grad, "grad_over_loss": grad / loss}
+
+
+def optdmd_timing(S, n, c, dmd, st, prec, exact_fit_s):
+    """OptDMD fit (Sec. 4.2) of the same snapshots: the exact fit's randomized
+    SVD, then the device-side variable-projection loop and one tall lift."""
+    stats = torch.zeros(4, dtype=torch.float64, device=S.device)
+    holder = {}
+
+    def fit():
+        holder["m"] = dmd.dmd_fit_optdmd(S, n, c["r"], oversample=c["oversample"], power_iters=c["power_iters"],
+                                         precision=prec, seed=c["seed"], stats=stats)
+
+    sec = event_time(fit, st, reps=2)
+    holder["m"].check()
+    f0, f, evals, acc = stats.cpu().tolist()
+    return {"fit_s": sec, "over_exact_fit": sec / exact_fit_s, "evaluations": int(evals), "accepted": int(acc),
+            "objective_start": f0, "objective_end": f}
 
 
 def device_info(dev):
@@ -633,6 +651,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("DMD_BENCH_PRECISION", "mixed"), choices=["fp32", "mixed"])
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side timing of the other form")
+    ap.add_argument("--no-optdmd", action="store_true", help="skip the OptDMD fit timing")
     ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel roofline timings")
     ap.add_argument("--config", default="cfg1", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")

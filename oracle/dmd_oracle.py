@@ -443,6 +443,28 @@ def optdmd(S: np.ndarray, r: int, lam0: np.ndarray | None = None, Omega: np.ndar
     return optdmd_modes(U, Y, p, kinds, info)
 
 
+def optdmd_from_gram(Wg: np.ndarray, r: int, X_rows: np.ndarray, **lm) -> dict:
+    """OptDMD (same definition as optdmd, Sec. 4.2) from inner products, for
+    snapshot matrices too tall to decompose in FP64: V and Sigma from
+    X^T X = V Sigma^2 V^T (Wg = S^T S as in exact_dmd_from_gram), alpha from
+    the exact-DMD eigenvalues of the same route, and the modes at some rows
+    of X only: U = X V Sigma^{-1} there, U B^T(:, i) at those rows, and
+    ||U B^T(:, i)||_2 = ||B(i, :)||_2 because U^T U = I."""
+    XtX = gram_blocks(Wg)[0]
+    ev, V = np.linalg.eigh(XtX)
+    idx = np.argsort(ev)[::-1][:r]
+    s, V = np.sqrt(ev[idx]), V[:, idx]
+    lam0 = exact_dmd_from_gram(Wg, r, np.zeros((0, XtX.shape[0])))["lam"]
+    Y = V * s[None, :]
+    p, kinds, info = optdmd_alpha(Y, lam0, **lm)
+    alpha = optdmd_alphas(p, kinds)
+    B, *_ = np.linalg.lstsq(vandermonde(alpha, Y.shape[0]), Y.astype(complex), rcond=None)
+    L = (np.asarray(X_rows, dtype=np.float64) @ (V / s[None, :])) @ B.T
+    b = np.linalg.norm(B, axis=1)
+    order = canonical_order(alpha)
+    return dict(lam=alpha[order], Phi_rows=(L / b[None, :])[:, order], b=b[order].astype(complex), **info)
+
+
 def optdmd_modes(U: np.ndarray, Y: np.ndarray, p: np.ndarray, kinds, info: dict) -> dict:
     """B = Phi(alpha)^+ Y at the fitted alpha, then Eq. phi_optdmd's modes and
     their norms as amplitudes, in canonical order."""

@@ -30,6 +30,12 @@ def match(lam_g, lam_o):
     return np.array(perm), worst
 
 
+def eig_frob(lam_g, lam_o):
+    """Relative Frobenius error of the eigenvalue vector after matching."""
+    perm, _ = match(lam_g, lam_o)
+    return rel(np.asarray(lam_g)[perm], lam_o)
+
+
 def oracle_model(S64: np.ndarray, r: int):
     ref = O.exact_dmd(S64, r)
     PhiR, beta, kinds = O.to_real_form(ref["Phi"], ref["lam"], ref["b"])

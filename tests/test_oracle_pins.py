@@ -606,3 +606,19 @@ def test_optdmd_beats_exact_dmd_on_noisy_data():
         e_ex.append(match_eigs(O.exact_dmd(S, r)["lam"], lam))
         e_opt.append(match_eigs(O.optdmd(S, r)["lam"], lam))
     assert np.mean(e_opt) < 0.5 * np.mean(e_ex), (e_opt, e_ex)
+
+
+def test_optdmd_gram_route_equals_svd_route():
+    """The inner-product evaluation of OptDMD (for tall data) returns the same
+    eigenvalues, modes and amplitudes as the SVD route on data small enough
+    for both."""
+    S, lam, _ = _exp_data(n=50, T=40, npairs=3, noise=1e-2, seed=8)
+    r = 7
+    a = O.optdmd(S, r)
+    b = O.optdmd_from_gram(S.T @ S, r, S[:, :-1])
+    assert match_eigs(a["lam"], b["lam"]) < 1e-9
+    pa = a["Phi"] * a["b"][None, :]
+    pb = b["Phi_rows"] * b["b"][None, :]
+    for j in range(r):
+        i = int(np.argmin(np.abs(b["lam"] - a["lam"][j])))
+        assert np.linalg.norm(pb[:, i] - pa[:, j]) < 1e-7 * np.linalg.norm(pa[:, j]), j
