@@ -158,7 +158,7 @@ DMD_EXPORT dmd_status dmd_fit(const dmd_fit_desc* desc, const float* S, const fl
 typedef struct dmd_optdmd_opts {
   int32_t max_evals;   /* objective evaluations of the Levenberg-Marquardt loop (0 = 40) */
   int32_t reserved;
-  double tol;          /* stop when an accepted step lowers the objective by <= tol of it (0 = 1e-10) */
+  double tol;          /* stop when the (taken or predicted) fall of the objective is <= tol of it (0 = 1e-10) */
   double mu0;          /* initial Marquardt damping, relative to diag(J^T J) (0 = 1e-3) */
 } dmd_optdmd_opts;
 
@@ -170,18 +170,19 @@ DMD_EXPORT dmd_status dmd_fit_optdmd_workspace_bytes(const dmd_fit_desc* desc, s
  *   min_{alpha, B} || V Sigma - Phi(alpha) B ||_F,  Phi(alpha)_{t, j} = alpha_j^t (t = 0..T-1),
  * by variable projection (B = Phi^+ V Sigma) and Levenberg-Marquardt on alpha
  * (FP64, conjugate pairs kept, Kaufman's Jacobian, Marquardt damping mu
- * diag(J^T J): an accepted step divides mu by 4, a rejected one multiplies
- * it by 4), starting from the exact-DMD eigenvalues.  The loop stops when an
- * accepted step lowers the objective by at most tol of it, when the step is
- * below 1e-12 of max |p|, when mu exceeds 1e12, or after max_evals
- * evaluations; the decisions are taken on the device (no host
- * synchronisation).  Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2 and
+ * diag(J^T J) with Nielsen's update: a taken step scales mu by
+ * max(1/3, 1 - (2 q - 1)^3), q = actual / predicted fall, a refused one by
+ * nu = 2, 4, 8, ...), starting from the exact-DMD eigenvalues.  The loop stops
+ * when a taken step lowers the objective by at most tol of it or is below
+ * 1e-12 of max |p|, when a refused step's predicted fall is at most tol of
+ * the objective, when mu exceeds 1e12, or after max_evals evaluations; the
+ * decisions are taken on the device (no host synchronisation).  Modes phi_i = U B^T(:, i) / ||U B^T(:, i)||_2 and
  * amplitudes b_i = ||U B^T(:, i)||_2 (so x_t ~ sum_i phi_i b_i alpha_i^t),
  * written in the real form and canonical order of dmd_fit; sigma as dmd_fit.
  * stats (device, 4 doubles, may be NULL): objective at the exact-DMD
  * eigenvalues, final objective, evaluations, accepted steps.  info as
  * dmd_fit (DMD_ENUMERIC if not even the starting point gave a finite
- * objective).  Errors: those of dmd_fit; EINVAL for q > 0. */
+ * objective).  Errors: those of dmd_fit; EINVAL for q > 0 or r > 200. */
 DMD_EXPORT dmd_status dmd_fit_optdmd(const dmd_fit_desc* desc, const dmd_optdmd_opts* opts, const float* S,
                           const double* Omega, float* Phi_R, double* modal, int32_t* info,
                           double* stats, void* workspace, size_t ws_bytes, void* stream);

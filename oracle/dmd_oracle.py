@@ -379,44 +379,49 @@ def varpro_jacobian(p: np.ndarray, kinds, Y: np.ndarray):
     return res, np.stack(cols, axis=1)
 
 
-def optdmd_alpha(Y: np.ndarray, lam0: np.ndarray, max_iter: int = 50, tol: float = 1e-10,
+def optdmd_alpha(Y: np.ndarray, lam0: np.ndarray, max_evals: int = 40, tol: float = 1e-10,
                  mu0: float = 1e-3):
     """Levenberg-Marquardt on the projected problem, from the eigenvalues lam0
-    (canonical order) of a standard DMD solve.  Each iteration solves
-    (J^T J + mu diag(J^T J)) delta = -J^T res; a trial point that lowers the
-    objective is taken and mu /= 4, otherwise mu *= 4 and the step is
-    re-solved.  Stops when the objective falls by no more than tol of itself,
-    when the step is below 1e-12 of max |p|, when mu exceeds 1e12 (no
-    decrease left at rounding level), or after max_iter iterations.
+    (canonical order) of a standard DMD solve.  Each step solves
+    (J^T J + mu diag(J^T J)) delta = -J^T res at the current point and
+    evaluates the objective f = ||res||^2 at p + delta.  The linear model
+    predicts the fall pred = -(2 g.delta + delta.J^T J.delta) (g = J^T res).
+    A trial that lowers f is taken and mu is scaled by
+    max(1/3, 1 - (2 rho - 1)^3) with rho = actual / predicted fall (nu = 2);
+    otherwise mu *= nu, nu *= 2 (Nielsen's damping update).  Stops when a taken
+    step lowers f by at most tol of it or is below 1e-12 of max |p|, when a
+    refused step's predicted fall is at most tol of f, when mu exceeds 1e12,
+    or after max_evals objective evaluations (the first one included).
     Returns (p, kinds, info dict)."""
     Y = np.asarray(Y, dtype=np.float64)
     kinds = pair_kinds(np.asarray(lam0, dtype=complex))
     p = optdmd_params(lam0, kinds)
     res, J = varpro_jacobian(p, kinds, Y)
     f = float(res @ res)
-    f0, mu, it = f, mu0, 0
-    for it in range(1, max_iter + 1):
-        A = J.T @ J
-        g = J.T @ res
-        dA = np.diag(np.diag(A))
-        taken = False
-        while mu <= 1e12:
-            delta = np.linalg.solve(A + mu * dA, -g)
-            p_new = p + delta
-            f_new = varpro_objective(p_new, kinds, Y)
-            if f_new < f:
-                taken = True
+    f0, mu, nu, evals, accepted = f, mu0, 2.0, 1, 0
+    A, g = J.T @ J, J.T @ res
+    while evals < max_evals:
+        delta = np.linalg.solve(A + mu * np.diag(np.diag(A)), -g)
+        p_new = p + delta
+        f_new = varpro_objective(p_new, kinds, Y)
+        evals += 1
+        pred = -(2.0 * g @ delta + delta @ A @ delta)
+        if f_new < f:
+            rho = (f - f_new) / pred if pred > 0 else 0.5
+            stop = (f - f_new) <= tol * f or np.max(np.abs(delta)) <= 1e-12 * max(1.0, np.max(np.abs(p_new)))
+            p, f = p_new, f_new
+            mu, nu = mu * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), 2.0
+            accepted += 1
+            if stop:
                 break
-            mu *= 4.0
-        if not taken:
-            break
-        small_step = np.max(np.abs(delta)) <= 1e-12 * max(1.0, np.max(np.abs(p)))
-        small_fall = (f - f_new) <= tol * f
-        p, f, mu = p_new, f_new, mu / 4.0
-        if small_step or small_fall:
-            break
-        res, J = varpro_jacobian(p, kinds, Y)
-    return p, kinds, dict(f0=f0, f=f, iters=it, mu=mu)
+            res, J = varpro_jacobian(p, kinds, Y)
+            A, g = J.T @ J, J.T @ res
+        else:
+            stop = pred <= tol * f
+            mu, nu = mu * nu, 2.0 * nu
+            if stop or mu > 1e12:
+                break
+    return p, kinds, dict(f0=f0, f=f, evals=evals, accepted=accepted, iters=accepted, mu=mu)
 
 
 def optdmd(S: np.ndarray, r: int, lam0: np.ndarray | None = None, Omega: np.ndarray | None = None,

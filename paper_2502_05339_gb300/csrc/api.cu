@@ -555,6 +555,8 @@ dmd_status dmd_fit_optdmd_workspace_bytes(const dmd_fit_desc* desc, size_t* byte
   DMD_TRY(validate_fit(desc));
   DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
   DMD_REQUIRE(desc->q == 0, "dmd_fit_optdmd: control inputs (q > 0) are not supported");
+  DMD_REQUIRE(desc->r <= 200, "dmd_fit_optdmd: r = %d above 200 (the small solver's factor lives in shared memory)",
+              desc->r);
   Arena a;
   FitBufs b;
   carve_fit(a, *desc, Tall{desc->precision}, b);

@@ -23,10 +23,12 @@
 //     (J^T J)_{kl} = sum s s' (E^T E)_{j j'} (B B^T)_{i i'},
 //     (J^T rho)_k  = -sum s (E^T rho B^T)_{j i},
 // r x r products only.  The projection is taken from the normal equations
-// G = Phi^T Phi = R^T R (FP64 Cholesky) with one refinement step.
+// G = Phi^T Phi = R^T R (FP64 Cholesky, then forward and back substitution)
+// with one refinement step.
 //
 // Control flow stays on the device: a decision kernel accepts the trial point
-// when the objective falls (mu /= 4) or rejects it (mu *= 4), and sets a stop
+// when the objective falls or rejects it (Levenberg-Marquardt damping with
+// Nielsen's update, see k_opt_decide), and sets a stop
 // flag on convergence; every later kernel of the loop then returns at once.
 // A fixed number of evaluations is therefore launched with no host
 // synchronisation, and the whole fit can be captured in a CUDA graph.
@@ -40,15 +42,15 @@ dmd_status dgemm_gated(int M, int N, int K, double alpha, const double* A, int l
                        int ldb, bool tb, double beta, double* C, int ldc, const int32_t* skip, cudaStream_t st);
 dmd_status cholesky_upper_gated(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
                                 cudaStream_t st);
-dmd_status tri_inv_upper_gated(int n, const double* R, int ldr, double* T, int ldt, const int32_t* skip,
-                               cudaStream_t st);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
+dmd_status chol_solve_gated(int n, const double* R, int ldr, const double* Bm, int ldb, int ncols, double alpha,
+                            double beta, double* X, int ldx, const int32_t* skip, cudaStream_t st);
 
 namespace {
 
 // state words: doubles sd[] and ints si[]
-enum { SD_F = 0, SD_MU, SD_F0, SD_EVALS, SD_ACCEPTED, SD_WORDS };
+enum { SD_F = 0, SD_MU, SD_F0, SD_EVALS, SD_ACCEPTED, SD_NU, SD_WORDS };
 enum { SI_DONE = 0, SI_FIRST, SI_WORDS };
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -93,6 +95,7 @@ __global__ void k_opt_init(int r, const double* __restrict__ modal, int* __restr
   sd[SD_F0] = 0.0;
   sd[SD_EVALS] = 0.0;
   sd[SD_ACCEPTED] = 0.0;
+  sd[SD_NU] = 2.0;
   si[SI_DONE] = 0;
   si[SI_FIRST] = 1;
 }
@@ -169,7 +172,12 @@ __global__ void k_opt_assemble(int r, const int* __restrict__ kinds, const doubl
 
 // Accept / reject the trial point and prepare the next step's system
 // A = J^T J + mu diag(J^T J) (of the kept point) and the step's base point.
-// One CTA.  rho = RE[:, 0:r] (T x r, ld T); Bt = B of the trial (r x r, ld r).
+// The linear model's predicted fall of f = ||rho||^2 for the step
+// delta = pt - p is pred = -(2 g.delta + delta.J^T J.delta); a taken step
+// scales mu by max(1/3, 1 - (2 q - 1)^3), q = actual / predicted fall, and
+// resets nu = 2; a refused one multiplies mu by nu and doubles nu (Nielsen's
+// update).  One CTA.  rho = RE[:, 0:r] (T x r, ld T); Bt = B of the trial
+// (r x r, ld r).
 __global__ void __launch_bounds__(512) k_opt_decide(int T, int r, const double* __restrict__ RE,
                                                     double* __restrict__ pt, double* __restrict__ p,
                                                     const double* __restrict__ JtJt, const double* __restrict__ gt,
@@ -191,17 +199,41 @@ __global__ void __launch_bounds__(512) k_opt_decide(int T, int r, const double* 
   }
   dstep = block_max(dstep, red);
   pmax = block_max(pmax, red);
-  const double f = sd[SD_F], mu = sd[SD_MU];
   const bool first = si[SI_FIRST] != 0;
+  double lin = 0.0, quad = 0.0;
+  if (!first) {
+    const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+    for (int a = warp; a < r; a += nw) {
+      double acc = 0.0;
+      for (int b = lane; b < r; b += 32) acc = fma(JtJ[b + (int64_t)a * r], pt[b] - p[b], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) quad = fma(pt[a] - p[a], acc, quad);
+    }
+    for (int i = tid; i < r; i += bd) lin = fma(g[i], pt[i] - p[i], lin);
+  }
+  lin = block_sum(lin, red);
+  quad = block_sum(quad, red);
+  const double pred = -(2.0 * lin + quad);
+  const double f = sd[SD_F], mu = sd[SD_MU], nu = sd[SD_NU];
   const bool accept = first ? (bool)isfinite(ft) : (ft < f);
-  double newmu;
+  double newmu, newnu;
   bool stop;
   if (accept) {
-    newmu = first ? mu : 0.25 * mu;
-    stop = !first && ((f - ft) <= tol * f || dstep <= 1e-12 * fmax(1.0, pmax));
+    if (first) {
+      newmu = mu;
+      newnu = nu;
+      stop = false;
+    } else {
+      const double q = pred > 0.0 ? (f - ft) / pred : 0.5;
+      const double c = 2.0 * q - 1.0;
+      newmu = mu * fmax(1.0 / 3.0, 1.0 - c * c * c);
+      newnu = 2.0;
+      stop = (f - ft) <= tol * f || dstep <= 1e-12 * fmax(1.0, pmax);
+    }
   } else {
-    newmu = 4.0 * mu;
-    stop = first || newmu > 1e12;   // a non-finite start cannot be improved on
+    newmu = mu * nu;
+    newnu = 2.0 * nu;
+    stop = first || pred <= tol * f || newmu > 1e12;   // a non-finite start cannot be improved on
   }
   __syncthreads();   // every thread has read the state before it changes
   const int64_t rr = (int64_t)r * r;
@@ -231,6 +263,7 @@ __global__ void __launch_bounds__(512) k_opt_decide(int T, int r, const double* 
       si[SI_FIRST] = 0;
     }
     sd[SD_MU] = newmu;
+    sd[SD_NU] = newnu;
     sd[SD_EVALS] += 1.0;
     if (stop) si[SI_DONE] = 1;
   }
@@ -305,8 +338,6 @@ void carve_optdmd(Arena& a, int T, int r, int l, OptBufs& o) {
   o.Phi = a.take<double>(Tr);
   o.RE = a.take<double>(2 * Tr);
   o.G = a.take<double>(rr);
-  o.Ri = a.take<double>(rr);
-  o.Ginv = a.take<double>(rr);
   o.H = a.take<double>(2 * rr);
   o.BC = a.take<double>(2 * rr);
   o.EtRE = a.take<double>(2 * rr);
@@ -318,8 +349,6 @@ void carve_optdmd(Arena& a, int T, int r, int l, OptBufs& o) {
   o.g = a.take<double>(r);
   o.Bk = a.take<double>(rr);
   o.A = a.take<double>(rr);
-  o.Ai = a.take<double>(rr);
-  o.tv = a.take<double>(r);
   o.p = a.take<double>(r);
   o.pt = a.take<double>(r);
   o.sd = a.take<double>(SD_WORDS);
@@ -354,15 +383,11 @@ dmd_status optdmd_small(int T, int r, int l, const double* Bsnap, const double* 
     // projection by the normal equations G = Phi^T Phi = R^T R, one refinement step
     DMD_TRY(dgemm_gated(r, r, T, 1.0, o.Phi, T, true, o.Phi, T, false, 0.0, o.G, r, skip, st));
     DMD_TRY(cholesky_upper_gated(r, o.G, r, 1e-14, o.sinfo, 81, skip, st));
-    DMD_TRY(tri_inv_upper_gated(r, o.G, r, o.Ri, r, skip, st));
-    DMD_TRY(dgemm_gated(r, r, r, 1.0, o.Ri, r, false, o.Ri, r, true, 0.0, o.Ginv, r, skip, st));
-    DMD_TRY(dgemm_gated(r, 2 * r, T, 1.0, o.Phi, T, true, o.YD, T, false, 0.0, o.H, r, skip, st));
-    DMD_TRY(dgemm_gated(r, 2 * r, r, 1.0, o.Ginv, r, false, o.H, r, false, 0.0, o.BC, r, skip, st));
     for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1) {
-        DMD_TRY(dgemm_gated(r, 2 * r, T, 1.0, o.Phi, T, true, o.RE, T, false, 0.0, o.H, r, skip, st));
-        DMD_TRY(dgemm_gated(r, 2 * r, r, 1.0, o.Ginv, r, false, o.H, r, false, 1.0, o.BC, r, skip, st));
-      }
+      // [B | C] (+)= G^{-1} Phi^T [Y | D]  (pass 0), G^{-1} Phi^T [rho | E]  (pass 1)
+      DMD_TRY(dgemm_gated(r, 2 * r, T, 1.0, o.Phi, T, true, pass == 0 ? o.YD : o.RE, T, false, 0.0, o.H, r, skip,
+                          st));
+      DMD_TRY(chol_solve_gated(r, o.G, r, o.H, r, 2 * r, 1.0, pass == 0 ? 0.0 : 1.0, o.BC, r, skip, st));
       DMD_CUDA_TRY(cudaMemcpyAsync(o.RE, o.YD, 2 * Tr * sizeof(double), cudaMemcpyDeviceToDevice, st));
       DMD_TRY(dgemm_gated(T, 2 * r, r, -1.0, o.Phi, T, false, o.BC, r, false, 1.0, o.RE, T, skip, st));
     }
@@ -378,9 +403,7 @@ dmd_status optdmd_small(int T, int r, int l, const double* Bsnap, const double* 
     if (it + 1 == max_evals) break;   // the last evaluation is only judged
     // step: (J^T J + mu diag) delta = -J^T rho, pt = p + delta
     DMD_TRY(cholesky_upper_gated(r, o.A, r, 1e-15, o.sinfo, 82, skip, st));
-    DMD_TRY(tri_inv_upper_gated(r, o.A, r, o.Ai, r, skip, st));
-    DMD_TRY(dgemm_gated(r, 1, r, 1.0, o.Ai, r, true, o.g, r, false, 0.0, o.tv, r, skip, st));
-    DMD_TRY(dgemm_gated(r, 1, r, -1.0, o.Ai, r, false, o.tv, r, false, 1.0, o.pt, r, skip, st));
+    DMD_TRY(chol_solve_gated(r, o.A, r, o.g, r, 1, -1.0, 1.0, o.pt, r, skip, st));
   }
   k_opt_layout<<<1, 256, 0, st>>>(r, o.kinds, o.p, o.Bk, modal, o.Wt, info, o.sd, stats);
   DMD_LAUNCH_CHECK();

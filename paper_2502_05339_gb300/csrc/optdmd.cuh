@@ -7,8 +7,8 @@
 namespace dmd {
 
 struct OptBufs {
-  double *YD, *Phi, *RE, *G, *Ri, *Ginv, *H, *BC, *EtRE, *Gb, *Hh, *JtJt, *gt, *JtJ, *g, *Bk, *A, *Ai, *tv, *p, *pt,
-      *sd, *Z, *Wt, *Mlift;
+  double *YD, *Phi, *RE, *G, *H, *BC, *EtRE, *Gb, *Hh, *JtJt, *gt, *JtJ, *g, *Bk, *A, *p, *pt, *sd, *Z, *Wt,
+      *Mlift;
   int* kinds;
   int32_t *si, *sinfo;
 };

@@ -46,6 +46,19 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// 1 / sqrt(x) for finite x > 0 (normal): the hardware's approximate
+// reciprocal square root refined by two Newton-Raphson steps
+// y <- y (3/2 - x/2 y^2) (quadratic convergence: ~22 -> ~44 -> full bits).
+// Replaces a square root followed by a division (~1250 cycles of dependent
+// FP64 latency on GB300) on the Cholesky's sequential pivot path.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = 0.5 * x;
+  y = y * fma(-h, y * y, 1.5);
+  return y * fma(-h, y * y, 1.5);
+}
+
 // ------------------------------------------------------------------ GEMM
 
 // C[M x N] = alpha op(A) op(B) + beta C (column-major; op = transpose when t* != 0).
@@ -1307,10 +1320,11 @@ __global__ void k_cholesky_smem(int n, double* G, int ld, double tau, int32_t* i
         piv = 0.0;   // dropped direction
         if (info) atomicAdd(&info[5], 1);
       } else {
-        piv = sqrt(d);
+        ipiv = rsqrt_nr(d);   // one lane: FP64 square root and division are slow
+        piv = d * ipiv;
       }
       if (piv >= 0.0) S[j + j * ldw] = piv;
-      ipiv = piv > 0.0 ? 1.0 / piv : 0.0;   // one lane: FP64 division is slow
+      if (!(piv > 0.0)) ipiv = 0.0;
     }
     __syncthreads();
     const double p = piv;
@@ -1433,6 +1447,56 @@ __global__ void __launch_bounds__(128) k_tri_inv_col(int n, const double* __rest
     __syncwarp();
   }
   for (int i = lane; i <= j; i += 32) out[i] = b[i];
+}
+
+// X[:, c] = alpha G^{-1} Bm[:, c] + beta X[:, c] for c < ncols, with the
+// Cholesky factor R (upper, R^T R = G, ld ldr; a zero diagonal entry marks a
+// dropped direction, whose component is set to zero) by forward substitution
+// R^T y = b and back substitution R x = y.  Every CTA stages R packed by
+// columns in shared memory; each warp solves one right-hand side, the lanes
+// sharing the scaled-column update of each step (no reductions).
+__global__ void __launch_bounds__(512) k_chol_solve_cols(int n, const double* __restrict__ R, int ldr,
+                                                         const double* __restrict__ Bm, int ldb, int ncols,
+                                                         double alpha, double beta, double* __restrict__ X,
+                                                         int ldx, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double* Rp = sm;                               // column i at offset i (i + 1) / 2
+  double* inv = Rp + (size_t)n * (n + 1) / 2;    // n
+  double* bw = inv + n + warp * n;               // this warp's right-hand side
+  for (int i = warp; i < n; i += nw) {
+    const int off = i * (i + 1) / 2;
+    for (int a = lane; a <= i; a += 32) Rp[off + a] = R[a + (int64_t)i * ldr];
+  }
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double d = R[i + (int64_t)i * ldr];
+    inv[i] = d == 0.0 ? 0.0 : 1.0 / d;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * nw + warp;
+  if (c >= ncols) return;
+  for (int i = lane; i < n; i += 32) bw[i] = Bm[i + (int64_t)c * ldb];
+  __syncwarp();
+  // R^T y = b: y_j = b_j / r_jj, then b_i -= r_ji y_j for i > j
+  for (int j = 0; j < n; ++j) {
+    const double yj = bw[j] * inv[j];
+    __syncwarp();
+    if (lane == 0) bw[j] = yj;
+    for (int i = j + 1 + lane; i < n; i += 32) bw[i] = fma(-Rp[i * (i + 1) / 2 + j], yj, bw[i]);
+    __syncwarp();
+  }
+  // R x = y: x_j = y_j / r_jj, then y_i -= r_ij x_j for i < j
+  for (int j = n - 1; j >= 0; --j) {
+    const double xj = bw[j] * inv[j];
+    const double* col = Rp + j * (j + 1) / 2;
+    __syncwarp();
+    if (lane == 0) bw[j] = xj;
+    for (int i = lane; i < j; i += 32) bw[i] = fma(-col[i], xj, bw[i]);
+    __syncwarp();
+  }
+  double* out = X + (int64_t)c * ldx;
+  for (int i = lane; i < n; i += 32) out[i] = beta == 0.0 ? alpha * bw[i] : fma(alpha, bw[i], beta * out[i]);
 }
 
 // Householder reflector of x[0..m) (x[0] = alpha): v (v[0] = 1) into v[],
@@ -1702,6 +1766,18 @@ dmd_status tri_inv_upper_gated(int n, const double* R, int ldr, double* T, int l
   } else {
     k_tri_inv_upper<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(n, R, ldr, T, ldt, skip);
   }
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status chol_solve_gated(int n, const double* R, int ldr, const double* Bm, int ldb, int ncols, double alpha,
+                            double beta, double* X, int ldx, const int32_t* skip, cudaStream_t st) {
+  const int warps = 16;
+  const size_t smem = ((size_t)n * (n + 1) / 2 + (size_t)n * (1 + warps)) * sizeof(double);
+  DMD_REQUIRE(smem <= kSmallSmemMax, "chol_solve: n = %d too large for shared memory", n);
+  DMD_TRY(set_smem((const void*)k_chol_solve_cols, smem));
+  k_chol_solve_cols<<<(unsigned)ceil_div(ncols, warps), 32 * warps, smem, st>>>(n, R, ldr, Bm, ldb, ncols, alpha,
+                                                                                beta, X, ldx, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

@@ -55,3 +55,18 @@ def test_host_side_queries_without_gpu(libdmd):
     assert L.dmd_predict_workspace_bytes(ctypes.byref(p), ctypes.byref(nb)) == 0
     # a too-small workspace is refused before any device work
     assert L.dmd_predict(ctypes.byref(p), 16, 16, 16, None, 16, 256, 8, None) == 2   # ENOMEM
+
+
+def test_optdmd_rejects_control_and_large_rank():
+    """Host-side argument checks of dmd_fit_optdmd (no GPU needed)."""
+    import ctypes
+    from paper_2502_05339_gb300 import dmd
+    L = dmd.lib()
+    nb = ctypes.c_size_t(0)
+    ok = dmd.FitDesc(n=4096, ldS=4096, ldPhi=4096, m=60, r=20, oversample=10, power_iters=2, q=0, precision=1, seed=0)
+    assert L.dmd_fit_optdmd_workspace_bytes(ctypes.byref(ok), ctypes.byref(nb)) == 0 and nb.value > 0
+    ctl = dmd.FitDesc(n=4096, ldS=4096, ldPhi=4096, m=60, r=20, oversample=10, power_iters=2, q=2, precision=1, seed=0)
+    assert L.dmd_fit_optdmd_workspace_bytes(ctypes.byref(ctl), ctypes.byref(nb)) == 1
+    big = dmd.FitDesc(n=4096, ldS=4096, ldPhi=4096, m=400, r=210, oversample=10, power_iters=2, q=0, precision=1,
+                      seed=0)
+    assert L.dmd_fit_optdmd_workspace_bytes(ctypes.byref(big), ctypes.byref(nb)) == 1

@@ -572,7 +572,7 @@ def test_optdmd_matches_unreduced_least_squares():
     U, s, Vt = np.linalg.svd(X, full_matrices=False)
     Y = Vt[:r].T * s[:r][None, :]
     lam0 = O.exact_dmd(S, r)["lam"]
-    p_opt, kinds, info = O.optdmd_alpha(Y, lam0, max_iter=200, tol=1e-15)
+    p_opt, kinds, info = O.optdmd_alpha(Y, lam0, max_evals=400, tol=1e-15)
     assert list(kinds) == [1, 2, 1, 2]
     T = Y.shape[0]
 
