@@ -266,6 +266,51 @@ def edit_modes(lam: np.ndarray, beta: np.ndarray, threshold: float, low, high, d
     return out_lam, out_beta
 
 
+def upsample(Phi: np.ndarray, lam: np.ndarray, H0: np.ndarray, L: np.ndarray, threshold: float,
+             dt: float = 1.0) -> np.ndarray:
+    """Upsampling evolution of Sec. 6.3.1 with a DMD basis (Phi, Lambda) of a
+    high-resolution simulation, a high-resolution initial state H_0 and
+    inputs L_1..L_T (columns of L, n x T, given on the high-resolution grid):
+      R_0 = Phi^+ H_0;  for t = 1..T:  R*_t = Lambda R_{t-1},  P_t = Phi^+ L_t,
+      R_t = S^L P_t + S^H R*_t,  H_t = Phi R_t.
+    S^L keeps the low-order modes (|Im Omega| < threshold, Omega = log(lambda) / dt;
+    the paper orders the modes by the size of their imaginary parts and takes
+    the low-order ones from the input), S^H the others.  Readings: Phi^+ (least
+    squares) where the paper writes Phi^T, since Phi is not orthogonal; the
+    low-order set by a frequency threshold as in temporal editing.
+    Returns [H_1 .. H_T] (real part, n x T)."""
+    Phi = np.asarray(Phi, dtype=complex)
+    lam = np.asarray(lam, dtype=complex)
+    low = np.abs(np.log(lam).imag / dt) < threshold
+
+    def proj(x):
+        c, *_ = np.linalg.lstsq(Phi, np.asarray(x, dtype=complex), rcond=None)
+        return c
+
+    R = proj(H0)
+    out = []
+    for t in range(L.shape[1]):
+        Rstar = lam * R
+        P = proj(L[:, t])
+        R = np.where(low, P, Rstar)
+        out.append((Phi @ R).real)
+    return np.stack(out, axis=1)
+
+
+def from_real_form(PhiR: np.ndarray, lam: np.ndarray):
+    """Complex modes of a real-form basis (inverse of to_real_form's mode part):
+    a pair's columns (Re phi, Im phi) give phi and conj(phi)."""
+    kinds = pair_kinds(lam)
+    Phi = np.zeros(PhiR.shape, dtype=complex)
+    for c in range(PhiR.shape[1]):
+        if kinds[c] == 1:
+            Phi[:, c] = PhiR[:, c] + 1j * PhiR[:, c + 1]
+            Phi[:, c + 1] = np.conj(Phi[:, c])
+        elif kinds[c] == 0:
+            Phi[:, c] = PhiR[:, c]
+    return Phi
+
+
 def predict_real(PhiR: np.ndarray, C: np.ndarray) -> np.ndarray:
     """Reconstruction as one real product F = Phi_R C."""
     return PhiR @ C

@@ -39,6 +39,10 @@ def _pins():
     yield lambda: P.pin_optdmd_noise_free(0)
     yield P.test_optdmd_matches_unreduced_least_squares
     yield P.test_optdmd_beats_exact_dmd_on_noisy_data
+    yield P.test_upsample_reproduces_model_trajectory
+    yield P.test_upsample_all_low_is_orthogonal_projection
+    yield P.test_upsample_all_high_is_prediction
+    yield P.test_upsample_is_linear_and_splits_by_frequency
 
 
 def _count_failures():
@@ -181,6 +185,29 @@ def _mut_modes_unit_amplitude(U, Y, p, kinds, info):
     return out
 
 
+def _upsample_variant(swap=False, transpose=False, stale=False):
+    def up(Phi, lam, H0, L, threshold, dt=1.0):
+        Phi = np.asarray(Phi, dtype=complex)
+        lam = np.asarray(lam, dtype=complex)
+        low = np.abs(np.log(lam).imag / dt) < threshold
+
+        def proj(x):
+            if transpose:
+                return Phi.T @ np.asarray(x, dtype=complex)          # Phi^T as printed, Phi not orthogonal
+            c, *_ = np.linalg.lstsq(Phi, np.asarray(x, dtype=complex), rcond=None)
+            return c
+
+        R = proj(H0)
+        out = []
+        for t in range(L.shape[1]):
+            Rstar = R if stale else lam * R                           # evolution step dropped
+            P = proj(L[:, t])
+            R = np.where(low, Rstar, P) if swap else np.where(low, P, Rstar)   # S^L and S^H swapped
+            out.append((Phi @ R).real)
+        return np.stack(out, axis=1)
+    return up
+
+
 MUTATIONS = [
     ("split_snapshots", _mut_split, O),
     ("reduced_operator", _mut_reduced_scale, O),
@@ -200,6 +227,9 @@ MUTATIONS = [
     ("vandermonde_dparams", _mut_dparams, O),
     ("optdmd_modes", _mut_modes_untransposed, O),
     ("optdmd_modes", _mut_modes_unit_amplitude, O),
+    ("upsample", _upsample_variant(swap=True), O),
+    ("upsample", _upsample_variant(transpose=True), O),
+    ("upsample", _upsample_variant(stale=True), O),
 ]
 
 

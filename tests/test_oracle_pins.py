@@ -622,3 +622,78 @@ def test_optdmd_gram_route_equals_svd_route():
     for j in range(r):
         i = int(np.argmin(np.abs(b["lam"] - a["lam"][j])))
         assert np.linalg.norm(pb[:, i] - pa[:, j]) < 1e-7 * np.linalg.norm(pa[:, j]), j
+
+
+# ------------------------------------------------------------ upsampling (Sec. 6.3.1)
+
+def _upsample_setup(seed=3, n=40, npairs=3):
+    g = np.random.default_rng(seed)
+    lam_p = np.exp(g.uniform(-0.05, 0.0, npairs) + 1j * np.array([0.05, 0.9, 2.0])[:npairs])
+    lam, cols = [], []
+    for j in range(npairs):
+        v = g.standard_normal(n) + 1j * g.standard_normal(n)
+        lam += [lam_p[j], np.conj(lam_p[j])]
+        cols += [v, np.conj(v)]
+    lam.append(0.93 + 0j)
+    cols.append(g.standard_normal(n) + 0j)
+    return np.array(lam), np.stack(cols, axis=1), g
+
+
+def test_upsample_reproduces_model_trajectory():
+    """Inputs on the model's own trajectory x_t = Phi Lambda^t z: the projection
+    of every input equals the evolved state, so any split of the modes returns
+    the trajectory (low-order modes from the input, high-order from the
+    evolution agree)."""
+    lam, Phi, g = _upsample_setup()
+    z = g.standard_normal(len(lam)) + 1j * g.standard_normal(len(lam))
+    z[1::2][:3] = np.conj(z[0::2][:3])
+    traj = np.stack([(Phi @ (lam ** t * z)).real for t in range(9)], axis=1)
+    for thr in (0.0, 0.5, 1.5, 10.0):
+        H = O.upsample(Phi, lam, traj[:, 0], traj[:, 1:], thr)
+        np.testing.assert_allclose(H, traj[:, 1:], atol=1e-10 * np.abs(traj).max())
+
+
+def test_upsample_all_low_is_orthogonal_projection():
+    """Every mode low-order: H_t is the least-squares projection of L_t onto
+    the span of the modes (residual orthogonal to every mode)."""
+    lam, Phi, g = _upsample_setup()
+    L = g.standard_normal((Phi.shape[0], 5))
+    H = O.upsample(Phi, lam, L[:, 0], L, threshold=1e9)
+    res = L - H
+    assert np.abs(Phi.conj().T @ res).max() < 1e-10 * np.abs(L).max()
+    # the part of L inside the span is kept exactly
+    Lin = np.repeat((Phi @ np.ones(len(lam))).real[:, None], 2, axis=1)
+    np.testing.assert_allclose(O.upsample(Phi, lam, Lin[:, 0], Lin, 1e9), Lin, atol=1e-10)
+
+
+def test_upsample_all_high_is_prediction():
+    """No low-order mode (threshold 0): the inputs are ignored and H_t is the
+    DMD prediction Phi Lambda^t Phi^+ H_0 (Eq. large_time_step)."""
+    lam, Phi, g = _upsample_setup()
+    H0 = g.standard_normal(Phi.shape[0])
+    L = g.standard_normal((Phi.shape[0], 6))
+    H = O.upsample(Phi, lam, H0, L, threshold=0.0)
+    z = np.linalg.pinv(Phi) @ H0
+    ref = np.stack([(Phi @ (lam ** t * z)).real for t in range(1, 7)], axis=1)
+    np.testing.assert_allclose(H, ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_upsample_is_linear_and_splits_by_frequency():
+    """The map (H_0, L) -> H is linear (Sec. 6.3.1); with a split between the
+    modes, the low-order coefficients of H_t follow the input at time t and
+    the high-order ones are the evolved initial state."""
+    lam, Phi, g = _upsample_setup()
+    n = Phi.shape[0]
+    a0, a1 = g.standard_normal(n), g.standard_normal(n)
+    A, B = g.standard_normal((n, 4)), g.standard_normal((n, 4))
+    thr = 0.5                       # low: the pair at 0.05 rad/step and the real mode
+    Hab = O.upsample(Phi, lam, 2 * a0 - 3 * a1, 2 * A - 3 * B, thr)
+    np.testing.assert_allclose(Hab, 2 * O.upsample(Phi, lam, a0, A, thr) - 3 * O.upsample(Phi, lam, a1, B, thr),
+                               atol=1e-10 * np.abs(Hab).max())
+    pinv = np.linalg.pinv(Phi)
+    low = np.abs(np.angle(lam)) < thr
+    z0 = pinv @ a0
+    for t in range(4):
+        c = pinv @ O.upsample(Phi, lam, a0, A, thr)[:, t]
+        np.testing.assert_allclose(c[low], (pinv @ A[:, t])[low], atol=1e-9)
+        np.testing.assert_allclose(c[~low], (lam ** (t + 1) * z0)[~low], atol=1e-9)
