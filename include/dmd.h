@@ -187,6 +187,47 @@ DMD_EXPORT dmd_status dmd_fit_optdmd(const dmd_fit_desc* desc, const dmd_optdmd_
                           const double* Omega, float* Phi_R, double* modal, int32_t* info,
                           double* stats, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- upsampling (Sec. 6.3.1) ------------------------------------------- */
+
+/* Upsampling request: a fitted high-resolution model (Phi_R n x r, ld ldPhi;
+ * modal of r columns, q = 0) and an input matrix `in` (n x (T+1) FP32, ld ldIn)
+ * whose column 0 is the high-resolution initial state H_0 and whose columns
+ * 1..T are the inputs L_1..L_T given on the high-resolution grid (e.g. a
+ * low-resolution simulation prolonged to it). */
+typedef struct dmd_upsample_desc {
+  int64_t n;
+  int64_t ldPhi;
+  int64_t ldIn;
+  int64_t ldOut;
+  int32_t r;
+  int32_t T;
+  int32_t precision;
+  int32_t gram_given;  /* 1: `gram` holds Phi_R^T Phi_R from an earlier call; 0: compute it (and store it in `gram` if non-NULL) */
+  double threshold;    /* low-order modes: |Im log(lambda)| / dt < threshold */
+  double dt;           /* time step of the model (> 0)                       */
+} dmd_upsample_desc;
+
+DMD_EXPORT dmd_status dmd_upsample_workspace_bytes(const dmd_upsample_desc* desc, size_t* bytes);
+
+/* Upsampling evolution (Sec. 6.3.1): R_0 = Phi^+ H_0 and, for t = 1..T,
+ * R_t = S^L Phi^+ L_t + S^H Lambda R_{t-1}, H_t = Phi R_t, where S^L keeps
+ * the low-order modes (|Im log(lambda)| / dt < threshold) and S^H the others;
+ * Phi^+ is the least-squares projection (G = Phi_R^T Phi_R by a Cholesky
+ * factor, Phi_R^T [H_0 | L] by one tall reduction).  G depends on the model
+ * only: `gram` (device, r x r FP64, may be NULL) receives it, and a later
+ * call with gram_given = 1 reuses it instead of the pass over Phi_R.  Lambda being diagonal,
+ * the high-order part is Lambda^t R_0 in closed form, so all T frames are one
+ * tall product out = Phi_R C (out: n x T FP32, ld ldOut, column t-1 = H_t).
+ * info (DMD_INFO_WORDS int32, device): DMD_ENUMERIC if G is not positive
+ * definite; modes that are numerically dependent are dropped (info[5]).
+ * Errors: EINVAL for bad sizes (n < 1, r < 1, r > 200, T < 1, ld* < n or not
+ * a multiple of 4, dt <= 0, threshold < 0), NULL pointers or gram_given
+ * without gram; ENOMEM if
+ * ws_bytes is below the query. */
+DMD_EXPORT dmd_status dmd_upsample(const dmd_upsample_desc* desc, const float* Phi_R, const double* modal,
+                        const float* in, float* out, double* gram, int32_t* info, void* workspace,
+                        size_t ws_bytes, void* stream);
+
 /* ---- prediction (Eq. large_time_step, Eq. reverse_simulation, Eq. external_forces) */
 
 DMD_EXPORT dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);

@@ -67,6 +67,10 @@ dmd_status tridiag_eig(int n, const double* A, int lda, double* ev, double* Y, d
 dmd_status lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb, double* X, int ldx,
                  int32_t* info, cudaStream_t st);
 dmd_status launch_coefficients(int r, int K, const double* modal, const int32_t* ks, double* C, cudaStream_t st);
+dmd_status launch_upsample_coeffs(int r, int T, const double* modal, double thr, double dt, const double* P,
+                                  double* C, cudaStream_t st);
+dmd_status chol_solve_gated(int n, const double* R, int ldr, const double* Bm, int ldb, int ncols, double alpha,
+                            double beta, double* X, int ldx, const int32_t* skip, cudaStream_t st);
 dmd_status launch_rollout(int r, int q, int steps, const double* modal, const float* u, double* Xi,
                           cudaStream_t st);
 dmd_status launch_gather_cols(int r, int K, const double* Xi, const int32_t* ks, int steps, double* C,
@@ -516,10 +520,89 @@ dmd_status with_arena(void* ws, size_t ws_bytes, F&& carve_and_run, size_t need)
   return carve_and_run(a);
 }
 
+// ------------------------------------------------------------ upsampling
+
+struct UpBufs {
+  double *G, *Pin, *P, *C;
+  void* gemm_ws;
+};
+
+void carve_upsample(Arena& a, const dmd_upsample_desc& d, UpBufs& b) {
+  const Tall tall{d.precision};
+  const int r = d.r, T = d.T;
+  b.G = a.take<double>((size_t)r * r);
+  b.Pin = a.take<double>((size_t)r * (T + 1));
+  b.P = a.take<double>((size_t)r * (T + 1));
+  b.C = a.take<double>((size_t)r * T);
+  size_t g = tall.tn_accurate_bytes(d.n, r, r);
+  g = std::max(g, tall.tn_bytes(d.n, r, T + 1));
+  g = std::max(g, tall.nn_bytes(d.n, r, T));
+  b.gemm_ws = a.take<char>(g, 1024);
+}
+
+dmd_status validate_upsample(const dmd_upsample_desc* d) {
+  DMD_REQUIRE(d != nullptr, "dmd_upsample: desc is NULL");
+  DMD_REQUIRE(d->n >= 1 && d->r >= 1 && d->r <= 200 && d->T >= 1 && d->r <= d->n,
+              "dmd_upsample: need n >= 1, 1 <= r <= min(200, n), T >= 1 (got n=%lld r=%d T=%d)", (long long)d->n,
+              d->r, d->T);
+  DMD_REQUIRE(d->ldPhi >= d->n && d->ldIn >= d->n && d->ldOut >= d->n && d->ldPhi % 4 == 0 && d->ldIn % 4 == 0 &&
+                  d->ldOut % 4 == 0,
+              "dmd_upsample: leading dimensions must be >= n and multiples of 4");
+  DMD_REQUIRE(valid_precision(d->precision), "dmd_upsample: bad precision %d", d->precision);
+  DMD_REQUIRE(d->dt > 0.0 && d->threshold >= 0.0, "dmd_upsample: need dt > 0 and threshold >= 0");
+  DMD_REQUIRE(d->gram_given == 0 || d->gram_given == 1, "dmd_upsample: gram_given must be 0 or 1");
+  return DMD_OK;
+}
+
 }  // namespace
 }  // namespace dmd
 
 using namespace dmd;
+
+extern "C" dmd_status dmd_upsample_workspace_bytes(const dmd_upsample_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_upsample(desc));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  Arena a;
+  UpBufs b;
+  carve_upsample(a, *desc, b);
+  *bytes = a.used + 256;
+  return DMD_OK;
+}
+
+// Sec. 6.3.1: G = Phi_R^T Phi_R (FP32 products, FP64 sums, both forms: its
+// Cholesky factor turns Phi_R^T [H_0 | L] into the least-squares coordinates),
+// P = G^{-1} Phi_R^T [H_0 | L], C from P (closed-form evolution of the
+// high-order modes), out = Phi_R C.
+extern "C" dmd_status dmd_upsample(const dmd_upsample_desc* desc, const float* Phi_R, const double* modal,
+                                   const float* in, float* out, double* gram, int32_t* info, void* workspace,
+                                   size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  DMD_TRY(dmd_upsample_workspace_bytes(desc, &need));
+  DMD_REQUIRE(Phi_R && modal && in && out && info, "dmd_upsample: NULL pointer argument");
+  DMD_REQUIRE(desc->gram_given == 0 || gram != nullptr, "dmd_upsample: gram_given needs gram");
+  const dmd_upsample_desc& d = *desc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    UpBufs b;
+    carve_upsample(a, d, b);
+    const Tall tall{d.precision};
+    const int r = d.r, T = d.T;
+    DMD_CUDA_TRY(cudaMemsetAsync(info, 0, DMD_INFO_WORDS * sizeof(int32_t), st));
+    if (d.gram_given) {
+      DMD_CUDA_TRY(cudaMemcpyAsync(b.G, gram, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      DMD_TRY(tall.tn_accurate(d.n, r, r, Phi_R, d.ldPhi, Phi_R, d.ldPhi, b.G, b.gemm_ws, st));
+      if (gram) {
+        DMD_CUDA_TRY(cudaMemcpyAsync(gram, b.G, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    DMD_TRY(tall.tn(d.n, r, T + 1, Phi_R, d.ldPhi, in, d.ldIn, b.Pin, b.gemm_ws, st));
+    DMD_TRY(cholesky_upper(r, b.G, r, 1e-13, info, 95, st));
+    DMD_TRY(chol_solve_gated(r, b.G, r, b.Pin, r, T + 1, 1.0, 0.0, b.P, r, nullptr, st));
+    DMD_TRY(launch_upsample_coeffs(r, T, modal, d.threshold, d.dt, b.P, b.C, st));
+    return tall.nn(d.n, r, T, Phi_R, d.ldPhi, b.C, out, d.ldOut, b.gemm_ws, st);
+  }, need);
+}
 
 extern "C" {
 

@@ -97,6 +97,41 @@ __global__ void k_edit_modes(int r, int q, const double* __restrict__ in, double
   }
 }
 
+// Upsampling evolution (Sec. 6.3.1) in closed form.  Lambda is diagonal in
+// modal coordinates, so the high-order part of R_t = S^L P_t + S^H Lambda
+// R_{t-1} is Lambda^t R_0 restricted to the high-order modes, and the
+// low-order part is the projection of the input: column t-1 of C (t = 1..T)
+// is [P_t on low-order modes; Lambda^t P_0 on the others] in the real form
+// (a pair rotates as the prediction coefficients do).  A mode is low-order
+// when |Im log(lambda)| / dt < thr.  P is r x (T+1) (column 0 = Phi^+ H_0).
+__global__ void k_upsample_coeffs(int r, int T, const double* __restrict__ modal, double thr, double dt,
+                                  const double* __restrict__ P, double* __restrict__ C) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)r * T) return;
+  const int c = (int)(e % r);
+  const int j = (int)(e / r);
+  const double lr = modal[c], li = modal[r + c];
+  if (li < 0.0) return;   // second column of a pair: written by the head
+  const bool pair = li > 0.0 && c + 1 < r;
+  const bool low = fabs(atan2(li, lr)) / dt < thr;
+  double* out = C + (int64_t)j * r;
+  const double* in = P + (int64_t)(j + 1) * r;
+  if (low) {
+    out[c] = in[c];
+    if (pair) out[c + 1] = in[c + 1];
+    return;
+  }
+  double pr, pi;
+  cpow_int(lr, li, j + 1, pr, pi);
+  if (pair) {
+    const double zr = P[c], zi = -P[c + 1];
+    out[c] = pr * zr - pi * zi;
+    out[c + 1] = -(pr * zi + pi * zr);
+  } else {
+    out[c] = pr * P[c];
+  }
+}
+
 __global__ void k_rollout(int r, int q, int steps, const double* __restrict__ modal,
                           const float* __restrict__ u, double* __restrict__ Xi) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,6 +369,15 @@ dmd_status launch_edit_modes(int r, int q, const double* in, double* out, double
                              const double* high, double dt, cudaStream_t st) {
   k_edit_modes<<<(unsigned)ceil_div(r, 128), 128, 0, st>>>(r, q, in, out, thr, low[0], low[1], low[2], high[0],
                                                             high[1], high[2], dt);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status launch_upsample_coeffs(int r, int T, const double* modal, double thr, double dt, const double* P,
+                                  double* C, cudaStream_t st) {
+  const int64_t total = (int64_t)r * T;
+  if (total == 0) return DMD_OK;
+  k_upsample_coeffs<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(r, T, modal, thr, dt, P, C);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

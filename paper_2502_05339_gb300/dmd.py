@@ -46,6 +46,12 @@ class OptDmdOpts(ctypes.Structure):
                 ("mu0", ctypes.c_double)]
 
 
+class UpsampleDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ldPhi", ctypes.c_int64), ("ldIn", ctypes.c_int64), ("ldOut", ctypes.c_int64),
+                ("r", ctypes.c_int32), ("T", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("gram_given", ctypes.c_int32), ("threshold", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
 class PredictDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ldPhi", ctypes.c_int64), ("ldOut", ctypes.c_int64),
                 ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("q", ctypes.c_int32),
@@ -66,6 +72,9 @@ SIGNATURES = {
     "dmd_launch_count": (ctypes.c_uint64, []),
     "dmd_fit_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _SZ]),
     "dmd_fit": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_upsample_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(UpsampleDesc), ctypes.POINTER(ctypes.c_size_t)]),
+    "dmd_upsample": (ctypes.c_int32, [ctypes.POINTER(UpsampleDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t,
+                                      _P]),
     "dmd_fit_optdmd_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), ctypes.POINTER(ctypes.c_size_t)]),
     "dmd_fit_optdmd": (ctypes.c_int32, [ctypes.POINTER(FitDesc), ctypes.POINTER(OptDmdOpts), _P, _P, _P, _P, _P,
                                         _P, _P, ctypes.c_size_t, _P]),
@@ -247,6 +256,37 @@ def dmd_fit_optdmd(S: torch.Tensor, n: int, r: int, *, oversample: int = 10, pow
     _check(lib().dmd_fit_optdmd(ctypes.byref(d), ctypes.byref(o), _ptr(S), _ptr(Omega), _ptr(Phi), _ptr(modal),
                                 _ptr(info), _ptr(stats), _ptr(ws), ws.numel(), _stream(dev)), "dmd_fit_optdmd")
     return DmdModel(Phi, modal, info, n, r, 0)
+
+
+def dmd_upsample(model: DmdModel, inputs: torch.Tensor, threshold: float, *, dt: float = 1.0, precision="fp32",
+                 out: torch.Tensor | None = None, info: torch.Tensor | None = None,
+                 gram: torch.Tensor | None = None, gram_given: bool = False) -> torch.Tensor:
+    """Upsampling evolution (Sec. 6.3.1): `inputs` (T+1, ldIn) float32 holds H_0
+    and L_1..L_T on the model's grid; returns H_1..H_T as (T, ldOut) float32.
+    Modes with |Im log(lambda)| / dt < threshold follow the inputs, the others
+    evolve from H_0.  `gram` (r x r float64 on the device) receives the model's
+    Gram Phi_R^T Phi_R, or supplies it when gram_given."""
+    _need_cuda(inputs, "inputs", torch.float32)
+    if model.q != 0:
+        raise ValueError("dmd_upsample: the model must have no control inputs")
+    dev = model.Phi_R.device
+    T = inputs.shape[0] - 1
+    ldOut = round_up(model.n, 32)
+    if out is None:
+        out = torch.empty((T, ldOut), dtype=torch.float32, device=dev)
+    _need_cuda(out, "out", torch.float32)
+    if info is None:
+        info = torch.zeros(INFO_WORDS, dtype=torch.int32, device=dev)
+    if gram is not None:
+        _need_cuda(gram, "gram", torch.float64)
+    d = UpsampleDesc(n=model.n, ldPhi=model.ldPhi, ldIn=inputs.shape[1], ldOut=out.shape[1], r=model.r, T=T,
+                     precision=_prec(precision), gram_given=1 if gram_given else 0, threshold=threshold, dt=dt)
+    nb = ctypes.c_size_t(0)
+    _check(lib().dmd_upsample_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)), "dmd_upsample_workspace_bytes")
+    ws = _workspace(nb.value, dev)
+    _check(lib().dmd_upsample(ctypes.byref(d), _ptr(model.Phi_R), _ptr(model.modal), _ptr(inputs), _ptr(out),
+                              _ptr(gram), _ptr(info), _ptr(ws), ws.numel(), _stream(dev)), "dmd_upsample")
+    return out
 
 
 def _ks_tensor(ks, dev) -> torch.Tensor:

@@ -174,6 +174,24 @@ def time_factors(sigma, omega, a, ks) -> np.ndarray:
     return T
 
 
+def prolong(S: torch.Tensor, N: int, dim: int, factor: int) -> torch.Tensor:
+    """Piecewise-constant prolongation of every snapshot (rows of S, (count, ld)
+    float32, dim stacked components of an N^dim grid) to the (factor N)^dim
+    grid: the stand-in for a low-resolution simulation's fields given on the
+    high-resolution grid (the upsampling inputs L_t).  Returns (count, ld')
+    float32 with ld' = round_up(dim (factor N)^dim, 32), zero padded."""
+    count = S.shape[0]
+    n = dim * N ** dim
+    Nf = factor * N
+    nf = dim * Nf ** dim
+    out = torch.zeros((count, round_up(nf, 32)), dtype=torch.float32, device=S.device)
+    comp = S[:, :n].reshape((count, dim) + (N,) * dim)
+    for ax in range(dim):
+        comp = comp.repeat_interleave(factor, dim=2 + ax)
+    out[:, :nf] = comp.reshape(count, nf)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # scene containers
 # ----------------------------------------------------------------------------

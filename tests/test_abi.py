@@ -70,3 +70,26 @@ def test_optdmd_rejects_control_and_large_rank():
     big = dmd.FitDesc(n=4096, ldS=4096, ldPhi=4096, m=400, r=210, oversample=10, power_iters=2, q=0, precision=1,
                       seed=0)
     assert L.dmd_fit_optdmd_workspace_bytes(ctypes.byref(big), ctypes.byref(nb)) == 1
+
+
+def test_upsample_argument_checks():
+    """Host-side checks of dmd_upsample's request (no GPU needed)."""
+    import ctypes
+    from paper_2502_05339_gb300 import dmd
+    L = dmd.lib()
+    nb = ctypes.c_size_t(0)
+
+    def desc(**kw):
+        base = dict(n=4096, ldPhi=4096, ldIn=4096, ldOut=4096, r=20, T=10, precision=1, gram_given=0,
+                    threshold=0.3, dt=1.0)
+        base.update(kw)
+        return dmd.UpsampleDesc(**base)
+
+    assert L.dmd_upsample_workspace_bytes(ctypes.byref(desc()), ctypes.byref(nb)) == 0 and nb.value > 0
+    for bad in (dict(T=0), dict(r=201), dict(ldIn=4094), dict(dt=0.0), dict(threshold=-1.0), dict(gram_given=2),
+                dict(ldOut=100)):
+        assert L.dmd_upsample_workspace_bytes(ctypes.byref(desc(**bad)), ctypes.byref(nb)) == 1, bad
+    d = desc(gram_given=1)
+    ws = ctypes.c_void_p(256)
+    # gram_given without a gram buffer is refused before anything is launched
+    assert L.dmd_upsample(ctypes.byref(d), ws, ws, ws, ws, None, ws, ws, 1 << 30, None) == 1
