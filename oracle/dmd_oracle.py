@@ -311,6 +311,44 @@ def from_real_form(PhiR: np.ndarray, lam: np.ndarray):
     return Phi
 
 
+def advect_density(rho0: np.ndarray, frames: np.ndarray, N: int, dim: int, dt: float) -> np.ndarray:
+    """Density carried by the DMD velocity frames (Sec. 7.2: the velocity from
+    the DMD model, the density by classical integration in it).  Semi-
+    Lagrangian steps on the periodic MAC grid of the snapshots:
+      rho_{k+1}(c) = rho_k(c - dt u_k(c)),
+    where u_k(c) is the velocity at the centre of cell c (per axis the mean
+    of the two faces around the cell; component d of a frame sits on the low
+    d-face of each cell) and rho_k is sampled by multilinear interpolation
+    with periodic wrap.  Grid units (cell size 1).  frames: n x K velocity
+    frames (n = dim N^dim); returns the densities rho_0..rho_K (N^dim x (K+1))."""
+    shape = (N,) * dim
+    c = N ** dim
+    rho = np.asarray(rho0, dtype=np.float64).reshape(shape)
+    idx = np.meshgrid(*([np.arange(N)] * dim), indexing="ij")
+    out = [rho.ravel().copy()]
+    for k in range(frames.shape[1]):
+        u = np.asarray(frames[:, k], dtype=np.float64)
+        pos = []
+        for d in range(dim):
+            face = u[d * c:(d + 1) * c].reshape(shape)
+            centre = 0.5 * (face + np.roll(face, -1, axis=d))
+            pos.append(idx[d] - dt * centre)
+        base = [np.floor(p).astype(np.int64) for p in pos]
+        frac = [p - b for p, b in zip(pos, base)]
+        new = np.zeros(shape)
+        for corner in range(1 << dim):
+            w = np.ones(shape)
+            ix = []
+            for d in range(dim):
+                bit = (corner >> d) & 1
+                w = w * (frac[d] if bit else 1.0 - frac[d])
+                ix.append((base[d] + bit) % N)
+            new += w * rho[tuple(ix)]
+        rho = new
+        out.append(rho.ravel().copy())
+    return np.stack(out, axis=1)
+
+
 def predict_real(PhiR: np.ndarray, C: np.ndarray) -> np.ndarray:
     """Reconstruction as one real product F = Phi_R C."""
     return PhiR @ C

@@ -43,6 +43,10 @@ def _pins():
     yield P.test_upsample_all_low_is_orthogonal_projection
     yield P.test_upsample_all_high_is_prediction
     yield P.test_upsample_is_linear_and_splits_by_frequency
+    yield lambda: P.test_advect_integer_shift_is_roll(2)
+    yield lambda: P.test_advect_integer_shift_is_roll(3)
+    yield P.test_advect_fractional_shift_is_linear_interpolation
+    yield P.test_advect_constant_and_still
 
 
 def _count_failures():
@@ -208,6 +212,39 @@ def _upsample_variant(swap=False, transpose=False, stale=False):
     return up
 
 
+def _advect_variant(forward=False, face_only=False, swap_w=False, axis_mix=False):
+    def adv(rho0, frames, N, dim, dt):
+        shape = (N,) * dim
+        c = N ** dim
+        rho = np.asarray(rho0, dtype=np.float64).reshape(shape)
+        idx = np.meshgrid(*([np.arange(N)] * dim), indexing="ij")
+        out = [rho.ravel().copy()]
+        for k in range(frames.shape[1]):
+            u = np.asarray(frames[:, k], dtype=np.float64)
+            pos = []
+            for d in range(dim):
+                dd = dim - 1 - d if axis_mix else d                   # components read for the wrong axes
+                face = u[dd * c:(dd + 1) * c].reshape(shape)
+                centre = face if face_only else 0.5 * (face + np.roll(face, -1, axis=d))   # no face average
+                pos.append(idx[d] + dt * centre if forward else idx[d] - dt * centre)       # traced forward
+            base = [np.floor(p).astype(np.int64) for p in pos]
+            frac = [p - b for p, b in zip(pos, base)]
+            new = np.zeros(shape)
+            for corner in range(1 << dim):
+                w = np.ones(shape)
+                ix = []
+                for d in range(dim):
+                    bit = (corner >> d) & 1
+                    hi = (1.0 - frac[d]) if swap_w else frac[d]        # interpolation weights swapped
+                    w = w * (hi if bit else 1.0 - hi)
+                    ix.append((base[d] + bit) % N)
+                new += w * rho[tuple(ix)]
+            rho = new
+            out.append(rho.ravel().copy())
+        return np.stack(out, axis=1)
+    return adv
+
+
 MUTATIONS = [
     ("split_snapshots", _mut_split, O),
     ("reduced_operator", _mut_reduced_scale, O),
@@ -230,6 +267,10 @@ MUTATIONS = [
     ("upsample", _upsample_variant(swap=True), O),
     ("upsample", _upsample_variant(transpose=True), O),
     ("upsample", _upsample_variant(stale=True), O),
+    ("advect_density", _advect_variant(forward=True), O),
+    ("advect_density", _advect_variant(face_only=True), O),
+    ("advect_density", _advect_variant(swap_w=True), O),
+    ("advect_density", _advect_variant(axis_mix=True), O),
 ]
 
 

@@ -697,3 +697,62 @@ def test_upsample_is_linear_and_splits_by_frequency():
         c = pinv @ O.upsample(Phi, lam, a0, A, thr)[:, t]
         np.testing.assert_allclose(c[low], (pinv @ A[:, t])[low], atol=1e-9)
         np.testing.assert_allclose(c[~low], (lam ** (t + 1) * z0)[~low], atol=1e-9)
+
+
+# ------------------------------------------------------ density advection (Sec. 7.2)
+
+def _uniform_frames(N, dim, vel, K):
+    c = N ** dim
+    f = np.zeros((dim * c, K))
+    for d in range(dim):
+        f[d * c:(d + 1) * c, :] = vel[d]
+    return f
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_advect_integer_shift_is_roll(dim):
+    """A uniform velocity moving one cell per step along every axis shifts the
+    density by one cell per step, exactly."""
+    N = 8
+    g = np.random.default_rng(1)
+    rho0 = g.standard_normal((N,) * dim)
+    out = O.advect_density(rho0.ravel(), _uniform_frames(N, dim, [1.0] * dim, 3), N, dim, dt=1.0)
+    ref = rho0
+    for k in range(1, 4):
+        ref = np.roll(ref, tuple([1] * dim), axis=tuple(range(dim)))
+        np.testing.assert_allclose(out[:, k].reshape((N,) * dim), ref, atol=1e-13)
+
+
+def test_advect_fractional_shift_is_linear_interpolation():
+    """A uniform fractional displacement s = s0 + f (cells) gives
+    (1 - f) roll(rho, s0) + f roll(rho, s0 + 1) per axis (2D: the tensor product)."""
+    N = 10
+    g = np.random.default_rng(2)
+    rho0 = g.standard_normal((N, N))
+    dt, vel = 0.7, (2.5, -1.2)
+    out = O.advect_density(rho0.ravel(), _uniform_frames(N, 2, vel, 1), N, 2, dt=dt)[:, 1].reshape(N, N)
+    ref = rho0
+    for ax, v in enumerate(vel):
+        s = dt * v
+        s0 = int(np.floor(s))
+        f = s - s0
+        ref = (1 - f) * np.roll(ref, s0, axis=ax) + f * np.roll(ref, s0 + 1, axis=ax)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+    assert abs(out.sum() - rho0.sum()) < 1e-10            # a uniform shift conserves mass
+
+
+def test_advect_constant_and_still():
+    """A constant density stays constant in any velocity field; zero velocity
+    leaves any density unchanged; the centre velocity is the mean of the two
+    faces (a field that is +1 and -1 on alternate faces does not move it)."""
+    N, dim = 6, 3
+    g = np.random.default_rng(3)
+    frames = g.standard_normal((dim * N ** dim, 2))
+    out = O.advect_density(np.full(N ** dim, 2.5), frames, N, dim, dt=0.8)
+    np.testing.assert_allclose(out, 2.5, atol=1e-12)
+    rho0 = g.standard_normal(N ** dim)
+    np.testing.assert_allclose(O.advect_density(rho0, np.zeros((dim * N ** dim, 2)), N, dim, 0.5)[:, 2], rho0)
+    alt = np.zeros((dim * N ** dim, 1))
+    ax0 = np.indices((N,) * dim)[0].ravel()
+    alt[: N ** dim, 0] = np.where(ax0 % 2 == 0, 1.0, -1.0)
+    np.testing.assert_allclose(O.advect_density(rho0, alt, N, dim, 0.9)[:, 1], rho0, atol=1e-13)
