@@ -228,6 +228,39 @@ DMD_EXPORT dmd_status dmd_upsample(const dmd_upsample_desc* desc, const float* P
                         const float* in, float* out, double* gram, int32_t* info, void* workspace,
                         size_t ws_bytes, void* stream);
 
+/* ---- density in the DMD velocity (Sec. 7.2) ----------------------------- */
+
+/* A model of velocity snapshots on a periodic N^dim MAC grid (dim 2 or 3,
+ * n = dim N^dim: component d of a frame on the low d-face of each cell, cells
+ * in C order over the axes) and a cell-centred density (N^dim FP32). */
+typedef struct dmd_advect_desc {
+  int64_t ldPhi;
+  int64_t ldRho;       /* leading dimension of the density frames (>= N^dim, multiple of 4) */
+  int32_t N;
+  int32_t dim;
+  int32_t r;
+  int32_t K;           /* steps: velocity frames u_0 .. u_{K-1}                  */
+  int32_t precision;
+  int32_t chunk;       /* velocity frames reconstructed per batch (0 = 256)       */
+  double dt;           /* step in grid cells per unit velocity                    */
+} dmd_advect_desc;
+
+DMD_EXPORT dmd_status dmd_advect_workspace_bytes(const dmd_advect_desc* desc, size_t* bytes);
+
+/* Density advected by the model's velocity (Sec. 7.2: velocity from the DMD
+ * model, density by classical integration in it): rho_{k+1}(c) =
+ * rho_k(c - dt u_k(c)), u_k = x_k of the model (Eq. large_time_step) at the
+ * centre of cell c (mean of the two faces per axis), rho_k by multilinear
+ * interpolation with periodic wrap.  rho (N^dim x (K+1) FP32, ld ldRho)
+ * receives rho_0 = rho0 and rho_1 .. rho_K.  Velocity frames are rebuilt in
+ * batches of `chunk` by the reconstruction product.  Errors: EINVAL for bad
+ * sizes (dim not 2 or 3, N < 2, N above 32768 (2D) or 1024 (3D), r < 1, K < 1, ldPhi < dim N^dim, ldRho <
+ * N^dim, leading dimensions not multiples of 4, non-finite dt) or NULL
+ * pointers; ENOMEM if ws_bytes is below the query. */
+DMD_EXPORT dmd_status dmd_advect_density(const dmd_advect_desc* desc, const float* Phi_R, const double* modal,
+                              const float* rho0, float* rho, void* workspace, size_t ws_bytes,
+                              void* stream);
+
 /* ---- prediction (Eq. large_time_step, Eq. reverse_simulation, Eq. external_forces) */
 
 DMD_EXPORT dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);

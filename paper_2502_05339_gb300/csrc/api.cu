@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 
 #include "common.cuh"
@@ -69,6 +70,8 @@ dmd_status lstsq(int mr, int nc, double* A, int ld, int nrhs, double* B, int ldb
 dmd_status launch_coefficients(int r, int K, const double* modal, const int32_t* ks, double* C, cudaStream_t st);
 dmd_status launch_upsample_coeffs(int r, int T, const double* modal, double thr, double dt, const double* P,
                                   double* C, cudaStream_t st);
+dmd_status launch_advect(int dim, int N, const float* rho, float* out, const float* u, float dt, cudaStream_t st);
+dmd_status launch_iota(int32_t* out, int count, int start, cudaStream_t st);
 dmd_status chol_solve_gated(int n, const double* R, int ldr, const double* Bm, int ldb, int ncols, double alpha,
                             double beta, double* X, int ldx, const int32_t* skip, cudaStream_t st);
 dmd_status launch_rollout(int r, int q, int steps, const double* modal, const float* u, double* Xi,
@@ -554,10 +557,91 @@ dmd_status validate_upsample(const dmd_upsample_desc* d) {
   return DMD_OK;
 }
 
+// ------------------------------------------------------ density advection
+
+struct AdvBufs {
+  int32_t* ks;
+  double* C;
+  float* U;
+  int64_t ldU;
+  int ch;
+  void* gemm_ws;
+};
+
+int64_t cells_of(const dmd_advect_desc& d) {
+  int64_t c = 1;
+  for (int i = 0; i < d.dim; ++i) c *= d.N;
+  return c;
+}
+
+void carve_advect(Arena& a, const dmd_advect_desc& d, AdvBufs& b) {
+  const Tall tall{d.precision};
+  const int64_t n = d.dim * cells_of(d);
+  b.ch = std::min(d.chunk > 0 ? d.chunk : 256, d.K);
+  b.ldU = round_up(n, 32);
+  b.ks = a.take<int32_t>(b.ch);
+  b.C = a.take<double>((size_t)d.r * b.ch);
+  b.U = a.take<float>((size_t)b.ldU * b.ch, 1024);
+  b.gemm_ws = a.take<char>(tall.nn_bytes(n, d.r, b.ch), 1024);
+}
+
+dmd_status validate_advect(const dmd_advect_desc* d) {
+  DMD_REQUIRE(d != nullptr, "dmd_advect_density: desc is NULL");
+  DMD_REQUIRE((d->dim == 2 || d->dim == 3) && d->N >= 2 && d->N <= (d->dim == 2 ? 32768 : 1024) && d->r >= 1 &&
+                  d->K >= 1,
+              "dmd_advect_density: need dim 2 or 3, 2 <= N <= 32768 (2D) or 1024 (3D), r >= 1, K >= 1 "
+              "(got dim=%d N=%d r=%d K=%d)", d->dim, d->N, d->r, d->K);
+  const int64_t cells = cells_of(*d);
+  DMD_REQUIRE(d->ldPhi >= d->dim * cells && d->ldRho >= cells && d->ldPhi % 4 == 0 && d->ldRho % 4 == 0,
+              "dmd_advect_density: leading dimensions must cover the grid and be multiples of 4");
+  DMD_REQUIRE(valid_precision(d->precision) && d->chunk >= 0, "dmd_advect_density: bad precision or chunk");
+  DMD_REQUIRE(std::isfinite(d->dt), "dmd_advect_density: dt must be finite");
+  return DMD_OK;
+}
+
 }  // namespace
 }  // namespace dmd
 
 using namespace dmd;
+
+extern "C" dmd_status dmd_advect_workspace_bytes(const dmd_advect_desc* desc, size_t* bytes) {
+  DMD_TRY(validate_advect(desc));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  Arena a;
+  AdvBufs b;
+  carve_advect(a, *desc, b);
+  *bytes = a.used + 256;
+  return DMD_OK;
+}
+
+extern "C" dmd_status dmd_advect_density(const dmd_advect_desc* desc, const float* Phi_R, const double* modal,
+                                         const float* rho0, float* rho, void* workspace, size_t ws_bytes,
+                                         void* stream) {
+  size_t need = 0;
+  DMD_TRY(dmd_advect_workspace_bytes(desc, &need));
+  DMD_REQUIRE(Phi_R && modal && rho0 && rho, "dmd_advect_density: NULL pointer argument");
+  const dmd_advect_desc& d = *desc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
+    AdvBufs b;
+    carve_advect(a, d, b);
+    const Tall tall{d.precision};
+    const int64_t cells = cells_of(d), n = d.dim * cells;
+    DMD_CUDA_TRY(cudaMemcpyAsync(rho, rho0, (size_t)cells * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    for (int k0 = 0; k0 < d.K; k0 += b.ch) {
+      const int c = std::min(b.ch, d.K - k0);
+      DMD_TRY(launch_iota(b.ks, c, k0, st));
+      DMD_TRY(launch_coefficients(d.r, c, modal, b.ks, b.C, st));
+      DMD_TRY(tall.nn(n, d.r, c, Phi_R, d.ldPhi, b.C, b.U, b.ldU, b.gemm_ws, st));
+      for (int j = 0; j < c; ++j) {
+        const int k = k0 + j;
+        DMD_TRY(launch_advect(d.dim, d.N, rho + (int64_t)k * d.ldRho, rho + (int64_t)(k + 1) * d.ldRho,
+                              b.U + (int64_t)j * b.ldU, (float)d.dt, st));
+      }
+    }
+    return DMD_OK;
+  }, need);
+}
 
 extern "C" dmd_status dmd_upsample_workspace_bytes(const dmd_upsample_desc* desc, size_t* bytes) {
   DMD_TRY(validate_upsample(desc));

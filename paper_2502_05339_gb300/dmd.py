@@ -52,6 +52,12 @@ class UpsampleDesc(ctypes.Structure):
                 ("gram_given", ctypes.c_int32), ("threshold", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
+class AdvectDesc(ctypes.Structure):
+    _fields_ = [("ldPhi", ctypes.c_int64), ("ldRho", ctypes.c_int64), ("N", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("dt", ctypes.c_double)]
+
+
 class PredictDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ldPhi", ctypes.c_int64), ("ldOut", ctypes.c_int64),
                 ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("q", ctypes.c_int32),
@@ -72,6 +78,8 @@ SIGNATURES = {
     "dmd_launch_count": (ctypes.c_uint64, []),
     "dmd_fit_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _SZ]),
     "dmd_fit": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_advect_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(AdvectDesc), ctypes.POINTER(ctypes.c_size_t)]),
+    "dmd_advect_density": (ctypes.c_int32, [ctypes.POINTER(AdvectDesc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "dmd_upsample_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(UpsampleDesc), ctypes.POINTER(ctypes.c_size_t)]),
     "dmd_upsample": (ctypes.c_int32, [ctypes.POINTER(UpsampleDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t,
                                       _P]),
@@ -286,6 +294,30 @@ def dmd_upsample(model: DmdModel, inputs: torch.Tensor, threshold: float, *, dt:
     ws = _workspace(nb.value, dev)
     _check(lib().dmd_upsample(ctypes.byref(d), _ptr(model.Phi_R), _ptr(model.modal), _ptr(inputs), _ptr(out),
                               _ptr(gram), _ptr(info), _ptr(ws), ws.numel(), _stream(dev)), "dmd_upsample")
+    return out
+
+
+def dmd_advect_density(model: DmdModel, rho0: torch.Tensor, N: int, dim: int, K: int, dt: float, *,
+                       precision="fp32", chunk: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Density advected by the model's velocity frames u_0..u_{K-1} (Sec. 7.2):
+    rho0 is the cell-centred density (N^dim float32 on the device); returns
+    rho_0..rho_K as a (K+1, ldRho) float32 tensor."""
+    _need_cuda(rho0, "rho0", torch.float32)
+    if model.q != 0:
+        raise ValueError("dmd_advect_density: the model must have no control inputs")
+    dev = model.Phi_R.device
+    cells = N ** dim
+    ldRho = round_up(cells, 32)
+    if out is None:
+        out = torch.empty((K + 1, ldRho), dtype=torch.float32, device=dev)
+    _need_cuda(out, "out", torch.float32)
+    d = AdvectDesc(ldPhi=model.ldPhi, ldRho=out.shape[1], N=N, dim=dim, r=model.r, K=K, precision=_prec(precision),
+                   chunk=chunk, dt=dt)
+    nb = ctypes.c_size_t(0)
+    _check(lib().dmd_advect_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)), "dmd_advect_workspace_bytes")
+    ws = _workspace(nb.value, dev)
+    _check(lib().dmd_advect_density(ctypes.byref(d), _ptr(model.Phi_R), _ptr(model.modal), _ptr(rho0), _ptr(out),
+                                    _ptr(ws), ws.numel(), _stream(dev)), "dmd_advect_density")
     return out
 
 

@@ -12,6 +12,9 @@ the same entry point twice, so a profiler can skip the first (warm-up) launch:
   gramq   tensor-core Gram Q^T Q (160 columns, BF16x3)
   sketch  tensor-core tall product X M (200 -> 160 columns, BF16x3)
   recon   reconstruction Phi_R C of 1000 frames (150 modes, BF16x3)
+  advect  density advection (Sec. 7.2) on a 128^3 grid: a random 150-mode
+          velocity model (RMS ~0.5 cells per unit step), 64 steps, frames rebuilt
+          in batches of 64 (rows fixed by the grid; --rows is ignored)
   optdmd  OptDMD fit (Sec. 4.2) of a 3D 70^3 x 3 linear-modes scene (1,029,000
           rows; 200 snapshots, 75 pairs with stratified frequencies, rank 150,
           BF16x3 tall passes): the small FP64 loop is independent of the rows
@@ -68,6 +71,13 @@ def run(case: str, rows: int, reps: int = 2):
         out = torch.empty((FRAMES, model.ldPhi), dtype=torch.float32, device="cuda")
         for _ in range(reps):
             dmd.dmd_predict(model, ks, precision="mixed", out=out)
+    elif case == "advect":
+        N = 128
+        model = _model(3 * N ** 3)
+        model.Phi_R.mul_(0.05)
+        rho0 = torch.rand(N ** 3, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_advect_density(model, rho0, N, 3, 64, 0.5, precision="mixed", chunk=64)
     elif case == "optdmd":
         import math
         from paper_2502_05339_gb300 import synth
@@ -82,7 +92,7 @@ def run(case: str, rows: int, reps: int = 2):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["gram", "tn", "gramq", "sketch", "recon", "optdmd"])
+    ap.add_argument("case", choices=["gram", "tn", "gramq", "sketch", "recon", "optdmd", "advect"])
     ap.add_argument("--rows", type=int, default=1 << 20)
     args = ap.parse_args()
     run(args.case, args.rows)
