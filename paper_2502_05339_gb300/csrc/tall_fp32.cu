@@ -233,6 +233,17 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
     first = false;
   };
 
+  // Shared-memory byte offsets of this thread's float4 loads (box_ld4 with
+  // the per-thread part folded in): A column ta + 16 i has (c & 7) = ta & 7,
+  // so its row-chunk k lands at ((k ^ (ta & 7)) << 4) in all four columns; B
+  // column 16 w + tb + 2 j has (c & 7) = tb + 2j mod 8, whose chunk offset is
+  // ((k ^ (2j mod 8)) << 4) XOR (tb << 4) = that + 16 tb when k is even and
+  // - 16 tb when k is odd.  With the k loop unrolled the loads then need no
+  // address arithmetic beyond an immediate offset.
+  const int ta7 = ta & 7;
+  const int colB = 16 * warp + tb;
+  const int tbs = 16 * tb;
+
   int stretch = 0;
   for (int q = 0; q < nq; ++q) {
     bool ok = true;
@@ -247,13 +258,18 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-#pragma unroll 1
+      const uint8_t* At = Ab + ta * 128;
+      const uint8_t* Bt = Bb + colB * 128;
+#pragma unroll
       for (int kq = 0; kq < TN_BR / 4; ++kq) {
         float4 av[4], bv[8];
+        const uint8_t* Ak = At + ((kq ^ ta7) << 4);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = box_ld4(Ab, ta + 16 * i, kq);
+        for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(Ak + i * 16 * 128);
+        const uint8_t* Bk = Bt + ((kq & 1) ? -tbs : tbs);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) bv[j] = box_ld4(Bb, 16 * warp + tb + 2 * j, kq);
+        for (int j = 0; j < 8; ++j)
+          bv[j] = *reinterpret_cast<const float4*>(Bk + 2 * j * 128 + ((kq ^ ((2 * j) & 7)) << 4));
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
