@@ -23,7 +23,7 @@
 //     (J^T J)_{kl} = sum s s' (E^T E)_{j j'} (B B^T)_{i i'},
 //     (J^T rho)_k  = -sum s (E^T rho B^T)_{j i},
 // r x r products only.  The projection is taken from the normal equations
-// G = Phi^T Phi = R^T R (FP64 Cholesky, then forward and back substitution)
+// G = Phi^T Phi = R^T R (FP64 Cholesky; R^{-1} by columns, then products)
 // with one refinement step.
 //
 // Control flow stays on the device: a decision kernel accepts the trial point
@@ -46,6 +46,8 @@ dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bo
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
 dmd_status chol_solve_gated(int n, const double* R, int ldr, const double* Bm, int ldb, int ncols, double alpha,
                             double beta, double* X, int ldx, const int32_t* skip, cudaStream_t st);
+dmd_status tri_inv_upper_gated(int n, const double* R, int ldr, double* T, int ldt, const int32_t* skip,
+                               cudaStream_t st);
 
 namespace {
 
@@ -338,6 +340,8 @@ void carve_optdmd(Arena& a, int T, int r, int l, OptBufs& o) {
   o.Phi = a.take<double>(Tr);
   o.RE = a.take<double>(2 * Tr);
   o.G = a.take<double>(rr);
+  o.Ri = a.take<double>(rr);
+  o.H2 = a.take<double>(2 * rr);
   o.H = a.take<double>(2 * rr);
   o.BC = a.take<double>(2 * rr);
   o.EtRE = a.take<double>(2 * rr);
@@ -383,11 +387,14 @@ dmd_status optdmd_small(int T, int r, int l, const double* Bsnap, const double* 
     // projection by the normal equations G = Phi^T Phi = R^T R, one refinement step
     DMD_TRY(dgemm_gated(r, r, T, 1.0, o.Phi, T, true, o.Phi, T, false, 0.0, o.G, r, skip, st));
     DMD_TRY(cholesky_upper_gated(r, o.G, r, 1e-14, o.sinfo, 81, skip, st));
+    DMD_TRY(tri_inv_upper_gated(r, o.G, r, o.Ri, r, skip, st));
     for (int pass = 0; pass < 2; ++pass) {
-      // [B | C] (+)= G^{-1} Phi^T [Y | D]  (pass 0), G^{-1} Phi^T [rho | E]  (pass 1)
+      // [B | C] (+)= R^{-1} R^{-T} Phi^T [Y | D]  (pass 0), ... Phi^T [rho | E]  (pass 1)
       DMD_TRY(dgemm_gated(r, 2 * r, T, 1.0, o.Phi, T, true, pass == 0 ? o.YD : o.RE, T, false, 0.0, o.H, r, skip,
                           st));
-      DMD_TRY(chol_solve_gated(r, o.G, r, o.H, r, 2 * r, 1.0, pass == 0 ? 0.0 : 1.0, o.BC, r, skip, st));
+      DMD_TRY(dgemm_gated(r, 2 * r, r, 1.0, o.Ri, r, true, o.H, r, false, 0.0, o.H2, r, skip, st));
+      DMD_TRY(dgemm_gated(r, 2 * r, r, 1.0, o.Ri, r, false, o.H2, r, false, pass == 0 ? 0.0 : 1.0, o.BC, r, skip,
+                          st));
       DMD_CUDA_TRY(cudaMemcpyAsync(o.RE, o.YD, 2 * Tr * sizeof(double), cudaMemcpyDeviceToDevice, st));
       DMD_TRY(dgemm_gated(T, 2 * r, r, -1.0, o.Phi, T, false, o.BC, r, false, 1.0, o.RE, T, skip, st));
     }

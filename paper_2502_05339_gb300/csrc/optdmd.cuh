@@ -7,7 +7,7 @@
 namespace dmd {
 
 struct OptBufs {
-  double *YD, *Phi, *RE, *G, *H, *BC, *EtRE, *Gb, *Hh, *JtJt, *gt, *JtJ, *g, *Bk, *A, *p, *pt, *sd, *Z, *Wt,
+  double *YD, *Phi, *RE, *G, *Ri, *H, *H2, *BC, *EtRE, *Gb, *Hh, *JtJt, *gt, *JtJ, *g, *Bk, *A, *p, *pt, *sd, *Z, *Wt,
       *Mlift;
   int* kinds;
   int32_t *si, *sinfo;
