@@ -154,12 +154,19 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The slowest rank's time (all ranks get it)."""
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, elapsed_max: float, world: int) -> float:
+    """Units all replicas processed over the slowest replica's time (weak scaling)."""
+    return units_per_rank * world / elapsed_max
 
 
 def run_ours(args):
@@ -224,8 +231,7 @@ def run_ours(args):
     elapsed = t0.elapsed_time(t1) / 1e3
     launches = (L.dmd_launch_count() - launches0) // max(args.steps, 1)
     elapsed_max = max_over_ranks(elapsed, world)
-    frames_total = K * args.steps * world
-    value = frames_total / elapsed_max
+    value = whole_job_rate(K * args.steps, elapsed_max, world)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = run_e2e(args, sc, c, dmd, dev, st, out, ks)
