@@ -192,14 +192,23 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
   __syncthreads();
 
   // Thread 0 keeps up to TN_STAGES boxes in flight; a stage is refilled once
-  // every warp has released it, so the warps never wait for one another.
+  // every warp has released it.  Before warp 0 waits for box q, box q must
+  // have been issued, which needs only box q - TN_STAGES released (long done
+  // in the steady state): that wait blocks.  Later boxes are issued when
+  // their stages are already free, without waiting, so warp 0 is not held to
+  // the pace of the slowest warp on the box it has just finished.
   int issued = 0;
-  auto produce = [&](int upto) -> bool {
+  auto produce = [&](int upto, bool block) -> bool {
     for (; issued < min(nq, upto); ++issued) {
       const int s = issued % TN_STAGES;
-      if (issued >= TN_STAGES &&
-          !mbar_wait(&empty[s], (uint32_t)(issued / TN_STAGES - 1) & 1u, abort_flag))
-        return false;
+      if (issued >= TN_STAGES) {
+        const uint32_t par = (uint32_t)(issued / TN_STAGES - 1) & 1u;
+        if (!block) {
+          if (!mbar_test(&empty[s], par)) return true;   // not free yet: try on a later box
+        } else if (!mbar_wait(&empty[s], par, abort_flag)) {
+          return false;
+        }
+      }
       uint8_t* buf = sm + s * TN_STAGE_BYTES;
       mbar_expect_tx(&full[s], TN_STAGE_BYTES);
       const int x = (int)(rbeg + (int64_t)issued * TN_BR);
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
   int stretch = 0;
   for (int q = 0; q < nq; ++q) {
     bool ok = true;
-    if (tid == 0) ok = produce(q + TN_STAGES);
+    if (tid == 0) ok = produce(q + 1, true) && produce(q + TN_STAGES, false);
     const int s = q % TN_STAGES;
     ok = ok && mbar_wait(&full[s], (uint32_t)(q / TN_STAGES) & 1u, abort_flag);
     if (!__all_sync(0xffffffffu, ok)) break;
