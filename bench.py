@@ -578,8 +578,47 @@ def cpu_model():
     return platform.machine()
 
 
+def gpu_local_cpus(dev):
+    """Host CPUs of the GPU's own NUMA node (sysfs local_cpulist of its PCI
+    function), or None when the system does not say."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None
+
+
 def run_e2e(args, sc, c, dmd, dev, st, out, ks):
-    """Same step through the public API with HOST snapshots in and HOST frames out."""
+    """Same step through the public API with HOST snapshots in and HOST frames out.
+    The pinned host buffers are allocated and first touched from the CPUs of
+    the GPU's own NUMA node when the system names them (what a host
+    application placing its buffers next to the GPU does)."""
+    n, K = sc.n, c["frames"]
+    old_aff = os.sched_getaffinity(0)
+    local = gpu_local_cpus(dev)
+    if local:
+        os.sched_setaffinity(0, local)
+    try:
+        return _run_e2e(args, sc, c, dmd, dev, st, out, ks, local)
+    finally:
+        os.sched_setaffinity(0, old_aff)
+
+
+def _run_e2e(args, sc, c, dmd, dev, st, out, ks, local):
+    """The snapshots go up and the frames come down in 8 slices spread over 4
+    copy streams, so several copy engines work at once (measured: 2.6k ->
+    4.6k frames/s against one copy each way; 8 streams gave no more)."""
     n, K = sc.n, c["frames"]
     try:
         S_host = torch.empty(sc.S.shape, dtype=torch.float32, pin_memory=True)
@@ -589,13 +628,43 @@ def run_e2e(args, sc, c, dmd, dev, st, out, ks):
         return {"value": None, "unit": "frames/s", "error": f"pinned host buffers: {e}"}
     S_dev = torch.empty_like(sc.S)
     steps = max(1, min(args.steps, 3))
+    copy_streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    pieces = 8
+    kt = ks if isinstance(ks, torch.Tensor) else torch.as_tensor(ks, dtype=torch.int32, device=dev)
+    rows_up = np.linspace(0, S_host.shape[0], pieces + 1).astype(int)
+    frames = np.linspace(0, K, pieces + 1).astype(int)
 
     def one():
-        S_dev.copy_(S_host, non_blocking=True)
+        start = torch.cuda.Event()
+        start.record(st)
+        done = []
+        for i in range(pieces):
+            cs = copy_streams[i % len(copy_streams)]
+            cs.wait_event(start)
+            with torch.cuda.stream(cs):
+                S_dev[rows_up[i]:rows_up[i + 1]].copy_(S_host[rows_up[i]:rows_up[i + 1]], non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(cs)
+                done.append(e)
+        for e in done:
+            st.wait_event(e)
         model = dmd.dmd_fit(S_dev, n, c["r"], oversample=c["oversample"], power_iters=c["power_iters"],
                             precision=args.precision, seed=c["seed"])
-        dmd.dmd_predict(model, ks, precision=args.precision, out=out)
-        F_host.copy_(out, non_blocking=True)
+        dmd.dmd_predict(model, kt, precision=args.precision, out=out)
+        ready = torch.cuda.Event()
+        ready.record(st)
+        outs = []
+        for i in range(pieces):
+            a, b = frames[i], frames[i + 1]
+            cs = copy_streams[i % len(copy_streams)]
+            cs.wait_event(ready)
+            with torch.cuda.stream(cs):
+                F_host[a:b].copy_(out[a:b], non_blocking=True)
+                e2 = torch.cuda.Event()
+                e2.record(cs)
+                outs.append(e2)
+        for e in outs:
+            st.wait_event(e)
 
     one()
     torch.cuda.synchronize()
@@ -608,7 +677,10 @@ def run_e2e(args, sc, c, dmd, dev, st, out, ks):
     torch.cuda.synchronize()
     sec = a.elapsed_time(b) / 1e3
     return {"value": K * steps / sec, "unit": "frames/s", "h2d_bytes_per_step": int(S_host.numel() * 4),
-            "d2h_bytes_per_step": int(F_host.numel() * 4), "steps": steps}
+            "d2h_bytes_per_step": int(F_host.numel() * 4), "steps": steps,
+            "host_cpus": f"{len(local)} GPU-local" if local else "unrestricted",
+            "copies": "8 slices each way over 4 copy streams",
+            "bytes_over_step_gbs": (S_host.numel() + F_host.numel()) * 4 * steps / sec / 1e9}
 
 
 # DRAM bytes per row of n (dram__bytes_read.sum + dram__bytes_write.sum of one
