@@ -688,7 +688,7 @@ def _run_e2e(args, sc, c, dmd, dev, st, out, ks, local):
 # summarised in profiles/tall_kernels_cfg1_1M_rows.md; traffic grows in
 # proportion to the rows, so a full launch moves these x n bytes.
 TRAFFIC_PER_ROW = {
-    "k_gemm_tn_f32 (snapshot Gram W = S^T S)": 1.047e9 / 1048576,
+    "k_gemm_tn_f32 (snapshot Gram W = S^T S)": 1.029e9 / 1048576,
     "k_umma_tn (X^T Q1, Q1^T S)": 1.596e9 / 1048576,
     "k_umma_tn (Gram Q1^T Q1)": 0.737e9 / 1048576,
     "k_umma_nn_bres (sketch Q1 = X M)": 1.463e9 / 1048576,
