@@ -93,3 +93,21 @@ def test_upsample_argument_checks():
     ws = ctypes.c_void_p(256)
     # gram_given without a gram buffer is refused before anything is launched
     assert L.dmd_upsample(ctypes.byref(d), ws, ws, ws, ws, None, ws, ws, 1 << 30, None) == 1
+
+
+def test_advect_argument_checks():
+    """Host-side checks of dmd_advect_density's request (no GPU needed)."""
+    import ctypes
+    from paper_2502_05339_gb300 import dmd
+    L = dmd.lib()
+    nb = ctypes.c_size_t(0)
+
+    def desc(**kw):
+        base = dict(ldPhi=2 * 32 * 32, ldRho=32 * 32, N=32, dim=2, r=10, K=5, precision=1, chunk=0, dt=0.5)
+        base.update(kw)
+        return dmd.AdvectDesc(**base)
+
+    assert L.dmd_advect_workspace_bytes(ctypes.byref(desc()), ctypes.byref(nb)) == 0 and nb.value > 0
+    for bad in (dict(dim=4), dict(N=1), dict(K=0), dict(r=0), dict(ldRho=1000), dict(ldPhi=2047),
+                dict(dt=float("nan")), dict(chunk=-1), dict(dim=3, N=2000, ldPhi=3 * 2000 ** 3, ldRho=2000 ** 3)):
+        assert L.dmd_advect_workspace_bytes(ctypes.byref(desc(**bad)), ctypes.byref(nb)) == 1, bad
