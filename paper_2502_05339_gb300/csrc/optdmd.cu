@@ -407,7 +407,7 @@ dmd_status optdmd_small(int T, int r, int l, const double* Bsnap, const double* 
     k_opt_decide<<<1, 512, 0, st>>>(T, r, o.RE, o.pt, o.p, o.JtJt, o.gt, o.JtJ, o.g, o.BC, o.Bk, o.A, o.sd, o.si,
                                     tol);
     DMD_LAUNCH_CHECK();
-    if (it + 1 == max_evals) break;   // the last evaluation is only judged
+    if (it + 1 == max_evals) break;   // the last evaluation is only accepted or refused
     // step: (J^T J + mu diag) delta = -J^T rho, pt = p + delta
     DMD_TRY(cholesky_upper_gated(r, o.A, r, 1e-15, o.sinfo, 82, skip, st));
     DMD_TRY(chol_solve_gated(r, o.A, r, o.g, r, 1, -1.0, 1.0, o.pt, r, skip, st));
