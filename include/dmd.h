@@ -6,7 +6,10 @@
  * snapshot matrix through a randomized SVD (Sec. 3.1, Sec. 4.3, Sec. 4.6) and
  * predicts many time points at once by exponential integration
  * u(t + k dt) = Phi Lambda^k z(t) (Eq. large_time_step), with a hand-written
- * adjoint of the prediction.
+ * adjoint of the prediction.  On top of the fit and the prediction: the
+ * OptDMD fit (Sec. 4.2), temporal editing (Eq. edit_temporal), upsampling
+ * evolution (Sec. 6.3.1), density advection in the model's velocity
+ * (Sec. 7.2) and a batched many-scene driver.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
