@@ -123,18 +123,15 @@ def fourier_potential(g: np.random.Generator, N: int, dim: int, kc: int,
     return f.to(dtype)
 
 
-def make_modes(N: int, dim: int, npairs: int, seed: int, kc: int | None = None,
-               device="cpu", dtype=torch.float64) -> torch.Tensor:
-    """Complex divergence-free modes as a real (2*npairs, n) tensor.
-
-    Row 2j is Re(phi_j), row 2j+1 is Im(phi_j); each complex mode has unit RMS.
-    """
+def iter_mode_pairs(N: int, dim: int, npairs: int, seed: int, kc: int | None = None,
+                    device="cpu", dtype=torch.float64):
+    """Yields (Re phi_j, Im phi_j) of each complex divergence-free mode in
+    turn (unit RMS per complex mode): the rows make_modes stacks, one pair
+    at a time for grids where all of them do not fit at once."""
     if kc is None:
         kc = 8 if dim == 2 else 4
     g = rng(seed)
-    n = dim * N ** dim
-    out = torch.empty((2 * npairs, n), dtype=dtype, device=device)
-    for j in range(npairs):
+    for _ in range(npairs):
         parts = []
         for _ in range(2):  # real and imaginary potentials
             if dim == 2:
@@ -144,8 +141,20 @@ def make_modes(N: int, dim: int, npairs: int, seed: int, kc: int | None = None,
                 parts.append(curl3d(*a))
         re, im = parts
         rms = torch.sqrt((re * re + im * im).mean())
-        out[2 * j] = (re / rms).to(dtype)
-        out[2 * j + 1] = (im / rms).to(dtype)
+        yield (re / rms).to(dtype), (im / rms).to(dtype)
+
+
+def make_modes(N: int, dim: int, npairs: int, seed: int, kc: int | None = None,
+               device="cpu", dtype=torch.float64) -> torch.Tensor:
+    """Complex divergence-free modes as a real (2*npairs, n) tensor.
+
+    Row 2j is Re(phi_j), row 2j+1 is Im(phi_j); each complex mode has unit RMS.
+    """
+    n = dim * N ** dim
+    out = torch.empty((2 * npairs, n), dtype=dtype, device=device)
+    for j, (re, im) in enumerate(iter_mode_pairs(N, dim, npairs, seed, kc, device, dtype)):
+        out[2 * j] = re
+        out[2 * j + 1] = im
     return out
 
 
@@ -274,6 +283,64 @@ def linear_modes_scene(N: int, dim: int, npairs: int, m: int, seed: int, *,
                  lam_pairs, modes, a * scale, extra=extra)
 
 
+def linear_modes_scene_lean(N: int, dim: int, npairs: int, m: int, seed: int, *,
+                            sigma_lo: float = -0.05, omega_hi: float = math.pi / 4,
+                            noise: float = 0.0, nonlinear: float = 0.0, stratified: bool = False,
+                            device="cpu", name: str = "", batch_pairs: int = 10) -> Scene:
+    """The recipe of linear_modes_scene for grids whose FP64 intermediates do
+    not fit in memory: the snapshots are accumulated in FP32 on `device` from
+    batches of `batch_pairs` modes (one FP32 matrix product per batch), then
+    scaled to RMS 1; the quadratic term (same selection of 4 pairs, relative
+    scale `nonlinear`) and the noise are added row by row.  The modes are not
+    kept (modes_true is None)."""
+    g = rng(seed)
+    n = dim * N ** dim
+    ld = round_up(n, LD_ALIGN)
+    sigma, omega, a = draw_spectrum(g, npairs, sigma_lo, omega_hi, stratified)
+    sel = list(g.choice(npairs, size=min(4, npairs), replace=False)) if nonlinear > 0.0 else []
+    ks = np.arange(m + 1)
+    T = torch.as_tensor(time_factors(sigma, omega, a, ks), device=device)        # (2P, m+1) FP64
+    S = torch.zeros((m + 1, ld), dtype=torch.float32, device=device)
+    kept = {}
+    rows, fields = [], []
+    for j, (re, im) in enumerate(iter_mode_pairs(N, dim, npairs, seed + 1, device=device)):
+        if j in sel:
+            kept[j] = (re, im)
+        rows += [2 * j, 2 * j + 1]
+        fields += [re.to(torch.float32), im.to(torch.float32)]
+        if len(fields) == 2 * batch_pairs or j == npairs - 1:
+            M = torch.stack(fields)                                             # (2b, n) FP32
+            Tb = T[rows].to(torch.float32)                                      # (2b, m+1)
+            S[:, :n].addmm_(Tb.T, M)
+            rows, fields = [], []
+            del M
+    ss = sum(float((S[k, :n].double() ** 2).sum()) for k in range(m + 1))
+    scale = 1.0 / math.sqrt(ss / ((m + 1) * n))
+    S[:, :n] *= scale
+    if sel:
+        def quad_row(k):
+            f = [(T[2 * j, k] * kept[j][0] + T[2 * j + 1, k] * kept[j][1]) * scale for j in sel]
+            acc = torch.zeros(n, dtype=torch.float64, device=device)
+            for i in range(len(f)):
+                for jj in range(i, len(f)):
+                    acc += f[i] * f[jj]
+            return acc
+        qq = sum(float((quad_row(k) ** 2).sum()) for k in range(m + 1))
+        qs = nonlinear / math.sqrt(qq / ((m + 1) * n))
+        for k in range(m + 1):
+            S[k, :n] += (qs * quad_row(k)).to(torch.float32)
+    if noise > 0.0:
+        tg = torch.Generator(device=device)
+        tg.manual_seed(seed + 7)
+        for k in range(m + 1):
+            S[k, :n] += noise * torch.randn(n, generator=tg, dtype=torch.float32, device=device)
+    lam = np.exp(sigma + 1j * omega)
+    lam_pairs = np.empty(2 * npairs, dtype=complex)
+    lam_pairs[0::2], lam_pairs[1::2] = lam, lam.conj()
+    extra = dict(sigma=sigma, omega=omega, scale=scale, noise=noise, nonlinear=nonlinear)
+    return Scene(name or f"linear{dim}d_{N}_lean", N, dim, n, m, ld, S, lam_pairs, None, a * scale, extra=extra)
+
+
 # ----------------------------------------------------------------------------
 # the benchmark configurations (sizes from the workload definitions)
 # ----------------------------------------------------------------------------
@@ -372,3 +439,11 @@ def config2(seed: int = 1002, device="cpu", N: int = 96, m: int = 300) -> Scene:
 def random_sketch(m: int, l: int, seed: int) -> np.ndarray:
     """Gaussian N(0,1) test matrix (m x l), drawn on the host with PCG64."""
     return rng(seed).standard_normal((m, l))
+
+
+def config4(seed: int = 1004, device="cpu", N: int = 256, m: int = 300) -> Scene:
+    """3D 256^3 x 3 (n = 50,331,648), m = 300 (~60 GB of FP32 snapshots), data
+    as config 1: 75 pairs, sigma ~ U(-0.02, 0), frequencies stratified over
+    (0, pi), quadratic term 1e-3, noise 1e-4; built by the lean generator."""
+    return linear_modes_scene_lean(N, 3, 75, m, seed, sigma_lo=-0.02, omega_hi=math.pi, stratified=True,
+                                   noise=1e-4, nonlinear=1e-3, device=device, name=f"cfg4_3d{N}")
