@@ -7,6 +7,8 @@ hold at any size: the reconstruction of the training window and its
 divergence (the data are divergence-free up to their noise), and the streamed
 loss and gradient against the same quantities from stored frames (block-wise
 dmd_predict and dmd_predict_backward)."""
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -30,6 +32,15 @@ def dmd():
 @pytest.fixture(scope="module")
 def fitted(dmd):
     sc = synth.config4(device="cuda")
+    model, r = _fit(dmd, sc)
+    yield sc, model, r
+    # hand the ~100 GB back to the device before the next test module
+    del sc, model
+    gc.collect()
+    torch.cuda.empty_cache()
+
+
+def _fit(dmd, sc):
     # A drawn pair can sit below what the fit resolves (a tiny random
     # amplitude under the noise): the fit then reports DMD_ERANK, and the
     # rank is lowered in steps of 2 (at most 10 below the workload's 150).
@@ -41,7 +52,7 @@ def fitted(dmd):
             break
         r -= 2
     model.check()
-    return sc, model, r
+    return model, r
 
 
 def _rel(a, b):
