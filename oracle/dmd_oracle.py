@@ -20,6 +20,13 @@ Definitions followed (paper sections / equations):
   B = U_B Sigma V^T, X ~ (Q U_B) Sigma V^T                       (Sec. 4.3)
 * DMD with control, z(t+dt) = Lambda z(t) + Phi^+ B q(t) dt      (Eq. external_forces)
   with the unknown-B least-squares fit of [A B] (the DMDc the paper cites)
+* OptDMD: min over alpha, B of ||conj(V) Sigma - Phi(alpha) B||_F with
+  Phi(alpha)_{ij} = alpha_j^(i-1), by variable projection and
+  Levenberg-Marquardt; phi_i = U B^T(:, i) / ||U B^T(:, i)||   (Sec. 4.2, Eqs. variable_projection,
+                                                                 phi_optdmd)
+* temporal editing Omega = log(lambda) / dt, per-cluster scales   (Eq. edit_temporal)
+* upsampling R_t = S^L Phi^+ L_t + S^H Lambda R_{t-1}, H_t = Phi R_t  (Sec. 6.3.1)
+* density carried by the DMD velocity frames, semi-Lagrangian    (Sec. 7.2)
 
 Readings where the paper is silent or garbled are the ones listed in the
 design notes: m+1 snapshot columns, exact (not projected) modes, b = Phi^+ x_0
