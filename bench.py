@@ -12,7 +12,8 @@ of the step (each timed alone on the step's shapes); `roofline` is the entry
 with the largest share of the step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32]
-                  [--impl ours|reference] [--config cfg1|cfg0]
+                  [--impl ours|reference] [--config cfg1|cfg0|...]
+  python bench.py --case gram|tn|gramq|sketch|recon|advect|optdmd [--rows N]
 
 Under torchrun each rank runs an independent replica on its own GPU (the fit
 has no cross-rank exchange in this build): value = all ranks' frames / the
@@ -826,9 +827,10 @@ def cpu_baseline(cfg, sample_rows=None):
     return {"value": c["frames"] / (fit_s + pred_s), "unit": "frames/s", "cores": cores, "kind": "oracle",
             "cpu": cpu_model(),
             "sample": f"{sc.name}: n={sc.n} rows ({sc.n / n_full:.4f} of the workload), m={c['m']}, r={c['r']}, "
-                      f"{c['frames']} frames; times scaled by n (fit {fit_s:.1f} s, predict {pred_s:.1f} s "
-                      f"at full n)",
-            "measured_s": t2 - t0}
+                      f"{c['frames']} frames; EXTRAPOLATED: the times measured on this sample are scaled "
+                      f"linearly by n (x{scale:.0f}; fit O(n m^2), prediction O(n r K)) to fit {fit_s:.1f} s and "
+                      f"predict {pred_s:.1f} s at full n",
+            "extrapolated": scale != 1.0, "scale_by_n": scale, "measured_s": t2 - t0}
 
 
 def run_reference(args):
@@ -855,6 +857,91 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# small cases of single kernels, for profilers (--case NAME [--rows N])
+#
+# Each case builds seeded random operands of the 128^3 x 3 workload's column
+# counts on cuda:0 with a reduced row count (default 1,048,576 rows: every
+# operand still exceeds the 129 MB L2, the whole case holds a few GB) and calls
+# the same entry point twice, so a profiler can skip the first (warm-up) launch:
+#
+#   gram    snapshot Gram W = S^T S on the CUDA cores (201 columns, symmetric)
+#   tn      tensor-core reduction Q^T S (160 x 201 columns, BF16x3)
+#   gramq   tensor-core Gram Q^T Q (160 columns, BF16x3)
+#   sketch  tensor-core tall product X M (200 -> 160 columns, BF16x3)
+#   recon   reconstruction Phi_R C of 1000 frames (150 modes, BF16x3)
+#   advect  density advection (Sec. 7.2) on a 128^3 grid: a random 150-mode
+#           velocity model (RMS ~0.5 cells per unit step), 64 steps, frames
+#           rebuilt in batches of 64 (rows fixed by the grid; --rows is ignored)
+#   optdmd  OptDMD fit (Sec. 4.2) of a 3D 70^3 x 3 linear-modes scene (1,029,000
+#           rows; 200 snapshots, 75 pairs with stratified frequencies, rank 150,
+#           BF16x3 tall passes): the small FP64 loop is independent of the rows
+# ---------------------------------------------------------------------------
+
+CASE_M, CASE_L, CASE_R, CASE_FRAMES = 200, 160, 150, 1000
+
+
+def _case_case_rand(rows, cols, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.randn((cols, rows), device="cuda", generator=g)
+
+
+def _case_model(rows):
+    P = _case_rand(rows, CASE_R, 3)
+    rng = np.random.default_rng(4)
+    lam = np.exp(rng.uniform(-0.02, 0, CASE_R // 2) + 1j * rng.uniform(0, np.pi, CASE_R // 2))
+    modal = np.zeros(4 * CASE_R)
+    modal[0:CASE_R:2], modal[1:CASE_R:2] = lam.real, lam.real
+    modal[CASE_R:2 * CASE_R:2], modal[CASE_R + 1:2 * CASE_R:2] = lam.imag, -lam.imag
+    modal[2 * CASE_R:3 * CASE_R] = rng.standard_normal(CASE_R)
+    from paper_2502_05339_gb300 import dmd
+    return dmd.DmdModel(P, torch.as_tensor(modal).cuda(), torch.zeros(8, dtype=torch.int32, device="cuda"),
+                        rows, CASE_R, 0)
+
+
+def run_case(case: str, rows: int, reps: int = 2):
+    from paper_2502_05339_gb300 import dmd
+    dmd.lib()
+    if case == "gram":
+        S = _case_rand(rows, CASE_M + 1, 1)
+        for _ in range(reps):
+            dmd.dmd_gemm_tn(S, S, rows, precision="fp32")
+    elif case in ("tn", "gramq"):
+        Q = _case_rand(rows, CASE_L, 2)
+        S = Q if case == "gramq" else _case_rand(rows, CASE_M + 1, 1)
+        for _ in range(reps):
+            dmd.dmd_gemm_tn(Q, S, rows, precision="mixed")
+    elif case == "sketch":
+        X = _case_rand(rows, CASE_M, 1)
+        M = torch.randn((CASE_L, CASE_M), dtype=torch.float64, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_gemm_tall(X, rows, M, precision="mixed")
+    elif case == "recon":
+        model = _case_model(rows)
+        ks = torch.arange(CASE_FRAMES, dtype=torch.int32, device="cuda")
+        out = torch.empty((CASE_FRAMES, model.ldPhi), dtype=torch.float32, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_predict(model, ks, precision="mixed", out=out)
+    elif case == "advect":
+        N = 128
+        model = _case_model(3 * N ** 3)
+        model.Phi_R.mul_(0.05)
+        rho0 = torch.rand(N ** 3, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_advect_density(model, rho0, N, 3, 64, 0.5, precision="mixed", chunk=64)
+    elif case == "optdmd":
+        import math
+        from paper_2502_05339_gb300 import synth
+        sc = synth.linear_modes_scene(70, 3, CASE_R // 2, CASE_M, 1001, sigma_lo=-0.02, omega_hi=math.pi,
+                                      stratified=True, noise=1e-4, nonlinear=1e-3, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_fit_optdmd(sc.S, sc.n, CASE_R, precision="mixed", seed=1001).check()
+    else:
+        raise SystemExit(f"unknown case {case!r}")
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -868,8 +955,14 @@ def main():
     ap.add_argument("--config", default="cfg1", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=None)
+    ap.add_argument("--case", default=None, help="run one kernel's small profiling case and exit")
+    ap.add_argument("--rows", type=int, default=1 << 20, help="rows of the --case operands")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.case:
+        run_case(args.case, args.rows)
+        print("ok", args.case, args.rows)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "cfg3":

@@ -324,6 +324,8 @@ DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float
  * errors of dmd_predict.
  * Set-up: the first call on each device looks up the array's device address
  * on that (current) device; make that first call before any stream capture.
+ * The address is kept for the life of the process: a device reset
+ * (cudaDeviceReset) after the first call is not supported.
  * Sharing: every call on a device uses the same array, and the array keeps
  * the previous call's contents (each call clears the part it uses before
  * use).  Calls whose GPU work overlaps -- on different streams, or from

@@ -137,6 +137,17 @@ struct Tall {
                          double* C, void* ws, cudaStream_t st) const {
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
+  // A reduction whose result feeds a fit that resolves weak directions of
+  // the data (the projection Q^T S of OptDMD, whose weakest eigenvalues are
+  // the most sensitive part of its objective): in the mixed form the FP32
+  // operands are split three ways (hi + mid + lo, exact for FP32) and six
+  // products are summed, so the rounding is that of FP32 products rather
+  // than the 2^-17 representation error of the two-way split.
+  dmd_status tn_precise(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
+                        double* C, void* ws, cudaStream_t st) const {
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 3, 256, ws, st);
+    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
+  }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
     // BF16x3 (hi/lo split, 3 products), TMEM flushed to FP64 every 256
@@ -413,7 +424,8 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
     DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Z, info, 12 + 4 * it, st));
   }
   // 5. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
-  DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
+  if (opt) DMD_TRY(tall.tn_precise(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
+  else DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
   DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));
   DMD_TRY(fit_glue_check_finite((int64_t)l * (m + 1), b.P, info, 90, st));
   if (q > 0) return fit_control(d, S, Ups, PhiR, modal, info, tall, b, st);
@@ -923,7 +935,8 @@ namespace dmd {
 // Forward prediction with a workspace sized for the forward pass alone (the
 // coefficient matrix, the control rollout and the tall product's scratch);
 // dmd_predict_workspace_bytes covers the backward and loss passes as well.
-// Used by dmd_predict_noalloc, whose workspace is a fixed device array.
+// Used by dmd_predict_noalloc, whose workspace is a fixed device array, and
+// by the batch driver; `who` names the caller's entry point in error messages.
 dmd_status predict_forward_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes) {
   DMD_TRY(validate_predict(desc, true));
   Arena a;
@@ -934,10 +947,11 @@ dmd_status predict_forward_workspace_bytes(const dmd_predict_desc* desc, size_t*
 }
 
 dmd_status predict_forward(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
-                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st) {
+                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st,
+                           const char* who) {
   DMD_TRY(validate_predict(desc, true));
-  DMD_REQUIRE(Phi_R && modal && k && out, "dmd_predict_noalloc: NULL pointer argument");
-  DMD_REQUIRE(desc->q == 0 || u != nullptr || desc->steps == 0, "dmd_predict_noalloc: q > 0 needs u");
+  DMD_REQUIRE(Phi_R && modal && k && out, "%s: NULL pointer argument", who);
+  DMD_REQUIRE(desc->q == 0 || u != nullptr || desc->steps == 0, "%s: q > 0 needs u", who);
   size_t need = 0;
   DMD_TRY(predict_forward_workspace_bytes(desc, &need));
   return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {

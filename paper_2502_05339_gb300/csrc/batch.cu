@@ -23,7 +23,8 @@
 namespace dmd {
 dmd_status predict_forward_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);
 dmd_status predict_forward(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
-                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st);
+                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st,
+                           const char* who);
 }  // namespace dmd
 
 namespace {
@@ -167,21 +168,31 @@ extern "C" dmd_status dmd_fit_predict_batch(int32_t count, const dmd_scene* scen
   DMD_CUDA_TRY(cudaEventRecord(L->fork, caller));
   for (int l = 0; l < lanes; ++l) DMD_CUDA_TRY(cudaStreamWaitEvent(L->stream[l], L->fork, 0));
   uint8_t* base = reinterpret_cast<uint8_t*>(workspace);
-  // scenes in index order within each lane
-  for (int i = 0; i < count; ++i) {
+  // scenes in index order within each lane; the first failure stops the
+  // enqueueing, and the lanes are joined back into the caller's stream
+  // whatever happened, so that the caller's stream waits for every piece of
+  // work already queued and a capture in progress stays well-formed
+  dmd_status status = DMD_OK;
+  for (int i = 0; i < count && status == DMD_OK; ++i) {
     const dmd_scene& s = scenes[i];
     const int l = lane_of[i];
     cudaStream_t st = L->stream[l];
     void* ws = base + lane_off[l];
-    DMD_TRY(dmd_fit(&s.fit, s.S, nullptr, nullptr, s.Phi_R, s.modal, s.info, ws, lane_bytes[l], st));
-    if (s.K > 0) {
+    status = dmd_fit(&s.fit, s.S, nullptr, nullptr, s.Phi_R, s.modal, s.info, ws, lane_bytes[l], st);
+    if (status == DMD_OK && s.K > 0) {
       const dmd_predict_desc p = predict_desc_of(s);
-      DMD_TRY(::dmd::predict_forward(&p, s.Phi_R, s.modal, s.k, nullptr, s.out, ws, lane_bytes[l], st));
+      status = ::dmd::predict_forward(&p, s.Phi_R, s.modal, s.k, nullptr, s.out, ws, lane_bytes[l], st,
+                                      "dmd_fit_predict_batch");
     }
   }
   for (int l = 0; l < lanes; ++l) {
-    DMD_CUDA_TRY(cudaEventRecord(L->done[l], L->stream[l]));
-    DMD_CUDA_TRY(cudaStreamWaitEvent(caller, L->done[l], 0));
+    const cudaError_t e1 = cudaEventRecord(L->done[l], L->stream[l]);
+    const cudaError_t e2 = cudaStreamWaitEvent(caller, L->done[l], 0);
+    if (status == DMD_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) {
+      ::dmd::set_error("dmd_fit_predict_batch: joining lane %d failed: %s", l,
+                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      status = DMD_ECUDA;
+    }
   }
-  return DMD_OK;
+  return status;
 }

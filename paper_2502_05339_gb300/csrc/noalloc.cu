@@ -21,7 +21,8 @@
 namespace dmd {
 dmd_status predict_forward_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);
 dmd_status predict_forward(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
-                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st);
+                           const float* u, float* out, void* workspace, size_t ws_bytes, cudaStream_t st,
+                           const char* who);
 }  // namespace dmd
 
 namespace {
@@ -75,5 +76,6 @@ extern "C" dmd_status dmd_predict_noalloc(const dmd_predict_desc* desc, const fl
   // The array keeps whatever the previous call left in it: start from zeros
   // so that no entry of this call's coefficients can come from that call.
   DMD_CUDA_TRY(cudaMemsetAsync(scratch, 0, need, (cudaStream_t)stream));
-  return ::dmd::predict_forward(desc, Phi_R, modal, k, u, out, scratch, need, (cudaStream_t)stream);
+  return ::dmd::predict_forward(desc, Phi_R, modal, k, u, out, scratch, need, (cudaStream_t)stream,
+                                "dmd_predict_noalloc");
 }

@@ -329,6 +329,36 @@ def _ks_tensor(ks, dev) -> torch.Tensor:
     return t
 
 
+def _check_frames(model: DmdModel, K: int, t: torch.Tensor, name: str):
+    """A (K, ld) frame tensor must hold K frames of at least n rows: the C ABI
+    cannot see a buffer's size, so a short one would be written past its end."""
+    if t.dim() != 2 or t.shape[0] < K or t.shape[1] < model.n:
+        raise ValueError(f"{name} must have shape (>= {K}, >= {model.n}), got {tuple(t.shape)}")
+    _need_cuda(t, name, torch.float32)
+
+
+def _check_control(model: DmdModel, u: torch.Tensor | None):
+    """u (steps, q) float32 on the device: needed exactly when the model has
+    control inputs."""
+    if model.q == 0:
+        if u is not None:
+            raise ValueError("u given for a model without control inputs")
+        return
+    if u is None:
+        raise ValueError(f"the model has q = {model.q} control inputs: u (steps, q) is required")
+    if u.dim() != 2 or u.shape[1] != model.q:
+        raise ValueError(f"u must have shape (steps, {model.q}), got {tuple(u.shape)}")
+    _need_cuda(u, "u", torch.float32)
+
+
+def _check_modal(model: DmdModel, modal: torch.Tensor | None) -> torch.Tensor:
+    md = model.modal if modal is None else modal
+    if md.numel() < modal_doubles(model.r, model.q):
+        raise ValueError(f"modal must hold {modal_doubles(model.r, model.q)} doubles, got {md.numel()}")
+    _need_cuda(md, "modal", torch.float64)
+    return md
+
+
 def _pdesc(model: DmdModel, K: int, ldOut: int, precision, steps: int = 0, chunk: int = 0) -> PredictDesc:
     return PredictDesc(n=model.n, ldPhi=model.ldPhi, ldOut=ldOut, r=model.r, K=K, q=model.q, steps=steps,
                        precision=_prec(precision), chunk=chunk)
@@ -347,14 +377,17 @@ def dmd_predict(model: DmdModel, ks, *, u: torch.Tensor | None = None, precision
     kt = _ks_tensor(ks, dev)
     K = kt.numel()
     ldOut = round_up(model.n, 32)
+    _check_control(model, u)
+    if modal is not None:
+        _check_modal(model, modal)
     steps = 0 if u is None else u.shape[0]
     if out is None:
         out = torch.empty((K, ldOut), dtype=torch.float32, device=dev)
-    _need_cuda(out, "out", torch.float32)
+    _check_frames(model, K, out, "out")
     ldOut = out.shape[1]
     d = _pdesc(model, K, ldOut, precision, steps)
     ws = _pred_ws(d, dev)
-    md = model.modal if modal is None else modal
+    md = _check_modal(model, modal)
     _check(lib().dmd_predict(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(out),
                              _ptr(ws), ws.numel(), _stream(dev)), "dmd_predict")
     return out
@@ -368,10 +401,11 @@ def dmd_predict_noalloc(model: DmdModel, ks, out: torch.Tensor, *, u: torch.Tens
     an int32 CUDA tensor if the caller must not allocate at all."""
     dev = model.Phi_R.device
     kt = _ks_tensor(ks, dev)
-    _need_cuda(out, "out", torch.float32)
+    _check_frames(model, kt.numel(), out, "out")
+    _check_control(model, u)
     steps = 0 if u is None else u.shape[0]
     d = _pdesc(model, kt.numel(), out.shape[1], precision, steps)
-    md = model.modal if modal is None else modal
+    md = _check_modal(model, modal)
     _check(lib().dmd_predict_noalloc(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(out),
                                      _stream(dev)), "dmd_predict_noalloc")
     return out
@@ -409,11 +443,12 @@ def dmd_predict_backward(model: DmdModel, ks, dOut: torch.Tensor, *, u: torch.Te
     """(d_modal, d_u) for dL/d(frames) = dOut (tensor (K, ldOut) float32)."""
     dev = model.Phi_R.device
     kt = _ks_tensor(ks, dev)
-    _need_cuda(dOut, "dOut", torch.float32)
+    _check_frames(model, kt.numel(), dOut, "dOut")
+    _check_control(model, u)
     steps = 0 if u is None else u.shape[0]
     d = _pdesc(model, kt.numel(), dOut.shape[1], precision, steps)
     ws = _pred_ws(d, dev)
-    md = model.modal if modal is None else modal
+    md = _check_modal(model, modal)
     dmodal = torch.empty_like(md)
     du = None if u is None else torch.empty_like(u)
     _check(lib().dmd_predict_backward(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(dOut),
@@ -430,10 +465,13 @@ def dmd_predict_loss(model: DmdModel, ks, target: torch.Tensor, w: torch.Tensor,
     kt = _ks_tensor(ks, dev)
     _need_cuda(target, "target", torch.float32)
     _need_cuda(w, "w", torch.float64)
+    if target.numel() < model.n or w.numel() < kt.numel():
+        raise ValueError(f"target must hold n = {model.n} values and w K = {kt.numel()} weights")
+    _check_control(model, u)
     steps = 0 if u is None else u.shape[0]
     d = _pdesc(model, kt.numel(), round_up(model.n, 32), precision, steps, chunk)
     ws = _pred_ws(d, dev)
-    md = model.modal if modal is None else modal
+    md = _check_modal(model, modal)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     dmodal = torch.empty_like(md) if want_grad else None
     du = torch.empty_like(u) if (want_grad and u is not None) else None

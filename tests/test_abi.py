@@ -111,3 +111,36 @@ def test_advect_argument_checks():
     for bad in (dict(dim=4), dict(N=1), dict(K=0), dict(r=0), dict(ldRho=1000), dict(ldPhi=2047),
                 dict(dt=float("nan")), dict(chunk=-1), dict(dim=3, N=2000, ldPhi=3 * 2000 ** 3, ldRho=2000 ** 3)):
         assert L.dmd_advect_workspace_bytes(ctypes.byref(desc(**bad)), ctypes.byref(nb)) == 1, bad
+
+
+def test_binding_refuses_short_outputs_and_bad_controls():
+    """The C ABI cannot see buffer sizes, so the binding checks them before any
+    call: a frame buffer with fewer than K frames or n rows, a missing,
+    misshaped or host-resident control sequence, and a short modal buffer are
+    refused on the host (no library call, no GPU needed)."""
+    import torch
+    from paper_2502_05339_gb300 import dmd
+    n, r = 100, 4
+    model = dmd.DmdModel(torch.zeros((r, 128)), torch.zeros(4 * r, dtype=torch.float64),
+                         torch.zeros(8, dtype=torch.int32), n, r, 0)
+    ks = list(range(10))
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(model, ks, out=torch.zeros((9, 128)))            # 9 < K frames
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(model, ks, out=torch.zeros((10, 96)))            # 96 < n rows
+    with pytest.raises(ValueError):
+        dmd.dmd_predict_noalloc(model, ks, torch.zeros((10, 64)))
+    with pytest.raises(ValueError):
+        dmd.dmd_predict_backward(model, ks, torch.zeros((3, 128)))
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(model, ks, u=torch.zeros((5, 2)), out=torch.zeros((10, 128)))   # no control inputs
+    ctl = dmd.DmdModel(torch.zeros((r, 128)), torch.zeros(6 * r, dtype=torch.float64),
+                       torch.zeros(8, dtype=torch.int32), n, r, 2)
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(ctl, ks, out=torch.zeros((10, 128)))             # q > 0 needs u
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(ctl, ks, u=torch.zeros((5, 3)), out=torch.zeros((10, 128)))   # q mismatch
+    with pytest.raises(TypeError):
+        dmd.dmd_predict_noalloc(ctl, ks, torch.zeros((10, 128)), u=torch.zeros((5, 2)))   # host u
+    with pytest.raises(ValueError):
+        dmd.dmd_predict(model, ks, out=torch.zeros((10, 128)), modal=torch.zeros(3, dtype=torch.float64))

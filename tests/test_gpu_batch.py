@@ -7,7 +7,9 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import dmd_oracle as O
 from paper_2502_05339_gb300 import synth
+from tests.gpu_util import cols, match, mode_product_error, oracle_model, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +58,33 @@ def test_batch_equals_single_scene_calls(dmd, scenes, prec):
         assert torch.equal(mb.modal, ms.modal)
         assert torch.equal(mb.Phi_R[:, :n], ms.Phi_R[:, :n])
         assert torch.equal(fb[:, :n], fs[:, :n])
+
+
+BAR = {"fp32": 1e-5, "mixed": 1e-4}   # relative Frobenius error bars
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_batch_matches_oracle(dmd, scenes, prec):
+    """Every scene of one batched call (uneven n, m and r, several scenes per
+    lane, so lane workspaces are reused and scenes run longest-first) against
+    the FP64 exact-DMD oracle of that scene (Sec. 3.1, Eq. large_time_step):
+    matched eigenvalues, the per-mode fields phi_j b_j and all frames, each
+    within the relative bar of the form."""
+    batch = dmd.Batch(scenes, lanes=3, precision=prec)
+    models, frames = batch.run()
+    torch.cuda.synchronize()
+    for (S, n, r, seed, ks), mb, fb in zip(scenes, models, frames):
+        mb.check()
+        S64 = S[:, :n].double().cpu().numpy().T
+        ref, PhiR_o, beta_o, _ = oracle_model(S64, r)
+        lam_g = mb.lam()
+        _, lam_err = match(lam_g, ref["lam"])
+        mp_frob, _ = mode_product_error(cols(mb.Phi_R, n), mb.beta(), lam_g, PhiR_o, beta_o, ref["lam"])
+        Fo = O.predict_real(PhiR_o, O.coefficients(ref["lam"], beta_o, ks))
+        ferr = rel(cols(fb, n), Fo)
+        assert lam_err < BAR[prec], (n, r, "eigenvalues", lam_err)
+        assert mp_frob < BAR[prec], (n, r, "mode products", mp_frob)
+        assert ferr < BAR[prec], (n, r, "frames", ferr)
 
 
 def test_batch_graph_replay(dmd, scenes):

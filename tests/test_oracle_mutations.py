@@ -31,6 +31,7 @@ def _pins():
     yield lambda: P.test_reversal(fx)
     yield lambda: P.test_mode_products_match_ground_truth(fx)
     yield P.test_int_power_matches_polar
+    yield P.test_from_real_form_inverts_real_form
     yield P.test_rsvd_exact_when_rank_le_sketch
     yield P.test_philox_published_vectors
     yield P.test_adjoint_matches_central_differences
@@ -125,6 +126,30 @@ def _mut_adjoint(lam, beta, ks, dC, kinds=None):
     c = c.copy()
     c[kk == 2] *= -1.0
     return a, b, c
+
+
+def _mut_from_real_form(PhiR, lam):
+    kinds = O.pair_kinds(lam)
+    Phi = np.zeros(PhiR.shape, dtype=complex)
+    for c in range(PhiR.shape[1]):
+        if kinds[c] == 1:
+            Phi[:, c] = PhiR[:, c] - 1j * PhiR[:, c + 1]           # Im phi conjugated
+            Phi[:, c + 1] = np.conj(Phi[:, c])
+        elif kinds[c] == 0:
+            Phi[:, c] = PhiR[:, c]
+    return Phi
+
+
+def _mut_from_real_form_partner(PhiR, lam):
+    kinds = O.pair_kinds(lam)
+    Phi = np.zeros(PhiR.shape, dtype=complex)
+    for c in range(PhiR.shape[1]):
+        if kinds[c] == 1:
+            Phi[:, c] = PhiR[:, c] + 1j * PhiR[:, c + 1]
+            Phi[:, c + 1] = Phi[:, c]                               # partner not conjugated
+        elif kinds[c] == 0:
+            Phi[:, c] = PhiR[:, c]
+    return Phi
 
 
 def _mut_philox(ctr, key):
@@ -258,6 +283,8 @@ MUTATIONS = [
     ("predict_adjoint", _mut_adjoint, O),
     ("philox4x32_10", _mut_philox, philox),
     ("mode_products", _mut_mode_products, O),
+    ("from_real_form", _mut_from_real_form, O),
+    ("from_real_form", _mut_from_real_form_partner, O),
     ("gram_blocks", _mut_gram_cross, O),
     ("gram_blocks", _mut_gram_rhs, O),
     ("vandermonde", _mut_vandermonde, O),

@@ -151,6 +151,44 @@ def test_real_form_matches_complex(exact_cfg0):
     np.testing.assert_allclose(C[:, 0], beta, atol=0)
 
 
+def test_from_real_form_inverts_real_form():
+    """from_real_form turns a real 2x2-block basis back into complex modes.
+
+    Pinned three ways: (a) a basis built by hand, whose complex modes are
+    known (a pair's columns (u, v) are the modes u + iv and u - iv, a real
+    eigenvalue's column is its mode); (b) the round trip through to_real_form
+    of conjugate-closed complex modes; (c) the complex prediction Phi Lambda^k b
+    of the recovered modes, with b rebuilt from beta (b = (beta_c - i beta_c+1)/2
+    for a pair's first member, its conjugate for the partner), equals the real
+    product Phi_R C (Eq. large_time_step)."""
+    g = np.random.default_rng(21)
+    n = 9
+    lam = np.array([0.95 * np.exp(0.4j), 0.95 * np.exp(-0.4j), 0.9 * np.exp(1.1j), 0.9 * np.exp(-1.1j), 0.7, -0.5])
+    u, v, p, q, w, z = (g.standard_normal(n) for _ in range(6))
+    PhiR = np.stack([u, v, p, q, w, z], axis=1)
+    Phi = O.from_real_form(PhiR, lam)
+    ref = np.stack([u + 1j * v, u - 1j * v, p + 1j * q, p - 1j * q, w + 0j, z + 0j], axis=1)
+    np.testing.assert_array_equal(Phi, ref)
+    # (b) round trip of conjugate-closed modes
+    a, c = g.standard_normal(n) + 1j * g.standard_normal(n), g.standard_normal(n) + 1j * g.standard_normal(n)
+    Phi_c = np.stack([a, a.conj(), c, c.conj(), w + 0j, z + 0j], axis=1)
+    b = np.array([0.3 - 0.2j, 0.3 + 0.2j, -1.1 + 0.5j, -1.1 - 0.5j, 0.8, -0.4])
+    PhiR2, beta, kinds = O.to_real_form(Phi_c, lam, b)
+    np.testing.assert_allclose(O.from_real_form(PhiR2, lam), Phi_c, rtol=0, atol=1e-15)
+    # (c) complex prediction with the recovered modes = real-form prediction
+    bb = np.zeros(len(lam), dtype=complex)
+    for col in range(len(lam)):
+        if kinds[col] == 1:
+            bb[col] = 0.5 * (beta[col] - 1j * beta[col + 1])
+            bb[col + 1] = np.conj(bb[col])
+        elif kinds[col] == 0:
+            bb[col] = beta[col]
+    ks = [0, 1, 5, 40, -3]
+    F = O.predict(O.from_real_form(PhiR2, lam), lam, bb, ks)
+    Fr = O.predict_real(PhiR2, O.coefficients(lam, beta, ks, kinds))
+    np.testing.assert_allclose(F, Fr, rtol=0, atol=1e-12 * np.abs(Fr).max())
+
+
 def test_int_power_matches_polar():
     z = np.array([0.97 * np.exp(0.3j), 1.01 * np.exp(-2.0j), -0.5 + 0j, 0.8j])
     for k in [0, 1, 2, 3, 17, 500, 1000, -1, -7]:
