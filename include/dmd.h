@@ -127,8 +127,21 @@ typedef struct dmd_predict_desc {
   int32_t q;
   int32_t steps;
   int32_t precision;
-  int32_t chunk;       /* frames per recompute chunk in the loss entry points (0 = 50) */
+  int32_t chunk;       /* frames per recompute chunk of the FP32-form loss (0 = 50) */
 } dmd_predict_desc;
+
+/* Per-frame loss of dmd_predict_loss, rho of the residual e = x - target
+ * (Sec. 7.2 asks for gradients of the prediction for inverse design and names
+ * no loss; the quadratic loss is the plain reading, the Huber loss the
+ * general, non-quadratic case). */
+typedef enum { DMD_LOSS_QUADRATIC = 0, DMD_LOSS_HUBER = 1 } dmd_loss_kind;
+typedef struct dmd_loss_opts {
+  int32_t kind;        /* DMD_LOSS_QUADRATIC: rho(e) = e^2 / 2;
+                          DMD_LOSS_HUBER: rho(e) = e^2 / 2 for |e| <= delta,
+                          delta (|e| - delta / 2) beyond */
+  int32_t reserved;    /* 0 */
+  double delta;        /* Huber width, > 0 (ignored for the quadratic loss) */
+} dmd_loss_opts;
 
 DMD_EXPORT const char* dmd_last_error(void);
 DMD_EXPORT const char* dmd_version(void);
@@ -288,16 +301,24 @@ DMD_EXPORT dmd_status dmd_predict_backward(const dmd_predict_desc* desc, const f
                                 const float* dOut, double* d_modal, float* d_u,
                                 void* workspace, size_t ws_bytes, void* stream);
 
-/* Streamed per-frame loss L = sum_j w_j * 0.5 * ||x_{k[j]} - target||^2 without
- * storing the trajectory: frames are recomputed in chunks of desc->chunk,
- * each chunk's residual is formed in the GEMM epilogue and reduced on the fly.
- * target: n FP32; w: K FP64 weights (device).  loss: one double (device).
- * With want_grad != 0 the same chunked recompute also accumulates
- * dC = Phi_R^T (w_j (x_j - target)) and writes d_modal / d_u as
- * dmd_predict_backward does. */
+/* Streamed per-frame loss L = sum_j w_j sum_i rho(x_{k[j]},i - target_i)
+ * (rho of dmd_loss_opts; opts NULL = quadratic, L = sum_j w_j ||x - target||^2 / 2)
+ * without storing the trajectory.  target: n FP32; w: K FP64 weights
+ * (device).  loss: one double (device).  With want_grad != 0 the gradient
+ * dC = Phi_R^T G, G_ij = w_j rho'(x_ij - target_i), is taken and d_modal /
+ * d_u are written as dmd_predict_backward does.
+ * Mixed form (r <= 160): the frames never reach memory.  The loss alone is
+ * the reconstruction kernel with a loss epilogue (Phi_R read once); with the
+ * gradient one kernel recomputes each 128-row x 128-frame tile on the tensor
+ * cores, forms G in its epilogue, keeps G in tensor memory and accumulates
+ * dC^T += G^T Phi_tile there (Phi_R read once per 128 frames), with FP64
+ * partials per CTA summed in a fixed order.
+ * FP32 form (and r > 160): frames are recomputed in chunks of desc->chunk;
+ * each chunk is written, turned into G by a loss kernel and reduced by the
+ * Phi_R^T G pass. */
 DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                             const int32_t* k, const float* u, const float* target,
-                            const double* w, int32_t want_grad, double* loss,
+                            const double* w, const dmd_loss_opts* opts, int32_t want_grad, double* loss,
                             double* d_modal, float* d_u, void* workspace, size_t ws_bytes,
                             void* stream);
 

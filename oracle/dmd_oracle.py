@@ -27,6 +27,8 @@ Definitions followed (paper sections / equations):
 * temporal editing Omega = log(lambda) / dt, per-cluster scales   (Eq. edit_temporal)
 * upsampling R_t = S^L Phi^+ L_t + S^H Lambda R_{t-1}, H_t = Phi R_t  (Sec. 6.3.1)
 * density carried by the DMD velocity frames, semi-Lagrangian    (Sec. 7.2)
+* streamed per-frame losses (quadratic, Huber) and their frame
+  gradients, for the adjoint of the prediction                    (Sec. 7.2)
 
 Readings where the paper is silent or garbled are the ones listed in the
 design notes: m+1 snapshot columns, exact (not projected) modes, b = Phi^+ x_0
@@ -764,3 +766,40 @@ def rollout_adjoint(L: np.ndarray, GR: np.ndarray, Xi: np.ndarray, dXi: np.ndarr
         elif kinds[c] == 0:
             dlam_re[c] = dLmat[c, c]
     return dlam_re, dlam_im, mu, du
+
+
+# ----------------------------------------------------------------------------
+# per-frame losses of the streamed objective (Sec. 7.2: gradients of the
+# prediction for inverse design; the paper names no loss)
+# ----------------------------------------------------------------------------
+
+
+def frame_loss(F: np.ndarray, tgt: np.ndarray, w: np.ndarray, kind: str = "quadratic", delta: float = 0.0) -> float:
+    """L = sum_j w_j sum_i rho(F_ij - tgt_i) for frames F (n x K), one target
+    field tgt (n) and frame weights w (K).  rho(e) = e^2 / 2 ("quadratic"), or
+    the Huber function of width delta ("huber"): e^2 / 2 for |e| <= delta and
+    delta (|e| - delta / 2) beyond (its two pieces meet with equal value and
+    slope at |e| = delta)."""
+    E = np.asarray(F, dtype=np.float64) - np.asarray(tgt, dtype=np.float64)[:, None]
+    if kind == "quadratic":
+        rho = 0.5 * E * E
+    elif kind == "huber":
+        A = np.abs(E)
+        rho = np.where(A <= delta, 0.5 * E * E, delta * (A - 0.5 * delta))
+    else:
+        raise ValueError(kind)
+    return float(np.sum(np.asarray(w, dtype=np.float64)[None, :] * rho))
+
+
+def frame_loss_grad(F: np.ndarray, tgt: np.ndarray, w: np.ndarray, kind: str = "quadratic",
+                    delta: float = 0.0) -> np.ndarray:
+    """dL/dF (n x K) of frame_loss: w_j rho'(F_ij - tgt_i) with rho'(e) = e, or
+    for the Huber function e inside [-delta, delta] and delta sign(e) outside."""
+    E = np.asarray(F, dtype=np.float64) - np.asarray(tgt, dtype=np.float64)[:, None]
+    if kind == "quadratic":
+        d = E
+    elif kind == "huber":
+        d = np.clip(E, -delta, delta)
+    else:
+        raise ValueError(kind)
+    return np.asarray(w, dtype=np.float64)[None, :] * d

@@ -85,7 +85,16 @@ dmd_status launch_rollout_adjoint(int r, int q, int steps, int K, const int32_t*
                                   double* dmodal, float* du, cudaStream_t st);
 int loss_blocks();
 dmd_status launch_loss_chunk(int64_t n, int nf, float* F, int64_t ldf, const float* tgt, const double* w,
-                             bool grad, double* partial, double* loss, bool accumulate, cudaStream_t st);
+                             bool grad, float delta, double* partial, double* loss, bool accumulate, cudaStream_t st);
+dmd_status launch_sum_partials(int count, const double* partial, double* out, bool accumulate, cudaStream_t st);
+int umma_loss_parts(int64_t n);
+dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, const float* tgt,
+                        const double* w, float delta, double* part, int* parts, void* ws, cudaStream_t st);
+bool umma_loss_grad_supported(int r);
+size_t umma_loss_grad_workspace_bytes(int64_t n, int r, int K);
+dmd_status umma_loss_grad(int64_t n, int r, int K, const float* Phi, int64_t ldPhi, const double* C,
+                          const float* tgt, const double* w, float delta, double* dC, double* loss_part, int* parts,
+                          void* ws, cudaStream_t st);
 dmd_status fit_glue_sigma(int l, int r, const double* ev, double* sigma, double* inv_sq, int32_t* info,
                           cudaStream_t st);
 dmd_status fit_glue_scale_cols(int rows, int cols, double* A, int lda, const double* s, cudaStream_t st);
@@ -135,17 +144,6 @@ struct Tall {
   }
   dmd_status tn_accurate(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                          double* C, void* ws, cudaStream_t st) const {
-    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
-  }
-  // A reduction whose result feeds a fit that resolves weak directions of
-  // the data (the projection Q^T S of OptDMD, whose weakest eigenvalues are
-  // the most sensitive part of its objective): in the mixed form the FP32
-  // operands are split three ways (hi + mid + lo, exact for FP32) and six
-  // products are summed, so the rounding is that of FP32 products rather
-  // than the 2^-17 representation error of the two-way split.
-  dmd_status tn_precise(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                        double* C, void* ws, cudaStream_t st) const {
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 3, 256, ws, st);
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
@@ -424,8 +422,7 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
     DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Z, info, 12 + 4 * it, st));
   }
   // 5. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
-  if (opt) DMD_TRY(tall.tn_precise(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
-  else DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
+  DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
   DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));
   DMD_TRY(fit_glue_check_finite((int64_t)l * (m + 1), b.P, info, 90, st));
   if (q > 0) return fit_control(d, S, Ups, PhiR, modal, info, tall, b, st);
@@ -468,6 +465,12 @@ struct PredBufs {
 
 int chunk_of(const dmd_predict_desc& d) { return d.chunk > 0 ? d.chunk : 50; }
 
+// The streamed loss runs on the tensor cores with the frames kept on chip
+// (mixed form, r <= 160); otherwise frames are recomputed in stored chunks.
+bool fused_loss(const dmd_predict_desc& d) {
+  return d.precision == DMD_MIXED_BF16X3 && umma_loss_grad_supported(d.r);
+}
+
 void carve_predict(Arena& a, const dmd_predict_desc& d, int mode, PredBufs& b) {
   // mode 0: forward, 1: backward from dOut, 2: streamed loss
   const Tall tall{d.precision};
@@ -478,13 +481,15 @@ void carve_predict(Arena& a, const dmd_predict_desc& d, int mode, PredBufs& b) {
   b.dC = (mode >= 1) ? a.take<double>((size_t)r * K) : nullptr;
   b.dXi = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
   b.Mu = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
-  b.partial = (mode == 2) ? a.take<double>((size_t)loss_blocks()) : nullptr;
+  b.partial = (mode == 2) ? a.take<double>((size_t)std::max(loss_blocks(), umma_loss_parts(d.n))) : nullptr;
+  const bool fused = mode == 2 && fused_loss(d);
   const int ch = std::min(chunk_of(d), K);
-  b.F = (mode == 2) ? a.take<float>((size_t)round_up(d.n, 32) * ch) : nullptr;
+  b.F = (mode == 2 && !fused) ? a.take<float>((size_t)round_up(d.n, 32) * ch) : nullptr;
   size_t g = 0;
   if (mode == 0) g = tall.nn_bytes(d.n, r, K);
   if (mode == 1) g = tall.tn_bytes(d.n, r, K);
-  if (mode == 2) g = std::max(tall.nn_bytes(d.n, r, ch), tall.tn_bytes(d.n, r, ch));
+  if (mode == 2 && fused) g = std::max(umma_nn_workspace_bytes(d.n, r, K), umma_loss_grad_workspace_bytes(d.n, r, K));
+  if (mode == 2 && !fused) g = std::max(tall.nn_bytes(d.n, r, ch), tall.tn_bytes(d.n, r, ch));
   b.gemm_ws = a.take<char>(g, 1024);
 }
 
@@ -814,11 +819,16 @@ dmd_status dmd_predict_backward(const dmd_predict_desc* desc, const float* Phi_R
 }
 
 dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, const double* modal, const int32_t* k,
-                            const float* u, const float* target, const double* w, int32_t want_grad, double* loss,
-                            double* d_modal, float* d_u, void* workspace, size_t ws_bytes, void* stream) {
+                            const float* u, const float* target, const double* w, const dmd_loss_opts* opts,
+                            int32_t want_grad, double* loss, double* d_modal, float* d_u, void* workspace,
+                            size_t ws_bytes, void* stream) {
   DMD_TRY(validate_predict(desc, false));
   DMD_REQUIRE(Phi_R && modal && k && target && w && loss, "dmd_predict_loss: NULL pointer argument");
   DMD_REQUIRE(!want_grad || d_modal, "dmd_predict_loss: want_grad needs d_modal");
+  DMD_REQUIRE(opts == nullptr || opts->kind == DMD_LOSS_QUADRATIC ||
+                  (opts->kind == DMD_LOSS_HUBER && std::isfinite(opts->delta) && opts->delta > 0.0),
+              "dmd_predict_loss: loss kind must be quadratic or Huber with a finite delta > 0");
+  const float delta = (opts && opts->kind == DMD_LOSS_HUBER) ? (float)opts->delta : 0.f;
   size_t need = 0;
   DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
   cudaStream_t st = (cudaStream_t)stream;
@@ -827,14 +837,28 @@ dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, co
     carve_predict(a, *desc, 2, b);
     const Tall tall{desc->precision};
     DMD_TRY(form_coefficients(*desc, modal, k, u, b, st));
-    const int ch = std::min(chunk_of(*desc), desc->K);
-    const int64_t ldF = round_up(desc->n, 32);
-    for (int j0 = 0; j0 < desc->K; j0 += ch) {
-      const int nf = std::min(ch, desc->K - j0);
-      DMD_TRY(tall.nn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.C + (size_t)j0 * desc->r, b.F, ldF, b.gemm_ws, st));
-      DMD_TRY(launch_loss_chunk(desc->n, nf, b.F, ldF, target, w + j0, want_grad != 0, b.partial, loss, j0 > 0, st));
+    if (fused_loss(*desc)) {
+      int parts = 0;
       if (want_grad)
-        DMD_TRY(tall.tn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.F, ldF, b.dC + (size_t)j0 * desc->r, b.gemm_ws, st));
+        DMD_TRY(umma_loss_grad(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, target, w, delta, b.dC, b.partial,
+                               &parts, b.gemm_ws, st));
+      else
+        DMD_TRY(umma_loss_nn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, target, w, delta, b.partial, &parts,
+                             b.gemm_ws, st));
+      DMD_TRY(launch_sum_partials(parts, b.partial, loss, false, st));
+    } else {
+      const int ch = std::min(chunk_of(*desc), desc->K);
+      const int64_t ldF = round_up(desc->n, 32);
+      for (int j0 = 0; j0 < desc->K; j0 += ch) {
+        const int nf = std::min(ch, desc->K - j0);
+        DMD_TRY(tall.nn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.C + (size_t)j0 * desc->r, b.F, ldF, b.gemm_ws,
+                        st));
+        DMD_TRY(launch_loss_chunk(desc->n, nf, b.F, ldF, target, w + j0, want_grad != 0, delta, b.partial, loss,
+                                  j0 > 0, st));
+        if (want_grad)
+          DMD_TRY(tall.tn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.F, ldF, b.dC + (size_t)j0 * desc->r,
+                          b.gemm_ws, st));
+      }
     }
     if (want_grad) return chain_rule(*desc, modal, k, u, d_modal, d_u, b, st);
     return DMD_OK;

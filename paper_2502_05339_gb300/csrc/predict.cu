@@ -331,9 +331,11 @@ __global__ void k_scatter_frames(int r, int K, int steps, const int32_t* __restr
 }
 
 // Loss of one chunk: partial[b] = sum over this block's rows of
-// sum_j w_j 0.5 (F_ij - tgt_i)^2; if grad, F <- w_j (F - tgt) in place.
+// sum_j w_j rho(F_ij - tgt_i) with rho(e) = e^2 / 2, or with delta > 0 the
+// Huber function (e^2 / 2 for |e| <= delta, delta (|e| - delta / 2) beyond);
+// if grad, F <- w_j rho'(F - tgt) in place.
 __global__ void k_loss_chunk(int64_t n, int nf, float* __restrict__ F, int64_t ldf, const float* __restrict__ tgt,
-                             const double* __restrict__ w, int grad, double* __restrict__ partial) {
+                             const double* __restrict__ w, int grad, float delta, double* __restrict__ partial) {
   // Each thread sums its elements of one frame in FP32 (a few dozen terms)
   // and carries the frame sums in FP64: FP64 arithmetic per element would be
   // bound by GB300's FP64 pipe (~64x slower than FP32).
@@ -344,12 +346,12 @@ __global__ void k_loss_chunk(int64_t n, int nf, float* __restrict__ F, int64_t l
     float* f = F + (int64_t)j * ldf;
     float acc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      const float d = f[i] - tgt[i];
-      const float wd = wj * d;
-      acc = fmaf(wd, d, acc);
-      if (grad) f[i] = wd;
+      const float d = f[i] - tgt[i], ad = fabsf(d);
+      const bool lin = delta > 0.f && ad > delta;
+      acc = fmaf(wj, lin ? delta * (ad - 0.5f * delta) : 0.5f * d * d, acc);
+      if (grad) f[i] = wj * (lin ? copysignf(delta, d) : d);
     }
-    loc += 0.5 * (double)acc;
+    loc += (double)acc;
   }
   const double s = block_sum(loc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -432,10 +434,17 @@ dmd_status launch_rollout_adjoint(int r, int q, int steps, int K, const int32_t*
 int loss_blocks() { return 1024; }
 
 dmd_status launch_loss_chunk(int64_t n, int nf, float* F, int64_t ldf, const float* tgt, const double* w,
-                             bool grad, double* partial, double* loss, bool accumulate, cudaStream_t st) {
-  k_loss_chunk<<<loss_blocks(), 256, 0, st>>>(n, nf, F, ldf, tgt, w, grad ? 1 : 0, partial);
+                             bool grad, float delta, double* partial, double* loss, bool accumulate, cudaStream_t st) {
+  k_loss_chunk<<<loss_blocks(), 256, 0, st>>>(n, nf, F, ldf, tgt, w, grad ? 1 : 0, delta, partial);
   DMD_LAUNCH_CHECK();
   k_sum_partials<<<1, 32, 0, st>>>(loss_blocks(), partial, loss, accumulate ? 1 : 0);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+// out (= or +=) the sum of partial[0 .. count) in index order.
+dmd_status launch_sum_partials(int count, const double* partial, double* out, bool accumulate, cudaStream_t st) {
+  k_sum_partials<<<1, 32, 0, st>>>(count, partial, out, accumulate ? 1 : 0);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

@@ -28,148 +28,11 @@
 
 #include "common.cuh"
 #include "ptx.cuh"
+#include "tcgen05.cuh"
 
 namespace dmd {
 
 namespace {
-
-// ------------------------------------------------------------ PTX helpers
-// (mbarrier, TMA and bulk-copy helpers are in ptx.cuh)
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, FP32 accumulation.
-__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-// D[tmem] (+)= A[tmem] * B[smem]^T (A: 128 lanes = rows, 8 columns per 16-wide K-slice)
-__device__ __forceinline__ void umma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle.  lbo: byte distance
-// between K-adjacent core matrices, sbo: between 8-row groups.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= (uint64_t)1 << 46;   // descriptor version of tcgen05
-  return d;                 // base offset 0, absolute LBO mode, layout type 0 = no swizzle
-}
-constexpr uint32_t kLBO = 128, kSBO = 256;
-
-// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Byte offset of the 16-byte chunk (row, half) of a rows x 16 K-slice.
-__device__ __forceinline__ uint32_t kslice_off(int row, int half) {
-  return (uint32_t)((row >> 3) * 256 + half * 128 + (row & 7) * 16);
-}
-
-__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
-// Split 16 consecutive-K FP32 values into hi/lo and store them as one K-slice
-// row (two 16-byte chunks each) at `hi` and `lo` (slice bases).
-__device__ __forceinline__ void split_store_row(const float* x, uint8_t* hi, uint8_t* lo, int row) {
-  uint32_t h[8], l[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]);
-    const __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * i + 1]);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-    h[i] = pack2(h0, h1);
-    l[i] = pack2(l0, l1);
-  }
-  *reinterpret_cast<uint4*>(hi + kslice_off(row, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(hi + kslice_off(row, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
-  *reinterpret_cast<uint4*>(lo + kslice_off(row, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
-  *reinterpret_cast<uint4*>(lo + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
-}
-
-// 3-way split x = hi + mid + lo (bf16 each; exact for FP32 x up to the last
-// bit of lo) stored as three K-slice planes spaced `plane` bytes apart.
-__device__ __forceinline__ void split3_store_row(const float* x, uint8_t* base, uint32_t plane, int row) {
-  uint32_t h[8], m[8], l[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    __nv_bfloat16 hv[2], mv[2], lv[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const float v = x[2 * i + t];
-      hv[t] = __float2bfloat16_rn(v);
-      const float r1 = v - __bfloat162float(hv[t]);
-      mv[t] = __float2bfloat16_rn(r1);
-      lv[t] = __float2bfloat16_rn(r1 - __bfloat162float(mv[t]));
-    }
-    h[i] = pack2(hv[0], hv[1]);
-    m[i] = pack2(mv[0], mv[1]);
-    l[i] = pack2(lv[0], lv[1]);
-  }
-  uint8_t* p0 = base;
-  uint8_t* p1 = base + plane;
-  uint8_t* p2 = base + 2 * plane;
-  *reinterpret_cast<uint4*>(p0 + kslice_off(row, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(p0 + kslice_off(row, 1)) = make_uint4(h[4], h[5], h[6], h[7]);
-  *reinterpret_cast<uint4*>(p1 + kslice_off(row, 0)) = make_uint4(m[0], m[1], m[2], m[3]);
-  *reinterpret_cast<uint4*>(p1 + kslice_off(row, 1)) = make_uint4(m[4], m[5], m[6], m[7]);
-  *reinterpret_cast<uint4*>(p2 + kslice_off(row, 0)) = make_uint4(l[0], l[1], l[2], l[3]);
-  *reinterpret_cast<uint4*>(p2 + kslice_off(row, 1)) = make_uint4(l[4], l[5], l[6], l[7]);
-}
-
-// Round a dynamic shared-memory pointer up to 1024 bytes by pointer
-// arithmetic (an integer round trip would lose the shared address space and
-// turn every later access into a generic one).
-__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-  return p + ((1024u - (su32(p) & 1023u)) & 1023u);
-}
 
 // ---------------------------------------------------- B operand pre-split
 
@@ -399,10 +262,20 @@ constexpr int AR_THREADS = 320;
 // is what bounds this kernel (measured: ~2.4 us per 30 MMAs whatever N).
 // Each epilogue warp writes its 32 rows in 16-column TMA stores through a
 // double-buffered 2 KB staging area.
+//
+// kLoss != 0: the frames are not stored.  The epilogue forms each frame's
+// residual against the target field, e = x - tgt (row-wise), and accumulates
+// the weighted per-frame loss w_j rho(e) of the streamed objective: rho(e) =
+// e^2 / 2, or with delta > 0 the Huber function (e^2 / 2 for |e| <= delta,
+// delta (|e| - delta / 2) beyond).  Each thread sums one 128-frame chunk of its
+// row in FP32 and carries the chunk sums in FP64; the CTA's sum (fixed order)
+// goes to loss_part[blockIdx.x].  Phi_R is read once per call.
+template <int kLoss>
 __global__ void __launch_bounds__(AR_THREADS, 1)
     k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
                    const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int sa, int nb,
-                   int nchunks, int64_t ntiles, int32_t* err) {
+                   int nchunks, int64_t ntiles, const float* __restrict__ tgt, const double* __restrict__ wgt,
+                   float delta, double* __restrict__ loss_part, int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * (uint32_t)bn * 32u;
@@ -420,7 +293,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   uint64_t* ares_full = acce + AR_ACC;  // [AR_MAXKS]: slice ks of the tile's A is in TMEM
   uint64_t* ares_free = ares_full + AR_MAXKS;  // MMAs of the tile finished reading A
   uint64_t* tdown = ares_free + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tdown + 1);
+  double* red = reinterpret_cast<double*>(tdown + 1);   // 4 epilogue warps' loss sums
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 4);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -584,8 +458,11 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     uint32_t accit = 0;
     int sbuf = 0;
     bool ok = true;
+    double lacc = 0.0;   // kLoss: this thread's (row's) loss
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const int row0 = (int)(tile * 128) + q * 32;
+      const bool row_ok = (int64_t)row0 + lane < n;
+      const float tv = (kLoss && row_ok) ? tgt[row0 + lane] : 0.f;
       for (int c = 0; c < nchunks; ++c, ++accit) {
         const uint32_t ab = accit % AR_ACC;
         if (!mbar_wait(&accf[ab], (accit / AR_ACC) & 1, abort_flag)) {
@@ -594,6 +471,29 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         }
         tc_after();
         const int cend = min(bn, N - c * bn);   // the last chunk may be ragged
+        if (kLoss) {
+          // this warp's copy of the chunk's weights (FP32) in its staging area
+          __syncwarp();
+          for (int j = lane; j < cend; j += 32) mystg[j] = (float)wgt[c * bn + j];
+          __syncwarp();
+          float s = 0.f;
+          for (int c0 = 0; c0 < cend; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (c0 + j < cend) {
+                const float e = v[j] - tv, ae = fabsf(e);
+                const float rho = (delta > 0.f && ae > delta) ? delta * (ae - 0.5f * delta) : 0.5f * e * e;
+                s = fmaf(mystg[c0 + j], rho, s);
+              }
+            }
+          }
+          if (row_ok) lacc += (double)s;
+          tc_before();
+          mbar_arrive(&acce[ab]);
+          continue;
+        }
         for (int c0 = 0; c0 < cend; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
@@ -615,7 +515,12 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         mbar_arrive(&acce[ab]);
       }
     }
-    if (lane == 0) bulk_wait0();
+    if (kLoss) {
+      const double ws = warp_sum(lacc);
+      if (lane == 0) red[q] = ws;
+    } else if (lane == 0) {
+      bulk_wait0();
+    }
   }
   tc_before();
   __syncthreads();
@@ -623,6 +528,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     tc_after();
     tmem_dealloc(tmem, 512);
   }
+  if (kLoss && threadIdx.x == 0) loss_part[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3]));
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8002);
 }
 
@@ -905,6 +811,8 @@ __global__ void k_reduce_parts(int ka, int nb, int parts, const double* __restri
 
 // ------------------------------------------------------------ host side
 
+}  // namespace
+
 int num_sms() {
   static int sms = 0;
   if (!sms) {
@@ -915,6 +823,8 @@ int num_sms() {
   }
   return sms;
 }
+
+namespace {
 
 constexpr int kMaxSmem = 227 * 1024;
 
@@ -1035,10 +945,43 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   DMD_LAUNCH_CHECK();
   CUtensorMap mapC;
   DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, 16));
-  DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_umma_nn_ares<<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks, ntiles,
-                                                  nullptr);
+  DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_umma_nn_ares<0><<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
+                                                     ntiles, nullptr, nullptr, 0.f, nullptr, nullptr);
   DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+int umma_loss_parts(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(n, 128))); }
+
+// Streamed loss of the frames F = A B (A n x Kd tall, B Kd x N FP64), the
+// frames never stored: part[0 .. *parts) receives each CTA's share of
+// sum_j w_j sum_i rho(F_ij - tgt_i) (rho quadratic, or Huber with delta > 0).
+dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, const float* tgt,
+                        const double* w, float delta, double* part, int* parts, void* ws, cudaStream_t st) {
+  const int ksteps = (int)ceil_div(Kd, 16);
+  const int64_t ntiles = ceil_div(n, 128);
+  const AresCfg cfg = ares_cfg(ksteps);
+  const int bn = cfg.bn;
+  if (bn == 0 || ksteps > AR_MAXKS || ares_smem(ksteps, bn, cfg.sa, cfg.nb) > (size_t)kMaxSmem) {
+    set_error("umma_loss_nn: inner dimension %d too large for the resident-A layout", Kd);
+    return DMD_EINVAL;
+  }
+  CUtensorMap mapA;
+  DMD_TRY(make_map(&mapA, A, n, Kd, lda, 128, 16));
+  const int grid = umma_loss_parts(n);
+  const size_t smem = ares_smem(ksteps, bn, cfg.sa, cfg.nb);
+  const int nchunks = (int)ceil_div(N, bn);
+  const int64_t work = (int64_t)nchunks * bn * ksteps;
+  uint8_t* split = reinterpret_cast<uint8_t*>(ws);
+  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split);
+  DMD_LAUNCH_CHECK();
+  DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // no frames are stored: the output map argument is unused (the A map stands in)
+  k_umma_nn_ares<1><<<grid, AR_THREADS, smem, st>>>(mapA, mapA, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
+                                                     ntiles, tgt, w, delta, part, nullptr);
+  DMD_LAUNCH_CHECK();
+  *parts = grid;
   return DMD_OK;
 }
 

@@ -58,6 +58,13 @@ class AdvectDesc(ctypes.Structure):
                 ("dt", ctypes.c_double)]
 
 
+class LossOpts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("delta", ctypes.c_double)]
+
+
+LOSS_KINDS = {"quadratic": 0, "huber": 1}
+
+
 class PredictDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("ldPhi", ctypes.c_int64), ("ldOut", ctypes.c_int64),
                 ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("q", ctypes.c_int32),
@@ -91,8 +98,9 @@ SIGNATURES = {
     "dmd_predict_noalloc": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P]),
     "dmd_predict_backward": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, _P, _P,
                                               ctypes.c_size_t, _P]),
-    "dmd_predict_loss": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_int32,
-                                          _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "dmd_predict_loss": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P,
+                                          ctypes.POINTER(LossOpts), ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t,
+                                          _P]),
     "dmd_edit_modes": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_double, _P, _P,
                                         ctypes.c_double, _P]),
     "dmd_autotune_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P,
@@ -459,8 +467,10 @@ def dmd_predict_backward(model: DmdModel, ks, dOut: torch.Tensor, *, u: torch.Te
 
 def dmd_predict_loss(model: DmdModel, ks, target: torch.Tensor, w: torch.Tensor, *, want_grad: bool = False,
                      u: torch.Tensor | None = None, precision="fp32", chunk: int = 50,
-                     modal: torch.Tensor | None = None):
-    """Streamed L = sum_j w_j 0.5 ||x_{k_j} - target||^2 (and its gradient)."""
+                     modal: torch.Tensor | None = None, loss: str = "quadratic", delta: float = 0.0):
+    """Streamed L = sum_j w_j sum_i rho(x_{k_j,i} - target_i) (and its gradient):
+    rho(e) = e^2 / 2 (loss="quadratic") or the Huber function of width delta
+    (loss="huber")."""
     dev = model.Phi_R.device
     kt = _ks_tensor(ks, dev)
     _need_cuda(target, "target", torch.float32)
@@ -472,13 +482,14 @@ def dmd_predict_loss(model: DmdModel, ks, target: torch.Tensor, w: torch.Tensor,
     d = _pdesc(model, kt.numel(), round_up(model.n, 32), precision, steps, chunk)
     ws = _pred_ws(d, dev)
     md = _check_modal(model, modal)
-    loss = torch.zeros(1, dtype=torch.float64, device=dev)
     dmodal = torch.empty_like(md) if want_grad else None
     du = torch.empty_like(u) if (want_grad and u is not None) else None
+    opts = LossOpts(kind=LOSS_KINDS[loss], reserved=0, delta=float(delta))
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
     _check(lib().dmd_predict_loss(ctypes.byref(d), _ptr(model.Phi_R), _ptr(md), _ptr(kt), _ptr(u), _ptr(target),
-                                  _ptr(w), 1 if want_grad else 0, _ptr(loss), _ptr(dmodal), _ptr(du), _ptr(ws),
-                                  ws.numel(), _stream(dev)), "dmd_predict_loss")
-    return loss, dmodal, du
+                                  _ptr(w), ctypes.byref(opts), 1 if want_grad else 0, _ptr(out), _ptr(dmodal),
+                                  _ptr(du), _ptr(ws), ws.numel(), _stream(dev)), "dmd_predict_loss")
+    return out, dmodal, du
 
 
 def dmd_sketch_matrix(m: int, l: int, seed: int, device="cuda") -> torch.Tensor:

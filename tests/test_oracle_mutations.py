@@ -35,6 +35,8 @@ def _pins():
     yield P.test_rsvd_exact_when_rank_le_sketch
     yield P.test_philox_published_vectors
     yield P.test_adjoint_matches_central_differences
+    yield P.test_frame_loss_closed_forms
+    yield P.test_huber_adjoint_matches_central_differences_on_a_crop
     yield P.test_gram_route_known_operator
     yield P.test_gram_route_equals_svd_route
     yield lambda: P.pin_optdmd_noise_free(0)
@@ -150,6 +152,29 @@ def _mut_from_real_form_partner(PhiR, lam):
         elif kinds[c] == 0:
             Phi[:, c] = PhiR[:, c]
     return Phi
+
+
+def _mut_huber_branches(F, tgt, w, kind="quadratic", delta=0.0):
+    E = np.asarray(F, dtype=np.float64) - np.asarray(tgt, dtype=np.float64)[:, None]
+    if kind == "huber":
+        A = np.abs(E)
+        rho = np.where(A <= delta, delta * (A - 0.5 * delta), 0.5 * E * E)   # pieces swapped
+        return float(np.sum(np.asarray(w)[None, :] * rho))
+    return float(np.sum(np.asarray(w)[None, :] * 0.5 * E * E))
+
+
+_orig_loss_grad = O.frame_loss_grad
+
+
+def _mut_huber_grad(F, tgt, w, kind="quadratic", delta=0.0):
+    if kind == "huber":
+        E = np.asarray(F, dtype=np.float64) - np.asarray(tgt, dtype=np.float64)[:, None]
+        return np.asarray(w)[None, :] * delta * np.sign(E)                  # clipped everywhere
+    return _orig_loss_grad(F, tgt, w, kind, delta)
+
+
+def _mut_loss_weight(F, tgt, w, kind="quadratic", delta=0.0):
+    return _orig_loss_grad(F, tgt, np.sqrt(w), kind, delta)                 # weights not applied linearly
 
 
 def _mut_philox(ctr, key):
@@ -283,6 +308,9 @@ MUTATIONS = [
     ("predict_adjoint", _mut_adjoint, O),
     ("philox4x32_10", _mut_philox, philox),
     ("mode_products", _mut_mode_products, O),
+    ("frame_loss", _mut_huber_branches, O),
+    ("frame_loss_grad", _mut_huber_grad, O),
+    ("frame_loss_grad", _mut_loss_weight, O),
     ("from_real_form", _mut_from_real_form, O),
     ("from_real_form", _mut_from_real_form_partner, O),
     ("gram_blocks", _mut_gram_cross, O),

@@ -364,6 +364,74 @@ def test_adjoint_matches_central_differences():
             assert abs(fd - ref) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_frame_loss_closed_forms():
+    """Quadratic and Huber per-frame losses on a worked example: frames
+    F = [[1, 3], [-2, 0.5]], target (0.5, -1), weights (2, 0.5), delta = 1 give
+    residuals [[0.5, 2.5], [-1, 1.5]]; quadratic L = 2 (0.125 + 0.5) +
+    0.5 (3.125 + 1.125) = 3.375; Huber L = 2 (0.125 + 0.5) + 0.5 (2 + 1) = 2.75
+    (|e| = 1 sits on the boundary, where both pieces give 1/2)."""
+    F = np.array([[1.0, 3.0], [-2.0, 0.5]])
+    tgt = np.array([0.5, -1.0])
+    w = np.array([2.0, 0.5])
+    assert O.frame_loss(F, tgt, w) == 3.375
+    assert O.frame_loss(F, tgt, w, "huber", 1.0) == 2.75
+    np.testing.assert_array_equal(O.frame_loss_grad(F, tgt, w), [[1.0, 1.25], [-2.0, 0.75]])
+    np.testing.assert_array_equal(O.frame_loss_grad(F, tgt, w, "huber", 1.0), [[1.0, 0.5], [-2.0, 0.5]])
+    # a Huber width above every residual is the quadratic loss; a tiny one is
+    # delta * (weighted L1 norm) to first order
+    g = np.random.default_rng(11)
+    F, tgt, w = g.standard_normal((30, 4)), g.standard_normal(30), g.uniform(0, 1, 4)
+    big = 2 * np.abs(F - tgt[:, None]).max()
+    assert abs(O.frame_loss(F, tgt, w, "huber", big) - O.frame_loss(F, tgt, w)) <= 1e-13 * O.frame_loss(F, tgt, w)
+    np.testing.assert_allclose(O.frame_loss_grad(F, tgt, w, "huber", big), O.frame_loss_grad(F, tgt, w), rtol=0,
+                               atol=0)
+    d = 1e-9
+    l1 = float(np.sum(w[None, :] * np.abs(F - tgt[:, None])))
+    assert abs(O.frame_loss(F, tgt, w, "huber", d) / d - l1) <= 1e-6 * l1
+
+
+def test_huber_adjoint_matches_central_differences_on_a_crop():
+    """The Huber loss's gradient through the prediction adjoint (dC = Phi_R^T
+    dL/dF, then the FP64 chain rule) against central differences of the FP64
+    Huber loss, on a 64-row spatial crop of a fitted model (delta = 0.1 RMS
+    of the residual, so both pieces are exercised).  The loss is piecewise
+    quadratic in beta, so central differences are exact up to rounding unless
+    a residual crosses +-delta within the step."""
+    lam, beta, kinds, PhiR, ks, tgt, w = _quad_loss_setup(seed=9)
+    rows = np.random.default_rng(2).choice(PhiR.shape[0], 64, replace=False)
+    PhiR, tgt = PhiR[rows], tgt[rows]
+    F = O.predict_real(PhiR, O.coefficients(lam, beta, ks, kinds))
+    delta = 0.1 * float(np.sqrt(np.mean((F - tgt[:, None]) ** 2)))
+    E = F - tgt[:, None]
+    assert 0.2 < np.mean(np.abs(E) > delta) < 0.98
+
+    def L(lm, bt):
+        return O.frame_loss(O.predict_real(PhiR, O.coefficients(lm, bt, ks, kinds)), tgt, w, "huber", delta)
+
+    dC = PhiR.T @ O.frame_loss_grad(F, tgt, w, "huber", delta)
+    dlr, dli, db = O.predict_adjoint(lam, beta, ks, dC, kinds)
+    h = 1e-7
+    for c in range(len(beta)):
+        bp, bm = beta.copy(), beta.copy()
+        bp[c] += h
+        bm[c] -= h
+        fd = (L(lam, bp) - L(lam, bm)) / (2 * h)
+        assert abs(fd - db[c]) <= 1e-6 * max(1.0, abs(fd)), (c, fd, db[c])
+    for c in range(len(beta)):
+        if kinds[c] == 2:
+            continue
+        for part, ref in ((1, dlr[c]), (1j, dli[c])):
+            if kinds[c] == 0 and part == 1j:
+                continue
+            lp, lm = lam.copy(), lam.copy()
+            lp[c] += h * part
+            lm[c] -= h * part
+            if kinds[c] == 1:
+                lp[c + 1], lm[c + 1] = np.conj(lp[c]), np.conj(lm[c])
+            fd = (L(lp, beta) - L(lm, beta)) / (2 * h)
+            assert abs(fd - ref) <= 1e-5 * max(1.0, abs(fd)), (c, part, fd, ref)
+
+
 # ------------------------------------------------------------------ DMDc
 
 
