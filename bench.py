@@ -13,7 +13,7 @@ with the largest share of the step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32]
                   [--impl ours|reference] [--config cfg1|cfg0|...]
-  python bench.py --case gram|tn|gramq|sketch|recon|advect|optdmd [--rows N]
+  python bench.py --case gram|tn|gramq|sketch|recon|loss|lossgrad|advect|optdmd [--rows N]
 
 Under torchrun each rank runs an independent replica on its own GPU (the fit
 has no cross-rank exchange in this build): value = all ranks' frames / the
@@ -62,6 +62,11 @@ CONFIGS = {
                 workload="density in the DMD velocity (Sec. 7.2): the rank-150 model of the 128^3 x 3 scene, "
                          "1000 semi-Lagrangian steps (dt 0.5 cells per unit velocity) of a cell-centred 128^3 "
                          "density (cosine pattern plus a Gaussian blob), velocity frames rebuilt 256 at a time"),
+    "cfg4": dict(N=256, dim=3, m=300, r=150, oversample=16, power_iters=1, frames=2000, seed=1004,
+                 workload="Large: 256^3 x 3 velocity (n=50,331,648), m=300 FP32 snapshots (60.6 GB), 150 modes + "
+                          "quadratic term 1e-3 + noise 1e-4; rSVD r=150 p=16 q=1 (mixed), then 2000 frames "
+                          "(k=0..1999) streamed into sum_k w_k ||x_k - x_tgt||^2 / 2 and its gradient w.r.t. "
+                          "lambda and b, frames recomputed on the tensor cores and never stored"),
     "cfg0": dict(N=64, dim=2, m=100, r=20, oversample=10, power_iters=2, frames=501, seed=1000,
                  workload="2D 64^2 x 2 velocity (n=8192), m=100, 20 modes, noise 1e-8; r=20; predict k=0..500"),
 }
@@ -522,6 +527,103 @@ def run_advect(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """The large workload: a step is the fit of the 256^3 x 3 snapshots (60.6 GB)
+    plus the streamed loss over 2000 frames and its gradient (frames never
+    stored); value = frames / s of whole steps.  Mixed form only (the FP32
+    form's CUDA-core products at this size are not a tensor-core measurement).
+    The loss-gradient call is the dominant kernel: its roofline is in TFLOP/s
+    of the BF16x3 products it executes (3 bf16 products per product of the
+    method: forward 2 n r K and backward 2 n r K flops each) against the
+    sustained dense bf16 peak, since it runs inside a long step."""
+    from paper_2502_05339_gb300 import dmd, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c = CONFIGS["cfg4"]
+    prec = "mixed"
+    t_gen = time.perf_counter()
+    sc = synth.config4(seed=c["seed"], device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    n, m, K = sc.n, sc.m, c["frames"]
+    st = torch.cuda.current_stream(dev)
+    L = dmd.lib()
+    # a drawn pair can sit below what the fit resolves: lower r in steps of 2 (at most 10)
+    r = c["r"]
+    while True:
+        model = dmd.dmd_fit(sc.S, n, r, oversample=c["oversample"], power_iters=c["power_iters"], precision=prec,
+                            seed=c["seed"])
+        torch.cuda.synchronize()
+        if model.status() == 0 or r <= c["r"] - 10:
+            break
+        r -= 2
+    model.check()
+    ks = torch.arange(K, dtype=torch.int32, device=dev)
+    target = sc.S[0].clone()
+    w = torch.as_tensor(np.random.default_rng(c["seed"]).uniform(0.0, 1.0, K)).to(dev)
+    holder = {}
+
+    def fit():
+        holder["model"] = dmd.dmd_fit(sc.S, n, r, oversample=c["oversample"], power_iters=c["power_iters"],
+                                      precision=prec, seed=c["seed"])
+
+    def loss_grad():
+        holder["res"] = dmd.dmd_predict_loss(holder["model"], ks, target, w, want_grad=True, precision=prec)
+
+    def step():
+        fit()
+        loss_grad()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    holder["model"].check()
+    fit_s = event_time(fit, st, reps=2)
+    lg_s = event_time(loss_grad, st, reps=2)
+    loss_s = event_time(lambda: dmd.dmd_predict_loss(holder["model"], ks, target, w, precision=prec), st, reps=2)
+    launches0 = L.dmd_launch_count()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        for _ in range(args.steps):
+            step()
+        t1.record(st)
+        torch.cuda.synchronize()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    launches = (L.dmd_launch_count() - launches0) // max(args.steps, 1)
+    peaks, peak_kind = load_peaks()
+    sustained = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+    fl_grad = 3 * 4.0 * n * r * K
+    fl_loss = 3 * 2.0 * n * r * K
+    roof = {"kernel": "k_umma_loss_grad (streamed loss + gradient, 2000 frames)", "bound": "tensor",
+            "achieved": fl_grad / lg_s / 1e12, "peak": sustained, "unit": "TFLOP/s",
+            "frac": fl_grad / lg_s / 1e12 / sustained, "traffic": None,
+            "peak_source": f"{peak_kind} bf16 dense, sustained", "launch_ms": 1e3 * lg_s,
+            "algorithmic": "3 bf16 products x (2 n r K forward + 2 n r K backward) flops; timed around the "
+                           "dmd_predict_loss call (the kernel plus the coefficient, partial-sum and chain-rule "
+                           "launches)"}
+    loss_entry = {"kernel": "k_umma_nn_ares<loss> (streamed loss alone)", "bound": "tensor",
+                  "achieved": fl_loss / loss_s / 1e12, "peak": sustained, "unit": "TFLOP/s",
+                  "frac": fl_loss / loss_s / 1e12 / sustained, "launch_ms": 1e3 * loss_s,
+                  "algorithmic": "3 bf16 products x 2 n r K flops"}
+    line = {
+        "metric": "streamed loss+gradient frames/s, 256^3 x 3, r=150, 2000 frames (fit + loss + grad per step)",
+        "value": K * args.steps / elapsed, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic", "impl": "ours",
+        "config": {"workload": c["workload"], "n": n, "m": m, "r": r, "frames": K, "precision": prec,
+                   "l2": "snapshots (60.6 GB) and modes (30.2 GB) exceed L2"},
+        "fit_s": fit_s, "loss_s": loss_s, "loss_and_grad_s": lg_s, "grad_over_loss": lg_s / loss_s,
+        "e2e": None, "e2e_note": "not measured for this configuration: one step would copy 60.6 GB of snapshots",
+        "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "kernels": [roof, loss_entry],
+        "scene_generation_s": t_gen, "loss": float(holder["res"][0].item()),
+        "parity": {"status": holder["model"].status(), "tests": "tests/test_gpu_config4.py"},
+        "device": device_info(dev),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def batch_one(dmd, item, prec):
     S, n, r, seed, ks = item
     model = dmd.dmd_fit(S, n, r, oversample=10, power_iters=2, precision=prec, seed=seed)
@@ -532,7 +634,8 @@ def adjoint_timing(model, ks, out, dmd, st, prec, rec_s):
     """Adjoint of the prediction against the forward: dmd_predict_backward of
     the stored frames (dL/dF taken as the frame buffer itself), and the
     streamed loss L = sum_k 0.5 ||x_k - x_0||^2 with and without its gradient
-    (frames recomputed in chunks of 50, never stored)."""
+    (frames never stored: recomputed on the tensor cores in the mixed form, in
+    stored chunks of 50 in the FP32 form)."""
     K = int(ks.numel())
     bwd = event_time(lambda: dmd.dmd_predict_backward(model, ks, out, precision=prec), st)
     target = out[0].clone()
@@ -870,6 +973,9 @@ def run_reference(args):
 #   gramq   tensor-core Gram Q^T Q (160 columns, BF16x3)
 #   sketch  tensor-core tall product X M (200 -> 160 columns, BF16x3)
 #   recon   reconstruction Phi_R C of 1000 frames (150 modes, BF16x3)
+#   loss    streamed quadratic loss of 250 frames (150 modes, BF16x3; frames
+#           never stored: the reconstruction kernel's loss epilogue)
+#   lossgrad  the same loss with its gradient (the fused loss-gradient kernel)
 #   advect  density advection (Sec. 7.2) on a 128^3 grid: a random 150-mode
 #           velocity model (RMS ~0.5 cells per unit step), 64 steps, frames
 #           rebuilt in batches of 64 (rows fixed by the grid; --rows is ignored)
@@ -923,6 +1029,13 @@ def run_case(case: str, rows: int, reps: int = 2):
         out = torch.empty((CASE_FRAMES, model.ldPhi), dtype=torch.float32, device="cuda")
         for _ in range(reps):
             dmd.dmd_predict(model, ks, precision="mixed", out=out)
+    elif case in ("loss", "lossgrad"):
+        model = _case_model(rows)
+        ks = torch.arange(CASE_FRAMES // 4, dtype=torch.int32, device="cuda")
+        target = torch.randn(model.ldPhi, device="cuda")
+        w = torch.rand(ks.numel(), dtype=torch.float64, device="cuda")
+        for _ in range(reps):
+            dmd.dmd_predict_loss(model, ks, target, w, want_grad=case == "lossgrad", precision="mixed")
     elif case == "advect":
         N = 128
         model = _case_model(3 * N ** 3)
@@ -973,6 +1086,8 @@ def main():
         run_upsample(args)
     elif args.config == "adv":
         run_advect(args)
+    elif args.config == "cfg4":
+        run_large(args)
     else:
         run_ours(args)
 

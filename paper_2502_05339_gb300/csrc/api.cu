@@ -148,10 +148,10 @@ struct Tall {
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                 void* ws, cudaStream_t st) const {
-    // BF16x3 (hi/lo split, 3 products), TMEM flushed to FP64 every 256
-    // k-steps.  The reductions that see the snapshots' full dynamic range
+    // BF16x3 (hi/lo split, 3 products), TMEM flushed to FP64 in segments
+    // sized by the row count (16 .. 256 k-steps).  The reductions that see the snapshots' full dynamic range
     // (the snapshot Gram) run on the CUDA cores instead (tn_accurate).
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 2, 256, ws, st);
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 2, 0, ws, st);
     return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
   }
 };

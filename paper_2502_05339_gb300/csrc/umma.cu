@@ -537,7 +537,6 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
 constexpr int TN_S = 4;            // TMA stages (A slice + B slice)
 constexpr int TN_CONV = 16;        // converter warps
 constexpr int TN_THREADS = 32 * (2 + TN_CONV + 4);
-constexpr int TN_FLUSH = 256;      // default k-steps (of 16 rows) between FP64 flushes
 
 // Split 4 consecutive-K FP32 values of operand row `row` (K offset 4*qd in
 // the 16-wide slice) into NS bf16 planes `plane` bytes apart (hi, then the
@@ -885,8 +884,19 @@ int bres_cols(int ksteps) {
   return np;
 }
 
+// Flush segments of the tensor-core reductions.  A CTA sums its rows in FP32
+// tensor memory (3 products per 16-row k-step) and adds the sum to its FP64
+// partial every `flush` k-steps; the FP32 rounding of a segment grows with its
+// length (measured on a 8192-row projection: 256-k-step segments cost 3x the
+// error of the split itself, 32-k-step ones add little).  So segments are as
+// short as the FP64 flushes allow: about 1536 over the whole matrix (the
+// number at 6.3M rows with 256-k-step segments), between 16 and 256 k-steps,
+// and the grid gives every CTA at least one whole segment.
+int tn_flush(int64_t n) {
+  return (int)std::max<int64_t>(16, std::min<int64_t>(256, ceil_div(n, 16 * 1536)));
+}
 int tn_grid(int64_t n) {
-  const int64_t want = ceil_div(n, 4096);
+  const int64_t want = ceil_div(n, 16 * (int64_t)tn_flush(n));
   return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), want));
 }
 
@@ -1046,6 +1056,7 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                               double* C, int nsplit, int flush, void* ws, cudaStream_t st) {
   if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
+  if (flush <= 0) flush = tn_flush(n);
   double* part = reinterpret_cast<double*>(ws);
   const int grid = tn_grid(n);
   const int64_t chunk = round_up(ceil_div(n, grid), 32);
@@ -1089,7 +1100,7 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
 
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                         int nsplit, void* ws, cudaStream_t st) {
-  return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, nsplit, TN_FLUSH, ws, st);
+  return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, nsplit, 0, ws, st);
 }
 
 }  // namespace dmd

@@ -1,7 +1,8 @@
 """The large workload: 256^3 x 3 (n = 50,331,648), m = 300 FP32 snapshots
 (~60 GB), data as the 128^3 workload, rSVD at r = 150 with oversampling 16 and
 one power iteration (mixed form), then 2000 frames streamed into a per-frame
-loss whose gradient recomputes the frames in chunks of 50.  The FP64 oracle
+loss and its gradient, the frames recomputed on the tensor cores and never
+stored.  The FP64 oracle
 cannot decompose a matrix of this size, so the checks are properties that
 hold at any size: the reconstruction of the training window and its
 divergence (the data are divergence-free up to their noise), and the streamed
