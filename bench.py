@@ -987,7 +987,7 @@ def run_reference(args):
 CASE_M, CASE_L, CASE_R, CASE_FRAMES = 200, 160, 150, 1000
 
 
-def _case_case_rand(rows, cols, seed):
+def _case_rand(rows, cols, seed):
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     return torch.randn((cols, rows), device="cuda", generator=g)

@@ -4,8 +4,9 @@
 #include <string.h>
 
 #include <algorithm>
-#include <cmath>
 #include <atomic>
+#include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "optdmd.cuh"
@@ -107,6 +108,50 @@ dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma_or
                                 int tag, cudaStream_t st);
 
 namespace {
+
+// ---------------------------------------------------------- side streams
+//
+// A few small solves of the fit are independent of the tall pass running at
+// the same time (the amplitudes' least squares beside the modes pass): they
+// are forked onto a side stream of the caller's stream and joined back with
+// events, so the caller's stream still orders all of the call's work and a
+// capture of it records the fork and the join.  Side streams and events are
+// created on first use, per (device, caller stream); a call made while a
+// stream capture is in progress must therefore not be the first on its
+// stream.  When the table is full the work simply stays on the caller's
+// stream.
+struct Side {
+  int dev = -1;
+  cudaStream_t origin = nullptr, side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxSides = 128;
+Side g_sides[kMaxSides];
+std::mutex g_side_mu;
+
+const Side* side_of(cudaStream_t origin) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  for (int i = 0; i < kMaxSides; ++i) {
+    Side& s = g_sides[i];
+    if (s.side != nullptr && s.dev == dev && s.origin == origin) return &s;
+    if (s.side == nullptr) {
+      Side t;
+      t.dev = dev;
+      t.origin = origin;
+      if (cudaStreamCreateWithFlags(&t.side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(t.side);
+        return nullptr;
+      }
+      s = t;
+      return &s;
+    }
+  }
+  return nullptr;
+}
 
 // ---------------------------------------------------------- precision dispatch
 
@@ -445,14 +490,26 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
     DMD_TRY(optdmd_small(m, r, l, B, b.YB, b.T2, modal, info, opt->stats, *opt->opts, *opt->bufs, st));
     return tall.nn(n, l, r, b.Q1, b.ldY, opt->bufs->Mlift, PhiR, d.ldPhi, b.gemm_ws, st);
   }
-  // 8. modes Phi_R = X' M_R with M_R = V Sigma^{-1} W_R
+  // 8. modes Phi_R = X' M_R with M_R = V Sigma^{-1} W_R, and beside it (on a
+  // side stream: one SM against a pass over X') 9. the amplitudes
+  // min || (Q^T X') M_R beta - Q^T x_0 || (Eq. projection in the Q basis)
   DMD_TRY(dgemm(m, r, r, 1.0, b.Vs, m, false, b.WR, r, false, 0.0, b.MR, m, st));
-  DMD_TRY(tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st));
-  // 9. amplitudes: min || (Q^T X') M_R beta - Q^T x_0 ||  (Eq. projection in the Q basis)
   DMD_TRY(dgemm(l, r, r, 1.0, b.Tmp, l, false, b.WR, r, false, 0.0, b.LS, l, st));
   DMD_TRY(fit_glue_copy(l, b.P, b.rhs, st));
-  DMD_TRY(lstsq(l, r, b.LS, l, 1, b.rhs, l, modal + 2 * r, r, info, st));
-  return DMD_OK;
+  const Side* sd = side_of(st);
+  cudaStream_t ss = st;
+  if (sd) {
+    DMD_CUDA_TRY(cudaEventRecord(sd->fork, st));
+    DMD_CUDA_TRY(cudaStreamWaitEvent(sd->side, sd->fork, 0));
+    ss = sd->side;
+  }
+  const dmd_status ls = lstsq(l, r, b.LS, l, 1, b.rhs, l, modal + 2 * r, r, info, ss);
+  const dmd_status md = ls == DMD_OK ? tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st) : ls;
+  if (sd) {   // join even after a failure, so the caller's stream covers all queued work
+    DMD_CUDA_TRY(cudaEventRecord(sd->join, sd->side));
+    DMD_CUDA_TRY(cudaStreamWaitEvent(st, sd->join, 0));
+  }
+  return md;
 }
 
 // ------------------------------------------------------------ predict layout
@@ -842,10 +899,18 @@ dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, co
       if (want_grad)
         DMD_TRY(umma_loss_grad(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, target, w, delta, b.dC, b.partial,
                                &parts, b.gemm_ws, st));
-      else
-        DMD_TRY(umma_loss_nn(desc->n, desc->r, desc->K, Phi_R, desc->ldPhi, b.C, target, w, delta, b.partial, &parts,
-                             b.gemm_ws, st));
-      DMD_TRY(launch_sum_partials(parts, b.partial, loss, false, st));
+      if (want_grad) {
+        DMD_TRY(launch_sum_partials(parts, b.partial, loss, false, st));
+      } else {
+        // the loss kernel stages the frames' weights in shared memory: at
+        // most 4096 frames per launch
+        for (int j0 = 0; j0 < desc->K; j0 += 4096) {
+          const int nf = std::min(4096, desc->K - j0);
+          DMD_TRY(umma_loss_nn(desc->n, desc->r, nf, Phi_R, desc->ldPhi, b.C + (size_t)j0 * desc->r, target, w + j0,
+                               delta, b.partial, &parts, b.gemm_ws, st));
+          DMD_TRY(launch_sum_partials(parts, b.partial, loss, j0 > 0, st));
+        }
+      }
     } else {
       const int ch = std::min(chunk_of(*desc), desc->K);
       const int64_t ldF = round_up(desc->n, 32);

@@ -465,11 +465,28 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
         const Real sc = Real(1) / (x - beta);
         const Real v1 = y * sc, v2 = z * sc;
         const int c0 = max(lo, k - 1);
-        for (int c = c0 + lane; c <= hi; c += 32) {
-          const Real p = tau * (HH(k, c) + v1 * HH(k + 1, c) + v2 * HH(k + 2, c));
-          HH(k, c) -= p;
-          HH(k + 1, c) -= p * v1;
-          HH(k + 2, c) -= p * v2;
+        // row update, batched like the column update below: every lane loads
+        // its columns' three entries first so the shared-memory latencies
+        // overlap, then updates them
+        for (int cb = c0; cb <= hi; cb += 32 * kHqrT) {
+          Real r0[kHqrT], r1[kHqrT], r2[kHqrT];
+#pragma unroll
+          for (int t = 0; t < kHqrT; ++t) {
+            const int c = cb + lane + 32 * t;
+            r0[t] = c <= hi ? HH(k, c) : Real(0);
+            r1[t] = c <= hi ? HH(k + 1, c) : Real(0);
+            r2[t] = c <= hi ? HH(k + 2, c) : Real(0);
+          }
+#pragma unroll
+          for (int t = 0; t < kHqrT; ++t) {
+            const int c = cb + lane + 32 * t;
+            const Real p = tau * (r0[t] + v1 * r1[t] + v2 * r2[t]);
+            if (c <= hi) {
+              HH(k, c) = r0[t] - p;
+              HH(k + 1, c) = r1[t] - p * v1;
+              HH(k + 2, c) = r2[t] - p * v2;
+            }
+          }
         }
         __syncwarp();
         if (k > lo && lane == 0) {

@@ -459,6 +459,13 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     int sbuf = 0;
     bool ok = true;
     double lacc = 0.0;   // kLoss: this thread's (row's) loss
+    // kLoss: every frame's weight as FP32, zero past N, in the staging area
+    // (whole chunks; the loss launcher keeps nchunks * bn <= 4096)
+    float* wall = reinterpret_cast<float*>(stg);
+    if (kLoss) {
+      for (int j = threadIdx.x - 192; j < nchunks * bn; j += 128) wall[j] = j < N ? (float)wgt[j] : 0.f;
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+    }
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const int row0 = (int)(tile * 128) + q * 32;
       const bool row_ok = (int64_t)row0 + lane < n;
@@ -472,21 +479,25 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         tc_after();
         const int cend = min(bn, N - c * bn);   // the last chunk may be ragged
         if (kLoss) {
-          // this warp's copy of the chunk's weights (FP32) in its staging area
-          __syncwarp();
-          for (int j = lane; j < cend; j += 32) mystg[j] = (float)wgt[c * bn + j];
-          __syncwarp();
+          // 64 columns per round: four loads in flight, one wait; columns past
+          // the chunk's frames carry weight 0 and are selected away (their
+          // accumulator entries may hold anything)
+          const float* wc = wall + c * bn;
           float s = 0.f;
-          for (int c0 = 0; c0 < cend; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+          for (int c0 = 0; c0 < cend; c0 += 64) {
+            uint32_t v[64];
+            const uint32_t ta = tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16);
+            tmem_ld16_nw(ta, v);
+            tmem_ld16_nw(ta + 16u, v + 16);
+            tmem_ld16_nw(ta + 32u, v + 32);
+            tmem_ld16_nw(ta + 48u, v + 48);
+            tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (c0 + j < cend) {
-                const float e = v[j] - tv, ae = fabsf(e);
-                const float rho = (delta > 0.f && ae > delta) ? delta * (ae - 0.5f * delta) : 0.5f * e * e;
-                s = fmaf(mystg[c0 + j], rho, s);
-              }
+            for (int j = 0; j < 64; ++j) {
+              const float e = __uint_as_float(v[j]) - tv, ae = fabsf(e);
+              const float rho = (delta > 0.f && ae > delta) ? delta * (ae - 0.5f * delta) : 0.5f * e * e;
+              const float t = wc[c0 + j] * rho;
+              s += (c0 + j < cend) ? t : 0.f;
             }
           }
           if (row_ok) lacc += (double)s;
@@ -971,10 +982,19 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
                         const double* w, float delta, double* part, int* parts, void* ws, cudaStream_t st) {
   const int ksteps = (int)ceil_div(Kd, 16);
   const int64_t ntiles = ceil_div(n, 128);
-  const AresCfg cfg = ares_cfg(ksteps);
+  // 128-frame chunks (the epilogue drains 64 columns per round), the
+  // deepest rings that fit
+  AresCfg cfg = {0, 0, 0};
+  for (int nb = 3; nb >= 2 && cfg.bn == 0; --nb)
+    for (int sa = 3; sa >= 2 && cfg.bn == 0; --sa)
+      if (ares_smem(ksteps, 128, sa, nb) <= (size_t)kMaxSmem) cfg = {128, sa, nb};
   const int bn = cfg.bn;
-  if (bn == 0 || ksteps > AR_MAXKS || ares_smem(ksteps, bn, cfg.sa, cfg.nb) > (size_t)kMaxSmem) {
+  if (bn == 0 || ksteps > AR_MAXKS) {
     set_error("umma_loss_nn: inner dimension %d too large for the resident-A layout", Kd);
+    return DMD_EINVAL;
+  }
+  if (ceil_div(N, bn) * bn > 4096) {
+    set_error("umma_loss_nn: %d frames in one call (at most 4096: the weights are staged in shared memory)", N);
     return DMD_EINVAL;
   }
   CUtensorMap mapA;

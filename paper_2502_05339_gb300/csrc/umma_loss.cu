@@ -55,7 +55,7 @@ namespace {
 
 constexpr int LG_THREADS = 320;
 constexpr int LG_MAXKS = 10;      // r <= 160
-constexpr int LG_RING = 4;        // TMA stages of FP32 Phi slices (8 KB each)
+constexpr int LG_RING = 7;        // TMA stages of FP32 Phi slices (8 KB each): as many as fit
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
 constexpr uint32_t LG_COL_D = 160, LG_COL_DC = 288, LG_COL_GLO = 448;
 
@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
       uint32_t it = 0;
-      bool issued[LG_RING] = {false, false, false, false};
-      uint32_t par[LG_RING] = {0, 0, 0, 0};
+      bool issued[LG_RING];
+      uint32_t par[LG_RING];
+      for (int i = 0; i < LG_RING; ++i) issued[i] = false, par[i] = 0;
       bool ok = true;
       for (int g = 0; ok && g < ngroups; ++g)
         for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)

@@ -30,3 +30,19 @@ def test_reconstruction_roofline_counts_phi_once_and_frames():
 def test_whole_job_rate_is_weak_scaling_aggregate():
     assert bench.whole_job_rate(1000.0, 0.5, 1) == pytest.approx(2000.0)
     assert bench.whole_job_rate(1000.0, 0.5, 4) == pytest.approx(8000.0)
+
+
+def test_profiling_case_helpers_resolve():
+    """Every helper the --case dispatcher calls is defined at module level."""
+    import ast
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")).read()
+    tree = ast.parse(src)
+    defined = {n.name for n in tree.body if isinstance(n, ast.FunctionDef)}
+    called = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.FunctionDef) and node.name in ("run_case", "_case_model"):
+            for sub in ast.walk(node):
+                if isinstance(sub, ast.Call) and isinstance(sub.func, ast.Name) and sub.func.id.startswith("_case"):
+                    called.add(sub.func.id)
+    assert called and called <= defined, called - defined
