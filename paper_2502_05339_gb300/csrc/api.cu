@@ -36,7 +36,7 @@ dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, co
 dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st);
 size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N);
 dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C,
-                        int64_t ldc, void* ws, cudaStream_t st);
+                        int64_t ldc, void* ws, cudaStream_t st, int spare_sms);
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                         double* C, int nsplit, void* ws, cudaStream_t st);
@@ -172,8 +172,8 @@ struct Tall {
     return tn_partial_doubles(n, Ka, N) * sizeof(double) + 256;
   }
   dmd_status nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
-                void* ws, cudaStream_t st) const {
-    if (nn_tensor(Kd)) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+                void* ws, cudaStream_t st, int spare_sms = 0) const {
+    if (nn_tensor(Kd)) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, spare_sms);
     float* B32 = reinterpret_cast<float*>(ws);
     DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st));
     return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st);
@@ -504,7 +504,7 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
     ss = sd->side;
   }
   const dmd_status ls = lstsq(l, r, b.LS, l, 1, b.rhs, l, modal + 2 * r, r, info, ss);
-  const dmd_status md = ls == DMD_OK ? tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st) : ls;
+  const dmd_status md = ls == DMD_OK ? tall.nn(n, m, r, Xp, d.ldS, b.MR, PhiR, d.ldPhi, b.gemm_ws, st, sd ? 1 : 0) : ls;
   if (sd) {   // join even after a failure, so the caller's stream covers all queued work
     DMD_CUDA_TRY(cudaEventRecord(sd->join, sd->side));
     DMD_CUDA_TRY(cudaStreamWaitEvent(st, sd->join, 0));

@@ -1752,6 +1752,10 @@ static size_t square_smem(int rows, int cols, size_t extra) {
   return ((size_t)(rows | 1) * cols + extra) * sizeof(double);
 }
 
+bool householder_cluster_fits(int n);
+dmd_status hessenberg_cluster(int n, double* A, int ld, double* tau, cudaStream_t st);
+dmd_status sytrd_cluster(int n, double* A, int ld, double* tau, cudaStream_t st);
+
 static dmd_status set_smem(const void* fn, size_t bytes) {
   DMD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return DMD_OK;
@@ -1813,6 +1817,7 @@ dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* inf
 }
 
 dmd_status hessenberg(int n, double* A, int ld, double* tau, cudaStream_t st) {
+  if (householder_cluster_fits(n)) return hessenberg_cluster(n, A, ld, tau, st);
   const size_t smem_s = square_smem(n, n, 2 * (size_t)n + 32);
   if (smem_s <= kSmallSmemMax) {
     DMD_TRY(set_smem((const void*)k_hessenberg_smem, smem_s));
@@ -1891,6 +1896,7 @@ dmd_status eig_layout(int n, const double* wr, const double* wi, const int* head
 }
 
 dmd_status sytrd(int n, double* A, int ld, double* tau, cudaStream_t st) {
+  if (householder_cluster_fits(n)) return sytrd_cluster(n, A, ld, tau, st);
   const size_t smem_s = square_smem(n, n, 2 * (size_t)n + 32);
   if (smem_s <= kSmallSmemMax) {
     DMD_TRY(set_smem((const void*)k_sytrd_smem, smem_s));

@@ -931,7 +931,7 @@ size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N) {
 }
 
 dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
-                        void* ws, cudaStream_t st) {
+                        void* ws, cudaStream_t st, int spare_sms) {
   if (n <= 0 || N <= 0) return DMD_OK;
   const int ksteps = (int)ceil_div(Kd, 16);
   const int64_t ntiles = ceil_div(n, 128);
@@ -939,7 +939,9 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   CUtensorMap mapA;
   DMD_TRY(make_map(&mapA, A, n, Kd, lda, 128, 16));
   const int Npmax = bres_cols(ksteps);
-  const int grid = (int)std::min<int64_t>(num_sms(), ntiles);
+  // persistent CTAs, one per SM; `spare_sms` SMs are left to work running
+  // beside this product on another stream
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms() - spare_sms, ntiles));
   if (N <= 256 && round_up(N, 16) <= Npmax) {
     const int Np = (int)round_up(N, 16);
     const int64_t work = (int64_t)Np * ksteps;
@@ -1038,10 +1040,10 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
       for (int sa = 2; sa <= 3 && status == DMD_OK; ++sa) {
         if (ares_smem(ksteps, bn, sa, nb) > (size_t)kMaxSmem) continue;
         g_ares_override = {bn, sa, nb};
-        status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+        status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0);
         if (status != DMD_OK) break;
         if (cudaEventRecord(e0, st) != cudaSuccess) status = DMD_ECUDA;
-        for (int r = 0; r < 2 && status == DMD_OK; ++r) status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st);
+        for (int r = 0; r < 2 && status == DMD_OK; ++r) status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0);
         if (status != DMD_OK) break;
         float ms = 0.f;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

@@ -20,18 +20,24 @@
 // accumulation).  dC_g^T is drained into a per-CTA FP64 partial every 32 tiles
 // (4096 rows) and at the end of the group; the partials are summed over CTAs
 // in a fixed order afterwards, so the result is deterministic.  Phi_R is read
-// once per frame group (its tile is loaded twice in a row, the second time
-// from L2, to be split into the two shared-memory layouts the two products
-// need), the coefficient group once per CTA.
+// once per frame group, the coefficient group once per CTA.
+//
+// One bf16 copy of the tile (hi and lo planes) serves both products: core
+// matrices of 8 rows x 8 modes (16-byte rows of 8 consecutive modes), at
+// (row / 8) * RS + (mode / 8) * 128 bytes with RS = 256 ks.  The forward
+// product reads it as its B operand K-major (N = rows, K = modes: K-adjacent
+// cores 128 B apart, 8-row groups RS apart), the backward product as its B
+// operand MN-major (N = modes, K = rows: K-adjacent cores RS apart, 8-mode
+// groups 128 B apart).  The copy is double-buffered, so converting the next
+// tile overlaps the current tile's products.
 //
 // Tensor memory (512 columns x 128 lanes, lane = frame of the group):
 //   [0, 16 ks)            C_g^T as the A operand (bf16 hi, then lo; ks = K-slices of r)
 //   [160, 288)            D, then G hi (8 row slices x 8 columns)
 //   [288, 288 + 16 ks)    dC_g^T accumulator (FP32, r padded to 16 ks columns)
 //   [448, 512)            G lo
-// Shared memory: a TMA ring of FP32 Phi slices (128 rows x 16 modes), Phi_tile
-// as the fwd B operand (N = rows, K = modes) and as the bwd B operand (N =
-// modes, K = rows), both K-major without swizzle, and the tile's targets.
+// Shared memory: a TMA ring of FP32 Phi slices (128 rows x 16 modes), the two
+// tile copies and the tile's targets.
 //
 // Roles (10 warps): 0 TMA producer, 1 MMA issuer, 2-5 converters (FP32 slice
 // -> bf16 planes), 6-9 epilogue (frame = TMEM lane).  Every wait is bounded
@@ -81,6 +87,19 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Row t's 16 modes of slice s, split into bf16 hi / lo, into the tile copy
+// (planes `hi` and `lo`, 8-row groups RS bytes apart).
+__device__ __forceinline__ void store_tile_row(const float* x, uint8_t* hi, uint8_t* lo, int t, int s, uint32_t RS) {
+  const uint32_t off = (uint32_t)(t >> 3) * RS + (uint32_t)s * 256u + (uint32_t)(t & 7) * 16u;
+  uint4 h0, l0, h1, l1;
+  split8(x, h0, l0);
+  split8(x + 8, h1, l1);
+  *reinterpret_cast<uint4*>(hi + off) = h0;
+  *reinterpret_cast<uint4*>(hi + off + 128) = h1;
+  *reinterpret_cast<uint4*>(lo + off) = l0;
+  *reinterpret_cast<uint4*>(lo + off + 128) = l1;
+}
+
 __global__ void __launch_bounds__(LG_THREADS, 1)
     k_umma_loss_grad(const __grid_constant__ CUtensorMap tmPhi, int64_t n, int r, int K, int ks,
                      const double* __restrict__ C, const float* __restrict__ tgt, const double* __restrict__ wgt,
@@ -89,22 +108,19 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const int Np = 16 * ks;                                    // r padded to the K-slices
-  const uint32_t fwd_plane = (uint32_t)ks * 4096u;           // ks slices x 128 rows x 32 B
-  const uint32_t bwd_slice = (uint32_t)Np * 32u;             // one 16-row K-slice, Np modes
-  const uint32_t bwd_plane = 8u * bwd_slice;
+  const uint32_t RS = (uint32_t)ks * 256u;                   // one 8-row group of the tile copy
+  const uint32_t plane = 16u * RS;                           // 128 rows x 16 ks modes x 2 bytes
   uint8_t* ring = sm;                                        // LG_RING x 8 KB
-  uint8_t* phif = ring + LG_RING * 8192;                     // fwd B: hi plane, lo plane
-  uint8_t* phib = phif + 2 * fwd_plane;                      // bwd B: hi plane, lo plane
-  float* tgs = reinterpret_cast<float*>(phib + 2 * bwd_plane);   // 4 warps x 128 targets
+  uint8_t* phi = ring + LG_RING * 8192;                      // 2 buffers x (hi plane, lo plane)
+  float* tgs = reinterpret_cast<float*>(phi + 4 * plane);    // 4 warps x 128 targets
   uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 4 * 128);
   uint64_t* full = bars;                          // [LG_RING] slice landed
   uint64_t* empty = full + LG_RING;               // [LG_RING] slice converted
-  uint64_t* fwd_full = empty + LG_RING;           // [LG_MAXKS] fwd B slice s of the tile ready
-  uint64_t* bwd_full = fwd_full + LG_MAXKS;       // whole bwd B of the tile ready
-  uint64_t* fwd_done = bwd_full + 1;              // fwd MMAs of the tile finished
+  uint64_t* phi_full = empty + LG_RING;           // [2][LG_MAXKS] slice s of buffer b converted
+  uint64_t* bwd_done = phi_full + 2 * LG_MAXKS;   // [2] the products reading buffer b finished
+  uint64_t* fwd_done = bwd_done + 2;              // fwd MMAs of the tile finished
   uint64_t* g_full = fwd_done + 1;                // G of the tile in TMEM
-  uint64_t* bwd_done = g_full + 1;                // bwd MMAs of the tile finished
-  uint64_t* ct_full = bwd_done + 1;               // C_g^T of the group in TMEM
+  uint64_t* ct_full = g_full + 1;                 // C_g^T of the group in TMEM
   uint64_t* dc_full = ct_full + 1;                // dC^T ready to drain
   uint64_t* dc_free = dc_full + 1;                // dC^T drained
   uint64_t* tdown = dc_free + 1;
@@ -118,11 +134,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 128);
     }
-    for (int i = 0; i < LG_MAXKS; ++i) mbar_init(&fwd_full[i], 128);
-    mbar_init(bwd_full, 128);
+    for (int i = 0; i < 2 * LG_MAXKS; ++i) mbar_init(&phi_full[i], 128);
+    mbar_init(&bwd_done[0], 1);
+    mbar_init(&bwd_done[1], 1);
     mbar_init(fwd_done, 1);
     mbar_init(g_full, 128);
-    mbar_init(bwd_done, 1);
     mbar_init(ct_full, 128);
     mbar_init(dc_full, 1);
     mbar_init(dc_free, 128);
@@ -136,7 +152,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   tc_after();
   const uint32_t tmem = *tslot;
   const int ngroups = (K + 127) / 128;
-  // flushes per group: after every LG_FLUSH tiles and after the group's last tile
+  // drains per group: after every LG_FLUSH tiles and after the group's last tile
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (warp == 0) {
@@ -149,27 +165,25 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       bool ok = true;
       for (int g = 0; ok && g < ngroups; ++g)
         for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)
-          for (int pass = 0; ok && pass < 2; ++pass)
-            for (int s = 0; s < ks; ++s, ++it) {
-              const uint32_t st = it % LG_RING;
-              if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
-                ok = false;
-                break;
-              }
-              mbar_expect_tx(&full[st], 8192);
-              tma_load_2d(ring + st * 8192, &tmPhi, &full[st], (int)(tile * 128), s * 16);
-              issued[st] = true;
-              par[st] = (it / LG_RING) & 1;
+          for (int s = 0; s < ks; ++s, ++it) {
+            const uint32_t st = it % LG_RING;
+            if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
+              ok = false;
+              break;
             }
+            mbar_expect_tx(&full[st], 8192);
+            tma_load_2d(ring + st * 8192, &tmPhi, &full[st], (int)(tile * 128), s * 16);
+            issued[st] = true;
+            par[st] = (it / LG_RING) & 1;
+          }
       for (int i = 0; i < LG_RING; ++i)
         if (issued[i]) mbar_wait_drain(&full[i], par[i]);
     }
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id_fwd = idesc_bf16(128, 128), id_bwd = idesc_bf16(128, Np);
-      const uint64_t f0 = sdesc(su32(phif), kLBO, kSBO), b0 = sdesc(su32(phib), kLBO, kSBO);
-      const uint64_t f_lo = fwd_plane >> 4, b_lo = bwd_plane >> 4;
+      const uint32_t id_fwd = idesc_bf16(128, 128);
+      const uint32_t id_bwd = idesc_bf16(128, Np) | (1u << 16);   // B operand MN-major
       const uint32_t ct_lo = (uint32_t)ks * 8u;
       uint32_t tit = 0, fl = 0;
       bool ok = true;
@@ -179,20 +193,23 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         int64_t j = 0;
         bool fresh = true;
         for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit, ++j) {
+          const uint32_t b = tit & 1, use = tit >> 1;
+          uint8_t* hi = phi + b * 2 * plane;
           // D / G hi must be free: the previous tile's bwd MMAs have read G
-          if (tit > 0 && !mbar_wait(bwd_done, (tit - 1) & 1, abort_flag)) {
+          if (tit > 0 && !mbar_wait(&bwd_done[(tit - 1) & 1], ((tit - 1) >> 1) & 1, abort_flag)) {
             ok = false;
             break;
           }
           tc_after();
+          const uint64_t f0 = sdesc(su32(hi), 128u, RS), f_lo = plane >> 4;
           for (int s = 0; s < ks; ++s) {
-            if (!mbar_wait(&fwd_full[s], tit & 1, abort_flag)) {
+            if (!mbar_wait(&phi_full[b * LG_MAXKS + s], use & 1, abort_flag)) {
               ok = false;
               break;
             }
             tc_after();
             const uint32_t ah = tmem + (uint32_t)s * 8u, al = ah + ct_lo;
-            const uint64_t bh = f0 + (uint64_t)((uint32_t)s * 256u), bl = bh + f_lo;
+            const uint64_t bh = f0 + (uint64_t)((uint32_t)s * 16u), bl = bh + f_lo;
             const uint32_t d = tmem + LG_COL_D;
             umma_bf16_ta(d, ah, bh, id_fwd, s > 0 ? 1u : 0u);
             umma_bf16_ta(d, ah, bl, id_fwd, 1u);
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
           }
           if (!ok) break;
           umma_commit(fwd_done);
-          if (!mbar_wait(g_full, tit & 1, abort_flag) || !mbar_wait(bwd_full, tit & 1, abort_flag)) {
+          if (!mbar_wait(g_full, tit & 1, abort_flag)) {
             ok = false;
             break;
           }
@@ -213,15 +230,16 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
             tc_after();
           }
           const uint32_t dc = tmem + LG_COL_DC;
+          const uint64_t b0 = sdesc(su32(hi), RS, 128u);   // MN-major: LBO along K (rows), SBO along N (modes)
           for (int s = 0; s < 8; ++s) {
             const uint32_t gh = tmem + LG_COL_D + (uint32_t)s * 8u, gl = tmem + LG_COL_GLO + (uint32_t)s * 8u;
-            const uint64_t bh = b0 + (uint64_t)(((uint32_t)s * bwd_slice) >> 4), bl = bh + b_lo;
+            const uint64_t bh = b0 + (uint64_t)((2u * (uint32_t)s * RS) >> 4), bl = bh + f_lo;
             umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
             umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
             umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
           }
           fresh = false;
-          umma_commit(bwd_done);
+          umma_commit(&bwd_done[b]);
           if ((j + 1) % LG_FLUSH == 0 || j + 1 == my_tiles) {
             umma_commit(dc_full);
             ++fl;
@@ -234,16 +252,18 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------- converters
-    const int t = threadIdx.x - 64;   // 0..127
+    const int t = threadIdx.x - 64;   // 0..127: row of the tile
     uint32_t it = 0, tit = 0;
     bool ok = true;
     for (int g = 0; ok && g < ngroups; ++g) {
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
-        // fwd B copy free once the previous tile's fwd MMAs are done
-        if (tit > 0 && !mbar_wait(fwd_done, (tit - 1) & 1, abort_flag)) {
+        const uint32_t b = tit & 1;
+        // buffer b is free once the products of the tile two back are done
+        if (tit >= 2 && !mbar_wait(&bwd_done[b], ((tit >> 1) - 1) & 1, abort_flag)) {
           ok = false;
           break;
         }
+        uint8_t* hi = phi + b * 2 * plane;
         for (int s = 0; s < ks; ++s, ++it) {
           const uint32_t st = it % LG_RING;
           if (!mbar_wait(&full[st], (it / LG_RING) & 1, abort_flag)) {
@@ -254,44 +274,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
           float x[16];
 #pragma unroll
           for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];   // row t, modes 16 s + c
-          uint8_t* hi = phif + (uint32_t)s * 4096u;
-          split_store_row(x, hi, hi + fwd_plane, t);
+          store_tile_row(x, hi, hi + plane, t, s, RS);
           fence_async_smem();
           mbar_arrive(&empty[st]);
-          mbar_arrive(&fwd_full[s]);
+          mbar_arrive(&phi_full[b * LG_MAXKS + s]);
         }
-        if (!ok) break;
-        // bwd B copy free once the previous tile's bwd MMAs are done
-        if (tit > 0 && !mbar_wait(bwd_done, (tit - 1) & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        for (int s = 0; s < ks; ++s, ++it) {
-          const uint32_t st = it % LG_RING;
-          if (!mbar_wait(&full[st], (it / LG_RING) & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          const float* src = reinterpret_cast<const float*>(ring + st * 8192);
-          // 16 modes x 16 groups of 8 rows: unit u = mode (u >> 4), row group (u & 15)
-#pragma unroll
-          for (int k2 = 0; k2 < 2; ++k2) {
-            const int u = t + 128 * k2;
-            const int jm = u >> 4, rg = u & 15;
-            const float4 a = *reinterpret_cast<const float4*>(src + jm * 128 + rg * 8);
-            const float4 b = *reinterpret_cast<const float4*>(src + jm * 128 + rg * 8 + 4);
-            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            uint4 h, l;
-            split8(x, h, l);
-            const uint32_t off = (uint32_t)(rg >> 1) * bwd_slice + kslice_off(s * 16 + jm, rg & 1);
-            *reinterpret_cast<uint4*>(phib + off) = h;
-            *reinterpret_cast<uint4*>(phib + bwd_plane + off) = l;
-          }
-          fence_async_smem();
-          mbar_arrive(&empty[st]);
-        }
-        if (!ok) break;
-        mbar_arrive(bwd_full);
       }
     }
   } else {
@@ -345,30 +332,36 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         }
         tc_after();
         float s_loss = 0.f;
-        for (int s = 0; s < 8; ++s) {
-          float v[16];
-          tmem_ld16(tmem + LG_COL_D + (uint32_t)s * 16u + lane_base, v);
-          uint32_t h[8], l[8];
+        for (int s2 = 0; s2 < 8; s2 += 2) {
+          uint32_t v[32];
+          tmem_ld16_nw(tmem + LG_COL_D + (uint32_t)s2 * 16u + lane_base, v);
+          tmem_ld16_nw(tmem + LG_COL_D + (uint32_t)(s2 + 1) * 16u + lane_base, v + 16);
+          tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float gv[2];
+          for (int half = 0; half < 2; ++half) {
+            const int s = s2 + half;
+            uint32_t h[8], l[8];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int tr = s * 16 + 2 * i + u;
-              const float e = v[2 * i + u] - tg[tr];
-              const bool live = f_ok && tr < rows;
-              s_loss += live ? w * rho_of(e, delta) : 0.f;
-              gv[u] = live ? w * drho_of(e, delta) : 0.f;
+            for (int i = 0; i < 8; ++i) {
+              float gv[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int tr = s * 16 + 2 * i + u;
+                const float e = __uint_as_float(v[half * 16 + 2 * i + u]) - tg[tr];
+                const bool live = f_ok && tr < rows;
+                s_loss += live ? w * rho_of(e, delta) : 0.f;
+                gv[u] = live ? w * drho_of(e, delta) : 0.f;
+              }
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(gv[0]), h1 = __float2bfloat16_rn(gv[1]);
+              h[i] = pack2(h0, h1);
+              l[i] = pack2(__float2bfloat16_rn(gv[0] - __bfloat162float(h0)),
+                           __float2bfloat16_rn(gv[1] - __bfloat162float(h1)));
             }
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(gv[0]), h1 = __float2bfloat16_rn(gv[1]);
-            h[i] = pack2(h0, h1);
-            l[i] = pack2(__float2bfloat16_rn(gv[0] - __bfloat162float(h0)),
-                         __float2bfloat16_rn(gv[1] - __bfloat162float(h1)));
+            // G hi of rows 16 s .. 16 s + 15 overwrites D columns 8 s .. 8 s + 7,
+            // which this thread has already loaded (slices s / 2 <= s)
+            tmem_st8(tmem + LG_COL_D + (uint32_t)s * 8u + lane_base, h);
+            tmem_st8(tmem + LG_COL_GLO + (uint32_t)s * 8u + lane_base, l);
           }
-          // G hi of rows 16 s .. 16 s + 15 overwrites D columns 8 s .. 8 s + 7,
-          // which this thread has already loaded (slices s / 2 <= s)
-          tmem_st8(tmem + LG_COL_D + (uint32_t)s * 8u + lane_base, h);
-          tmem_st8(tmem + LG_COL_GLO + (uint32_t)s * 8u + lane_base, l);
         }
         lacc += (double)s_loss;
         tmem_st_wait();
@@ -423,8 +416,7 @@ __global__ void k_reduce_dc(int64_t count, int parts, const double* __restrict__
 }
 
 size_t lg_smem(int ks) {
-  const size_t Np = 16 * (size_t)ks;
-  return 1024 + (size_t)LG_RING * 8192 + 2 * (size_t)ks * 4096 + 2 * 8 * Np * 32 + 4 * 128 * 4 + 512;
+  return 1024 + (size_t)LG_RING * 8192 + 4 * 16 * (size_t)ks * 256 + 4 * 128 * 4 + 512;
 }
 
 int lg_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(n, 128))); }
