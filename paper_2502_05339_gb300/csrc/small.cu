@@ -1753,6 +1753,9 @@ static size_t square_smem(int rows, int cols, size_t extra) {
 }
 
 bool householder_cluster_fits(int n);
+bool cholesky_cluster_fits(int n);
+dmd_status cholesky_cluster(int n, double* G, int ld, double tau, int32_t* info, int tag, bool fp32,
+                            const int32_t* skip, cudaStream_t st);
 dmd_status hessenberg_cluster(int n, double* A, int ld, double* tau, cudaStream_t st);
 dmd_status sytrd_cluster(int n, double* A, int ld, double* tau, cudaStream_t st);
 
@@ -1763,6 +1766,7 @@ static dmd_status set_smem(const void* fn, size_t bytes) {
 
 dmd_status cholesky_upper_gated(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
                                 cudaStream_t st) {
+  if (cholesky_cluster_fits(n)) return cholesky_cluster(n, G, ld, tau, info, tag, false, skip, st);
   const size_t smem = square_smem(n, n, (size_t)n + 32);
   if (smem <= kSmallSmemMax) {
     DMD_TRY(set_smem((const void*)k_cholesky_smem, smem));
@@ -1808,6 +1812,7 @@ dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cu
 }
 
 dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
+  if (cholesky_cluster_fits(n)) return cholesky_cluster(n, G, ld, tau, info, tag, true, nullptr, st);
   const size_t smem = ((size_t)(n | 1) * n + n) * sizeof(float);
   if (smem > kSmallSmemMax) return cholesky_upper(n, G, ld, tau, info, tag, st);
   DMD_TRY(set_smem((const void*)k_cholesky_f32, smem));

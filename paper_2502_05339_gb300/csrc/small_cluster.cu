@@ -253,4 +253,168 @@ dmd_status sytrd_cluster(int n, double* A, int ld, double* tau, cudaStream_t st)
   return DMD_OK;
 }
 
+// ----------------------------------------------------------------- Cholesky
+//
+// G (n x n, ld; upper triangle read) -> upper R with R^T R = G, strict lower
+// part zeroed; the pivot rule of the one-CTA kernels: a pivot not above
+// tau * max_i G_ii drops its direction (row j of R is zero, counted in
+// info[5]); a non-finite pivot is DMD_ENONFINITE and an all-zero diagonal
+// DMD_ENUMERIC (the factorisation then stops and leaves G as it is).
+// Column b is owned by CTA b % CL.  Step j of the right-looking
+// factorisation needs row j of the current matrix and pivot j; both are
+// broadcast at the end of step j - 1 (each CTA sends its updated entries of
+// row j, the owner of column j its pivot decision), so every step has one
+// cluster barrier.  Real = double, or float for the near-identity Grams of
+// the second CholeskyQR pass (input and output stay FP64).
+namespace {
+
+template <class Real>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CL_THREADS)
+    k_cholesky_cl(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* __restrict__ skip) {
+  // a device-side flag (iterative callers stop without a host round trip):
+  // every CTA of the cluster reads the same value, before any barrier
+  if (skip != nullptr && *skip != 0) return;
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int ldw = n | 1, ncl = (n + CL - 1) / CL;
+  extern __shared__ __align__(16) unsigned char smc[];
+  Real* S = reinterpret_cast<Real*>(smc);                 // n x ncl (rows 0..b of local column b)
+  Real* rowb = S + (size_t)ldw * ncl;                     // [2][n] row j of the current matrix
+  const size_t pb_off = ((((size_t)ldw * ncl + 2 * (size_t)n) * sizeof(Real)) + 15) & ~(size_t)15;
+  double* pb = reinterpret_cast<double*>(smc + pb_off);   // [2][4]: piv, ipiv, state
+  double* dm = pb + 8;                                    // [CL] per-CTA max of the diagonal
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  // load the upper triangle of the local columns; this CTA's largest diagonal entry
+  for (int jl = warp; c + CL * jl < n; jl += nw) {
+    const int b = c + CL * jl;
+    for (int a = lane; a <= b; a += 32) S[a + jl * ldw] = (Real)G[a + (int64_t)b * ld];
+  }
+  __shared__ double red[32];
+  double loc = 0.0;
+  for (int jl = tid; c + CL * jl < n; jl += bd) {
+    const double d = G[(c + CL * jl) + (int64_t)(c + CL * jl) * ld];
+    loc = (isfinite(loc) && isfinite(d)) ? fmax(loc, d) : (double)NAN;
+  }
+  // fmax drops NaN: carry non-finite diagonals explicitly
+  {
+    double v = loc;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = (isfinite(v) && isfinite(u)) ? fmax(v, u) : (double)NAN;
+    }
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = red[0];
+      for (int i = 1; i < nw; ++i) t = (isfinite(t) && isfinite(red[i])) ? fmax(t, red[i]) : (double)NAN;
+      for (int r = 0; r < CL; ++r) cl.map_shared_rank(dm, r)[c] = t;
+    }
+  }
+  __syncthreads();
+  cl.sync();
+  double dmax = dm[0];
+  for (int r = 1; r < CL; ++r) dmax = (isfinite(dmax) && isfinite(dm[r])) ? fmax(dmax, dm[r]) : (double)NAN;
+  const double floor_ = tau * dmax;
+
+  // pivot decision of column j (by its owner, single thread): state 0 take,
+  // 1 drop, 2 stop.  Broadcast with row j's entries of the owner.
+  auto decide = [&](int j, int buf) {
+    const double d = (double)S[j + (j / CL) * ldw];
+    double piv = 0.0, ipiv = 0.0, state = 0.0;
+    if (!isfinite(d) || !isfinite(dmax)) {
+      raise_status(info, DMD_ENONFINITE, tag * 1000 + j);
+      state = 2.0;
+    } else if (!(dmax > 0.0)) {
+      raise_status(info, DMD_ENUMERIC, tag * 1000 + j);
+      state = 2.0;
+    } else if (!(d > floor_)) {
+      state = 1.0;
+      if (info) atomicAdd(&info[5], 1);
+    } else {
+      ipiv = rsqrt(d);
+      piv = d * ipiv;
+    }
+    for (int r = 0; r < CL; ++r) {
+      double* p = cl.map_shared_rank(pb, r) + 4 * buf;
+      p[0] = piv;
+      p[1] = ipiv;
+      p[2] = state;
+    }
+  };
+  // broadcast this CTA's entries of row j (columns b >= j)
+  auto send_row = [&](int j, int buf) {
+    for (int jl = first_local(j, c) + tid; jl < ncl && c + CL * jl < n; jl += bd) {
+      const Real v = S[j + jl * ldw];
+      for (int r = 0; r < CL; ++r) cl.map_shared_rank(rowb, r)[buf * n + c + CL * jl] = v;
+    }
+  };
+  if (n > 0) {
+    send_row(0, 0);
+    if (c == 0 && tid == 0) decide(0, 0);
+  }
+  cl.sync();
+  bool stopped = false;
+  for (int j = 0; j < n; ++j) {
+    const int buf = j & 1;
+    const double* p = pb + 4 * buf;
+    if (p[2] == 2.0) {
+      stopped = true;
+      break;
+    }
+    const bool take = p[2] == 0.0;
+    const Real ip = (Real)p[1];
+    const Real* row = rowb + buf * n;
+    const int j0 = first_local(j + 1, c);
+    // R's row j in the local columns, and the owner's diagonal entry
+    if (c == j % CL && tid == 0) S[j + (j / CL) * ldw] = (Real)p[0];
+    for (int jl = j0 + tid; jl < ncl && c + CL * jl < n; jl += bd)
+      S[j + jl * ldw] = take ? row[c + CL * jl] * ip : Real(0);
+    // trailing update S[a, b] -= r_a r_b, j < a <= b, for the local columns b
+    if (take) {
+      for (int jl = j0 + warp; jl < ncl && c + CL * jl < n; jl += nw) {
+        const int b = c + CL * jl;
+        const Real rb = row[b] * ip;
+        Real* col = S + jl * ldw;
+        for (int a = j + 1 + lane; a <= b; a += 32) col[a] -= (row[a] * ip) * rb;
+      }
+    }
+    __syncthreads();
+    if (j + 1 < n) {
+      send_row(j + 1, buf ^ 1);
+      if (c == (j + 1) % CL && tid == 0) decide(j + 1, buf ^ 1);
+    }
+    cl.sync();
+  }
+  if (!stopped) {
+    for (int jl = warp; c + CL * jl < n; jl += nw) {
+      const int b = c + CL * jl;
+      for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = a <= b ? (double)S[a + jl * ldw] : 0.0;
+    }
+  }
+  cl.sync();
+}
+
+template <class Real>
+dmd_status cholesky_cluster_t(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
+                              cudaStream_t st) {
+  const int ncl = (n + CL - 1) / CL;
+  const size_t pb_off = ((((size_t)(n | 1) * ncl + 2 * (size_t)n) * sizeof(Real)) + 15) & ~(size_t)15;
+  const size_t smem = pb_off + (8 + CL) * sizeof(double);
+  if (smem > 48 * 1024)
+    DMD_CUDA_TRY(cudaFuncSetAttribute(k_cholesky_cl<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_cholesky_cl<Real><<<CL, CL_THREADS, smem, st>>>(n, G, ld, tau, info, tag, skip);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+}  // namespace
+
+bool cholesky_cluster_fits(int n) { return n >= 32 && n <= 512; }
+
+dmd_status cholesky_cluster(int n, double* G, int ld, double tau, int32_t* info, int tag, bool fp32,
+                            const int32_t* skip, cudaStream_t st) {
+  return fp32 ? cholesky_cluster_t<float>(n, G, ld, tau, info, tag, skip, st)
+              : cholesky_cluster_t<double>(n, G, ld, tau, info, tag, skip, st);
+}
+
 }  // namespace dmd

@@ -13,14 +13,17 @@
 // its 128-row tiles of Phi_R and for each tile:
 //   fwd   D (128 frames x 128 rows) = C_g^T Phi_tile^T        (tensor memory)
 //   epi   one thread per frame: e = x - t, loss += w rho(e), g = w rho'(e),
-//         g split into bf16 hi / lo and written back into tensor memory as
-//         the A operand of the next product
+//         g split into bf16 hi / lo and written back into tensor memory over
+//         D as the A operand of the next product
 //   bwd   dC_g^T (128 frames x r) += G^T Phi_tile                (tensor memory)
 // with every product in the BF16x3 form (hi*hi + hi*lo + lo*hi, FP32
-// accumulation).  dC_g^T is drained into a per-CTA FP64 partial every 32 tiles
-// (4096 rows) and at the end of the group; the partials are summed over CTAs
-// in a fixed order afterwards, so the result is deterministic.  Phi_R is read
-// once per frame group, the coefficient group once per CTA.
+// accumulation).  D / G is double-buffered and the MMA thread issues
+// fwd(t + 1) before bwd(t), so the tensor pipe works on the next tile while
+// the epilogue turns the current one into G.  dC_g^T is drained into a
+// per-CTA FP64 partial every 32 tiles (4096 rows) and at the end of the
+// group; the partials are summed over CTAs in a fixed order afterwards, so
+// the result is deterministic.  Phi_R is read once per frame group, the
+// coefficient group once per CTA.
 //
 // One bf16 copy of the tile (hi and lo planes) serves both products: core
 // matrices of 8 rows x 8 modes (16-byte rows of 8 consecutive modes), at
@@ -32,12 +35,13 @@
 // tile overlaps the current tile's products.
 //
 // Tensor memory (512 columns x 128 lanes, lane = frame of the group):
-//   [0, 16 ks)            C_g^T as the A operand (bf16 hi, then lo; ks = K-slices of r)
-//   [160, 288)            D, then G hi (8 row slices x 8 columns)
-//   [288, 288 + 16 ks)    dC_g^T accumulator (FP32, r padded to 16 ks columns)
-//   [448, 512)            G lo
-// Shared memory: a TMA ring of FP32 Phi slices (128 rows x 16 modes), the two
-// tile copies and the tile's targets.
+//   [0, 8 ks)                    C_g^T hi as an A operand (ks = K-slices of r)
+//   [80, 208), [208, 336)        D, then G (hi in its first 64 columns, lo in
+//                                the last 64), two buffers
+//   [336, 336 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
+// C_g^T lo is an A operand in shared memory (K-major, the tile layout with
+// frames for rows).  Shared memory also holds a TMA ring of FP32 Phi slices
+// (128 rows x 16 modes), the two tile copies and the tile's targets.
 //
 // Roles (10 warps): 0 TMA producer, 1 MMA issuer, 2-5 converters (FP32 slice
 // -> bf16 planes), 6-9 epilogue (frame = TMEM lane).  Every wait is bounded
@@ -61,9 +65,9 @@ namespace {
 
 constexpr int LG_THREADS = 320;
 constexpr int LG_MAXKS = 10;      // r <= 160
-constexpr int LG_RING = 7;        // TMA stages of FP32 Phi slices (8 KB each): as many as fit
+constexpr int LG_RING = 3;        // TMA stages of FP32 Phi slices (8 KB each): as many as fit
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
-constexpr uint32_t LG_COL_D = 160, LG_COL_DC = 288, LG_COL_GLO = 448;
+constexpr uint32_t LG_COL_D = 80, LG_COL_DC = 336;   // D / G buffers at 80 and 208
 
 __device__ __forceinline__ float rho_of(float e, float delta) {
   const float ae = fabsf(e);
@@ -108,19 +112,21 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const int Np = 16 * ks;                                    // r padded to the K-slices
-  const uint32_t RS = (uint32_t)ks * 256u;                   // one 8-row group of the tile copy
+  const uint32_t RS = (uint32_t)ks * 256u;                   // one 8-row group of a tile-layout copy
   const uint32_t plane = 16u * RS;                           // 128 rows x 16 ks modes x 2 bytes
   uint8_t* ring = sm;                                        // LG_RING x 8 KB
   uint8_t* phi = ring + LG_RING * 8192;                      // 2 buffers x (hi plane, lo plane)
-  float* tgs = reinterpret_cast<float*>(phi + 4 * plane);    // 4 warps x 128 targets
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 4 * 128);
+  uint8_t* ctlo = phi + 4 * plane;                           // C_g^T lo (frames x modes)
+  float* tgs = reinterpret_cast<float*>(ctlo + plane);       // [2][128] targets of the tile
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 2 * 128);
   uint64_t* full = bars;                          // [LG_RING] slice landed
   uint64_t* empty = full + LG_RING;               // [LG_RING] slice converted
-  uint64_t* phi_full = empty + LG_RING;           // [2][LG_MAXKS] slice s of buffer b converted
-  uint64_t* bwd_done = phi_full + 2 * LG_MAXKS;   // [2] the products reading buffer b finished
-  uint64_t* fwd_done = bwd_done + 2;              // fwd MMAs of the tile finished
-  uint64_t* g_full = fwd_done + 1;                // G of the tile in TMEM
-  uint64_t* ct_full = g_full + 1;                 // C_g^T of the group in TMEM
+  uint64_t* phi_full = empty + LG_RING;           // [2][LG_MAXKS] slice s of tile buffer b converted
+  uint64_t* bwd_done = phi_full + 2 * LG_MAXKS;   // [2] the bwd MMAs of buffer b's tile finished
+  uint64_t* fwd_done = bwd_done + 2;              // [2] the fwd MMAs of buffer b's tile finished
+  uint64_t* g_full = fwd_done + 2;                // [2] G of buffer b's tile in TMEM
+  uint64_t* tg_full = g_full + 2;                 // [2] targets of buffer b's tile in place
+  uint64_t* ct_full = tg_full + 2;                // C_g^T of the group in place
   uint64_t* dc_full = ct_full + 1;                // dC^T ready to drain
   uint64_t* dc_free = dc_full + 1;                // dC^T drained
   uint64_t* tdown = dc_free + 1;
@@ -135,10 +141,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       mbar_init(&empty[i], 128);
     }
     for (int i = 0; i < 2 * LG_MAXKS; ++i) mbar_init(&phi_full[i], 128);
-    mbar_init(&bwd_done[0], 1);
-    mbar_init(&bwd_done[1], 1);
-    mbar_init(fwd_done, 1);
-    mbar_init(g_full, 128);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bwd_done[i], 1);
+      mbar_init(&fwd_done[i], 1);
+      mbar_init(&g_full[i], 128);
+      mbar_init(&tg_full[i], 128);
+    }
     mbar_init(ct_full, 128);
     mbar_init(dc_full, 1);
     mbar_init(dc_free, 128);
@@ -152,8 +160,14 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   tc_after();
   const uint32_t tmem = *tslot;
   const int ngroups = (K + 127) / 128;
-  // drains per group: after every LG_FLUSH tiles and after the group's last tile
+  // tiles of this CTA per group; a group's items are its tiles, and the items
+  // of all groups form one sequence u = 0, 1, ... (u & 1 selects the buffers)
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_tiles * ngroups;
+  auto drain_after = [&](int64_t u) {   // dC^T is drained after item u's bwd
+    const int64_t j = u % my_tiles;
+    return (j + 1) % LG_FLUSH == 0 || j + 1 == my_tiles;
+  };
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -163,19 +177,20 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       uint32_t par[LG_RING];
       for (int i = 0; i < LG_RING; ++i) issued[i] = false, par[i] = 0;
       bool ok = true;
-      for (int g = 0; ok && g < ngroups; ++g)
-        for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)
-          for (int s = 0; s < ks; ++s, ++it) {
-            const uint32_t st = it % LG_RING;
-            if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
-              ok = false;
-              break;
-            }
-            mbar_expect_tx(&full[st], 8192);
-            tma_load_2d(ring + st * 8192, &tmPhi, &full[st], (int)(tile * 128), s * 16);
-            issued[st] = true;
-            par[st] = (it / LG_RING) & 1;
+      for (int64_t u = 0; ok && u < items; ++u) {
+        const int64_t tile = blockIdx.x + (u % my_tiles) * gridDim.x;
+        for (int s = 0; s < ks; ++s, ++it) {
+          const uint32_t st = it % LG_RING;
+          if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
           }
+          mbar_expect_tx(&full[st], 8192);
+          tma_load_2d(ring + st * 8192, &tmPhi, &full[st], (int)(tile * 128), s * 16);
+          issued[st] = true;
+          par[st] = (it / LG_RING) & 1;
+        }
+      }
       for (int i = 0; i < LG_RING; ++i)
         if (issued[i]) mbar_wait_drain(&full[i], par[i]);
     }
@@ -184,68 +199,69 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     if (lane == 0) {
       const uint32_t id_fwd = idesc_bf16(128, 128);
       const uint32_t id_bwd = idesc_bf16(128, Np) | (1u << 16);   // B operand MN-major
-      const uint32_t ct_lo = (uint32_t)ks * 8u;
-      uint32_t tit = 0, fl = 0;
-      bool ok = true;
-      for (int g = 0; ok && g < ngroups; ++g) {
-        if (!mbar_wait(ct_full, g & 1, abort_flag)) break;
-        tc_after();
-        int64_t j = 0;
-        bool fresh = true;
-        for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit, ++j) {
-          const uint32_t b = tit & 1, use = tit >> 1;
-          uint8_t* hi = phi + b * 2 * plane;
-          // D / G hi must be free: the previous tile's bwd MMAs have read G
-          if (tit > 0 && !mbar_wait(&bwd_done[(tit - 1) & 1], ((tit - 1) >> 1) & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
+      const uint64_t ctl0 = sdesc(su32(ctlo), 128u, RS);           // C_g^T lo, K-major
+      uint32_t fl = 0;
+      bool ok = true, fresh = true;
+      // fwd(u): D of item u into buffer u & 1
+      auto fwd = [&](int64_t u) -> bool {
+        const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
+        if (u % my_tiles == 0) {   // first tile of a group: its coefficients must be in place
+          if (!mbar_wait(ct_full, (uint32_t)(u / my_tiles) & 1, abort_flag)) return false;
           tc_after();
-          const uint64_t f0 = sdesc(su32(hi), 128u, RS), f_lo = plane >> 4;
-          for (int s = 0; s < ks; ++s) {
-            if (!mbar_wait(&phi_full[b * LG_MAXKS + s], use & 1, abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_after();
-            const uint32_t ah = tmem + (uint32_t)s * 8u, al = ah + ct_lo;
-            const uint64_t bh = f0 + (uint64_t)((uint32_t)s * 16u), bl = bh + f_lo;
-            const uint32_t d = tmem + LG_COL_D;
-            umma_bf16_ta(d, ah, bh, id_fwd, s > 0 ? 1u : 0u);
-            umma_bf16_ta(d, ah, bl, id_fwd, 1u);
-            umma_bf16_ta(d, al, bh, id_fwd, 1u);
-          }
-          if (!ok) break;
-          umma_commit(fwd_done);
-          if (!mbar_wait(g_full, tit & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_after();
-          if (fresh && fl > 0) {   // the previous drain must have read dC^T
-            if (!mbar_wait(dc_free, (fl - 1) & 1, abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_after();
-          }
-          const uint32_t dc = tmem + LG_COL_DC;
-          const uint64_t b0 = sdesc(su32(hi), RS, 128u);   // MN-major: LBO along K (rows), SBO along N (modes)
-          for (int s = 0; s < 8; ++s) {
-            const uint32_t gh = tmem + LG_COL_D + (uint32_t)s * 8u, gl = tmem + LG_COL_GLO + (uint32_t)s * 8u;
-            const uint64_t bh = b0 + (uint64_t)((2u * (uint32_t)s * RS) >> 4), bl = bh + f_lo;
-            umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
-            umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
-            umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
-          }
-          fresh = false;
-          umma_commit(&bwd_done[b]);
-          if ((j + 1) % LG_FLUSH == 0 || j + 1 == my_tiles) {
-            umma_commit(dc_full);
-            ++fl;
-            fresh = true;
-          }
         }
+        const uint8_t* hi = phi + b * 2 * plane;
+        const uint64_t f0 = sdesc(su32(hi), 128u, RS), f_lo = plane >> 4;
+        const uint32_t d = tmem + LG_COL_D + b * 128u;
+        for (int s = 0; s < ks; ++s) {
+          if (!mbar_wait(&phi_full[b * LG_MAXKS + s], use & 1, abort_flag)) return false;
+          tc_after();
+          const uint32_t ah = tmem + (uint32_t)s * 8u;
+          const uint64_t al = ctl0 + (uint64_t)((uint32_t)s * 16u);
+          const uint64_t bh = f0 + (uint64_t)((uint32_t)s * 16u), bl = bh + f_lo;
+          umma_bf16_ta(d, ah, bh, id_fwd, s > 0 ? 1u : 0u);
+          umma_bf16_ta(d, ah, bl, id_fwd, 1u);
+          umma_bf16(d, al, bh, id_fwd, 1u);
+        }
+        umma_commit(&fwd_done[b]);
+        return true;
+      };
+      // bwd(u): dC^T += G(u)^T Phi_tile(u)
+      auto bwd = [&](int64_t u) -> bool {
+        const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
+        if (!mbar_wait(&g_full[b], use & 1, abort_flag)) return false;
+        tc_after();
+        if (fresh && fl > 0) {   // the previous drain must have read dC^T
+          if (!mbar_wait(dc_free, (fl - 1) & 1, abort_flag)) return false;
+          tc_after();
+        }
+        const uint8_t* hi = phi + b * 2 * plane;
+        const uint64_t b0 = sdesc(su32(hi), RS, 128u), f_lo = plane >> 4;   // MN-major: LBO along K, SBO along N
+        const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + b * 128u;
+        for (int s = 0; s < 8; ++s) {
+          const uint32_t gh = g0 + (uint32_t)s * 8u, gl = g0 + 64u + (uint32_t)s * 8u;
+          const uint64_t bh = b0 + (uint64_t)((2u * (uint32_t)s * RS) >> 4), bl = bh + f_lo;
+          umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
+          umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
+          umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
+        }
+        fresh = false;
+        umma_commit(&bwd_done[b]);
+        if (drain_after(u)) {
+          umma_commit(dc_full);
+          ++fl;
+          fresh = true;
+        }
+        return true;
+      };
+      // issue order fwd(0), then per item: fwd(u + 1) before bwd(u), except
+      // across a group boundary, where the next group's coefficients are
+      // loaded only after item u's drain
+      if (items > 0) ok = fwd(0);
+      for (int64_t u = 0; ok && u < items; ++u) {
+        const bool next_same_group = u + 1 < items && (u + 1) % my_tiles != 0;
+        if (next_same_group) ok = fwd(u + 1);
+        ok = ok && bwd(u);
+        if (ok && u + 1 < items && !next_same_group) ok = fwd(u + 1);
       }
       umma_commit(tdown);
       mbar_wait_drain(tdown, 0);
@@ -253,32 +269,27 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   } else if (warp < 6) {
     // ------------------------------------------------------------- converters
     const int t = threadIdx.x - 64;   // 0..127: row of the tile
-    uint32_t it = 0, tit = 0;
+    uint32_t it = 0;
     bool ok = true;
-    for (int g = 0; ok && g < ngroups; ++g) {
-      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
-        const uint32_t b = tit & 1;
-        // buffer b is free once the products of the tile two back are done
-        if (tit >= 2 && !mbar_wait(&bwd_done[b], ((tit >> 1) - 1) & 1, abort_flag)) {
+    for (int64_t u = 0; ok && u < items; ++u) {
+      const uint32_t b = (uint32_t)(u & 1);
+      // tile buffer b is free once the bwd MMAs of item u - 2 are done
+      if (u >= 2 && !mbar_wait(&bwd_done[b], (uint32_t)((u >> 1) - 1) & 1, abort_flag)) break;
+      uint8_t* hi = phi + b * 2 * plane;
+      for (int s = 0; s < ks; ++s, ++it) {
+        const uint32_t st = it % LG_RING;
+        if (!mbar_wait(&full[st], (it / LG_RING) & 1, abort_flag)) {
           ok = false;
           break;
         }
-        uint8_t* hi = phi + b * 2 * plane;
-        for (int s = 0; s < ks; ++s, ++it) {
-          const uint32_t st = it % LG_RING;
-          if (!mbar_wait(&full[st], (it / LG_RING) & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          const float* src = reinterpret_cast<const float*>(ring + st * 8192);
-          float x[16];
+        const float* src = reinterpret_cast<const float*>(ring + st * 8192);
+        float x[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];   // row t, modes 16 s + c
-          store_tile_row(x, hi, hi + plane, t, s, RS);
-          fence_async_smem();
-          mbar_arrive(&empty[st]);
-          mbar_arrive(&phi_full[b * LG_MAXKS + s]);
-        }
+        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];   // row t, modes 16 s + c
+        store_tile_row(x, hi, hi + plane, t, s, RS);
+        fence_async_smem();
+        mbar_arrive(&empty[st]);
+        mbar_arrive(&phi_full[b * LG_MAXKS + s]);
       }
     }
   } else {
@@ -286,16 +297,17 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     const int q = warp & 3;
     const int f = q * 32 + lane;                             // frame within the group = TMEM lane
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float* tg = tgs + q * 128;
-    uint32_t tit = 0, fl = 0;
+    uint32_t fl = 0;
     bool ok = true;
     double lacc = 0.0;
-    for (int g = 0; ok && g < ngroups; ++g) {
+    for (int64_t u = 0; ok && u < items; ++u) {
+      const int g = (int)(u / my_tiles);
+      const int64_t j = u % my_tiles;
       const int fr = g * 128 + f;                            // frame index
       const bool f_ok = fr < K;
       const float w = f_ok ? (float)wgt[fr] : 0.f;
-      // C_g^T into TMEM: lane f holds C[:, fr] split into bf16 hi / lo
-      {
+      if (j == 0) {
+        // C_g^T: lane f holds C[:, fr] split into bf16 hi (TMEM) and lo (shared memory)
         const double* col = C + (int64_t)fr * r;
         for (int s = 0; s < ks; ++s) {
           uint32_t h[8], l[8];
@@ -309,88 +321,82 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                          __float2bfloat16_rn((float)(v1 - (double)__bfloat162float(h1))));
           }
           tmem_st8(tmem + (uint32_t)s * 8u + lane_base, h);
-          tmem_st8(tmem + (uint32_t)(ks + s) * 8u + lane_base, l);
+          const uint32_t off = (uint32_t)(f >> 3) * RS + (uint32_t)s * 256u + (uint32_t)(f & 7) * 16u;
+          *reinterpret_cast<uint4*>(ctlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          *reinterpret_cast<uint4*>(ctlo + off + 128) = make_uint4(l[4], l[5], l[6], l[7]);
         }
         tmem_st_wait();
+        fence_async_smem();
         tc_before();
         mbar_arrive(ct_full);
       }
-      int64_t j = 0;
-      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit, ++j) {
-        const int64_t row0 = tile * 128;
-        __syncwarp();
+      const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
+      const int64_t row0 = (blockIdx.x + j * gridDim.x) * 128;
+      float* tg = tgs + b * 128;
+      tg[f] = row0 + f < n ? tgt[row0 + f] : 0.f;
+      mbar_arrive(&tg_full[b]);   // the four epilogue warps share the tile's targets
+      const int rows = (int)((n - row0) < 128 ? (n - row0) : 128);
+      if (!mbar_wait(&tg_full[b], use & 1, abort_flag) || !mbar_wait(&fwd_done[b], use & 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_after();
+      const uint32_t dcol = tmem + LG_COL_D + b * 128u + lane_base;
+      uint32_t v[128];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int64_t row = row0 + lane + 32 * i;
-          tg[lane + 32 * i] = row < n ? tgt[row] : 0.f;
+      for (int s = 0; s < 8; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
+      tmem_ld_wait();
+      float s_loss = 0.f;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float gv[2];
+#pragma unroll
+          for (int uu = 0; uu < 2; ++uu) {
+            const int tr = s * 16 + 2 * i + uu;
+            const float e = __uint_as_float(v[tr]) - tg[tr];
+            const bool live = f_ok && tr < rows;
+            s_loss += live ? w * rho_of(e, delta) : 0.f;
+            gv[uu] = live ? w * drho_of(e, delta) : 0.f;
+          }
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(gv[0]), h1 = __float2bfloat16_rn(gv[1]);
+          h[i] = pack2(h0, h1);
+          l[i] = pack2(__float2bfloat16_rn(gv[0] - __bfloat162float(h0)),
+                       __float2bfloat16_rn(gv[1] - __bfloat162float(h1)));
         }
-        __syncwarp();
-        const int rows = (int)((n - row0) < 128 ? (n - row0) : 128);
-        if (!mbar_wait(fwd_done, tit & 1, abort_flag)) {
+        // G over D: every D value of the tile is already in registers
+        tmem_st8(dcol + (uint32_t)s * 8u, h);
+        tmem_st8(dcol + 64u + (uint32_t)s * 8u, l);
+      }
+      lacc += (double)s_loss;
+      tmem_st_wait();
+      tc_before();
+      mbar_arrive(&g_full[b]);
+      if (drain_after(u)) {
+        // drain dC^T (lane f = frame, columns = modes) into this CTA's FP64 partial
+        if (!mbar_wait(dc_full, fl & 1, abort_flag)) {
           ok = false;
           break;
         }
         tc_after();
-        float s_loss = 0.f;
-        for (int s2 = 0; s2 < 8; s2 += 2) {
-          uint32_t v[32];
-          tmem_ld16_nw(tmem + LG_COL_D + (uint32_t)s2 * 16u + lane_base, v);
-          tmem_ld16_nw(tmem + LG_COL_D + (uint32_t)(s2 + 1) * 16u + lane_base, v + 16);
-          tmem_ld_wait();
+        double* dst = part + ((int64_t)blockIdx.x * K + fr) * r;
+        const bool first = j < LG_FLUSH;
+        for (int s = 0; s < ks; ++s) {
+          float dv[16];
+          tmem_ld16(tmem + LG_COL_DC + (uint32_t)s * 16u + lane_base, dv);
+          if (f_ok) {
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const int s = s2 + half;
-            uint32_t h[8], l[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              float gv[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int tr = s * 16 + 2 * i + u;
-                const float e = __uint_as_float(v[half * 16 + 2 * i + u]) - tg[tr];
-                const bool live = f_ok && tr < rows;
-                s_loss += live ? w * rho_of(e, delta) : 0.f;
-                gv[u] = live ? w * drho_of(e, delta) : 0.f;
-              }
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(gv[0]), h1 = __float2bfloat16_rn(gv[1]);
-              h[i] = pack2(h0, h1);
-              l[i] = pack2(__float2bfloat16_rn(gv[0] - __bfloat162float(h0)),
-                           __float2bfloat16_rn(gv[1] - __bfloat162float(h1)));
+            for (int c = 0; c < 16; ++c) {
+              const int m = s * 16 + c;
+              if (m < r) dst[m] = first ? (double)dv[c] : dst[m] + (double)dv[c];
             }
-            // G hi of rows 16 s .. 16 s + 15 overwrites D columns 8 s .. 8 s + 7,
-            // which this thread has already loaded (slices s / 2 <= s)
-            tmem_st8(tmem + LG_COL_D + (uint32_t)s * 8u + lane_base, h);
-            tmem_st8(tmem + LG_COL_GLO + (uint32_t)s * 8u + lane_base, l);
           }
         }
-        lacc += (double)s_loss;
-        tmem_st_wait();
         tc_before();
-        mbar_arrive(g_full);
-        if ((j + 1) % LG_FLUSH == 0 || j + 1 == my_tiles) {
-          // drain dC^T (lane f = frame, columns = modes) into this CTA's FP64 partial
-          if (!mbar_wait(dc_full, fl & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_after();
-          double* dst = part + ((int64_t)blockIdx.x * K + fr) * r;
-          const bool first = j < LG_FLUSH;
-          for (int s = 0; s < ks; ++s) {
-            float v[16];
-            tmem_ld16(tmem + LG_COL_DC + (uint32_t)s * 16u + lane_base, v);
-            if (f_ok) {
-#pragma unroll
-              for (int c = 0; c < 16; ++c) {
-                const int m = s * 16 + c;
-                if (m < r) dst[m] = first ? (double)v[c] : dst[m] + (double)v[c];
-              }
-            }
-          }
-          tc_before();
-          mbar_arrive(dc_free);
-          ++fl;
-        }
+        mbar_arrive(dc_free);
+        ++fl;
       }
     }
     const double ws = warp_sum(lacc);
@@ -416,7 +422,7 @@ __global__ void k_reduce_dc(int64_t count, int parts, const double* __restrict__
 }
 
 size_t lg_smem(int ks) {
-  return 1024 + (size_t)LG_RING * 8192 + 4 * 16 * (size_t)ks * 256 + 4 * 128 * 4 + 512;
+  return 1024 + (size_t)LG_RING * 8192 + 5 * 16 * (size_t)ks * 256 + 2 * 128 * 4 + 512;
 }
 
 int lg_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(n, 128))); }
