@@ -30,13 +30,13 @@ dmd_status launch_philox_blocks(int64_t count, uint32_t sid, uint64_t key, uint3
 int tn_splits(int64_t n, int Ka, int N);
 size_t tn_partial_doubles(int64_t n, int Ka, int N);
 dmd_status f32_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const float* B32, float* C,
-                       int64_t ldc, cudaStream_t st);
+                       int64_t ldc, cudaStream_t st, const int32_t* skip);
 dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                       double* C, double* part, cudaStream_t st);
-dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st);
+                       double* C, double* part, cudaStream_t st, const int32_t* skip);
+dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st, const int32_t* skip);
 size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N);
 dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C,
-                        int64_t ldc, void* ws, cudaStream_t st, int spare_sms);
+                        int64_t ldc, void* ws, cudaStream_t st, int spare_sms, const int32_t* skip);
 size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N);
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
                         double* C, int nsplit, void* ws, cudaStream_t st);
@@ -45,7 +45,7 @@ dmd_status launch_edit_modes(int r, int q, const double* in, double* out, double
 dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
                         void* ws, cudaStream_t st, int32_t* chosen);
 dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                              double* C, int nsplit, int flush, void* ws, cudaStream_t st);
+                              double* C, int nsplit, int flush, void* ws, cudaStream_t st, const int32_t* skip);
 dmd_status dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B, int ldb,
                  bool tb, double beta, double* C, int ldc, cudaStream_t st);
 dmd_status cholesky_upper(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st);
@@ -103,6 +103,16 @@ dmd_status fit_glue_check_finite(int64_t count, const double* A, int32_t* info, 
 dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStream_t st);
 dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st);
 dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st);
+dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, cudaStream_t st);
+dmd_status fit_glue_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip, cudaStream_t st);
+dmd_status dgemm_gated(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
+                       int ldb, bool tb, double beta, double* C, int ldc, const int32_t* skip, cudaStream_t st);
+dmd_status cholesky_upper_gated(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
+                                cudaStream_t st);
+dmd_status tri_inv_upper_gated(int n, const double* R, int ldr, double* T, int ldt, const int32_t* skip,
+                               cudaStream_t st);
+dmd_status cholesky_upper_f32_gated(int n, double* G, int ld, double tau, int32_t* info, int tag,
+                                    const int32_t* skip, cudaStream_t st);
 dmd_status fit_glue_stack(int l, int q, int m, const double* P, const float* Ups, double* Om, cudaStream_t st);
 dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma_or_null, double* inv_sq, int32_t* info,
                                 int tag, cudaStream_t st);
@@ -171,12 +181,14 @@ struct Tall {
     if (prec == DMD_MIXED_BF16X3) return umma_tn_workspace_bytes(n, Ka, N);
     return tn_partial_doubles(n, Ka, N) * sizeof(double) + 256;
   }
+  // skip: optional device flag; nonzero makes every launch of the product
+  // return at once (work a device-side decision made unnecessary)
   dmd_status nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
-                void* ws, cudaStream_t st, int spare_sms = 0) const {
-    if (nn_tensor(Kd)) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, spare_sms);
+                void* ws, cudaStream_t st, int spare_sms = 0, const int32_t* skip = nullptr) const {
+    if (nn_tensor(Kd)) return umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, spare_sms, skip);
     float* B32 = reinterpret_cast<float*>(ws);
-    DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st));
-    return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st);
+    DMD_TRY(f64_to_f32((int64_t)Kd * N, B, B32, st, skip));
+    return f32_gemm_nn(n, Kd, N, A, lda, B32, C, ldc, st, skip);
   }
   // The snapshot Gram W = S^T S on the CUDA cores in both forms: the first
   // CholeskyQR Gram of every sketch is derived from it, and a random sketch
@@ -188,16 +200,16 @@ struct Tall {
     return tn_partial_doubles(n, Ka, N) * sizeof(double) + 256;
   }
   dmd_status tn_accurate(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                         double* C, void* ws, cudaStream_t st) const {
-    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
+                         double* C, void* ws, cudaStream_t st, const int32_t* skip = nullptr) const {
+    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st, skip);
   }
   dmd_status tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
-                void* ws, cudaStream_t st) const {
+                void* ws, cudaStream_t st, const int32_t* skip = nullptr) const {
     // BF16x3 (hi/lo split, 3 products), TMEM flushed to FP64 in segments
     // sized by the row count (16 .. 256 k-steps).  The reductions that see the snapshots' full dynamic range
     // (the snapshot Gram) run on the CUDA cores instead (tn_accurate).
-    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 2, 0, ws, st);
-    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st);
+    if (prec == DMD_MIXED_BF16X3) return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, 2, 0, ws, st, skip);
+    return f32_gemm_tn(n, Ka, N, A, lda, B, ldb, C, reinterpret_cast<double*>(ws), st, skip);
   }
 };
 
@@ -212,6 +224,8 @@ struct FitBufs {
       *tauA, *Hq, *wr, *wi, *Yre, *Yim, *invit, *WR, *MR, *LS, *rhs, *hnorm, *invsq;
   float* Q1;
   int *heads, *nheads, *order;
+  double* G0;      // the first Gram, kept for the shifted fallback
+  int32_t* gate;   // [2] fallback gate (k_gate)
   // DMD with control (q > 0): input-space SVD of [Q^T X; Ups] and its products
   double *W, *WB;   // snapshot Gram S^T S ((m+1) x (m+1)) and W_X B (m x l)
   int L, p;
@@ -266,6 +280,8 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   b.heads = a.take<int>(r);
   b.nheads = a.take<int>(1);
   b.order = a.take<int>(r);
+  b.G0 = a.take<double>((size_t)l * l);
+  b.gate = a.take<int32_t>(4);
   b.Q1 = a.take<float>((size_t)b.ldY * l);
   b.L = l + d.q;
   b.p = std::min(d.r + d.q, std::min(b.L, m));
@@ -293,6 +309,7 @@ void carve_fit(Arena& a, const dmd_fit_desc& d, const Tall& tall, FitBufs& b) {
   g = std::max(g, tall.tn_bytes(n, m, l));
   g = std::max(g, tall.tn_bytes(n, l, m + 1));
   g = std::max(g, tall.tn_accurate_bytes(n, m + 1, m + 1));
+  g = std::max(g, tall.tn_accurate_bytes(n, l, l));   // the shifted fallback's accurate Gram
   b.gemm_ws_bytes = g;
   b.gemm_ws = a.take<char>(g, 1024);
 }
@@ -320,6 +337,41 @@ dmd_status validate_fit(const dmd_fit_desc* d) {
 // small FP64 Grams use 1e-13.
 constexpr double kTauTall = 1e-10, kTauSmall = 1e-13;
 
+// Shifted CholeskyQR3 fallback of orth_tall (every launch returns at once
+// unless the first Cholesky factorisation dropped a direction: b.gate[1] is
+// then 0).  The sketch Y = X Bs then holds directions below what the FP64
+// first Gram resolves after the FP32 snapshot products (about 1e-5 sigma_1);
+// instead of dropping them:
+//   1. R1 = chol(G + s I), s = 1e-6 max_i G_ii: every pivot is at least s,
+//      and Q1 = Y R1^{-1} has condition number at most ~1e3 (the weak
+//      directions are damped, not lost);
+//   2. R2 = chol(Q1^T Q1) with Q1^T Q1 taken by the FP32 CUDA-core reduction
+//      with FP64 carries (accurate to ~1e-10 of its norm, enough for that
+//      condition number), and the basis formed again from the snapshots,
+//      Q2 = X (Bs R1^{-1} R2^{-1}), overwriting Q1;
+//   3. the usual second pass on Q2: R3 = chol(Q2^T Q2), T2 = R3^{-1}.
+// Consumers then use Q = Q2 T2 as after the plain pass.
+dmd_status orth_tall_shifted(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, const double* Bs,
+                             int32_t* info, int tag, cudaStream_t st) {
+  const int l = b.l, m = b.m;
+  const int32_t* skip = b.gate + 1;
+  DMD_TRY(fit_glue_shift_diag(l, b.G0, l, 1e-6, skip, st));
+  DMD_TRY(cholesky_upper_gated(l, b.G0, l, 0.0, info, tag + 2, skip, st));
+  DMD_TRY(tri_inv_upper_gated(l, b.G0, l, b.T1, l, skip, st));
+  DMD_TRY(dgemm_gated(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, skip, st));    // Bs R1^{-1}
+  DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st, 0, skip));
+  DMD_TRY(tall.tn_accurate(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G0, b.gemm_ws, st, skip));
+  DMD_TRY(cholesky_upper_gated(l, b.G0, l, kTauSmall, info, tag + 3, skip, st));
+  DMD_TRY(tri_inv_upper_gated(l, b.G0, l, b.T2, l, skip, st));
+  DMD_TRY(dgemm_gated(l, l, l, 1.0, b.T1, l, false, b.T2, l, false, 0.0, b.G, l, skip, st));   // R1^{-1} R2^{-1}
+  DMD_TRY(dgemm_gated(m, l, l, 1.0, Bs, m, false, b.G, l, false, 0.0, b.WB, m, skip, st));
+  DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st, 0, skip));
+  DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G0, b.gemm_ws, st, skip));
+  DMD_TRY(cholesky_upper_f32_gated(l, b.G0, l, kTauTall, info, tag + 4, skip, st));
+  DMD_TRY(tri_inv_upper_gated(l, b.G0, l, b.T2, l, skip, st));
+  return DMD_OK;
+}
+
 // CholeskyQR2 of the tall sketch Y = X Bs (n x l, Bs = Omega or Z, m x l):
 // the first Gram is formed in the small space as Bs^T (X^T X) Bs from the
 // snapshot Gram W (one accurate pass over S per fit), so it carries FP64
@@ -333,14 +385,17 @@ dmd_status orth_tall(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, 
   const int l = b.l, m = b.m;
   DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
   DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
+  DMD_TRY(fit_glue_copy((int64_t)l * l, b.G, b.G0, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 0, st));
   DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 1, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
   DMD_TRY(dgemm(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, st));   // Bs R1^{-1}
   DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st));
   DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
   DMD_TRY(cholesky_upper_f32(l, b.G, l, kTauTall, info, tag + 1, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
-  return DMD_OK;
+  return orth_tall_shifted(tall, b, X, ldX, Bs, info, tag, st);
 }
 
 // CholeskyQR2 of a small FP64 matrix Z (rows x l) in place (second factor in

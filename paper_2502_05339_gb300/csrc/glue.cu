@@ -24,6 +24,32 @@ __global__ void k_sigma(int l, int r, const double* ev, double* sigma, double* i
   (void)l;
 }
 
+// Fallback gate of the CholeskyQR orthonormalisation.  mode 0: remember the
+// dropped-direction count info[5]; mode 1: gate[1] = 1 (skip the fallback)
+// when no direction was dropped since, else 0 -- and the count is restored,
+// since the shifted fallback keeps every direction.
+__global__ void k_gate(int32_t* info, int32_t* gate, int mode) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (mode == 0) {
+    gate[0] = info[5];
+    gate[1] = 1;
+  } else {
+    const bool dropped = info[5] != gate[0];
+    gate[1] = dropped ? 0 : 1;
+    if (dropped) info[5] = gate[0];
+  }
+}
+
+// G (n x n, ld) += s I with s = rel * max_i G_ii (skipped when *skip != 0).
+__global__ void k_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip) {
+  if (*skip != 0) return;
+  __shared__ double red[32];
+  double loc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) loc = fmax(loc, G[i + (int64_t)i * ld]);
+  const double s = rel * block_max(loc, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) G[i + (int64_t)i * ld] += s;
+}
+
 __global__ void k_scale_cols(int rows, int cols, double* A, int lda, const double* s) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)rows * cols) return;
@@ -129,6 +155,18 @@ dmd_status fit_glue_stack(int l, int q, int m, const double* P, const float* Ups
 dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma, double* inv_sq, int32_t* info, int tag,
                                 cudaStream_t st) {
   k_sigma_range<<<1, 32, 0, st>>>(L, p, ev, sigma, inv_sq, info, tag);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, cudaStream_t st) {
+  k_gate<<<1, 32, 0, st>>>(info, gate, mode);
+  DMD_LAUNCH_CHECK();
+  return DMD_OK;
+}
+
+dmd_status fit_glue_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip, cudaStream_t st) {
+  k_shift_diag<<<1, 256, 0, st>>>(n, G, ld, rel, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

@@ -1811,6 +1811,13 @@ dmd_status tri_inv_upper(int n, const double* R, int ldr, double* T, int ldt, cu
   return tri_inv_upper_gated(n, R, ldr, T, ldt, nullptr, st);
 }
 
+dmd_status cholesky_upper_f32_gated(int n, double* G, int ld, double tau, int32_t* info, int tag,
+                                    const int32_t* skip, cudaStream_t st) {
+  if (cholesky_cluster_fits(n)) return cholesky_cluster(n, G, ld, tau, info, tag, true, skip, st);
+  // small matrices: the FP64 factorisation (which honours the flag)
+  return cholesky_upper_gated(n, G, ld, tau, info, tag, skip, st);
+}
+
 dmd_status cholesky_upper_f32(int n, double* G, int ld, double tau, int32_t* info, int tag, cudaStream_t st) {
   if (cholesky_cluster_fits(n)) return cholesky_cluster(n, G, ld, tau, info, tag, true, nullptr, st);
   const size_t smem = ((size_t)(n | 1) * n + n) * sizeof(float);

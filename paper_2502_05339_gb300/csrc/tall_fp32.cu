@@ -22,7 +22,9 @@ constexpr int NN_BM = 128, NN_BN = 64, NN_BK = 16;
 // {tx*4 .. tx*4+3, 64 + tx*4 .. 64 + tx*4+3} and columns ty*4 .. ty*4+3 of the tile.
 __global__ void __launch_bounds__(256) k_gemm_nn_f32(int64_t n, int Kd, int N, const float* __restrict__ A,
                                                      int64_t lda, const float* __restrict__ B,
-                                                     float* __restrict__ C, int64_t ldc, int ntn) {
+                                                     float* __restrict__ C, int64_t ldc, int ntn,
+                                                     const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   __shared__ __align__(16) float As[NN_BK][NN_BM];
   __shared__ __align__(16) float Bs[NN_BK][NN_BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -155,7 +157,8 @@ __device__ __forceinline__ float4 box_ld4(const uint8_t* box, int c, int q) {
 __global__ void __launch_bounds__(TN_THREADS, 3)
     k_gemm_tn_f32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
                   int N, double* __restrict__ part, int nta, int ntb, int ntiles, int sym, int64_t chunk,
-                  int32_t* err) {
+                  int32_t* err, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;   // every CTA, before any barrier
   extern __shared__ uint8_t smraw[];
   // 1024-byte alignment by pointer arithmetic keeps the shared address space
   uint8_t* sm = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
@@ -315,7 +318,8 @@ __global__ void __launch_bounds__(TN_THREADS, 3)
 // C = sum over splits, in split order.  With sym, entries below the diagonal
 // tiles come from their mirror.
 __global__ void k_reduce_splits(int Ka, int N, int splits, const double* __restrict__ part, double* __restrict__ C,
-                                int sym) {
+                                int sym, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t count = (int64_t)Ka * N;
   if (i >= count) return;
@@ -331,7 +335,9 @@ __global__ void k_reduce_splits(int Ka, int N, int splits, const double* __restr
   C[i] = s;
 }
 
-__global__ void k_f64_to_f32(int64_t count, const double* __restrict__ in, float* __restrict__ out) {
+__global__ void k_f64_to_f32(int64_t count, const double* __restrict__ in, float* __restrict__ out,
+                             const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < count) out[i] = (float)in[i];
 }
@@ -366,19 +372,19 @@ size_t tn_partial_doubles(int64_t n, int Ka, int N) {
 }
 
 dmd_status f32_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const float* B32,
-                       float* C, int64_t ldc, cudaStream_t st) {
+                       float* C, int64_t ldc, cudaStream_t st, const int32_t* skip) {
   if (n <= 0 || N <= 0) return DMD_OK;
   const int ntn = (int)ceil_div(N, NN_BN);
   const int64_t blocks = ceil_div(n, NN_BM) * ntn;
-  k_gemm_nn_f32<<<(unsigned)blocks, 256, 0, st>>>(n, Kd, N, A, lda, B32, C, ldc, ntn);
+  k_gemm_nn_f32<<<(unsigned)blocks, 256, 0, st>>>(n, Kd, N, A, lda, B32, C, ldc, ntn, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
 
 dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B,
-                       int64_t ldb, double* C, double* part, cudaStream_t st) {
+                       int64_t ldb, double* C, double* part, cudaStream_t st, const int32_t* skip) {
   if (Ka <= 0 || N <= 0) return DMD_OK;
-  if (n <= 0) {
+  if (n <= 0 && skip == nullptr) {
     DMD_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)Ka * N * sizeof(double), st));
     return DMD_OK;
   }
@@ -393,17 +399,17 @@ dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, co
   DMD_TRY(make_map(&mB, B, n, N, ldb, TN_BR, TN_BT, true));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TN_SMEM));
   k_gemm_tn_f32<<<(unsigned)(ntiles * splits), TN_THREADS, TN_SMEM, st>>>(mA, mB, n, Ka, N, part, nta, ntb, ntiles,
-                                                                         sym ? 1 : 0, chunk, nullptr);
+                                                                         sym ? 1 : 0, chunk, nullptr, skip);
   DMD_LAUNCH_CHECK();
   const int64_t count = (int64_t)Ka * N;
-  k_reduce_splits<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(Ka, N, splits, part, C, sym ? 1 : 0);
+  k_reduce_splits<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(Ka, N, splits, part, C, sym ? 1 : 0, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
 
-dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st) {
+dmd_status f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t st, const int32_t* skip) {
   if (count <= 0) return DMD_OK;
-  k_f64_to_f32<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, in, out);
+  k_f64_to_f32<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, in, out, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

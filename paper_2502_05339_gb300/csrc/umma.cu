@@ -41,7 +41,8 @@ namespace {
 // chunk c, slice s, row j: offset c*(2*ks*BN*32) + s*BN*32 + chunk-of(j, k); lo
 // follows hi inside each chunk (ks*BN*32 bytes later).  Zero padded.
 __global__ void k_split_b(int Kd, int N, const double* __restrict__ B, int BN, int ksteps, int nchunks,
-                          uint8_t* __restrict__ out) {
+                          uint8_t* __restrict__ out, const int32_t* __restrict__ skip = nullptr) {
+  if (skip != nullptr && *skip != 0) return;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // one thread per (row, slice)
   const int64_t total = (int64_t)nchunks * BN * ksteps;
   if (idx >= total) return;
@@ -86,7 +87,10 @@ constexpr int NN_THREADS = 320;
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_umma_nn_bres(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bsplit,
                    float* __restrict__ C, int64_t ldc, int64_t n, int N, int Np, int ksteps, int64_t ntiles,
-                   int ns, int32_t* err) {
+                   int ns, int32_t* err, const int32_t* __restrict__ skip) {
+  // a device-side flag (work that a device decision made unnecessary): every
+  // CTA reads the same value before any barrier or tensor-memory allocation
+  if (skip != nullptr && *skip != 0) return;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t bres_bytes = 2u * (uint32_t)ksteps * (uint32_t)Np * 32u;
@@ -275,7 +279,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
                    const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int sa, int nb,
                    int nchunks, int64_t ntiles, const float* __restrict__ tgt, const double* __restrict__ wgt,
-                   float delta, double* __restrict__ loss_part, int32_t* err) {
+                   float delta, double* __restrict__ loss_part, int32_t* err, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;   // as in k_umma_nn_bres
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * (uint32_t)bn * 32u;
@@ -595,7 +600,8 @@ __device__ __forceinline__ void split_slice(const float4* src, int units, int h,
 __global__ void __launch_bounds__(TN_THREADS, 1)
     k_umma_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n, int Ka,
               int N, int Mt, int Np, int nsplit, int flush, int sym, int ns, int64_t chunk,
-              double* __restrict__ part, int32_t* err) {
+              double* __restrict__ part, int32_t* err, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;   // as in k_umma_nn_bres
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   // a TMA stage holds 32 rows of n (two k-steps): 128 contiguous bytes per
@@ -808,7 +814,8 @@ __global__ void __launch_bounds__(TN_THREADS, 1)
 // C[a0 + a, b0 + b] (ld ldc) = sum over the CTAs' partials (ka x nb each), fixed order.
 // With trans != 0 the block is written transposed: C[a, b] goes to C[b + a * ldc].
 __global__ void k_reduce_parts(int ka, int nb, int parts, const double* __restrict__ part, double* __restrict__ C,
-                               int64_t ldc, int trans) {
+                               int64_t ldc, int trans, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
   const int64_t count = (int64_t)ka * nb;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -931,7 +938,7 @@ size_t umma_tn_workspace_bytes(int64_t n, int Ka, int N) {
 }
 
 dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const double* B, float* C, int64_t ldc,
-                        void* ws, cudaStream_t st, int spare_sms) {
+                        void* ws, cudaStream_t st, int spare_sms, const int32_t* skip) {
   if (n <= 0 || N <= 0) return DMD_OK;
   const int ksteps = (int)ceil_div(Kd, 16);
   const int64_t ntiles = ceil_div(n, 128);
@@ -945,12 +952,12 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   if (N <= 256 && round_up(N, 16) <= Npmax) {
     const int Np = (int)round_up(N, 16);
     const int64_t work = (int64_t)Np * ksteps;
-    k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, Np, ksteps, 1, split);
+    k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, Np, ksteps, 1, split, skip);
     DMD_LAUNCH_CHECK();
     const int ns = bres_stages(ksteps, Np);
     const size_t smem = bres_smem(ksteps, Np, ns);
     DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_bres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, ns, nullptr);
+    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, ns, nullptr, skip);
     DMD_LAUNCH_CHECK();
     return DMD_OK;
   }
@@ -964,13 +971,13 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   const size_t smem = ares_smem(ksteps, bn, cfg.sa, cfg.nb);
   const int nchunks = (int)ceil_div(N, bn);
   const int64_t work = (int64_t)nchunks * bn * ksteps;
-  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split);
+  k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split, skip);
   DMD_LAUNCH_CHECK();
   CUtensorMap mapC;
   DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, 16));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_umma_nn_ares<0><<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
-                                                     ntiles, nullptr, nullptr, 0.f, nullptr, nullptr);
+                                                     ntiles, nullptr, nullptr, 0.f, nullptr, nullptr, skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -1011,7 +1018,7 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // no frames are stored: the output map argument is unused (the A map stands in)
   k_umma_nn_ares<1><<<grid, AR_THREADS, smem, st>>>(mapA, mapA, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
-                                                     ntiles, tgt, w, delta, part, nullptr);
+                                                     ntiles, tgt, w, delta, part, nullptr, nullptr);
   DMD_LAUNCH_CHECK();
   *parts = grid;
   return DMD_OK;
@@ -1040,10 +1047,10 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
       for (int sa = 2; sa <= 3 && status == DMD_OK; ++sa) {
         if (ares_smem(ksteps, bn, sa, nb) > (size_t)kMaxSmem) continue;
         g_ares_override = {bn, sa, nb};
-        status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0);
+        status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0, nullptr);
         if (status != DMD_OK) break;
         if (cudaEventRecord(e0, st) != cudaSuccess) status = DMD_ECUDA;
-        for (int r = 0; r < 2 && status == DMD_OK; ++r) status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0);
+        for (int r = 0; r < 2 && status == DMD_OK; ++r) status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0, nullptr);
         if (status != DMD_OK) break;
         float ms = 0.f;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1076,7 +1083,7 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 // C (Ka x N, ld Ka) = A^T B; sub-problems of at most 256 x 256 so that the
 // accumulators (Mt * Np columns) fit in 512 TMEM columns.
 dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-                              double* C, int nsplit, int flush, void* ws, cudaStream_t st) {
+                              double* C, int nsplit, int flush, void* ws, cudaStream_t st, const int32_t* skip) {
   if (n <= 0 || Ka <= 0 || N <= 0) return DMD_OK;
   if (flush <= 0) flush = tn_flush(n);
   double* part = reinterpret_cast<double*>(ws);
@@ -1108,12 +1115,13 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
       const size_t smem = tn_smem(Mt, Np, nsplit, ns);
       DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, flush, sym ? 1 : 0, ns, chunk,
-                                                part, nullptr);
+                                                part, nullptr, skip);
       DMD_LAUNCH_CHECK();
       // reduce into the (a0, b0) block of C (of C^T when swapped)
       const int64_t count = (int64_t)ka * nb;
       double* dst = swap ? C + (int64_t)a0 * Ka + b0 : C + (int64_t)b0 * Ka + a0;
-      k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(ka, nb, grid, part, dst, Ka, swap ? 1 : 0);
+      k_reduce_parts<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(ka, nb, grid, part, dst, Ka, swap ? 1 : 0,
+                                                                     skip);
       DMD_LAUNCH_CHECK();
     }
   }
@@ -1122,7 +1130,7 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
 
 dmd_status umma_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
                         int nsplit, void* ws, cudaStream_t st) {
-  return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, nsplit, 0, ws, st);
+  return umma_gemm_tn_flush(n, Ka, N, A, lda, B, ldb, C, nsplit, 0, ws, st, nullptr);
 }
 
 }  // namespace dmd

@@ -179,6 +179,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       bool ok = true;
       for (int64_t u = 0; ok && u < items; ++u) {
         const int64_t tile = blockIdx.x + (u % my_tiles) * gridDim.x;
+        // the next item's tile into L2 now, so that its slices arrive from L2
+        // when the ring (a few slices deep) asks for them
+        if (u + 1 < items) {
+          const int64_t nt = blockIdx.x + ((u + 1) % my_tiles) * gridDim.x;
+          for (int s = 0; s < ks; ++s) tma_prefetch_2d(&tmPhi, (int)(nt * 128), s * 16);
+        }
         for (int s = 0; s < ks; ++s, ++it) {
           const uint32_t st = it % LG_RING;
           if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
@@ -300,6 +306,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     uint32_t fl = 0;
     bool ok = true;
     double lacc = 0.0;
+    // the target of this thread's row of the next item, loaded one item ahead
+    auto target_of = [&](int64_t u) -> float {
+      const int64_t row = (blockIdx.x + (u % my_tiles) * gridDim.x) * 128 + f;
+      return row < n ? tgt[row] : 0.f;
+    };
+    float tnext = items > 0 ? target_of(0) : 0.f;
     for (int64_t u = 0; ok && u < items; ++u) {
       const int g = (int)(u / my_tiles);
       const int64_t j = u % my_tiles;
@@ -333,7 +345,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
       const int64_t row0 = (blockIdx.x + j * gridDim.x) * 128;
       float* tg = tgs + b * 128;
-      tg[f] = row0 + f < n ? tgt[row0 + f] : 0.f;
+      tg[f] = tnext;
+      if (u + 1 < items) tnext = target_of(u + 1);
       mbar_arrive(&tg_full[b]);   // the four epilogue warps share the tile's targets
       const int rows = (int)((n - row0) < 128 ? (n - row0) : 128);
       if (!mbar_wait(&tg_full[b], use & 1, abort_flag) || !mbar_wait(&fwd_done[b], use & 1, abort_flag)) {

@@ -154,3 +154,50 @@ def test_dmdc_adjoint_central_differences(dmd, scene):
         fd = (loss(U64, bp) - loss(U64, bm)) / (2 * h)
         gd = dm[2 * r + c]
         assert abs(fd - gd) <= 1e-3 * max(abs(fd), 1e-2 * np.abs(dm[2 * r:3 * r]).max()), (c, fd, gd)
+
+
+@pytest.fixture(scope="module")
+def scene_cfg2():
+    """The DMD-with-control workload's recipe (50 latent pairs, q = 8 blob
+    forces, piecewise-constant inputs, the full m = 300) on a 24^3 x 3 grid:
+    its weakest latent direction sits at sigma_100 / sigma_1 = 6.4e-6, below
+    what the first CholeskyQR pass resolves, so the fit takes the shifted
+    fallback."""
+    sc = synth.controlled_scene(24, 3, 50, 300, 8, 1002)
+    ref = O.dmdc(sc.X().numpy(), sc.extra["U"], 100)
+    return sc, ref
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_dmdc_full_rank_recipe(dmd, scene_cfg2, prec):
+    """r = 100 fits (no direction dropped, no DMD_ERANK), and the controlled
+    rollout of a new input sequence (200 steps) matches the oracle's within
+    the bar of the form.  Eigenvalues: the FP64 oracle's own eigenvalues move
+    by 8.2e-6 (worst single value) when the snapshots are perturbed at the
+    FP32 rounding (relative 1e-7) and by 2.5e-2 at the BF16x3 split's 7.6e-6,
+    so the FP32 form is graded on its eigenvalue vector (relative Frobenius,
+    bar 1e-5) and the mixed form on the rollout only."""
+    sc, ref = scene_cfg2
+    Ups = torch.as_tensor(sc.extra["U"].T.astype(np.float32)).contiguous().cuda()
+    model = dmd.dmd_fit(sc.S.cuda(), sc.n, 100, oversample=10, power_iters=2, precision=prec, seed=1002, Ups=Ups)
+    torch.cuda.synchronize()
+    model.check()
+    lam_g = model.lam()
+    perm, worst = match(lam_g, ref["lam"])
+    lam_frob = rel(lam_g[perm], ref["lam"])
+    g = np.random.default_rng(12)
+    T = 200
+    U2 = synth.piecewise_controls(g, 8, T)
+    PhiR_o, beta_o, kinds_o = O.to_real_form(ref["Phi"], ref["lam"], ref["b"])
+    L = O.real_block_operator(ref["lam"], kinds_o)
+    GR = O.real_form_control(ref["G"], kinds_o)
+    ks = list(range(0, T + 1, 10))
+    Fo = (PhiR_o @ O.rollout_real(L, beta_o, GR, U2, T))[:, ks]
+    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()
+    F = cols(dmd.dmd_predict(model, ks, u=u, precision=prec), sc.n)
+    ferr = rel(F, Fo)
+    print(f"[{prec}] r=100: eigenvalue vector {lam_frob:.2e} (worst {worst:.2e}); rollout frames {ferr:.2e}; "
+          f"dropped directions reported {int(model.info[5].item())}")
+    assert ferr < BAR[prec], ferr
+    if prec == "fp32":
+        assert lam_frob < BAR[prec], lam_frob
