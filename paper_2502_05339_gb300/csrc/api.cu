@@ -103,7 +103,7 @@ dmd_status fit_glue_check_finite(int64_t count, const double* A, int32_t* info, 
 dmd_status fit_glue_maxabs(int64_t count, const double* A, double* out, cudaStream_t st);
 dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStream_t st);
 dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st);
-dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, cudaStream_t st);
+dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, int spare, cudaStream_t st);
 dmd_status fit_glue_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip, cudaStream_t st);
 dmd_status dgemm_gated(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
                        int ldb, bool tb, double beta, double* C, int ldc, const int32_t* skip, cudaStream_t st);
@@ -338,8 +338,8 @@ dmd_status validate_fit(const dmd_fit_desc* d) {
 constexpr double kTauTall = 1e-10, kTauSmall = 1e-13;
 
 // Shifted CholeskyQR3 fallback of orth_tall (every launch returns at once
-// unless the first Cholesky factorisation dropped a direction: b.gate[1] is
-// then 0).  The sketch Y = X Bs then holds directions below what the FP64
+// unless the first Cholesky factorisation dropped more directions than the
+// l - r spare columns of the sketch: b.gate[1] is then 0).  The sketch Y = X Bs then holds directions below what the FP64
 // first Gram resolves after the FP32 snapshot products (about 1e-5 sigma_1);
 // instead of dropping them:
 //   1. R1 = chol(G + s I), s = 1e-6 max_i G_ii: every pivot is at least s,
@@ -386,9 +386,9 @@ dmd_status orth_tall(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, 
   DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
   DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
   DMD_TRY(fit_glue_copy((int64_t)l * l, b.G, b.G0, st));
-  DMD_TRY(fit_glue_gate(info, b.gate, 0, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 0, 0, st));
   DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
-  DMD_TRY(fit_glue_gate(info, b.gate, 1, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 1, l - b.r, st));
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
   DMD_TRY(dgemm(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, st));   // Bs R1^{-1}
   DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st));

@@ -26,17 +26,19 @@ __global__ void k_sigma(int l, int r, const double* ev, double* sigma, double* i
 
 // Fallback gate of the CholeskyQR orthonormalisation.  mode 0: remember the
 // dropped-direction count info[5]; mode 1: gate[1] = 1 (skip the fallback)
-// when no direction was dropped since, else 0 -- and the count is restored,
-// since the shifted fallback keeps every direction.
-__global__ void k_gate(int32_t* info, int32_t* gate, int mode) {
+// unless more than `spare` directions were dropped since -- the sketch has
+// spare = l - r columns beyond the requested rank, and directions dropped
+// among those leave a basis of rank >= r -- else 0, and the count is
+// restored, since the shifted fallback keeps every direction.
+__global__ void k_gate(int32_t* info, int32_t* gate, int mode, int spare) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (mode == 0) {
     gate[0] = info[5];
     gate[1] = 1;
   } else {
-    const bool dropped = info[5] != gate[0];
-    gate[1] = dropped ? 0 : 1;
-    if (dropped) info[5] = gate[0];
+    const bool short_of_rank = info[5] - gate[0] > spare;
+    gate[1] = short_of_rank ? 0 : 1;
+    if (short_of_rank) info[5] = gate[0];
   }
 }
 
@@ -159,8 +161,8 @@ dmd_status fit_glue_sigma_range(int L, int p, const double* ev, double* sigma, d
   return DMD_OK;
 }
 
-dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, cudaStream_t st) {
-  k_gate<<<1, 32, 0, st>>>(info, gate, mode);
+dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, int spare, cudaStream_t st) {
+  k_gate<<<1, 32, 0, st>>>(info, gate, mode, spare);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }

@@ -168,15 +168,28 @@ def scene_cfg2():
     return sc, ref
 
 
+# The rollout of a new input sequence at r = 100 is ill-conditioned in the
+# data: the FP64 oracle's own rollout (200 steps, this scene) moves by 8.2e-5
+# when the snapshots are perturbed by a relative 1e-7 (FP32 rounding) and by
+# 1.3e-2 at 7.6e-6 (the BF16x3 split's rounding), while its reconstruction of
+# the training window moves by ~1e-7.  The training window is graded at the
+# plain bars, the new-input rollout at bars derived from that sensitivity:
+# FP32 1e-3, ten times the response to a 1e-7 perturbation; mixed 1e-2, below
+# the response to a 7.6e-6 perturbation because the split's rounding is not an
+# independent perturbation of every snapshot entry (its errors average over
+# the 41,472 rows; measured: 1.5e-3).
+ROLLOUT_BAR = {"fp32": 1e-3, "mixed": 1e-2}
+
+
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
 def test_dmdc_full_rank_recipe(dmd, scene_cfg2, prec):
-    """r = 100 fits (no direction dropped, no DMD_ERANK), and the controlled
-    rollout of a new input sequence (200 steps) matches the oracle's within
-    the bar of the form.  Eigenvalues: the FP64 oracle's own eigenvalues move
-    by 8.2e-6 (worst single value) when the snapshots are perturbed at the
-    FP32 rounding (relative 1e-7) and by 2.5e-2 at the BF16x3 split's 7.6e-6,
-    so the FP32 form is graded on its eigenvalue vector (relative Frobenius,
-    bar 1e-5) and the mixed form on the rollout only."""
+    """r = 100 fits (the shifted fallback keeps the weakest latent directions:
+    no DMD_ERANK); the reconstruction of the training window with the
+    training inputs matches the FP64 oracle's within the plain bar of the
+    form; the rollout of a new input sequence (200 steps) within the derived
+    ROLLOUT_BAR; and in the FP32 form the eigenvalue vector within 1e-5
+    (relative Frobenius: the worst single eigenvalue of the oracle itself
+    moves 8.2e-6 at a 1e-7 perturbation)."""
     sc, ref = scene_cfg2
     Ups = torch.as_tensor(sc.extra["U"].T.astype(np.float32)).contiguous().cuda()
     model = dmd.dmd_fit(sc.S.cuda(), sc.n, 100, oversample=10, power_iters=2, precision=prec, seed=1002, Ups=Ups)
@@ -185,19 +198,23 @@ def test_dmdc_full_rank_recipe(dmd, scene_cfg2, prec):
     lam_g = model.lam()
     perm, worst = match(lam_g, ref["lam"])
     lam_frob = rel(lam_g[perm], ref["lam"])
-    g = np.random.default_rng(12)
-    T = 200
-    U2 = synth.piecewise_controls(g, 8, T)
     PhiR_o, beta_o, kinds_o = O.to_real_form(ref["Phi"], ref["lam"], ref["b"])
     L = O.real_block_operator(ref["lam"], kinds_o)
     GR = O.real_form_control(ref["G"], kinds_o)
-    ks = list(range(0, T + 1, 10))
-    Fo = (PhiR_o @ O.rollout_real(L, beta_o, GR, U2, T))[:, ks]
-    u = torch.as_tensor(U2.T.astype(np.float32)).contiguous().cuda()
-    F = cols(dmd.dmd_predict(model, ks, u=u, precision=prec), sc.n)
-    ferr = rel(F, Fo)
-    print(f"[{prec}] r=100: eigenvalue vector {lam_frob:.2e} (worst {worst:.2e}); rollout frames {ferr:.2e}; "
-          f"dropped directions reported {int(model.info[5].item())}")
-    assert ferr < BAR[prec], ferr
+
+    def both(U_in, T, ks):
+        Fo = (PhiR_o @ O.rollout_real(L, beta_o, GR, U_in, T))[:, ks]
+        u = torch.as_tensor(U_in.T.astype(np.float32)).contiguous().cuda()
+        return cols(dmd.dmd_predict(model, ks, u=u, precision=prec), sc.n), Fo
+
+    Fw, Fwo = both(sc.extra["U"], sc.m, list(range(0, sc.m + 1, 10)))
+    werr = rel(Fw, Fwo)
+    g = np.random.default_rng(12)
+    Fr, Fro = both(synth.piecewise_controls(g, 8, 200), 200, list(range(0, 201, 10)))
+    rerr = rel(Fr, Fro)
+    print(f"[{prec}] r=100: training window {werr:.2e}; new-input rollout {rerr:.2e}; eigenvalue vector "
+          f"{lam_frob:.2e} (worst {worst:.2e})")
+    assert werr < BAR[prec], werr
+    assert rerr < ROLLOUT_BAR[prec], rerr
     if prec == "fp32":
         assert lam_frob < BAR[prec], lam_frob
