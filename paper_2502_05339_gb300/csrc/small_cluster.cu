@@ -231,7 +231,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CL_THREADS)
 }  // namespace
 
 // Cluster versions are used from this size up (smaller matrices stay on one CTA).
-bool householder_cluster_fits(int n) { return n >= 32 && n <= 256; }
+bool householder_cluster_fits(int n) { return n >= 96 && n <= 256; }
 
 dmd_status hessenberg_cluster(int n, double* A, int ld, double* tau, cudaStream_t st) {
   const int ncl = (n + CL - 1) / CL;
@@ -409,7 +409,7 @@ dmd_status cholesky_cluster_t(int n, double* G, int ld, double tau, int32_t* inf
 
 }  // namespace
 
-bool cholesky_cluster_fits(int n) { return n >= 32 && n <= 512; }
+bool cholesky_cluster_fits(int n) { return n >= 96 && n <= 512; }
 
 dmd_status cholesky_cluster(int n, double* G, int ld, double tau, int32_t* info, int tag, bool fp32,
                             const int32_t* skip, cudaStream_t st) {

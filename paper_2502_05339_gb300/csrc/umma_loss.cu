@@ -36,15 +36,19 @@
 //
 // Tensor memory (512 columns x 128 lanes, lane = frame of the group):
 //   [0, 8 ks)                    C_g^T hi as an A operand (ks = K-slices of r)
-//   [80, 208), [208, 336)        D, then G (hi in its first 64 columns, lo in
-//                                the last 64), two buffers
+//   [80, 208), [208, 336)        D, then G, two buffers: the tile's rows
+//                                0..63 and 64..127 are handled by separate
+//                                epilogue warps, each writing G over its own
+//                                64 D columns (hi of its four 16-row slices,
+//                                then lo)
 //   [336, 336 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
 // C_g^T lo is an A operand in shared memory (K-major, the tile layout with
 // frames for rows).  Shared memory also holds a TMA ring of FP32 Phi slices
 // (128 rows x 16 modes), the two tile copies and the tile's targets.
 //
-// Roles (10 warps): 0 TMA producer, 1 MMA issuer, 2-5 converters (FP32 slice
-// -> bf16 planes), 6-9 epilogue (frame = TMEM lane).  Every wait is bounded
+// Roles (14 warps): 0 TMA producer, 1 MMA issuer, 2-5 converters (FP32 slice
+// -> bf16 planes), 6-13 epilogue (frame = TMEM lane; two warps per lane
+// quarter, one per half of the tile's rows).  Every wait is bounded
 // (2 s); a wait that runs out aborts the CTA: roles leave their loops, the
 // producer and the MMA issuer drain what they issued, TMEM is freed and the
 // status word gets DMD_ETIMEOUT.
@@ -63,19 +67,11 @@ int num_sms();
 
 namespace {
 
-constexpr int LG_THREADS = 320;
+constexpr int LG_THREADS = 448;   // 14 warps: producer, MMA issuer, 4 converters, 8 epilogue
 constexpr int LG_MAXKS = 10;      // r <= 160
 constexpr int LG_RING = 3;        // TMA stages of FP32 Phi slices (8 KB each): as many as fit
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
 constexpr uint32_t LG_COL_D = 80, LG_COL_DC = 336;   // D / G buffers at 80 and 208
-
-__device__ __forceinline__ float rho_of(float e, float delta) {
-  const float ae = fabsf(e);
-  return (delta > 0.f && ae > delta) ? delta * (ae - 0.5f * delta) : 0.5f * e * e;
-}
-__device__ __forceinline__ float drho_of(float e, float delta) {
-  return (delta > 0.f && fabsf(e) > delta) ? copysignf(delta, e) : e;
-}
 
 // Split 8 consecutive FP32 values into bf16 hi / lo 16-byte chunks.
 __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
@@ -104,6 +100,7 @@ __device__ __forceinline__ void store_tile_row(const float* x, uint8_t* hi, uint
   *reinterpret_cast<uint4*>(lo + off + 128) = l1;
 }
 
+template <bool kHuber>
 __global__ void __launch_bounds__(LG_THREADS, 1)
     k_umma_loss_grad(const __grid_constant__ CUtensorMap tmPhi, int64_t n, int r, int K, int ks,
                      const double* __restrict__ C, const float* __restrict__ tgt, const double* __restrict__ wgt,
@@ -130,8 +127,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   uint64_t* dc_full = ct_full + 1;                // dC^T ready to drain
   uint64_t* dc_free = dc_full + 1;                // dC^T drained
   uint64_t* tdown = dc_free + 1;
-  double* red = reinterpret_cast<double*>(tdown + 1);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 4);
+  double* red = reinterpret_cast<double*>(tdown + 1);   // 8 epilogue warps' loss sums
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 8);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -144,12 +141,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bwd_done[i], 1);
       mbar_init(&fwd_done[i], 1);
-      mbar_init(&g_full[i], 128);
-      mbar_init(&tg_full[i], 128);
+      mbar_init(&g_full[i], 256);
+      mbar_init(&tg_full[i], 256);
     }
-    mbar_init(ct_full, 128);
+    mbar_init(ct_full, 256);
     mbar_init(dc_full, 1);
-    mbar_init(dc_free, 128);
+    mbar_init(dc_free, 256);
     mbar_init(tdown, 1);
     *abort_flag = 0;
     fence_barrier_init();
@@ -244,7 +241,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         const uint64_t b0 = sdesc(su32(hi), RS, 128u), f_lo = plane >> 4;   // MN-major: LBO along K, SBO along N
         const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + b * 128u;
         for (int s = 0; s < 8; ++s) {
-          const uint32_t gh = g0 + (uint32_t)s * 8u, gl = g0 + 64u + (uint32_t)s * 8u;
+          // G of row slice s: in the D columns of its half, hi then lo
+          const uint32_t gh = g0 + (uint32_t)(s >> 2) * 64u + (uint32_t)(s & 3) * 8u, gl = gh + 32u;
           const uint64_t bh = b0 + (uint64_t)((2u * (uint32_t)s * RS) >> 4), bl = bh + f_lo;
           umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
           umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
@@ -300,42 +298,47 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     }
   } else {
     // --------------------------------------------------------------- epilogue
-    const int q = warp & 3;
+    const int q = warp & 3;                                  // lane quarter (TMEM access rule)
+    const int h = (warp - 6) >> 2;                           // half of the tile's rows: 0..63 / 64..127
     const int f = q * 32 + lane;                             // frame within the group = TMEM lane
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int s_lo = h * ((ks + 1) >> 1), s_hi = h ? ks : ((ks + 1) >> 1);   // coefficient slices of this half
     uint32_t fl = 0;
     bool ok = true;
     double lacc = 0.0;
-    // the target of this thread's row of the next item, loaded one item ahead
+    // the target of row f of the next item (loaded one item ahead by the
+    // first half's threads, which fill the shared copy)
     auto target_of = [&](int64_t u) -> float {
       const int64_t row = (blockIdx.x + (u % my_tiles) * gridDim.x) * 128 + f;
       return row < n ? tgt[row] : 0.f;
     };
-    float tnext = items > 0 ? target_of(0) : 0.f;
+    float tnext = (items > 0 && h == 0) ? target_of(0) : 0.f;
     for (int64_t u = 0; ok && u < items; ++u) {
       const int g = (int)(u / my_tiles);
       const int64_t j = u % my_tiles;
       const int fr = g * 128 + f;                            // frame index
       const bool f_ok = fr < K;
+      // frames past K get weight 0, rows past n give e = 0 - 0 (zero-filled
+      // Phi rows, zero targets): neither needs a mask below
       const float w = f_ok ? (float)wgt[fr] : 0.f;
       if (j == 0) {
         // C_g^T: lane f holds C[:, fr] split into bf16 hi (TMEM) and lo (shared memory)
         const double* col = C + (int64_t)fr * r;
-        for (int s = 0; s < ks; ++s) {
-          uint32_t h[8], l[8];
+        for (int s = s_lo; s < s_hi; ++s) {
+          uint32_t hh[8], ll[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int m0 = s * 16 + 2 * i;
             const double v0 = (f_ok && m0 < r) ? col[m0] : 0.0, v1 = (f_ok && m0 + 1 < r) ? col[m0 + 1] : 0.0;
             const __nv_bfloat16 h0 = __float2bfloat16_rn((float)v0), h1 = __float2bfloat16_rn((float)v1);
-            h[i] = pack2(h0, h1);
-            l[i] = pack2(__float2bfloat16_rn((float)(v0 - (double)__bfloat162float(h0))),
-                         __float2bfloat16_rn((float)(v1 - (double)__bfloat162float(h1))));
+            hh[i] = pack2(h0, h1);
+            ll[i] = pack2(__float2bfloat16_rn((float)(v0 - (double)__bfloat162float(h0))),
+                          __float2bfloat16_rn((float)(v1 - (double)__bfloat162float(h1))));
           }
-          tmem_st8(tmem + (uint32_t)s * 8u + lane_base, h);
+          tmem_st8(tmem + (uint32_t)s * 8u + lane_base, hh);
           const uint32_t off = (uint32_t)(f >> 3) * RS + (uint32_t)s * 256u + (uint32_t)(f & 7) * 16u;
-          *reinterpret_cast<uint4*>(ctlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-          *reinterpret_cast<uint4*>(ctlo + off + 128) = make_uint4(l[4], l[5], l[6], l[7]);
+          *reinterpret_cast<uint4*>(ctlo + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+          *reinterpret_cast<uint4*>(ctlo + off + 128) = make_uint4(ll[4], ll[5], ll[6], ll[7]);
         }
         tmem_st_wait();
         fence_async_smem();
@@ -343,52 +346,64 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         mbar_arrive(ct_full);
       }
       const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
-      const int64_t row0 = (blockIdx.x + j * gridDim.x) * 128;
       float* tg = tgs + b * 128;
-      tg[f] = tnext;
-      if (u + 1 < items) tnext = target_of(u + 1);
-      mbar_arrive(&tg_full[b]);   // the four epilogue warps share the tile's targets
-      const int rows = (int)((n - row0) < 128 ? (n - row0) : 128);
+      if (h == 0) {
+        tg[f] = tnext;
+        if (u + 1 < items) tnext = target_of(u + 1);
+      }
+      mbar_arrive(&tg_full[b]);
       if (!mbar_wait(&tg_full[b], use & 1, abort_flag) || !mbar_wait(&fwd_done[b], use & 1, abort_flag)) {
         ok = false;
         break;
       }
       tc_after();
-      const uint32_t dcol = tmem + LG_COL_D + b * 128u + lane_base;
-      uint32_t v[128];
+      // this half's 64 D columns (rows 64 h .. 64 h + 63 of the tile)
+      const uint32_t dcol = tmem + LG_COL_D + b * 128u + (uint32_t)h * 64u + lane_base;
+      uint32_t v[64];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
+      for (int s = 0; s < 4; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
       tmem_ld_wait();
+      const float* tgh = tg + h * 64;
       float s_loss = 0.f;
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        uint32_t h[8], l[8];
+      for (int s = 0; s < 4; ++s) {
+        uint32_t hh[8], ll[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          float gv[2];
-#pragma unroll
-          for (int uu = 0; uu < 2; ++uu) {
-            const int tr = s * 16 + 2 * i + uu;
-            const float e = __uint_as_float(v[tr]) - tg[tr];
-            const bool live = f_ok && tr < rows;
-            s_loss += live ? w * rho_of(e, delta) : 0.f;
-            gv[uu] = live ? w * drho_of(e, delta) : 0.f;
+          const float2 tt = *reinterpret_cast<const float2*>(tgh + s * 16 + 2 * i);
+          const float e0 = __uint_as_float(v[s * 16 + 2 * i]) - tt.x;
+          const float e1 = __uint_as_float(v[s * 16 + 2 * i + 1]) - tt.y;
+          float g0, g1;
+          if (kHuber) {
+            const float a0 = fabsf(e0), a1 = fabsf(e1);
+            g0 = w * fminf(fmaxf(e0, -delta), delta);
+            g1 = w * fminf(fmaxf(e1, -delta), delta);
+            s_loss += w * (a0 > delta ? delta * (a0 - 0.5f * delta) : 0.5f * e0 * e0);
+            s_loss += w * (a1 > delta ? delta * (a1 - 0.5f * delta) : 0.5f * e1 * e1);
+          } else {
+            g0 = w * e0;
+            g1 = w * e1;
+            s_loss = fmaf(g0, e0, s_loss);   // halved after the tile
+            s_loss = fmaf(g1, e1, s_loss);
           }
-          const __nv_bfloat16 h0 = __float2bfloat16_rn(gv[0]), h1 = __float2bfloat16_rn(gv[1]);
-          h[i] = pack2(h0, h1);
-          l[i] = pack2(__float2bfloat16_rn(gv[0] - __bfloat162float(h0)),
-                       __float2bfloat16_rn(gv[1] - __bfloat162float(h1)));
+          const __nv_bfloat162 hv = __floats2bfloat162_rn(g0, g1);
+          const float2 hf = __bfloat1622float2(hv);
+          const __nv_bfloat162 lv = __floats2bfloat162_rn(g0 - hf.x, g1 - hf.y);
+          hh[i] = bf2_bits(hv);
+          ll[i] = bf2_bits(lv);
         }
-        // G over D: every D value of the tile is already in registers
-        tmem_st8(dcol + (uint32_t)s * 8u, h);
-        tmem_st8(dcol + 64u + (uint32_t)s * 8u, l);
+        // G of row slice 4 h + s over this half's D columns, which this
+        // thread has loaded: hi at 8 s, lo at 32 + 8 s
+        tmem_st8(dcol + (uint32_t)s * 8u, hh);
+        tmem_st8(dcol + 32u + (uint32_t)s * 8u, ll);
       }
-      lacc += (double)s_loss;
+      lacc += kHuber ? (double)s_loss : 0.5 * (double)s_loss;
       tmem_st_wait();
       tc_before();
       mbar_arrive(&g_full[b]);
       if (drain_after(u)) {
-        // drain dC^T (lane f = frame, columns = modes) into this CTA's FP64 partial
+        // drain dC^T (lane f = frame, columns = modes; this half's slices)
+        // into this CTA's FP64 partial
         if (!mbar_wait(dc_full, fl & 1, abort_flag)) {
           ok = false;
           break;
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         tc_after();
         double* dst = part + ((int64_t)blockIdx.x * K + fr) * r;
         const bool first = j < LG_FLUSH;
-        for (int s = 0; s < ks; ++s) {
+        for (int s = s_lo; s < s_hi; ++s) {
           float dv[16];
           tmem_ld16(tmem + LG_COL_DC + (uint32_t)s * 16u + lane_base, dv);
           if (f_ok) {
@@ -413,7 +428,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       }
     }
     const double ws = warp_sum(lacc);
-    if (lane == 0) red[q] = ws;
+    if (lane == 0) red[warp - 6] = ws;
   }
   tc_before();
   __syncthreads();
@@ -421,7 +436,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     tc_after();
     tmem_dealloc(tmem, 512);
   }
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+  if (threadIdx.x == 0)
+    loss_part[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8004);
 }
 
@@ -467,8 +483,9 @@ dmd_status umma_loss_grad(int64_t n, int r, int K, const float* Phi, int64_t ldP
   DMD_TRY(make_map(&map, Phi, n, r, ldPhi, 128, 16));
   const size_t smem = lg_smem(ks);
   double* part = reinterpret_cast<double*>(ws);
-  DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_loss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_umma_loss_grad<<<grid, LG_THREADS, smem, st>>>(map, n, r, K, ks, C, tgt, w, delta, ntiles, part, loss_part,
+  auto kern = delta > 0.f ? k_umma_loss_grad<true> : k_umma_loss_grad<false>;
+  DMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, LG_THREADS, smem, st>>>(map, n, r, K, ks, C, tgt, w, delta, ntiles, part, loss_part,
                                                    nullptr);
   DMD_LAUNCH_CHECK();
   const int64_t count = (int64_t)K * r;
