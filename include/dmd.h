@@ -149,6 +149,22 @@ DMD_EXPORT const char* dmd_version(void);
  * (host-side counter, for accounting in benchmarks). */
 DMD_EXPORT uint64_t dmd_launch_count(void);
 
+/* Asynchronous status of the calls that have no info argument (dmd_predict,
+ * dmd_predict_backward, dmd_predict_loss, dmd_predict_noalloc,
+ * dmd_advect_density and the component kernels): a tensor-core or TMA kernel
+ * of such a call whose bounded wait ran out (2 s) writes DMD_ETIMEOUT to
+ * words[0] and the site to words[4] of a per-device status word, the first
+ * failure winning.  (The fits, dmd_upsample and each scene of
+ * dmd_fit_predict_batch report to their own info instead.)
+ * Copies the current device's word (DMD_INFO_WORDS int32) into the host
+ * array `words` after the work already queued on `stream` has finished
+ * (the stream is synchronised), and zeroes it when `clear` is non-zero.
+ * The word's device address is looked up once per device, so, as for
+ * dmd_predict_noalloc, a device reset (cudaDeviceReset) after the first call
+ * of the library on that device is not supported.
+ * Errors: DMD_EINVAL for a NULL `words`, DMD_ECUDA if a copy fails. */
+DMD_EXPORT dmd_status dmd_async_status(int32_t* words, int32_t clear, void* stream);
+
 /* ---- fit ---------------------------------------------------------------- */
 
 /* Workspace bytes dmd_fit needs for this problem (host-side query, no GPU). */
@@ -279,6 +295,7 @@ DMD_EXPORT dmd_status dmd_advect_density(const dmd_advect_desc* desc, const floa
 
 /* ---- prediction (Eq. large_time_step, Eq. reverse_simulation, Eq. external_forces) */
 
+/* Workspace bytes of dmd_predict and dmd_predict_backward (host-side query). */
 DMD_EXPORT dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* bytes);
 
 /* out (n x K FP32, ld desc->ldOut): frame j is x_{k[j]} = Phi_R C[:, j].
@@ -309,13 +326,18 @@ DMD_EXPORT dmd_status dmd_predict_backward(const dmd_predict_desc* desc, const f
  * d_u are written as dmd_predict_backward does.
  * Mixed form (r <= 160): the frames never reach memory.  The loss alone is
  * the reconstruction kernel with a loss epilogue (Phi_R read once); with the
- * gradient one kernel recomputes each 128-row x 128-frame tile on the tensor
- * cores, forms G in its epilogue, keeps G in tensor memory and accumulates
- * dC^T += G^T Phi_tile there (Phi_R read once per 128 frames), with FP64
- * partials per CTA summed in a fixed order.
+ * gradient Phi_R is first copied once into the workspace as bf16 hi / lo
+ * planes in the tensor cores' operand layout (4 bytes per row and mode,
+ * r padded to a multiple of 16), then one kernel recomputes each 128-row x
+ * 128-frame tile on the tensor cores from that copy, forms G in its
+ * epilogue, keeps G in tensor memory and accumulates dC^T += G^T Phi_tile
+ * there (the copy read once per 128 frames), with FP64 partials per CTA
+ * summed in a fixed order.
  * FP32 form (and r > 160): frames are recomputed in chunks of desc->chunk;
  * each chunk is written, turned into G by a loss kernel and reduced by the
  * Phi_R^T G pass. */
+DMD_EXPORT dmd_status dmd_predict_loss_workspace_bytes(const dmd_predict_desc* desc, int32_t want_grad,
+                                                       size_t* bytes);
 DMD_EXPORT dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                             const int32_t* k, const float* u, const float* target,
                             const double* w, const dmd_loss_opts* opts, int32_t want_grad, double* loss,

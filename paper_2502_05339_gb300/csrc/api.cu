@@ -496,6 +496,7 @@ struct OptRequest {
 
 dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, const double* Omega, float* PhiR,
                     double* modal, int32_t* info, FitBufs& b, cudaStream_t st, const OptRequest* opt = nullptr) {
+  const StatusScope scope(info);   // bounded waits of this fit report to info
   const Tall tall{d.precision};
   const int64_t n = b.n;
   const int m = b.m, l = b.l, r = b.r, q = b.q;
@@ -584,24 +585,28 @@ bool fused_loss(const dmd_predict_desc& d) {
 }
 
 void carve_predict(Arena& a, const dmd_predict_desc& d, int mode, PredBufs& b) {
-  // mode 0: forward, 1: backward from dOut, 2: streamed loss
+  // mode 0: forward, 1: backward from dOut, 2: streamed loss, 3: streamed
+  // loss and its gradient
   const Tall tall{d.precision};
   const int r = d.r, K = d.K;
   const int steps = d.q > 0 ? d.steps : 0;
+  const bool grad = mode == 1 || mode == 3, loss = mode >= 2;
   b.C = a.take<double>((size_t)r * K);
   b.Xi = a.take<double>((size_t)r * (steps + 1));
-  b.dC = (mode >= 1) ? a.take<double>((size_t)r * K) : nullptr;
-  b.dXi = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
-  b.Mu = (mode >= 1) ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
-  b.partial = (mode == 2) ? a.take<double>((size_t)std::max(loss_blocks(), umma_loss_parts(d.n))) : nullptr;
-  const bool fused = mode == 2 && fused_loss(d);
+  b.dC = grad ? a.take<double>((size_t)r * K) : nullptr;
+  b.dXi = grad ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
+  b.Mu = grad ? a.take<double>((size_t)r * (steps + 1)) : nullptr;
+  b.partial = loss ? a.take<double>((size_t)std::max(loss_blocks(), umma_loss_parts(d.n))) : nullptr;
+  const bool fused = loss && fused_loss(d);
   const int ch = std::min(chunk_of(d), K);
-  b.F = (mode == 2 && !fused) ? a.take<float>((size_t)round_up(d.n, 32) * ch) : nullptr;
+  b.F = (loss && !fused) ? a.take<float>((size_t)round_up(d.n, 32) * ch) : nullptr;
   size_t g = 0;
   if (mode == 0) g = tall.nn_bytes(d.n, r, K);
   if (mode == 1) g = tall.tn_bytes(d.n, r, K);
-  if (mode == 2 && fused) g = std::max(umma_nn_workspace_bytes(d.n, r, K), umma_loss_grad_workspace_bytes(d.n, r, K));
-  if (mode == 2 && !fused) g = std::max(tall.nn_bytes(d.n, r, ch), tall.tn_bytes(d.n, r, ch));
+  if (mode == 2 && fused) g = umma_nn_workspace_bytes(d.n, r, std::min(K, 4096));
+  if (mode == 3 && fused) g = umma_loss_grad_workspace_bytes(d.n, r, K);
+  if (mode == 2 && !fused) g = tall.nn_bytes(d.n, r, ch);
+  if (mode == 3 && !fused) g = std::max(tall.nn_bytes(d.n, r, ch), tall.tn_bytes(d.n, r, ch));
   b.gemm_ws = a.take<char>(g, 1024);
 }
 
@@ -800,6 +805,7 @@ extern "C" dmd_status dmd_upsample(const dmd_upsample_desc* desc, const float* P
     carve_upsample(a, d, b);
     const Tall tall{d.precision};
     const int r = d.r, T = d.T;
+    const StatusScope scope(info);
     DMD_CUDA_TRY(cudaMemsetAsync(info, 0, DMD_INFO_WORDS * sizeof(int32_t), st));
     if (d.gram_given) {
       DMD_CUDA_TRY(cudaMemcpyAsync(b.G, gram, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -822,6 +828,17 @@ extern "C" {
 const char* dmd_last_error(void) { return g_err; }
 const char* dmd_version(void) { return "libdmd 0.1 (sm_103a)"; }
 uint64_t dmd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+dmd_status dmd_async_status(int32_t* words, int32_t clear, void* stream) {
+  DMD_REQUIRE(words != nullptr, "dmd_async_status: words is NULL");
+  int32_t* w = async_status_word();
+  DMD_REQUIRE(w != nullptr, "dmd_async_status: no status word on the current device");
+  cudaStream_t st = (cudaStream_t)stream;
+  DMD_CUDA_TRY(cudaMemcpyAsync(words, w, DMD_INFO_WORDS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (clear) DMD_CUDA_TRY(cudaMemsetAsync(w, 0, DMD_INFO_WORDS * sizeof(int32_t), st));
+  DMD_CUDA_TRY(cudaStreamSynchronize(st));
+  return DMD_OK;
+}
 
 dmd_status dmd_fit_workspace_bytes(const dmd_fit_desc* desc, size_t* bytes) {
   DMD_TRY(validate_fit(desc));
@@ -886,13 +903,23 @@ dmd_status dmd_predict_workspace_bytes(const dmd_predict_desc* desc, size_t* byt
   DMD_TRY(validate_predict(desc, false));
   DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
   size_t best = 0;
-  for (int mode = 0; mode < 3; ++mode) {
+  for (int mode = 0; mode < 2; ++mode) {
     Arena a;
     PredBufs b;
     carve_predict(a, *desc, mode, b);
     best = std::max(best, a.used + 256);
   }
   *bytes = best;
+  return DMD_OK;
+}
+
+dmd_status dmd_predict_loss_workspace_bytes(const dmd_predict_desc* desc, int32_t want_grad, size_t* bytes) {
+  DMD_TRY(validate_predict(desc, false));
+  DMD_REQUIRE(bytes != nullptr, "bytes is NULL");
+  Arena a;
+  PredBufs b;
+  carve_predict(a, *desc, want_grad ? 3 : 2, b);
+  *bytes = a.used + 256;
   return DMD_OK;
 }
 
@@ -942,11 +969,11 @@ dmd_status dmd_predict_loss(const dmd_predict_desc* desc, const float* Phi_R, co
               "dmd_predict_loss: loss kind must be quadratic or Huber with a finite delta > 0");
   const float delta = (opts && opts->kind == DMD_LOSS_HUBER) ? (float)opts->delta : 0.f;
   size_t need = 0;
-  DMD_TRY(dmd_predict_workspace_bytes(desc, &need));
+  DMD_TRY(dmd_predict_loss_workspace_bytes(desc, want_grad, &need));
   cudaStream_t st = (cudaStream_t)stream;
   return with_arena(workspace, ws_bytes, [&](Arena& a) -> dmd_status {
     PredBufs b;
-    carve_predict(a, *desc, 2, b);
+    carve_predict(a, *desc, want_grad ? 3 : 2, b);
     const Tall tall{desc->precision};
     DMD_TRY(form_coefficients(*desc, modal, k, u, b, st));
     if (fused_loss(*desc)) {

@@ -180,6 +180,7 @@ extern "C" dmd_status dmd_fit_predict_batch(int32_t count, const dmd_scene* scen
     void* ws = base + lane_off[l];
     status = dmd_fit(&s.fit, s.S, nullptr, nullptr, s.Phi_R, s.modal, s.info, ws, lane_bytes[l], st);
     if (status == DMD_OK && s.K > 0) {
+      const ::dmd::StatusScope scope(s.info);   // the scene's waits report to its own info
       const dmd_predict_desc p = predict_desc_of(s);
       status = ::dmd::predict_forward(&p, s.Phi_R, s.modal, s.k, nullptr, s.out, ws, lane_bytes[l], st,
                                       "dmd_fit_predict_batch");

@@ -52,6 +52,24 @@ void count_launch();
     }                                                                              \
   } while (0)
 
+// Status word that the bounded device waits report to (DMD_ETIMEOUT): for
+// kernels launched from this host thread while a StatusScope is open, the
+// running entry point's info (the fits); otherwise the current device's
+// asynchronous status word, which dmd_async_status reads and clears.
+int32_t* status_word();
+int32_t* async_status_word();
+
+class StatusScope {
+ public:
+  explicit StatusScope(int32_t* word);
+  ~StatusScope();
+  StatusScope(const StatusScope&) = delete;
+  StatusScope& operator=(const StatusScope&) = delete;
+
+ private:
+  int32_t* prev_;
+};
+
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t x, int64_t a) { return (x + a - 1) / a; }
 

@@ -1,9 +1,17 @@
 // Small element-wise steps between the stages of the fit.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace dmd {
 
 namespace {
+
+// Asynchronous status words of the entry points without an info argument
+// (one copy per device, zero-initialised when the module loads).
+__device__ int32_t g_async_status[DMD_INFO_WORDS];
+
+thread_local int32_t* t_status = nullptr;
 
 // sigma_i = sqrt(max(ev_i, 0)) for the r leading eigenvalues of B B^T
 // (descending), inv_sq_i = 1 / ev_i; rank guard sigma_{r-1} > 1e-6 sigma_0.
@@ -179,5 +187,25 @@ dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st) {
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
+
+int32_t* async_status_word() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int32_t*> addr[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  int32_t* a = addr[dev].load(std::memory_order_acquire);
+  if (a == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_async_status) != cudaSuccess) return nullptr;
+    a = static_cast<int32_t*>(p);
+    addr[dev].store(a, std::memory_order_release);
+  }
+  return a;
+}
+
+int32_t* status_word() { return t_status != nullptr ? t_status : async_status_word(); }
+
+StatusScope::StatusScope(int32_t* word) : prev_(t_status) { t_status = word; }
+StatusScope::~StatusScope() { t_status = prev_; }
 
 }  // namespace dmd

@@ -399,7 +399,7 @@ dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, co
   DMD_TRY(make_map(&mB, B, n, N, ldb, TN_BR, TN_BT, true));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TN_SMEM));
   k_gemm_tn_f32<<<(unsigned)(ntiles * splits), TN_THREADS, TN_SMEM, st>>>(mA, mB, n, Ka, N, part, nta, ntb, ntiles,
-                                                                         sym ? 1 : 0, chunk, nullptr, skip);
+                                                                         sym ? 1 : 0, chunk, status_word(), skip);
   DMD_LAUNCH_CHECK();
   const int64_t count = (int64_t)Ka * N;
   k_reduce_splits<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(Ka, N, splits, part, C, sym ? 1 : 0, skip);

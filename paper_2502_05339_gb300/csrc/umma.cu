@@ -957,7 +957,8 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
     const int ns = bres_stages(ksteps, Np);
     const size_t smem = bres_smem(ksteps, Np, ns);
     DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_bres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, ns, nullptr, skip);
+    k_umma_nn_bres<<<grid, NN_THREADS, smem, st>>>(mapA, split, C, ldc, n, N, Np, ksteps, ntiles, ns, status_word(),
+                                                   skip);
     DMD_LAUNCH_CHECK();
     return DMD_OK;
   }
@@ -977,7 +978,7 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, 16));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_umma_nn_ares<0><<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
-                                                     ntiles, nullptr, nullptr, 0.f, nullptr, nullptr, skip);
+                                                     ntiles, nullptr, nullptr, 0.f, nullptr, status_word(), skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
@@ -1018,7 +1019,7 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // no frames are stored: the output map argument is unused (the A map stands in)
   k_umma_nn_ares<1><<<grid, AR_THREADS, smem, st>>>(mapA, mapA, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
-                                                     ntiles, tgt, w, delta, part, nullptr, nullptr);
+                                                     ntiles, tgt, w, delta, part, status_word(), nullptr);
   DMD_LAUNCH_CHECK();
   *parts = grid;
   return DMD_OK;
@@ -1115,7 +1116,7 @@ dmd_status umma_gemm_tn_flush(int64_t n, int Ka, int N, const float* A, int64_t 
       const size_t smem = tn_smem(Mt, Np, nsplit, ns);
       DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_umma_tn<<<grid, TN_THREADS, smem, st>>>(mA, mB, n, ka, nb, Mt, Np, nsplit, flush, sym ? 1 : 0, ns, chunk,
-                                                part, nullptr, skip);
+                                                part, status_word(), skip);
       DMD_LAUNCH_CHECK();
       // reduce into the (a0, b0) block of C (of C^T when swapped)
       const int64_t count = (int64_t)ka * nb;

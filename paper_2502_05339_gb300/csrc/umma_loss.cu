@@ -9,49 +9,54 @@
 // the chain rule to lambda, beta (and the control inputs) is small FP64 work
 // done elsewhere.
 //
-// k_umma_loss_grad works on 128-frame groups.  For one group, every CTA walks
-// its 128-row tiles of Phi_R and for each tile:
-//   fwd   D (128 frames x 128 rows) = C_g^T Phi_tile^T        (tensor memory)
+// k_split_phi first writes Phi_R once as bf16 hi / lo planes in the operand
+// layout of the tensor cores, tile by tile (below); k_umma_loss_grad then
+// works on 128-frame groups.  For one group, every CTA walks its 96-row tiles
+// and for each tile:
+//   load  the tile's hi and lo planes by bulk copies straight into shared
+//         memory (no conversion on the SM)
+//   fwd   D (128 frames x 96 rows) = C_g^T Phi_tile^T          (tensor memory)
 //   epi   one thread per frame: e = x - t, loss += w rho(e), g = w rho'(e),
 //         g split into bf16 hi / lo and written back into tensor memory over
 //         D as the A operand of the next product
 //   bwd   dC_g^T (128 frames x r) += G^T Phi_tile                (tensor memory)
 // with every product in the BF16x3 form (hi*hi + hi*lo + lo*hi, FP32
-// accumulation).  D / G is double-buffered and the MMA thread issues
-// fwd(t + 1) before bwd(t), so the tensor pipe works on the next tile while
-// the epilogue turns the current one into G.  dC_g^T is drained into a
-// per-CTA FP64 partial every 32 tiles (4096 rows) and at the end of the
-// group; the partials are summed over CTAs in a fixed order afterwards, so
-// the result is deterministic.  Phi_R is read once per frame group, the
+// accumulation).  The MMA thread issues fwd(t + 1) before bwd(t), so the
+// tensor pipe works on the next tile while the epilogue turns the current one
+// into G (D / G is double-buffered).  Three tile buffers keep the loads off
+// that chain: the copies of tile t + 2 go out when bwd(t - 1) has finished,
+// and fwd(t + 2) is issued only after fwd(t + 1) and bwd(t), which hide
+// them; the producer also prefetches the tile three items ahead into L2.
+// (Two buffers of 128-row tiles, the shared-memory limit with 128 rows, left
+// the tensor pipe idle for each tile's load.)  dC_g^T is drained into a
+// per-CTA FP64 partial every 32 tiles and at the end of the group; the
+// partials are summed over CTAs in a fixed order afterwards, so the result is
+// deterministic.  The split copy is read once per frame group, the
 // coefficient group once per CTA.
 //
-// One bf16 copy of the tile (hi and lo planes) serves both products: core
-// matrices of 8 rows x 8 modes (16-byte rows of 8 consecutive modes), at
-// (row / 8) * RS + (mode / 8) * 128 bytes with RS = 256 ks.  The forward
-// product reads it as its B operand K-major (N = rows, K = modes: K-adjacent
-// cores 128 B apart, 8-row groups RS apart), the backward product as its B
-// operand MN-major (N = modes, K = rows: K-adjacent cores RS apart, 8-mode
-// groups 128 B apart).  The copy is double-buffered, so converting the next
-// tile overlaps the current tile's products.
+// Split tile layout (one plane = 2 ks groups of 8 modes, ks = K-slices of r):
+// 8-mode group g of a 96-row tile is 1536 contiguous bytes, row t's 8 modes
+// (bf16) at t * 16; groups follow each other, and a tile is its hi plane then
+// its lo plane.  In shared memory the same bytes serve both products: the
+// forward product reads them as its B operand K-major (N = rows: 8-row groups
+// 128 B apart; K = modes: K-adjacent groups 1536 B apart), the backward
+// product as its B operand MN-major (K = rows: 8-row groups 128 B apart;
+// N = modes: 8-mode groups 1536 B apart).
 //
 // Tensor memory (512 columns x 128 lanes, lane = frame of the group):
-//   [0, 8 ks)                    C_g^T hi as an A operand (ks = K-slices of r)
-//   [80, 208), [208, 336)        D, then G, two buffers: the tile's rows
-//                                0..63 and 64..127 are handled by separate
+//   [0, 8 ks), [80, 80 + 8 ks)   C_g^T hi and lo as A operands
+//   [160, 256), [256, 352)       D, then G, two buffers: the tile's rows
+//                                0..47 and 48..95 are handled by separate
 //                                epilogue warps, each writing G over its own
-//                                64 D columns (hi of its four 16-row slices,
+//                                48 D columns (hi of its three 16-row slices,
 //                                then lo)
-//   [336, 336 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
-// C_g^T lo is an A operand in shared memory (K-major, the tile layout with
-// frames for rows).  Shared memory also holds a TMA ring of FP32 Phi slices
-// (128 rows x 16 modes), the two tile copies and the tile's targets.
+//   [352, 352 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
 //
-// Roles (14 warps): 0 TMA producer, 1 MMA issuer, 2-5 converters (FP32 slice
-// -> bf16 planes), 6-13 epilogue (frame = TMEM lane; two warps per lane
-// quarter, one per half of the tile's rows).  Every wait is bounded
-// (2 s); a wait that runs out aborts the CTA: roles leave their loops, the
-// producer and the MMA issuer drain what they issued, TMEM is freed and the
-// status word gets DMD_ETIMEOUT.
+// Roles (10 warps): 0 producer (bulk copies), 1 MMA issuer, 2-9 epilogue
+// (frame = TMEM lane; two warps per lane quarter, one per half of the tile's
+// rows).  Every wait is bounded (2 s); a wait that runs out aborts the CTA:
+// roles leave their loops, the producer and the MMA issuer drain what they
+// issued, TMEM is freed and the status word gets DMD_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -67,11 +72,18 @@ int num_sms();
 
 namespace {
 
-constexpr int LG_THREADS = 448;   // 14 warps: producer, MMA issuer, 4 converters, 8 epilogue
+constexpr int LG_THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue
 constexpr int LG_MAXKS = 10;      // r <= 160
-constexpr int LG_RING = 3;        // TMA stages of FP32 Phi slices (8 KB each): as many as fit
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
-constexpr uint32_t LG_COL_D = 80, LG_COL_DC = 336;   // D / G buffers at 80 and 208
+constexpr int LG_TR = 96;         // rows of a tile
+constexpr int LG_NBUF = 3;        // tile buffers in shared memory
+constexpr uint32_t LG_HALF = LG_TR / 2;   // rows (D columns) per epilogue half
+constexpr int LG_HS = LG_TR / 32;         // 16-row slices per half
+// tensor-memory columns: C_g^T hi, C_g^T lo, two D / G buffers, dC_g^T
+constexpr uint32_t LG_COL_CTHI = 0, LG_COL_CTLO = 8 * LG_MAXKS, LG_COL_D = 16 * LG_MAXKS,
+                   LG_COL_DC = LG_COL_D + 2 * LG_TR;
+static_assert(LG_COL_DC + 16 * LG_MAXKS <= 512, "tensor-memory layout exceeds 512 columns");
+constexpr uint32_t LG_GROUP = LG_TR * 16;  // bytes of one 8-mode group of a tile plane
 
 // Split 8 consecutive FP32 values into bf16 hi / lo 16-byte chunks.
 __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
@@ -87,45 +99,51 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Row t's 16 modes of slice s, split into bf16 hi / lo, into the tile copy
-// (planes `hi` and `lo`, 8-row groups RS bytes apart).
-__device__ __forceinline__ void store_tile_row(const float* x, uint8_t* hi, uint8_t* lo, int t, int s, uint32_t RS) {
-  const uint32_t off = (uint32_t)(t >> 3) * RS + (uint32_t)s * 256u + (uint32_t)(t & 7) * 16u;
-  uint4 h0, l0, h1, l1;
-  split8(x, h0, l0);
-  split8(x + 8, h1, l1);
-  *reinterpret_cast<uint4*>(hi + off) = h0;
-  *reinterpret_cast<uint4*>(hi + off + 128) = h1;
-  *reinterpret_cast<uint4*>(lo + off) = l0;
-  *reinterpret_cast<uint4*>(lo + off + 128) = l1;
+// Phi_R (n x r FP32, column-major, ld ldPhi) -> the split tile layout above:
+// one thread per (tile, 8-mode group, row); zeros past n and past r.
+__global__ void k_split_phi(int64_t n, int r, int G, const float* __restrict__ Phi, int64_t ldPhi, int64_t ntiles,
+                            uint8_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // ((tile * G) + group) * LG_TR + row
+  if (i >= ntiles * G * LG_TR) return;
+  const int t = (int)(i % LG_TR);
+  const int64_t tg = i / LG_TR;
+  const int g = (int)(tg % G);
+  const int64_t tile = tg / G;
+  const int64_t row = tile * LG_TR + t;
+  float x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = g * 8 + c;
+    x[c] = (row < n && j < r) ? Phi[(int64_t)j * ldPhi + row] : 0.f;
+  }
+  uint4 hi, lo;
+  split8(x, hi, lo);
+  uint8_t* dst = out + ((tile * 2) * G + g) * (int64_t)LG_GROUP + t * 16;
+  *reinterpret_cast<uint4*>(dst) = hi;
+  *reinterpret_cast<uint4*>(dst + (int64_t)G * LG_GROUP) = lo;
 }
 
 template <bool kHuber>
 __global__ void __launch_bounds__(LG_THREADS, 1)
-    k_umma_loss_grad(const __grid_constant__ CUtensorMap tmPhi, int64_t n, int r, int K, int ks,
+    k_umma_loss_grad(const uint8_t* __restrict__ tiles, int64_t n, int r, int K, int ks,
                      const double* __restrict__ C, const float* __restrict__ tgt, const double* __restrict__ wgt,
                      float delta, int64_t ntiles, double* __restrict__ part, double* __restrict__ loss_part,
                      int32_t* err) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
   const int Np = 16 * ks;                                    // r padded to the K-slices
-  const uint32_t RS = (uint32_t)ks * 256u;                   // one 8-row group of a tile-layout copy
-  const uint32_t plane = 16u * RS;                           // 128 rows x 16 ks modes x 2 bytes
-  uint8_t* ring = sm;                                        // LG_RING x 8 KB
-  uint8_t* phi = ring + LG_RING * 8192;                      // 2 buffers x (hi plane, lo plane)
-  uint8_t* ctlo = phi + 4 * plane;                           // C_g^T lo (frames x modes)
-  float* tgs = reinterpret_cast<float*>(ctlo + plane);       // [2][128] targets of the tile
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 2 * 128);
-  uint64_t* full = bars;                          // [LG_RING] slice landed
-  uint64_t* empty = full + LG_RING;               // [LG_RING] slice converted
-  uint64_t* phi_full = empty + LG_RING;           // [2][LG_MAXKS] slice s of tile buffer b converted
-  uint64_t* bwd_done = phi_full + 2 * LG_MAXKS;   // [2] the bwd MMAs of buffer b's tile finished
-  uint64_t* fwd_done = bwd_done + 2;              // [2] the fwd MMAs of buffer b's tile finished
-  uint64_t* g_full = fwd_done + 2;                // [2] G of buffer b's tile in TMEM
-  uint64_t* tg_full = g_full + 2;                 // [2] targets of buffer b's tile in place
-  uint64_t* ct_full = tg_full + 2;                // C_g^T of the group in place
-  uint64_t* dc_full = ct_full + 1;                // dC^T ready to drain
-  uint64_t* dc_free = dc_full + 1;                // dC^T drained
+  const uint32_t plane = (uint32_t)ks * 2u * LG_GROUP;       // one tile plane: LG_TR rows x 16 ks modes x 2 bytes
+  uint8_t* phi = sm;                                         // LG_NBUF buffers x (hi plane, lo plane)
+  float* tgs = reinterpret_cast<float*>(phi + 2 * LG_NBUF * plane);   // [2][LG_TR] targets of the tile
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 2 * LG_TR);
+  uint64_t* phi_full = bars;                           // [LG_NBUF][LG_MAXKS] slice s of tile buffer b landed
+  uint64_t* bwd_done = phi_full + LG_NBUF * LG_MAXKS;  // [LG_NBUF] the bwd MMAs of tile buffer b's tile finished
+  uint64_t* fwd_done = bwd_done + LG_NBUF;             // [2] the fwd MMAs into D / G buffer d finished
+  uint64_t* g_full = fwd_done + 2;                     // [2] G in D / G buffer d
+  uint64_t* tg_full = g_full + 2;                      // [2] targets of the item in place
+  uint64_t* ct_full = tg_full + 2;                     // C_g^T of the group in place
+  uint64_t* dc_full = ct_full + 1;                     // dC^T ready to drain
+  uint64_t* dc_free = dc_full + 1;                     // dC^T drained
   uint64_t* tdown = dc_free + 1;
   double* red = reinterpret_cast<double*>(tdown + 1);   // 8 epilogue warps' loss sums
   uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 8);
@@ -133,13 +151,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < LG_RING; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 128);
-    }
-    for (int i = 0; i < 2 * LG_MAXKS; ++i) mbar_init(&phi_full[i], 128);
+    for (int i = 0; i < LG_NBUF * LG_MAXKS; ++i) mbar_init(&phi_full[i], 1);
+    for (int i = 0; i < LG_NBUF; ++i) mbar_init(&bwd_done[i], 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&bwd_done[i], 1);
       mbar_init(&fwd_done[i], 1);
       mbar_init(&g_full[i], 256);
       mbar_init(&tg_full[i], 256);
@@ -158,9 +172,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   const uint32_t tmem = *tslot;
   const int ngroups = (K + 127) / 128;
   // tiles of this CTA per group; a group's items are its tiles, and the items
-  // of all groups form one sequence u = 0, 1, ... (u & 1 selects the buffers)
+  // of all groups form one sequence u = 0, 1, ...: item u uses tile buffer
+  // u % LG_NBUF and D / G buffer u & 1
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t items = my_tiles * ngroups;
+  const int64_t tile_bytes = 2 * (int64_t)plane;
+  auto tile_of = [&](int64_t u) { return blockIdx.x + (u % my_tiles) * gridDim.x; };
   auto drain_after = [&](int64_t u) {   // dC^T is drained after item u's bwd
     const int64_t j = u % my_tiles;
     return (j + 1) % LG_FLUSH == 0 || j + 1 == my_tiles;
@@ -169,87 +186,88 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
-      uint32_t it = 0;
-      bool issued[LG_RING];
-      uint32_t par[LG_RING];
-      for (int i = 0; i < LG_RING; ++i) issued[i] = false, par[i] = 0;
-      bool ok = true;
-      for (int64_t u = 0; ok && u < items; ++u) {
-        const int64_t tile = blockIdx.x + (u % my_tiles) * gridDim.x;
-        // the next item's tile into L2 now, so that its slices arrive from L2
-        // when the ring (a few slices deep) asks for them
-        if (u + 1 < items) {
-          const int64_t nt = blockIdx.x + ((u + 1) % my_tiles) * gridDim.x;
-          for (int s = 0; s < ks; ++s) tma_prefetch_2d(&tmPhi, (int)(nt * 128), s * 16);
+      int64_t last[LG_NBUF];
+      for (int b = 0; b < LG_NBUF; ++b) last[b] = -1;
+      for (int64_t u = 0; u < items; ++u) {
+        const uint32_t b = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF);
+        // tile buffer b is free once the bwd MMAs of item u - LG_NBUF are done
+        if (u >= LG_NBUF && !mbar_wait(&bwd_done[b], (use - 1) & 1, abort_flag)) break;
+        // the tile of item u + LG_NBUF into L2 now; its copies are issued LG_NBUF items later
+        if (u + LG_NBUF < items) {
+          const uint8_t* nx = tiles + tile_of(u + LG_NBUF) * tile_bytes;
+          bulk_prefetch_l2(nx, plane);
+          bulk_prefetch_l2(nx + plane, plane);
         }
-        for (int s = 0; s < ks; ++s, ++it) {
-          const uint32_t st = it % LG_RING;
-          if (!mbar_wait(&empty[st], ((it / LG_RING) & 1) ^ 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&full[st], 8192);
-          tma_load_2d(ring + st * 8192, &tmPhi, &full[st], (int)(tile * 128), s * 16);
-          issued[st] = true;
-          par[st] = (it / LG_RING) & 1;
+        const uint8_t* src = tiles + tile_of(u) * tile_bytes;
+        uint8_t* dst = phi + b * 2 * plane;
+        for (int s = 0; s < ks; ++s) {
+          uint64_t* bar = &phi_full[b * LG_MAXKS + s];
+          mbar_expect_tx(bar, 2 * 2 * LG_GROUP);
+          bulk_g2s(dst + s * 2 * LG_GROUP, src + s * 2 * LG_GROUP, 2 * LG_GROUP, bar);
+          bulk_g2s(dst + plane + s * 2 * LG_GROUP, src + plane + s * 2 * LG_GROUP, 2 * LG_GROUP, bar);
         }
+        last[b] = u;
       }
-      for (int i = 0; i < LG_RING; ++i)
-        if (issued[i]) mbar_wait_drain(&full[i], par[i]);
+      // the copies in flight land before the CTA tears down
+      for (int b = 0; b < LG_NBUF; ++b)
+        if (last[b] >= 0)
+          for (int s = 0; s < ks; ++s)
+            mbar_wait_drain(&phi_full[b * LG_MAXKS + s], (uint32_t)(last[b] / LG_NBUF) & 1);
     }
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id_fwd = idesc_bf16(128, 128);
+      const uint32_t id_fwd = idesc_bf16(128, LG_TR);
       const uint32_t id_bwd = idesc_bf16(128, Np) | (1u << 16);   // B operand MN-major
-      const uint64_t ctl0 = sdesc(su32(ctlo), 128u, RS);           // C_g^T lo, K-major
       uint32_t fl = 0;
       bool ok = true, fresh = true;
-      // fwd(u): D of item u into buffer u & 1
+      // fwd(u): D of item u into D / G buffer u & 1; A = C_g^T (hi, lo) from
+      // tensor memory, B = the tile K-major (K-adjacent 8-mode groups
+      // LG_GROUP apart, 8-row groups 128 B apart)
       auto fwd = [&](int64_t u) -> bool {
-        const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
+        const uint32_t tb = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF), d = (uint32_t)(u & 1);
         if (u % my_tiles == 0) {   // first tile of a group: its coefficients must be in place
           if (!mbar_wait(ct_full, (uint32_t)(u / my_tiles) & 1, abort_flag)) return false;
           tc_after();
         }
-        const uint8_t* hi = phi + b * 2 * plane;
-        const uint64_t f0 = sdesc(su32(hi), 128u, RS), f_lo = plane >> 4;
-        const uint32_t d = tmem + LG_COL_D + b * 128u;
+        const uint64_t f0 = sdesc(su32(phi + tb * 2 * plane), LG_GROUP, 128u), f_lo = plane >> 4;
+        const uint32_t dcol = tmem + LG_COL_D + d * LG_TR;
         for (int s = 0; s < ks; ++s) {
-          if (!mbar_wait(&phi_full[b * LG_MAXKS + s], use & 1, abort_flag)) return false;
+          if (!mbar_wait(&phi_full[tb * LG_MAXKS + s], use & 1, abort_flag)) return false;
           tc_after();
-          const uint32_t ah = tmem + (uint32_t)s * 8u;
-          const uint64_t al = ctl0 + (uint64_t)((uint32_t)s * 16u);
-          const uint64_t bh = f0 + (uint64_t)((uint32_t)s * 16u), bl = bh + f_lo;
-          umma_bf16_ta(d, ah, bh, id_fwd, s > 0 ? 1u : 0u);
-          umma_bf16_ta(d, ah, bl, id_fwd, 1u);
-          umma_bf16(d, al, bh, id_fwd, 1u);
+          const uint32_t ah = tmem + LG_COL_CTHI + (uint32_t)s * 8u, al = tmem + LG_COL_CTLO + (uint32_t)s * 8u;
+          const uint64_t bh = f0 + (uint64_t)((uint32_t)s * (2u * LG_GROUP >> 4)), bl = bh + f_lo;
+          umma_bf16_ta(dcol, ah, bh, id_fwd, s > 0 ? 1u : 0u);
+          umma_bf16_ta(dcol, ah, bl, id_fwd, 1u);
+          umma_bf16_ta(dcol, al, bh, id_fwd, 1u);
         }
-        umma_commit(&fwd_done[b]);
+        umma_commit(&fwd_done[d]);
         return true;
       };
-      // bwd(u): dC^T += G(u)^T Phi_tile(u)
+      // bwd(u): dC^T += G(u)^T Phi_tile(u); B = the tile MN-major (K = rows:
+      // LBO, 8-row groups 128 B apart; N = modes: SBO, 8-mode groups LG_GROUP apart)
       auto bwd = [&](int64_t u) -> bool {
-        const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
-        if (!mbar_wait(&g_full[b], use & 1, abort_flag)) return false;
+        const uint32_t tb = (uint32_t)(u % LG_NBUF), d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
+        if (!mbar_wait(&g_full[d], used & 1, abort_flag)) return false;
         tc_after();
         if (fresh && fl > 0) {   // the previous drain must have read dC^T
           if (!mbar_wait(dc_free, (fl - 1) & 1, abort_flag)) return false;
           tc_after();
         }
-        const uint8_t* hi = phi + b * 2 * plane;
-        const uint64_t b0 = sdesc(su32(hi), RS, 128u), f_lo = plane >> 4;   // MN-major: LBO along K, SBO along N
-        const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + b * 128u;
-        for (int s = 0; s < 8; ++s) {
+        const uint64_t b0 = sdesc(su32(phi + tb * 2 * plane), 128u, LG_GROUP), f_lo = plane >> 4;
+        const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + d * LG_TR;
+#pragma unroll
+        for (int s = 0; s < LG_TR / 16; ++s) {
           // G of row slice s: in the D columns of its half, hi then lo
-          const uint32_t gh = g0 + (uint32_t)(s >> 2) * 64u + (uint32_t)(s & 3) * 8u, gl = gh + 32u;
-          const uint64_t bh = b0 + (uint64_t)((2u * (uint32_t)s * RS) >> 4), bl = bh + f_lo;
+          const uint32_t gh = g0 + (uint32_t)(s / LG_HS) * LG_HALF + (uint32_t)(s % LG_HS) * 8u;
+          const uint32_t gl = gh + LG_HALF / 2;
+          const uint64_t bh = b0 + (uint64_t)((uint32_t)s * (256u >> 4)), bl = bh + f_lo;
           umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
           umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
           umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
         }
         fresh = false;
-        umma_commit(&bwd_done[b]);
+        umma_commit(&bwd_done[tb]);
         if (drain_after(u)) {
           umma_commit(dc_full);
           ++fl;
@@ -270,36 +288,10 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       umma_commit(tdown);
       mbar_wait_drain(tdown, 0);
     }
-  } else if (warp < 6) {
-    // ------------------------------------------------------------- converters
-    const int t = threadIdx.x - 64;   // 0..127: row of the tile
-    uint32_t it = 0;
-    bool ok = true;
-    for (int64_t u = 0; ok && u < items; ++u) {
-      const uint32_t b = (uint32_t)(u & 1);
-      // tile buffer b is free once the bwd MMAs of item u - 2 are done
-      if (u >= 2 && !mbar_wait(&bwd_done[b], (uint32_t)((u >> 1) - 1) & 1, abort_flag)) break;
-      uint8_t* hi = phi + b * 2 * plane;
-      for (int s = 0; s < ks; ++s, ++it) {
-        const uint32_t st = it % LG_RING;
-        if (!mbar_wait(&full[st], (it / LG_RING) & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        const float* src = reinterpret_cast<const float*>(ring + st * 8192);
-        float x[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];   // row t, modes 16 s + c
-        store_tile_row(x, hi, hi + plane, t, s, RS);
-        fence_async_smem();
-        mbar_arrive(&empty[st]);
-        mbar_arrive(&phi_full[b * LG_MAXKS + s]);
-      }
-    }
   } else {
     // --------------------------------------------------------------- epilogue
     const int q = warp & 3;                                  // lane quarter (TMEM access rule)
-    const int h = (warp - 6) >> 2;                           // half of the tile's rows: 0..63 / 64..127
+    const int h = (warp - 2) >> 2;                           // half of the tile's rows
     const int f = q * 32 + lane;                             // frame within the group = TMEM lane
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const int s_lo = h * ((ks + 1) >> 1), s_hi = h ? ks : ((ks + 1) >> 1);   // coefficient slices of this half
@@ -309,8 +301,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     // the target of row f of the next item (loaded one item ahead by the
     // first half's threads, which fill the shared copy)
     auto target_of = [&](int64_t u) -> float {
-      const int64_t row = (blockIdx.x + (u % my_tiles) * gridDim.x) * 128 + f;
-      return row < n ? tgt[row] : 0.f;
+      const int64_t row = tile_of(u) * LG_TR + f;
+      return (f < LG_TR && row < n) ? tgt[row] : 0.f;
     };
     float tnext = (items > 0 && h == 0) ? target_of(0) : 0.f;
     for (int64_t u = 0; ok && u < items; ++u) {
@@ -322,7 +314,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       // Phi rows, zero targets): neither needs a mask below
       const float w = f_ok ? (float)wgt[fr] : 0.f;
       if (j == 0) {
-        // C_g^T: lane f holds C[:, fr] split into bf16 hi (TMEM) and lo (shared memory)
+        // C_g^T: lane f holds C[:, fr] split into bf16 hi and lo (tensor memory)
         const double* col = C + (int64_t)fr * r;
         for (int s = s_lo; s < s_hi; ++s) {
           uint32_t hh[8], ll[8];
@@ -335,38 +327,35 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
             ll[i] = pack2(__float2bfloat16_rn((float)(v0 - (double)__bfloat162float(h0))),
                           __float2bfloat16_rn((float)(v1 - (double)__bfloat162float(h1))));
           }
-          tmem_st8(tmem + (uint32_t)s * 8u + lane_base, hh);
-          const uint32_t off = (uint32_t)(f >> 3) * RS + (uint32_t)s * 256u + (uint32_t)(f & 7) * 16u;
-          *reinterpret_cast<uint4*>(ctlo + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
-          *reinterpret_cast<uint4*>(ctlo + off + 128) = make_uint4(ll[4], ll[5], ll[6], ll[7]);
+          tmem_st8(tmem + LG_COL_CTHI + (uint32_t)s * 8u + lane_base, hh);
+          tmem_st8(tmem + LG_COL_CTLO + (uint32_t)s * 8u + lane_base, ll);
         }
         tmem_st_wait();
-        fence_async_smem();
         tc_before();
         mbar_arrive(ct_full);
       }
-      const uint32_t b = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
-      float* tg = tgs + b * 128;
+      const uint32_t d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
+      float* tg = tgs + d * LG_TR;
       if (h == 0) {
-        tg[f] = tnext;
+        if (f < LG_TR) tg[f] = tnext;
         if (u + 1 < items) tnext = target_of(u + 1);
       }
-      mbar_arrive(&tg_full[b]);
-      if (!mbar_wait(&tg_full[b], use & 1, abort_flag) || !mbar_wait(&fwd_done[b], use & 1, abort_flag)) {
+      mbar_arrive(&tg_full[d]);
+      if (!mbar_wait(&tg_full[d], used & 1, abort_flag) || !mbar_wait(&fwd_done[d], used & 1, abort_flag)) {
         ok = false;
         break;
       }
       tc_after();
-      // this half's 64 D columns (rows 64 h .. 64 h + 63 of the tile)
-      const uint32_t dcol = tmem + LG_COL_D + b * 128u + (uint32_t)h * 64u + lane_base;
-      uint32_t v[64];
+      // this half's LG_HALF D columns (rows LG_HALF h .. of the tile)
+      const uint32_t dcol = tmem + LG_COL_D + d * LG_TR + (uint32_t)h * LG_HALF + lane_base;
+      uint32_t v[LG_HALF];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
+      for (int s = 0; s < LG_HS; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
       tmem_ld_wait();
-      const float* tgh = tg + h * 64;
+      const float* tgh = tg + h * LG_HALF;
       float s_loss = 0.f;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
+      for (int s = 0; s < LG_HS; ++s) {
         uint32_t hh[8], ll[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -392,15 +381,15 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
           hh[i] = bf2_bits(hv);
           ll[i] = bf2_bits(lv);
         }
-        // G of row slice 4 h + s over this half's D columns, which this
-        // thread has loaded: hi at 8 s, lo at 32 + 8 s
+        // G of row slice LG_HS h + s over this half's D columns, which this
+        // thread has loaded: hi at 8 s, lo at LG_HALF / 2 + 8 s
         tmem_st8(dcol + (uint32_t)s * 8u, hh);
-        tmem_st8(dcol + 32u + (uint32_t)s * 8u, ll);
+        tmem_st8(dcol + LG_HALF / 2 + (uint32_t)s * 8u, ll);
       }
       lacc += kHuber ? (double)s_loss : 0.5 * (double)s_loss;
       tmem_st_wait();
       tc_before();
-      mbar_arrive(&g_full[b]);
+      mbar_arrive(&g_full[d]);
       if (drain_after(u)) {
         // drain dC^T (lane f = frame, columns = modes; this half's slices)
         // into this CTA's FP64 partial
@@ -428,7 +417,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
       }
     }
     const double ws = warp_sum(lacc);
-    if (lane == 0) red[warp - 6] = ws;
+    if (lane == 0) red[warp - 2] = ws;
   }
   tc_before();
   __syncthreads();
@@ -451,10 +440,20 @@ __global__ void k_reduce_dc(int64_t count, int parts, const double* __restrict__
 }
 
 size_t lg_smem(int ks) {
-  return 1024 + (size_t)LG_RING * 8192 + 5 * 16 * (size_t)ks * 256 + 2 * 128 * 4 + 512;
+  // LG_NBUF tile buffers (hi + lo planes), targets, barriers
+  return 1024 + 2 * LG_NBUF * (size_t)ks * 2 * LG_GROUP + 2 * LG_TR * 4 + 512;
 }
 
-int lg_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(n, 128))); }
+int lg_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), ceil_div(n, LG_TR))); }
+
+size_t lg_part_bytes(int64_t n, int r, int K) {
+  return (size_t)round_up((int64_t)lg_grid(n) * K * r * (int64_t)sizeof(double), 1024);
+}
+
+size_t lg_split_bytes(int64_t n, int r) {
+  const int64_t ks = ceil_div(r, 16);
+  return (size_t)(ceil_div(n, LG_TR) * 2 * (2 * ks) * (int64_t)LG_GROUP);
+}
 
 }  // namespace
 
@@ -462,9 +461,10 @@ int lg_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(num_
 
 bool umma_loss_grad_supported(int r) { return r >= 1 && r <= 16 * LG_MAXKS; }
 
-// Workspace of umma_loss_grad: the per-CTA FP64 partials of dC (grid x K x r).
+// Workspace of umma_loss_grad: the per-CTA FP64 partials of dC (grid x K x r)
+// and the split tile copy of Phi_R (4 bytes per row and padded mode).
 size_t umma_loss_grad_workspace_bytes(int64_t n, int r, int K) {
-  return (size_t)lg_grid(n) * (size_t)K * (size_t)r * sizeof(double) + 256;
+  return lg_part_bytes(n, r, K) + lg_split_bytes(n, r) + 256;
 }
 
 // loss_part[0 .. *parts) receives each CTA's loss; dC (r x K FP64) the
@@ -476,17 +476,19 @@ dmd_status umma_loss_grad(int64_t n, int r, int K, const float* Phi, int64_t ldP
     set_error("umma_loss_grad: r = %d outside 1..%d", r, 16 * LG_MAXKS);
     return DMD_EINVAL;
   }
-  const int ks = (int)ceil_div(r, 16);
-  const int64_t ntiles = ceil_div(n, 128);
+  const int ks = (int)ceil_div(r, 16), G = 2 * ks;
+  const int64_t ntiles = ceil_div(n, LG_TR);
   const int grid = lg_grid(n);
-  CUtensorMap map;
-  DMD_TRY(make_map(&map, Phi, n, r, ldPhi, 128, 16));
-  const size_t smem = lg_smem(ks);
   double* part = reinterpret_cast<double*>(ws);
+  uint8_t* tiles = reinterpret_cast<uint8_t*>(ws) + lg_part_bytes(n, r, K);   // 1024-byte aligned
+  const int64_t threads = ntiles * G * LG_TR;
+  k_split_phi<<<(unsigned)ceil_div(threads, 256), 256, 0, st>>>(n, r, G, Phi, ldPhi, ntiles, tiles);
+  DMD_LAUNCH_CHECK();
+  const size_t smem = lg_smem(ks);
   auto kern = delta > 0.f ? k_umma_loss_grad<true> : k_umma_loss_grad<false>;
   DMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, LG_THREADS, smem, st>>>(map, n, r, K, ks, C, tgt, w, delta, ntiles, part, loss_part,
-                                                   nullptr);
+  kern<<<grid, LG_THREADS, smem, st>>>(tiles, n, r, K, ks, C, tgt, w, delta, ntiles, part, loss_part,
+                                       status_word());
   DMD_LAUNCH_CHECK();
   const int64_t count = (int64_t)K * r;
   k_reduce_dc<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, grid, part, dC);

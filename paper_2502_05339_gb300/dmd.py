@@ -83,6 +83,7 @@ SIGNATURES = {
     "dmd_last_error": (ctypes.c_char_p, []),
     "dmd_version": (ctypes.c_char_p, []),
     "dmd_launch_count": (ctypes.c_uint64, []),
+    "dmd_async_status": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "dmd_fit_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _SZ]),
     "dmd_fit": (ctypes.c_int32, [ctypes.POINTER(FitDesc), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "dmd_advect_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(AdvectDesc), ctypes.POINTER(ctypes.c_size_t)]),
@@ -94,6 +95,7 @@ SIGNATURES = {
     "dmd_fit_optdmd": (ctypes.c_int32, [ctypes.POINTER(FitDesc), ctypes.POINTER(OptDmdOpts), _P, _P, _P, _P, _P,
                                         _P, _P, ctypes.c_size_t, _P]),
     "dmd_predict_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _SZ]),
+    "dmd_predict_loss_workspace_bytes": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), ctypes.c_int32, _SZ]),
     "dmd_predict": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "dmd_predict_noalloc": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P]),
     "dmd_predict_backward": (ctypes.c_int32, [ctypes.POINTER(PredictDesc), _P, _P, _P, _P, _P, _P, _P, _P,
@@ -141,6 +143,18 @@ def lib() -> ctypes.CDLL:
 def _check(status: int, what: str):
     if status != 0:
         raise DmdError(what, status, lib().dmd_last_error().decode())
+
+
+def async_status(device=None, clear: bool = True) -> list[int]:
+    """The asynchronous status words of the current (or given) device after
+    the work queued on its current stream: [0] is DMD_ETIMEOUT if a bounded
+    wait of a call without an info argument ran out, [4] its site."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    words = (ctypes.c_int32 * INFO_WORDS)()
+    with torch.cuda.device(dev):
+        _check(lib().dmd_async_status(ctypes.cast(words, ctypes.c_void_p), 1 if clear else 0, _stream(dev)),
+               "dmd_async_status")
+    return list(words)
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -480,7 +494,10 @@ def dmd_predict_loss(model: DmdModel, ks, target: torch.Tensor, w: torch.Tensor,
     _check_control(model, u)
     steps = 0 if u is None else u.shape[0]
     d = _pdesc(model, kt.numel(), round_up(model.n, 32), precision, steps, chunk)
-    ws = _pred_ws(d, dev)
+    nb = ctypes.c_size_t(0)
+    _check(lib().dmd_predict_loss_workspace_bytes(ctypes.byref(d), 1 if want_grad else 0, ctypes.byref(nb)),
+           "dmd_predict_loss_workspace_bytes")
+    ws = _workspace(nb.value, dev)
     md = _check_modal(model, modal)
     dmodal = torch.empty_like(md) if want_grad else None
     du = torch.empty_like(u) if (want_grad and u is not None) else None

@@ -55,6 +55,16 @@ def test_host_side_queries_without_gpu(libdmd):
     assert L.dmd_predict_workspace_bytes(ctypes.byref(p), ctypes.byref(nb)) == 0
     # a too-small workspace is refused before any device work
     assert L.dmd_predict(ctypes.byref(p), 16, 16, 16, None, 16, 256, 8, None) == 2   # ENOMEM
+    assert L.dmd_async_status(None, 1, None) == 1                                      # EINVAL: no host array
+    # the mixed-form loss gradient holds a bf16 hi / lo copy of Phi_R (4 bytes
+    # per row and mode, r padded to 16); the loss alone and dmd_predict do not
+    p = dmd.PredictDesc(n=6291456, ldPhi=6291456, ldOut=6291456, r=150, K=1000, q=0, steps=0, precision=1, chunk=0)
+    nl, ng, npred = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert L.dmd_predict_loss_workspace_bytes(ctypes.byref(p), 0, ctypes.byref(nl)) == 0
+    assert L.dmd_predict_loss_workspace_bytes(ctypes.byref(p), 1, ctypes.byref(ng)) == 0
+    assert L.dmd_predict_workspace_bytes(ctypes.byref(p), ctypes.byref(npred)) == 0
+    split = 6291456 * 160 * 4
+    assert ng.value >= split and nl.value < split and npred.value < split
 
 
 def test_optdmd_rejects_control_and_large_rank():

@@ -94,6 +94,9 @@ def test_fused_loss_many_tiles(dmd, kind):
     model, PhiR, lam, beta = _model(dmd, 700_001, 75, 0, 22)
     ks = list(range(300))
     _check(dmd, model, PhiR, lam, beta, ks, "mixed", kind, 6)
+    # none of the tensor-core kernels' bounded waits ran out
+    words = dmd.async_status()
+    assert words[0] == 0, words
 
 
 def test_loss_options_are_checked(dmd):
