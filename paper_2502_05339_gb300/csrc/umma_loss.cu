@@ -21,14 +21,13 @@
 //         D as the A operand of the next product
 //   bwd   dC_g^T (128 frames x r) += G^T Phi_tile                (tensor memory)
 // with every product in the BF16x3 form (hi*hi + hi*lo + lo*hi, FP32
-// accumulation).  The MMA thread issues fwd(t + 1) before bwd(t), so the
-// tensor pipe works on the next tile while the epilogue turns the current one
-// into G (D / G is double-buffered).  Three tile buffers keep the loads off
-// that chain: the copies of tile t + 2 go out when bwd(t - 1) has finished,
-// and fwd(t + 2) is issued only after fwd(t + 1) and bwd(t), which hide
-// them; the producer also prefetches the tile three items ahead into L2.
-// (Two buffers of 128-row tiles, the shared-memory limit with 128 rows, left
-// the tensor pipe idle for each tile's load.)  dC_g^T is drained into a
+// accumulation).  The forward and the backward products are issued by two
+// threads: a tcgen05.mma holds its issuing thread ~130 cycles, about twice
+// what the tensor pipe needs for these shapes, so one issuer leaves the pipe
+// half idle.  D / G is double-buffered (fwd(t + 2) waits for bwd(t) to
+// finish); three tile buffers let the copies of tile t + 3 go out as soon
+// as bwd(t) has finished, and the producer prefetches that tile into L2
+// three items ahead.  dC_g^T is drained into a
 // per-CTA FP64 partial every 32 tiles and at the end of the group; the
 // partials are summed over CTAs in a fixed order afterwards, so the result is
 // deterministic.  The split copy is read once per frame group, the
@@ -52,11 +51,12 @@
 //                                then lo)
 //   [352, 352 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
 //
-// Roles (10 warps): 0 producer (bulk copies), 1 MMA issuer, 2-9 epilogue
-// (frame = TMEM lane; two warps per lane quarter, one per half of the tile's
-// rows).  Every wait is bounded (2 s); a wait that runs out aborts the CTA:
-// roles leave their loops, the producer and the MMA issuer drain what they
-// issued, TMEM is freed and the status word gets DMD_ETIMEOUT.
+// Roles (11 warps): 0 producer (bulk copies), 1 forward MMA issuer, 2-9
+// epilogue (frame = TMEM lane; two warps per lane quarter, one per half of
+// the tile's rows), 10 backward MMA issuer.  Every wait is bounded (2 s); a
+// wait that runs out aborts the CTA: roles leave their loops, the producer
+// and the MMA issuers drain what they issued, TMEM is freed and the status
+// word gets DMD_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -72,7 +72,8 @@ int num_sms();
 
 namespace {
 
-constexpr int LG_THREADS = 320;   // 10 warps: producer, MMA issuer, 8 epilogue
+constexpr int LG_THREADS = 352;   // 11 warps: producer, fwd issuer, 8 epilogue, bwd issuer
+constexpr int LG_WARP_BWD = 10;   // the warp that issues the backward products
 constexpr int LG_MAXKS = 10;      // r <= 160
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
 constexpr int LG_TR = 96;         // rows of a tile
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     mbar_init(ct_full, 256);
     mbar_init(dc_full, 1);
     mbar_init(dc_free, 256);
-    mbar_init(tdown, 1);
+    mbar_init(tdown, 2);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -214,78 +215,81 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
           for (int s = 0; s < ks; ++s)
             mbar_wait_drain(&phi_full[b * LG_MAXKS + s], (uint32_t)(last[b] / LG_NBUF) & 1);
     }
-  } else if (warp == 1) {
-    // -------------------------------------------------------------- MMA issuer
+  } else if (warp == 1 || warp == LG_WARP_BWD) {
+    // ------------------------------------------------------------- MMA issuers
+    // Two issuing threads, one per product: a tcgen05.mma holds its issuing
+    // thread ~130 cycles (measured) while the tensor pipe runs it in about
+    // half that, so one thread issuing both products would leave the pipe
+    // idle.  The products order through barriers: fwd(u) overwrites D / G
+    // buffer u & 1 once bwd(u - 2) has finished; bwd(u) reads G(u) once the
+    // epilogue has written it.
     if (lane == 0) {
-      const uint32_t id_fwd = idesc_bf16(128, LG_TR);
-      const uint32_t id_bwd = idesc_bf16(128, Np) | (1u << 16);   // B operand MN-major
-      uint32_t fl = 0;
-      bool ok = true, fresh = true;
-      // fwd(u): D of item u into D / G buffer u & 1; A = C_g^T (hi, lo) from
-      // tensor memory, B = the tile K-major (K-adjacent 8-mode groups
-      // LG_GROUP apart, 8-row groups 128 B apart)
-      auto fwd = [&](int64_t u) -> bool {
-        const uint32_t tb = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF), d = (uint32_t)(u & 1);
-        if (u % my_tiles == 0) {   // first tile of a group: its coefficients must be in place
-          if (!mbar_wait(ct_full, (uint32_t)(u / my_tiles) & 1, abort_flag)) return false;
-          tc_after();
+      bool ok = true;
+      if (warp == 1) {
+        // fwd(u): D of item u into D / G buffer u & 1; A = C_g^T (hi, lo)
+        // from tensor memory, B = the tile K-major (K-adjacent 8-mode groups
+        // LG_GROUP apart, 8-row groups 128 B apart)
+        const uint32_t id_fwd = idesc_bf16(128, LG_TR);
+        for (int64_t u = 0; ok && u < items; ++u) {
+          const uint32_t tb = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF), d = (uint32_t)(u & 1);
+          if (u >= 2) {
+            const int64_t p = u - 2;
+            if (!(ok = mbar_wait(&bwd_done[p % LG_NBUF], (uint32_t)(p / LG_NBUF) & 1, abort_flag))) break;
+            tc_after();
+          }
+          if (u % my_tiles == 0) {   // first tile of a group: its coefficients must be in place
+            if (!(ok = mbar_wait(ct_full, (uint32_t)(u / my_tiles) & 1, abort_flag))) break;
+            tc_after();
+          }
+          const uint64_t f0 = sdesc(su32(phi + tb * 2 * plane), LG_GROUP, 128u), f_lo = plane >> 4;
+          const uint32_t dcol = tmem + LG_COL_D + d * LG_TR;
+          for (int s = 0; s < ks; ++s) {
+            if (!(ok = mbar_wait(&phi_full[tb * LG_MAXKS + s], use & 1, abort_flag))) break;
+            tc_after();
+            const uint32_t ah = tmem + LG_COL_CTHI + (uint32_t)s * 8u, al = tmem + LG_COL_CTLO + (uint32_t)s * 8u;
+            const uint64_t bh = f0 + (uint64_t)((uint32_t)s * (2u * LG_GROUP >> 4)), bl = bh + f_lo;
+            umma_bf16_ta(dcol, ah, bh, id_fwd, s > 0 ? 1u : 0u);
+            umma_bf16_ta(dcol, ah, bl, id_fwd, 1u);
+            umma_bf16_ta(dcol, al, bh, id_fwd, 1u);
+          }
+          if (ok) umma_commit(&fwd_done[d]);
         }
-        const uint64_t f0 = sdesc(su32(phi + tb * 2 * plane), LG_GROUP, 128u), f_lo = plane >> 4;
-        const uint32_t dcol = tmem + LG_COL_D + d * LG_TR;
-        for (int s = 0; s < ks; ++s) {
-          if (!mbar_wait(&phi_full[tb * LG_MAXKS + s], use & 1, abort_flag)) return false;
+      } else {
+        // bwd(u): dC^T += G(u)^T Phi_tile(u); B = the tile MN-major (K = rows:
+        // LBO, 8-row groups 128 B apart; N = modes: SBO, 8-mode groups LG_GROUP apart)
+        const uint32_t id_bwd = idesc_bf16(128, Np) | (1u << 16);
+        uint32_t fl = 0;
+        bool fresh = true;
+        for (int64_t u = 0; ok && u < items; ++u) {
+          const uint32_t tb = (uint32_t)(u % LG_NBUF), d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
+          if (!(ok = mbar_wait(&g_full[d], used & 1, abort_flag))) break;
           tc_after();
-          const uint32_t ah = tmem + LG_COL_CTHI + (uint32_t)s * 8u, al = tmem + LG_COL_CTLO + (uint32_t)s * 8u;
-          const uint64_t bh = f0 + (uint64_t)((uint32_t)s * (2u * LG_GROUP >> 4)), bl = bh + f_lo;
-          umma_bf16_ta(dcol, ah, bh, id_fwd, s > 0 ? 1u : 0u);
-          umma_bf16_ta(dcol, ah, bl, id_fwd, 1u);
-          umma_bf16_ta(dcol, al, bh, id_fwd, 1u);
-        }
-        umma_commit(&fwd_done[d]);
-        return true;
-      };
-      // bwd(u): dC^T += G(u)^T Phi_tile(u); B = the tile MN-major (K = rows:
-      // LBO, 8-row groups 128 B apart; N = modes: SBO, 8-mode groups LG_GROUP apart)
-      auto bwd = [&](int64_t u) -> bool {
-        const uint32_t tb = (uint32_t)(u % LG_NBUF), d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
-        if (!mbar_wait(&g_full[d], used & 1, abort_flag)) return false;
-        tc_after();
-        if (fresh && fl > 0) {   // the previous drain must have read dC^T
-          if (!mbar_wait(dc_free, (fl - 1) & 1, abort_flag)) return false;
-          tc_after();
-        }
-        const uint64_t b0 = sdesc(su32(phi + tb * 2 * plane), 128u, LG_GROUP), f_lo = plane >> 4;
-        const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + d * LG_TR;
+          if (fresh && fl > 0) {   // the previous drain must have read dC^T
+            if (!(ok = mbar_wait(dc_free, (fl - 1) & 1, abort_flag))) break;
+            tc_after();
+          }
+          const uint64_t b0 = sdesc(su32(phi + tb * 2 * plane), 128u, LG_GROUP), f_lo = plane >> 4;
+          const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + d * LG_TR;
 #pragma unroll
-        for (int s = 0; s < LG_TR / 16; ++s) {
-          // G of row slice s: in the D columns of its half, hi then lo
-          const uint32_t gh = g0 + (uint32_t)(s / LG_HS) * LG_HALF + (uint32_t)(s % LG_HS) * 8u;
-          const uint32_t gl = gh + LG_HALF / 2;
-          const uint64_t bh = b0 + (uint64_t)((uint32_t)s * (256u >> 4)), bl = bh + f_lo;
-          umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
-          umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
-          umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
+          for (int s = 0; s < LG_TR / 16; ++s) {
+            // G of row slice s: in the D columns of its half, hi then lo
+            const uint32_t gh = g0 + (uint32_t)(s / LG_HS) * LG_HALF + (uint32_t)(s % LG_HS) * 8u;
+            const uint32_t gl = gh + LG_HALF / 2;
+            const uint64_t bh = b0 + (uint64_t)((uint32_t)s * (256u >> 4)), bl = bh + f_lo;
+            umma_bf16_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
+            umma_bf16_ta(dc, gh, bl, id_bwd, 1u);
+            umma_bf16_ta(dc, gl, bh, id_bwd, 1u);
+          }
+          fresh = false;
+          umma_commit(&bwd_done[tb]);
+          if (drain_after(u)) {
+            umma_commit(dc_full);
+            ++fl;
+            fresh = true;
+          }
         }
-        fresh = false;
-        umma_commit(&bwd_done[tb]);
-        if (drain_after(u)) {
-          umma_commit(dc_full);
-          ++fl;
-          fresh = true;
-        }
-        return true;
-      };
-      // issue order fwd(0), then per item: fwd(u + 1) before bwd(u), except
-      // across a group boundary, where the next group's coefficients are
-      // loaded only after item u's drain
-      if (items > 0) ok = fwd(0);
-      for (int64_t u = 0; ok && u < items; ++u) {
-        const bool next_same_group = u + 1 < items && (u + 1) % my_tiles != 0;
-        if (next_same_group) ok = fwd(u + 1);
-        ok = ok && bwd(u);
-        if (ok && u + 1 < items && !next_same_group) ok = fwd(u + 1);
       }
-      umma_commit(tdown);
+      umma_commit(tdown);   // one arrival per issuer, when its products have finished
       mbar_wait_drain(tdown, 0);
     }
   } else {
