@@ -20,6 +20,8 @@
 // Every kernel that can fail writes DMD_ENUMERIC / DMD_ENONFINITE to info[0].
 #include <float.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace dmd {
@@ -369,12 +371,16 @@ struct EpsOf<float> {
 // refined in FP64 by k_hess_rqi.
 constexpr int kHqrT = 5;   // rows per lane per batch of the column update (160 per warp)
 
-template <class Real>
+// kSmem: the matrix lives in shared memory, addressed as such with 32-bit
+// indices (a pointer that may point to either space compiles to generic
+// loads and stores, which made every bulge step about twice as slow).
+template <class Real, bool kSmem>
 __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi, Real* Hscratch,
-                      int in_smem, int32_t* info) {
+                      int32_t* info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using Idx = typename std::conditional<kSmem, int, int64_t>::type;
   const int ldw = n | 1;
-  Real* H = in_smem ? reinterpret_cast<Real*>(smem_raw) : Hscratch;
+  Real* H = kSmem ? reinterpret_cast<Real*>(smem_raw) : Hscratch;
   const int lane = threadIdx.x;
   // Deflation threshold.  These eigenvalues only seed the FP64
   // Rayleigh-quotient refinement: an eigenvalue deflated at a subdiagonal of
@@ -388,13 +394,13 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
   for (int j = 0; j < n; ++j) {
     for (int i = lane; i < n; i += 32) {
       const Real v = (i <= j + 1) ? (Real)Hin[i + (int64_t)j * ldh] : Real(0);
-      H[i + (int64_t)j * ldw] = v;
+      H[(Idx)i + (Idx)j * (Idx)ldw] = v;
       amax = fmax(amax, fabs(v));
     }
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   __syncwarp();
-#define HH(i, j) H[(i) + (int64_t)(j) * ldw]
+#define HH(i, j) H[(Idx)(i) + (Idx)(j) * (Idx)ldw]
   Real anorm = amax;
   if (anorm == Real(0)) anorm = 1;
   int hi = n - 1, its = 0, total = 0;
@@ -460,9 +466,10 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
       // reflector P = I - tau v v^T, v = [1, v1, v2], P [x y z]^T = [beta 0 0]^T
       const Real nrm = sqrt(x * x + y * y + z * z);
       if (nrm != Real(0) && (y != Real(0) || z != Real(0))) {
+        // fast division: these eigenvalues only seed the FP64 refinement
         const Real beta = x <= Real(0) ? nrm : -nrm;
-        const Real tau = (beta - x) / beta;
-        const Real sc = Real(1) / (x - beta);
+        const Real tau = __fdividef(beta - x, beta);
+        const Real sc = __fdividef(Real(1), x - beta);
         const Real v1 = y * sc, v2 = z * sc;
         const int c0 = max(lo, k - 1);
         // row update, batched like the column update below: every lane loads
@@ -528,8 +535,8 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
       const Real nrm = sqrt(x * x + y * y);
       if (nrm != Real(0) && y != Real(0)) {
         const Real beta = x <= Real(0) ? nrm : -nrm;
-        const Real tau = (beta - x) / beta;
-        const Real v1 = y / (x - beta);
+        const Real tau = __fdividef(beta - x, beta);
+        const Real v1 = __fdividef(y, x - beta);
         const int k = hi - 1;
         for (int c = max(lo, k - 1) + lane; c <= hi; c += 32) {
           const Real p = tau * (HH(k, c) + v1 * HH(k + 1, c));
@@ -1862,11 +1869,14 @@ bool hqr_fits_smem(int n) { return hqr_smem_bytes(n) <= 200 * 1024; }
 // FP32 Francis QR for the eigenvalue estimates (refined in FP64 by hess_eigvecs).
 dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
                cudaStream_t st) {
-  const bool in_smem = hqr_fits_smem(n);
-  const size_t smem = in_smem ? hqr_smem_bytes(n) : 0;
-  if (smem > 48 * 1024)
-    DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_hqr<float><<<1, 32, smem, st>>>(n, H, ldh, wr, wi, reinterpret_cast<float*>(scratch), in_smem ? 1 : 0, info);
+  if (hqr_fits_smem(n)) {
+    const size_t smem = hqr_smem_bytes(n);
+    if (smem > 48 * 1024)
+      DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_hqr<float, true><<<1, 32, smem, st>>>(n, H, ldh, wr, wi, nullptr, info);
+  } else {
+    k_hqr<float, false><<<1, 32, 0, st>>>(n, H, ldh, wr, wi, reinterpret_cast<float*>(scratch), info);
+  }
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
