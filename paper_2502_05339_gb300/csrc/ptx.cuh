@@ -57,6 +57,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* abo
   }
   return true;
 }
+// The same wait with cluster-scope acquire, for barriers that CTAs of the
+// cluster arrive on remotely.
+__device__ __forceinline__ bool mbar_test_cl(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity, int* abort_flag) {
+  if (mbar_test_cl(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_test_cl(b, parity)) {
+    if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      atomicExch(abort_flag, 1);
+      return false;
+    }
+  }
+  return true;
+}
+// Arrive on the mbarrier at the offset of `b` in the shared memory of the
+// cluster's CTA `rank` (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* b, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(su32(b)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Teardown wait: bounded, ignores the abort flag.
 __device__ __forceinline__ void mbar_wait_drain(uint64_t* b, uint32_t parity) {
   const uint64_t t0 = gtimer();
