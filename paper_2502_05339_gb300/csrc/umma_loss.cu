@@ -89,14 +89,15 @@ constexpr int LG_THREADS = 352;   // 11 warps: producer, fwd issuer / relay, 8 e
 constexpr int LG_WARP_BWD = 10;   // the warp that issues the backward products
 constexpr int LG_MAXKS = 10;      // r <= 160
 constexpr int LG_FLUSH = 32;      // tiles between FP64 drains of dC^T
-constexpr int LG_TR = 96;         // rows of a tile
-constexpr int LG_NBUF = 3;        // tile buffers in shared memory
+constexpr int LG_TR = 192;        // rows of a tile
 constexpr int LG_FRAMES = 256;    // frames of a group (128 per CTA of the pair)
-constexpr uint32_t LG_HALF = LG_TR / 2;   // rows (D columns) per epilogue half; rows per forward view
-constexpr int LG_HS = LG_TR / 32;         // 16-row slices per half
-// tensor-memory columns: C_g^T hi, C_g^T lo, two D / G buffers, dC_g^T
+constexpr uint32_t LG_HALF = LG_TR / 2;   // rows of a row half (a forward view)
+constexpr uint32_t LG_QR = 48;            // rows (D columns) of a quarter: the unit of G and of bwd
+constexpr int LG_NQ = LG_TR / LG_QR;      // quarters of a tile
+constexpr int LG_QS = LG_QR / 16;         // 16-row k-steps per quarter
+// tensor-memory columns: C_g^T hi, C_g^T lo, one D / G accumulator, dC_g^T
 constexpr uint32_t LG_COL_CTHI = 0, LG_COL_CTLO = 8 * LG_MAXKS, LG_COL_D = 16 * LG_MAXKS,
-                   LG_COL_DC = LG_COL_D + 2 * LG_TR;
+                   LG_COL_DC = LG_COL_D + LG_TR;
 static_assert(LG_COL_DC + 16 * LG_MAXKS <= 512, "tensor-memory layout exceeds 512 columns");
 constexpr uint32_t LG_GROUP = LG_HALF * 16;  // bytes of one 8-mode group of a row half
 
@@ -152,16 +153,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
   const int Np = 16 * ks;                                    // r padded to the K-slices
   const int G = 2 * ks;                                      // 8-mode groups of r padded
   const uint32_t vplane = (uint32_t)G * LG_GROUP;            // one view plane (hi or lo)
-  const uint32_t bufsz = 4 * vplane;                         // forward hi, lo; backward hi, lo
-  uint8_t* phi = sm;                                         // LG_NBUF tile buffers
-  float* tgs = reinterpret_cast<float*>(phi + LG_NBUF * bufsz);   // [2][LG_TR] targets of the tile
+  const uint32_t vsz = 2 * vplane;                           // one view (hi and lo planes)
+  uint8_t* fview = sm;                                       // [2] forward views
+  uint8_t* bview = sm + 2 * vsz;                             // the backward view
+  float* tgs = reinterpret_cast<float*>(sm + 3 * vsz);       // [2][LG_TR] targets of the tile
   uint64_t* bars = reinterpret_cast<uint64_t*>(tgs + 2 * LG_TR);
-  uint64_t* phi_full = bars;                    // [LG_NBUF] this CTA's views of tile buffer b landed
-  uint64_t* phi_peer = phi_full + LG_NBUF;      // [LG_NBUF] (even CTA) the odd CTA's views landed
-  uint64_t* bwd_done = phi_peer + LG_NBUF;      // [LG_NBUF] the bwd products of tile buffer b's tile finished
-  uint64_t* fwd_done = bwd_done + LG_NBUF;      // [2] the fwd products into D / G buffer d finished
-  uint64_t* g_full = fwd_done + 2;              // [2] (even CTA) G in D / G buffer d in both CTAs
-  uint64_t* tg_full = g_full + 2;               // [2] targets of the item in place
+  uint64_t* fv_full = bars;                     // [2] this CTA's forward view b landed
+  uint64_t* fv_peer = fv_full + 2;              // [2] (even CTA) the odd CTA's forward view b landed
+  uint64_t* bv_full = fv_peer + 2;              // this CTA's backward view landed
+  uint64_t* bv_peer = bv_full + 1;              // (even CTA) the odd CTA's backward view landed
+  // one fwd completion barrier per forward-view buffer: with a single one,
+  // fwd(u - 1) could complete before the producer looks for fwd(u - 2) and
+  // the parity of the phase it waits for would come round again
+  uint64_t* fwd_done = bv_peer + 1;             // [2] the fwd products of the item in view buffer b finished
+  uint64_t* bwd_done = fwd_done + 2;            // the bwd products of the item finished
+  uint64_t* g_full = bwd_done + 1;              // [LG_NQ] (even CTA) G of quarter k in both CTAs
+  uint64_t* tg_full = g_full + LG_NQ;           // [2] targets of the item in place
   uint64_t* ct_full = tg_full + 2;              // (even CTA) C_g^T of the group in place in both CTAs
   uint64_t* dc_full = ct_full + 1;              // dC^T ready to drain
   uint64_t* dc_free = dc_full + 1;              // (even CTA) dC^T drained in both CTAs
@@ -175,16 +182,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
   const bool lead = crank == 0;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < LG_NBUF; ++i) {
-      mbar_init(&phi_full[i], 1);
-      mbar_init(&phi_peer[i], 1);
-      mbar_init(&bwd_done[i], 1);
-    }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&fwd_done[i], 1);
-      mbar_init(&g_full[i], 512);
+      mbar_init(&fv_full[i], 1);
+      mbar_init(&fv_peer[i], 1);
       mbar_init(&tg_full[i], 256);
     }
+    mbar_init(bv_full, 1);
+    mbar_init(bv_peer, 1);
+    mbar_init(&fwd_done[0], 1);
+    mbar_init(&fwd_done[1], 1);
+    mbar_init(bwd_done, 1);
+    for (int k = 0; k < LG_NQ; ++k) mbar_init(&g_full[k], 256);
     mbar_init(ct_full, 512);
     mbar_init(dc_full, 1);
     mbar_init(dc_free, 512);
@@ -200,8 +208,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
   const uint32_t tmem = *tslot;
   const int ngroups = (K + LG_FRAMES - 1) / LG_FRAMES;
   // tiles of this pair per group; a group's items are its tiles, and the
-  // items of all groups form one sequence u = 0, 1, ...: item u uses tile
-  // buffer u % LG_NBUF and D / G buffer u & 1
+  // items of all groups form one sequence u = 0, 1, ...: item u uses forward
+  // view buffer u & 1
   const int64_t pr = blockIdx.x >> 1, npairs = gridDim.x >> 1;
   const int64_t my_tiles = ntiles > pr ? (ntiles - 1 - pr) / npairs + 1 : 0;
   const int64_t items = my_tiles * ngroups;
@@ -214,68 +222,66 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
+    // forward view of item u into buffer u & 1 once fwd(u - 2) has finished;
+    // backward view of item u once bwd(u - 1) has finished
     if (lane == 0) {
-      int64_t last[LG_NBUF];
-      for (int b = 0; b < LG_NBUF; ++b) last[b] = -1;
       const uint32_t half = (uint32_t)ks * LG_GROUP;   // one row half of a backward view plane
+      int64_t lastf[2] = {-1, -1}, lastb = -1;
       for (int64_t u = 0; u < items; ++u) {
-        const uint32_t b = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF);
-        // tile buffer b is free once the bwd products of item u - LG_NBUF are done
-        if (u >= LG_NBUF && !mbar_wait(&bwd_done[b], (use - 1) & 1, abort_flag)) break;
-        if (u + LG_NBUF < items) bulk_prefetch_l2(tiles + tile_of(u + LG_NBUF) * tile_bytes, 4 * vplane);
+        const uint32_t fb = (uint32_t)(u & 1);
+        if (u >= 2 && !mbar_wait(&fwd_done[fb], (uint32_t)((u - 2) >> 1) & 1, abort_flag)) break;
         const uint8_t* src = tiles + tile_of(u) * tile_bytes;
-        uint8_t* dst = phi + b * bufsz;
-        uint64_t* bar = &phi_full[b];
-        mbar_expect_tx(bar, bufsz);
-        for (uint32_t p = 0; p < 2; ++p) {
-          const uint8_t* sp = src + p * 2 * vplane;
-          // forward view: row half crank, all mode groups
-          bulk_g2s(dst + p * vplane, sp + crank * vplane, vplane, bar);
-          // backward view: mode groups crank ks .. of both row halves
+        if (lead && u + 2 < items) bulk_prefetch_l2(tiles + tile_of(u + 2) * tile_bytes, 4 * vplane);
+        mbar_expect_tx(&fv_full[fb], vsz);
+        for (uint32_t p = 0; p < 2; ++p)   // row half crank, all mode groups
+          bulk_g2s(fview + fb * vsz + p * vplane, src + p * 2 * vplane + crank * vplane, vplane, &fv_full[fb]);
+        lastf[fb] = u;
+        if (u >= 1 && !mbar_wait(bwd_done, (uint32_t)(u - 1) & 1, abort_flag)) break;
+        mbar_expect_tx(bv_full, vsz);
+        for (uint32_t p = 0; p < 2; ++p)   // mode groups crank ks .. of both row halves
           for (uint32_t h = 0; h < 2; ++h)
-            bulk_g2s(dst + 2 * vplane + p * vplane + h * half, sp + h * vplane + crank * half, half, bar);
-        }
-        last[b] = u;
+            bulk_g2s(bview + p * vplane + h * half, src + p * 2 * vplane + h * vplane + crank * half, half, bv_full);
+        lastb = u;
       }
       // the copies in flight land before the CTA tears down
-      for (int b = 0; b < LG_NBUF; ++b)
-        if (last[b] >= 0) mbar_wait_drain(&phi_full[b], (uint32_t)(last[b] / LG_NBUF) & 1);
+      for (int b = 0; b < 2; ++b)
+        if (lastf[b] >= 0) mbar_wait_drain(&fv_full[b], (uint32_t)(lastf[b] >> 1) & 1);
+      if (lastb >= 0) mbar_wait_drain(bv_full, (uint32_t)lastb & 1);
     }
   } else if (!lead && warp == 1) {
-    // ---------------------------------------------- relay (odd CTA): tiles landed
+    // ---------------------------------------------- relay (odd CTA): views landed
     if (lane == 0) {
       for (int64_t u = 0; u < items; ++u) {
-        const uint32_t b = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF);
-        if (!mbar_wait(&phi_full[b], use & 1, abort_flag)) break;
-        mbar_arrive_remote(&phi_peer[b], 0);
+        const uint32_t fb = (uint32_t)(u & 1);
+        if (!mbar_wait(&fv_full[fb], (uint32_t)(u >> 1) & 1, abort_flag)) break;
+        mbar_arrive_remote(&fv_peer[fb], 0);
+        if (!mbar_wait(bv_full, (uint32_t)u & 1, abort_flag)) break;
+        mbar_arrive_remote(bv_peer, 0);
       }
     }
   } else if (lead && (warp == 1 || warp == LG_WARP_BWD)) {
     // ---------------------------------------------- MMA issuers (even CTA)
     // Two issuing threads, one per product; they order through barriers:
-    // fwd(u) overwrites D / G buffer u & 1 once bwd(u - 2) has finished;
-    // bwd(u) reads G(u) once both CTAs' epilogues have written it.
+    // fwd(u) overwrites D / G once bwd(u - 1) has finished; bwd(u) reads G of
+    // quarter k once both CTAs' epilogues have written it.
     if (lane == 0) {
       bool ok = true;
       if (warp == 1) {
-        // fwd(u): D of item u into D / G buffer u & 1; A = C_g^T (hi, lo) from
-        // tensor memory, B = the forward views (K-major: K-adjacent 8-mode
-        // groups LG_GROUP apart, 8-row groups 128 B apart)
+        // fwd(u): D of item u; A = C_g^T (hi, lo) from tensor memory, B = the
+        // forward views (K-major: K-adjacent 8-mode groups LG_GROUP apart,
+        // 8-row groups 128 B apart)
         const uint32_t id_fwd = idesc_bf16(256, LG_TR);
+        const uint32_t dcol = tmem + LG_COL_D;
         for (int64_t u = 0; ok && u < items; ++u) {
-          const uint32_t tb = (uint32_t)(u % LG_NBUF), use = (uint32_t)(u / LG_NBUF), d = (uint32_t)(u & 1);
-          if (u >= 2) {
-            const int64_t p = u - 2;
-            if (!(ok = mbar_wait(&bwd_done[p % LG_NBUF], (uint32_t)(p / LG_NBUF) & 1, abort_flag))) break;
-          }
+          const uint32_t fb = (uint32_t)(u & 1), use = (uint32_t)(u >> 1);
+          if (u >= 1)
+            if (!(ok = mbar_wait(bwd_done, (uint32_t)(u - 1) & 1, abort_flag))) break;
           if (u % my_tiles == 0)   // first tile of a group: both CTAs' coefficients in place
             if (!(ok = mbar_wait_cl(ct_full, (uint32_t)(u / my_tiles) & 1, abort_flag))) break;
-          if (!(ok = mbar_wait(&phi_full[tb], use & 1, abort_flag) &&
-                     mbar_wait_cl(&phi_peer[tb], use & 1, abort_flag)))
+          if (!(ok = mbar_wait(&fv_full[fb], use & 1, abort_flag) && mbar_wait_cl(&fv_peer[fb], use & 1, abort_flag)))
             break;
           tc_after();
-          const uint64_t f0 = sdesc(su32(phi + tb * bufsz), LG_GROUP, 128u), f_lo = vplane >> 4;
-          const uint32_t dcol = tmem + LG_COL_D + d * LG_TR;
+          const uint64_t f0 = sdesc(su32(fview + fb * vsz), LG_GROUP, 128u), f_lo = vplane >> 4;
           for (int s = 0; s < ks; ++s) {
             const uint32_t ah = tmem + LG_COL_CTHI + (uint32_t)s * 8u, al = tmem + LG_COL_CTLO + (uint32_t)s * 8u;
             const uint64_t bh = f0 + (uint64_t)((uint32_t)s * (2u * LG_GROUP >> 4)), bl = bh + f_lo;
@@ -283,37 +289,43 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
             umma_pair_ta(dcol, ah, bl, id_fwd, 1u);
             umma_pair_ta(dcol, al, bh, id_fwd, 1u);
           }
-          umma_commit_pair(&fwd_done[d]);
+          umma_commit_pair(&fwd_done[fb]);
         }
       } else {
-        // bwd(u): dC^T += G(u)^T Phi_tile(u); B = the backward views
-        // (MN-major: K = rows, LBO, 8-row groups 128 B apart, the second
+        // bwd(u), quarter by quarter: dC^T += G_k^T Phi_k; B = the backward
+        // view (MN-major: K = rows, LBO, 8-row groups 128 B apart, the second
         // row half ks LG_GROUP on; N = modes, SBO, 8-mode groups LG_GROUP apart)
         const uint32_t id_bwd = idesc_bf16(256, Np) | (1u << 16);
         const uint32_t half = (uint32_t)ks * LG_GROUP;
+        const uint32_t bv = su32(bview);
+        const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D;
         uint32_t fl = 0;
         bool fresh = true;
         for (int64_t u = 0; ok && u < items; ++u) {
-          const uint32_t tb = (uint32_t)(u % LG_NBUF), d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
-          if (!(ok = mbar_wait_cl(&g_full[d], used & 1, abort_flag))) break;
+          if (!(ok = mbar_wait(bv_full, (uint32_t)u & 1, abort_flag) &&
+                     mbar_wait_cl(bv_peer, (uint32_t)u & 1, abort_flag)))
+            break;
           if (fresh && fl > 0)   // the previous drain must have read dC^T in both CTAs
             if (!(ok = mbar_wait_cl(dc_free, (fl - 1) & 1, abort_flag))) break;
-          tc_after();
-          const uint32_t bv = su32(phi + tb * bufsz + 2 * vplane);
-          const uint32_t dc = tmem + LG_COL_DC, g0 = tmem + LG_COL_D + d * LG_TR;
+          for (int k = 0; ok && k < LG_NQ; ++k) {
+            if (!(ok = mbar_wait_cl(&g_full[k], (uint32_t)u & 1, abort_flag))) break;
+            tc_after();
 #pragma unroll
-          for (int s = 0; s < LG_TR / 16; ++s) {
-            // G of row slice s: in the D columns of its half, hi then lo
-            const uint32_t gh = g0 + (uint32_t)(s / LG_HS) * LG_HALF + (uint32_t)(s % LG_HS) * 8u;
-            const uint32_t gl = gh + LG_HALF / 2;
-            const uint32_t sa = bv + (uint32_t)(s / LG_HS) * half + (uint32_t)(s % LG_HS) * 256u;
-            const uint64_t bh = sdesc(sa, 128u, LG_GROUP), bl = sdesc(sa + vplane, 128u, LG_GROUP);
-            umma_pair_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
-            umma_pair_ta(dc, gh, bl, id_bwd, 1u);
-            umma_pair_ta(dc, gl, bh, id_bwd, 1u);
+            for (int i = 0; i < LG_QS; ++i) {
+              const int s = k * LG_QS + i;   // 16-row k-step of the tile
+              // G of that slice: in quarter k's D columns, hi then lo
+              const uint32_t gh = g0 + (uint32_t)k * LG_QR + (uint32_t)i * 8u, gl = gh + LG_QR / 2;
+              const uint32_t hh = (uint32_t)(s * 16) / LG_HALF;                  // row half
+              const uint32_t sa = bv + hh * half + ((uint32_t)(s * 16) % LG_HALF) / 8u * 128u;
+              const uint64_t bh = sdesc(sa, 128u, LG_GROUP), bl = sdesc(sa + vplane, 128u, LG_GROUP);
+              umma_pair_ta(dc, gh, bh, id_bwd, (fresh && s == 0) ? 0u : 1u);
+              umma_pair_ta(dc, gh, bl, id_bwd, 1u);
+              umma_pair_ta(dc, gl, bh, id_bwd, 1u);
+            }
           }
+          if (!ok) break;
           fresh = false;
-          umma_commit_pair(&bwd_done[tb]);
+          umma_commit_pair(bwd_done);
           if (drain_after(u)) {
             umma_commit_pair(dc_full);
             ++fl;
@@ -325,21 +337,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
     }
   } else if (warp >= 2 && warp < 10) {
     // --------------------------------------------------------------- epilogue
+    // Warp (lane quarter q, h) turns row quarters h and h + 2 into G, in
+    // that order, so that quarters 0 and 1 are ready first.
     const int q = warp & 3;                                  // lane quarter (TMEM access rule)
-    const int h = (warp - 2) >> 2;                           // half of the tile's rows
+    const int h = (warp - 2) >> 2;
     const int f = q * 32 + lane;                             // frame within this CTA's half = TMEM lane
+    const int e = h * 128 + f;                               // this thread's row of the tile's targets
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const int s_lo = h * ((ks + 1) >> 1), s_hi = h ? ks : ((ks + 1) >> 1);   // coefficient slices of this half
+    const int s_lo = h * ((ks + 1) >> 1), s_hi = h ? ks : ((ks + 1) >> 1);   // coefficient slices of this h
     uint32_t fl = 0;
     bool ok = true;
     double lacc = 0.0;
-    // the target of row f of the next item (loaded one item ahead by the
-    // first half's threads, which fill the shared copy)
+    // the target of row e of the next item (loaded one item ahead)
     auto target_of = [&](int64_t u) -> float {
-      const int64_t row = tile_of(u) * LG_TR + f;
-      return (f < LG_TR && row < n) ? tgt[row] : 0.f;
+      const int64_t row = tile_of(u) * LG_TR + e;
+      return (e < LG_TR && row < n) ? tgt[row] : 0.f;
     };
-    float tnext = (items > 0 && h == 0) ? target_of(0) : 0.f;
+    float tnext = items > 0 ? target_of(0) : 0.f;
     for (int64_t u = 0; ok && u < items; ++u) {
       const int g = (int)(u / my_tiles);
       const int64_t j = u % my_tiles;
@@ -371,60 +385,59 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LG_THREADS, 1)
       }
       const uint32_t d = (uint32_t)(u & 1), used = (uint32_t)(u >> 1);
       float* tg = tgs + d * LG_TR;
-      if (h == 0) {
-        if (f < LG_TR) tg[f] = tnext;
-        if (u + 1 < items) tnext = target_of(u + 1);
-      }
+      if (e < LG_TR) tg[e] = tnext;
+      if (u + 1 < items) tnext = target_of(u + 1);
       mbar_arrive(&tg_full[d]);
       if (!mbar_wait(&tg_full[d], used & 1, abort_flag) || !mbar_wait(&fwd_done[d], used & 1, abort_flag)) {
         ok = false;
         break;
       }
       tc_after();
-      // this half's LG_HALF D columns (rows LG_HALF h .. of the tile)
-      const uint32_t dcol = tmem + LG_COL_D + d * LG_TR + (uint32_t)h * LG_HALF + lane_base;
-      uint32_t v[LG_HALF];
-#pragma unroll
-      for (int s = 0; s < LG_HS; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
-      tmem_ld_wait();
-      const float* tgh = tg + h * LG_HALF;
       float s_loss = 0.f;
+      for (int kk = 0; kk < 2; ++kk) {
+        const int k = h + 2 * kk;                            // row quarter
+        const uint32_t dcol = tmem + LG_COL_D + (uint32_t)k * LG_QR + lane_base;
+        uint32_t v[LG_QR];
 #pragma unroll
-      for (int s = 0; s < LG_HS; ++s) {
-        uint32_t hh[8], ll[8];
+        for (int s = 0; s < LG_QS; ++s) tmem_ld16_nw(dcol + (uint32_t)s * 16u, v + 16 * s);
+        tmem_ld_wait();
+        const float* tgq = tg + k * LG_QR;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float2 tt = *reinterpret_cast<const float2*>(tgh + s * 16 + 2 * i);
-          const float e0 = __uint_as_float(v[s * 16 + 2 * i]) - tt.x;
-          const float e1 = __uint_as_float(v[s * 16 + 2 * i + 1]) - tt.y;
-          float g0, g1;
-          if (kHuber) {
-            const float a0 = fabsf(e0), a1 = fabsf(e1);
-            g0 = w * fminf(fmaxf(e0, -delta), delta);
-            g1 = w * fminf(fmaxf(e1, -delta), delta);
-            s_loss += w * (a0 > delta ? delta * (a0 - 0.5f * delta) : 0.5f * e0 * e0);
-            s_loss += w * (a1 > delta ? delta * (a1 - 0.5f * delta) : 0.5f * e1 * e1);
-          } else {
-            g0 = w * e0;
-            g1 = w * e1;
-            s_loss = fmaf(g0, e0, s_loss);   // halved after the tile
-            s_loss = fmaf(g1, e1, s_loss);
+        for (int s = 0; s < LG_QS; ++s) {
+          uint32_t hh[8], ll[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float2 tt = *reinterpret_cast<const float2*>(tgq + s * 16 + 2 * i);
+            const float e0 = __uint_as_float(v[s * 16 + 2 * i]) - tt.x;
+            const float e1 = __uint_as_float(v[s * 16 + 2 * i + 1]) - tt.y;
+            float g0, g1;
+            if (kHuber) {
+              const float a0 = fabsf(e0), a1 = fabsf(e1);
+              g0 = w * fminf(fmaxf(e0, -delta), delta);
+              g1 = w * fminf(fmaxf(e1, -delta), delta);
+              s_loss += w * (a0 > delta ? delta * (a0 - 0.5f * delta) : 0.5f * e0 * e0);
+              s_loss += w * (a1 > delta ? delta * (a1 - 0.5f * delta) : 0.5f * e1 * e1);
+            } else {
+              g0 = w * e0;
+              g1 = w * e1;
+              s_loss = fmaf(g0, e0, s_loss);   // halved after the tile
+              s_loss = fmaf(g1, e1, s_loss);
+            }
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(g0, g1);
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(g0 - hf.x, g1 - hf.y);
+            hh[i] = bf2_bits(hv);
+            ll[i] = bf2_bits(lv);
           }
-          const __nv_bfloat162 hv = __floats2bfloat162_rn(g0, g1);
-          const float2 hf = __bfloat1622float2(hv);
-          const __nv_bfloat162 lv = __floats2bfloat162_rn(g0 - hf.x, g1 - hf.y);
-          hh[i] = bf2_bits(hv);
-          ll[i] = bf2_bits(lv);
+          // G of slice s of quarter k over its D columns: hi at 8 s, lo at LG_QR / 2 + 8 s
+          tmem_st8(dcol + (uint32_t)s * 8u, hh);
+          tmem_st8(dcol + LG_QR / 2 + (uint32_t)s * 8u, ll);
         }
-        // G of row slice LG_HS h + s over this half's D columns, which this
-        // thread has loaded: hi at 8 s, lo at LG_HALF / 2 + 8 s
-        tmem_st8(dcol + (uint32_t)s * 8u, hh);
-        tmem_st8(dcol + LG_HALF / 2 + (uint32_t)s * 8u, ll);
+        tmem_st_wait();
+        tc_before();
+        mbar_arrive_remote(&g_full[k], 0);
       }
       lacc += kHuber ? (double)s_loss : 0.5 * (double)s_loss;
-      tmem_st_wait();
-      tc_before();
-      mbar_arrive_remote(&g_full[d], 0);
       if (drain_after(u)) {
         // drain dC^T (lane f = frame, columns = modes; this half's slices)
         // into the pair's FP64 partial
@@ -480,8 +493,8 @@ __global__ void k_reduce_dc(int64_t count, int parts, const double* __restrict__
 }
 
 size_t lg_smem(int ks) {
-  // LG_NBUF tile buffers (four view planes each), targets, barriers
-  return 1024 + (size_t)LG_NBUF * 4 * (size_t)(2 * ks) * LG_GROUP + 2 * LG_TR * 4 + 512;
+  // two forward views and one backward view (hi and lo planes each), targets, barriers
+  return 1024 + 3 * 2 * (size_t)(2 * ks) * LG_GROUP + 2 * LG_TR * 4 + 512;
 }
 
 // CTA pairs: one per two SMs, at most one per tile
