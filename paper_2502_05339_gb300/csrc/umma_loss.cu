@@ -14,62 +14,67 @@
 // CTA pairs (2-CTA clusters) and works on 256-frame groups: CTA c of a pair
 // holds frames 128 c .. 128 c + 127 of the group in its tensor-memory lanes,
 // and the even CTA issues every product once for both (M = 256).  For one
-// group, each pair walks its 96-row tiles and for each tile:
+// group, each pair walks its 192-row tiles and for each tile:
 //   load  each CTA its two views of the tile (below) by bulk copies straight
 //         into its shared memory (no conversion on the SM)
-//   fwd   D (256 frames x 96 rows) = C_g^T Phi_tile^T          (tensor memory)
+//   fwd   D (256 frames x 192 rows) = C_g^T Phi_tile^T         (tensor memory)
 //   epi   one thread per frame: e = x - t, loss += w rho(e), g = w rho'(e),
 //         g split into bf16 hi / lo and written back into tensor memory over
-//         D as the A operand of the next product
-//   bwd   dC_g^T (256 frames x r) += G^T Phi_tile                (tensor memory)
+//         D as the A operand of the backward product, one 48-row quarter at
+//         a time
+//   bwd   dC_g^T (256 frames x r) += G_k^T Phi_k, quarter by quarter,
+//         each as soon as both CTAs have written its G           (tensor memory)
 // with every product in the BF16x3 form (hi*hi + hi*lo + lo*hi, FP32
-// accumulation).  A tcgen05.mma holds its issuing thread ~130 cycles
-// (measured), about twice what the tensor pipe needs for these shapes, so
-// the pair form halves the instructions per frame, and the forward and
-// backward products are issued by two threads.  D / G is double-buffered
-// (fwd(t + 2) waits for bwd(t) to finish); three tile buffers let the copies
-// of tile t + 3 go out as soon as bwd(t) has finished, and each producer
-// prefetches that tile into L2 three items ahead.  dC_g^T is drained into a
-// per-pair FP64 partial every 32 tiles and at the end of the group; the
-// partials are summed over pairs in a fixed order afterwards, so the result
-// is deterministic.  The split copy is read once per 256-frame group (each
-// byte by both CTAs of a pair, the second read from L2), the coefficient
-// group once per CTA.
+// accumulation).  A tcgen05.mma holds its issuing thread ~130-160 cycles
+// (measured), more than the tensor pipe needs for these shapes, so the
+// design minimises instructions per row: the pair form (M = 256) and the
+// wide forward product (N = 192 rows) give 66 instructions per 192 rows and
+// 256 frames; the forward and backward products are issued by two threads.
+// The one D / G accumulator is overwritten by fwd(t + 1) once bwd(t) has
+// finished; only the first quarter's epilogue is exposed.  Forward views are
+// double-buffered (the copies of tile t + 2 go out when fwd(t) has
+// finished), the backward view single-buffered (its copies for tile t + 1
+// go out when bwd(t) has finished and land while fwd(t + 1) runs); the even
+// CTA prefetches tile t + 2 into L2.  dC_g^T is drained into a per-pair FP64
+// partial every 32 tiles and at the end of the group; the partials are
+// summed over pairs in a fixed order afterwards, so the result is
+// deterministic.  The split copy is read once per 256-frame group (each byte
+// by both CTAs of a pair, the second read from L2), the coefficient group
+// once per CTA.
 //
 // Split tile layout (ks = K-slices of r; a plane holds 2 ks groups of 8
-// modes): for plane p (hi, lo) and row half h (rows 48 h .. 48 h + 47),
-// 8-mode group g is 768 contiguous bytes, row t's 8 modes (bf16) at t * 16,
-// at ((p * 2 + h) * 2 ks + g) * 768 within the tile.  The products split B
+// modes): for plane p (hi, lo) and row half h (rows 96 h .. 96 h + 95),
+// 8-mode group g is 1536 contiguous bytes, row t's 8 modes (bf16) at t * 16,
+// at ((p * 2 + h) * 2 ks + g) * 1536 within the tile.  The products split B
 // between the CTAs of the pair along N, so CTA c keeps two views of a tile
 // in its shared memory:
 //   forward view: row half c, all mode groups (N = rows: the pair's B has
-//     rows 0..47 from CTA 0, 48..95 from CTA 1), read K-major (K-adjacent
-//     groups 768 B apart, 8-row groups 128 B apart);
+//     rows 0..95 from CTA 0, 96..191 from CTA 1), read K-major (K-adjacent
+//     groups 1536 B apart, 8-row groups 128 B apart);
 //   backward view: both row halves, mode groups c ks .. c ks + ks - 1
 //     (N = modes: the first half from CTA 0), read MN-major (K = rows: 8-row
-//     groups 128 B apart, the second half 768 ks B on; N: groups 768 B apart).
+//     groups 128 B apart, the second half 1536 ks B on; N: groups 1536 B
+//     apart).
 // Each view is one contiguous run (forward) or two (backward) of the tile.
 //
 // Tensor memory (512 columns x 128 lanes per CTA, lane = frame of its half
 // of the group), allocated for the pair:
 //   [0, 8 ks), [80, 80 + 8 ks)   C_g^T hi and lo as A operands
-//   [160, 256), [256, 352)       D, then G, two buffers: the tile's rows
-//                                0..47 and 48..95 are handled by separate
-//                                epilogue warps, each writing G over its own
-//                                48 D columns (hi of its three 16-row slices,
-//                                then lo)
+//   [160, 352)                   D, then G: quarter k (rows 48 k ..) in
+//                                columns 48 k ..: hi of its three 16-row
+//                                slices, then lo
 //   [352, 352 + 16 ks)           dC_g^T accumulator (FP32, r padded to 16 ks)
 //
 // Roles (11 warps per CTA): 0 producer (bulk copies into its own CTA), 1 the
 // forward MMA issuer (even CTA) or the relay that tells the even CTA when
-// the odd CTA's tile has landed, 2-9 epilogue (frame = TMEM lane; two warps
-// per lane quarter, one per half of the tile's rows; they arrive on the even
-// CTA's barriers), 10 the backward MMA issuer (even CTA).  The products'
-// completions arrive on the barriers of both CTAs.  Every wait is bounded
-// (2 s); a wait that runs out aborts the CTA: roles leave their loops, the
-// producer and the issuers drain what they issued, the pair meets at a
-// cluster barrier, tensor memory is freed and the status word gets
-// DMD_ETIMEOUT.
+// the odd CTA's views have landed, 2-9 epilogue (frame = TMEM lane; two
+// warps per lane quarter, one for row quarters 0 and 2, one for 1 and 3;
+// they arrive on the even CTA's barriers), 10 the backward MMA issuer (even
+// CTA).  The products' completions arrive on the barriers of both CTAs.
+// Every wait is bounded (2 s); a wait that runs out aborts the CTA: roles
+// leave their loops, the producer and the issuers drain what they issued,
+// the pair meets at a cluster barrier, tensor memory is freed and the
+// status word gets DMD_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
