@@ -342,6 +342,187 @@ __global__ void k_f64_to_f32(int64_t count, const double* __restrict__ in, float
   if (i < count) out[i] = (float)in[i];
 }
 
+// ------------------------------------------------- symmetric Gram, one read
+
+// Symmetric Gram C = A^T A of a tall A with at most 8 * GR_MAXNS columns,
+// every CTA forming the whole upper triangle of its row chunk from one read
+// of that chunk (the 64 x 64 tiles of k_gemm_tn_f32 re-read A once per tile
+// and form ~1.4x the distinct entries of a 201-column Gram).  The Ka columns
+// are dealt into NS = ceil(Ka / 8) strided sets, set I = {I, I + NS, ...,
+// I + 7 NS}; thread t owns the 8 x 8 block of set pair (I, J), I <= J, the
+// t-th in row order (NS (NS + 1) / 2 <= 351 blocks; the sets are strided so
+// that the 128-byte swizzle spreads a warp's loads over the banks).  Per
+// 32-row stage (TMA box {32 rows, 8 NS columns}, 128-byte swizzle, columns
+// past Ka zero-filled) a thread forms its 64 partial dot products in FP32
+// (acc, registers, the block in two 8 x 4 halves), adds them into FP32 sums
+// over 32 stages (mid, 1024 rows; in shared memory, element e of thread t
+// at e * GR_THREADS + t), then into this CTA's FP64 partial, which it alone
+// writes: the accuracy scheme of k_gemm_tn_f32.  Entry (a, b) of the upper triangle lands at
+// part[cta][min(a, b) + max(a, b) Ka]; a diagonal block's entries below its
+// diagonal are its duplicates and are not written.
+constexpr int GR_THREADS = 352, GR_MAXNS = 26, GR_STAGES = 4, GR_BR = 32;
+
+__device__ __forceinline__ void gram_pair(int t, int ns, int& I, int& J) {
+  I = 0;
+  while (t >= ns - I) {
+    t -= ns - I;
+    ++I;
+  }
+  J = I + t;
+}
+
+// Fold a thread's FP32 sums over 1024 rows into the CTA's FP64 partial (out
+// of line: it would otherwise hold registers across the stage loop).
+__device__ __noinline__ void gram_flush(float* mid, double* out, int I, int J, int ns, int Ka, int tid, bool first) {
+  for (int i = 0; i < 8; ++i) {
+    const int a = I + ns * i;
+    for (int j = 0; j < 8; ++j) {
+      const int b = J + ns * j;
+      float* mp = mid + (i * 8 + j) * GR_THREADS + tid;
+      if (a < Ka && b < Ka && (I != J || a <= b)) {
+        double* o = out + (int64_t)max(a, b) * Ka + min(a, b);
+        *o = first ? (double)*mp : *o + (double)*mp;
+      }
+      *mp = 0.f;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GR_THREADS, 1)
+    k_gram_f32(const __grid_constant__ CUtensorMap tmA, int64_t n, int Ka, int ns, double* __restrict__ part,
+               int64_t chunk, int32_t* err, const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;   // every CTA, before any barrier
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
+  const uint32_t box = (uint32_t)GR_BR * 4u * 8u * (uint32_t)ns;   // bytes of one stage
+  float* mid = reinterpret_cast<float*>(sm + GR_STAGES * box);   // [64][GR_THREADS]
+  uint64_t* full = reinterpret_cast<uint64_t*>(mid + 64 * GR_THREADS);
+  uint64_t* empty = full + GR_STAGES;
+  int* abort_flag = reinterpret_cast<int*>(empty + GR_STAGES);
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int kWarps = GR_THREADS / 32;
+  const int nblk = ns * (ns + 1) / 2;
+  const bool active = tid < nblk;
+  int I = 0, J = 0;
+  if (active) gram_pair(tid, ns, I, J);
+  const int64_t rbeg = (int64_t)blockIdx.x * chunk;
+  const int64_t rend = min(n, rbeg + chunk);
+  const int nq = rbeg < rend ? (int)((rend - rbeg + GR_BR - 1) / GR_BR) : 0;
+  if (tid == 0) {
+    for (int i = 0; i < GR_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kWarps);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // thread 0 keeps up to GR_STAGES boxes in flight (as in k_gemm_tn_f32)
+  int issued = 0;
+  auto produce = [&](int upto, bool block) -> bool {
+    for (; issued < min(nq, upto); ++issued) {
+      const int s = issued % GR_STAGES;
+      if (issued >= GR_STAGES) {
+        const uint32_t par = (uint32_t)(issued / GR_STAGES - 1) & 1u;
+        if (!block) {
+          if (!mbar_test(&empty[s], par)) return true;
+        } else if (!mbar_wait(&empty[s], par, abort_flag)) {
+          return false;
+        }
+      }
+      mbar_expect_tx(&full[s], box);
+      tma_load_2d(sm + s * box, &tmA, &full[s], (int)(rbeg + (int64_t)issued * GR_BR), 0);
+    }
+    return true;
+  };
+
+  for (int e = 0; e < 64; ++e) mid[e * GR_THREADS + tid] = 0.f;
+  double* out = part + (int64_t)blockIdx.x * Ka * Ka;
+  bool first = true;
+  auto flush = [&]() {
+    gram_flush(mid, out, I, J, ns, Ka, tid, first);
+    first = false;
+  };
+  // byte offset of the 16-byte chunk of rows 4 q .. 4 q + 3 of box column c
+  auto at = [&](int c, int q) -> uint32_t { return (uint32_t)c * 128u + ((uint32_t)(q ^ (c & 7)) << 4); };
+
+  int stretch = 0;
+  for (int qq = 0; qq < nq; ++qq) {
+    bool ok = true;
+    if (tid == 0) ok = produce(qq + 1, true) && produce(qq + GR_STAGES, false);
+    const int s = qq % GR_STAGES;
+    ok = ok && mbar_wait(&full[s], (uint32_t)(qq / GR_STAGES) & 1u, abort_flag);
+    if (!__all_sync(0xffffffffu, ok)) break;
+    if (active) {
+      const uint8_t* bx = sm + s * box;
+      // the 8 x 8 block in two 8 x 4 halves (registers): 32 rows each
+#pragma unroll 1
+      for (int jh = 0; jh < 2; ++jh) {
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+        for (int q = 0; q < GR_BR / 4; ++q) {
+          float4 bv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            bv[j] = *reinterpret_cast<const float4*>(bx + at(J + ns * (4 * jh + j), q));
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 av = *reinterpret_cast<const float4*>(bx + at(I + ns * i, q));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float& c = acc[i][j];
+              c = fmaf(av.x, bv[j].x, c);
+              c = fmaf(av.y, bv[j].y, c);
+              c = fmaf(av.z, bv[j].z, c);
+              c = fmaf(av.w, bv[j].w, c);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) mid[(i * 8 + 4 * jh + j) * GR_THREADS + tid] += acc[i][j];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
+    if (active && ++stretch == 32) {   // 1024 rows, then fold into FP64
+      stretch = 0;
+      flush();
+    }
+  }
+  if (active && (stretch > 0 || first)) flush();
+  // on an abort, let the loads still in flight land before the CTA exits
+  if (tid == 0 && *reinterpret_cast<volatile int*>(abort_flag)) {
+    for (int q = max(0, issued - GR_STAGES); q < issued; ++q)
+      mbar_wait_drain(&full[q % GR_STAGES], (uint32_t)(q / GR_STAGES) & 1u);
+    raise_status(err, DMD_ETIMEOUT, 8102);
+  }
+}
+
+// C[a, b] = C[b, a] = sum over CTAs (fixed order) of part[cta][min + max Ka].
+__global__ void k_reduce_gram(int Ka, int parts, const double* __restrict__ part, double* __restrict__ C,
+                              const int32_t* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t count = (int64_t)Ka * Ka;
+  if (i >= count) return;
+  const int a = (int)(i % Ka), b = (int)(i / Ka);
+  const int64_t src = (int64_t)max(a, b) * Ka + min(a, b);
+  double s = 0.0;
+  for (int p = 0; p < parts; ++p) s += part[(int64_t)p * count + src];
+  C[i] = s;
+}
+
+size_t gram_smem(int ns) {
+  return 1024 + (size_t)GR_STAGES * GR_BR * 4 * 8 * ns + 64 * GR_THREADS * 4 + 2 * GR_STAGES * 8 + 16;
+}
+
 int sm_count() {
   static int cached = 0;
   if (!cached) {
@@ -368,7 +549,9 @@ int tn_splits(int64_t n, int Ka, int N) {
 }
 
 size_t tn_partial_doubles(int64_t n, int Ka, int N) {
-  return (size_t)tn_splits(n, Ka, N) * Ka * N;
+  size_t d = (size_t)tn_splits(n, Ka, N) * Ka * N;
+  if (Ka == N && Ka <= 8 * GR_MAXNS) d = std::max(d, (size_t)sm_count() * Ka * Ka);   // k_gram_f32's partials
+  return d;
 }
 
 dmd_status f32_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, const float* B32,
@@ -386,6 +569,23 @@ dmd_status f32_gemm_tn(int64_t n, int Ka, int N, const float* A, int64_t lda, co
   if (Ka <= 0 || N <= 0) return DMD_OK;
   if (n <= 0 && skip == nullptr) {
     DMD_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)Ka * N * sizeof(double), st));
+    return DMD_OK;
+  }
+  if (A == B && Ka == N && lda == ldb && Ka <= 8 * GR_MAXNS) {
+    // a symmetric Gram: every CTA forms the whole triangle of its row chunk
+    const int ns = (int)ceil_div(Ka, 8);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(), ceil_div(n, 1024)));
+    const int64_t chunk = round_up(ceil_div(n, grid), GR_BR);
+    const int parts = (int)ceil_div(n, chunk);   // every CTA owns rows
+    CUtensorMap mA;
+    DMD_TRY(make_map(&mA, A, n, Ka, lda, GR_BR, 8 * ns, true));
+    const size_t smem = gram_smem(ns);
+    DMD_CUDA_TRY(cudaFuncSetAttribute(k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gram_f32<<<(unsigned)parts, GR_THREADS, smem, st>>>(mA, n, Ka, ns, part, chunk, status_word(), skip);
+    DMD_LAUNCH_CHECK();
+    const int64_t count = (int64_t)Ka * Ka;
+    k_reduce_gram<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(Ka, parts, part, C, skip);
+    DMD_LAUNCH_CHECK();
     return DMD_OK;
   }
   int splits = tn_splits(n, Ka, N);

@@ -72,6 +72,22 @@ def test_gemm_tn(dmd, prec, n, Ka, N):
     assert rel(C.cpu().numpy().T, ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("n,Ka", [(1_000_003, 201), (5003, 9), (70_001, 208), (70_001, 209)])
+def test_symmetric_gram_fp32(dmd, n, Ka):
+    """The snapshot-Gram shape A^T A on the CUDA cores: up to 208 columns one
+    CTA forms the whole triangle of its row chunk (201 columns: the 128^3 x 3
+    snapshot matrix's m + 1; 9: two column sets; 208: the largest), beyond
+    that the tiled kernel (209).  Against the FP64 product at the FP32 bar,
+    exactly symmetric, and the same bits on a second call."""
+    A = _tall(n, Ka, 11 * n + Ka).cuda()
+    C = dmd.dmd_gemm_tn(A, A, n, precision="fp32")
+    ref = cols(A.cpu(), n).T @ cols(A.cpu(), n)
+    Cn = C.cpu().numpy()
+    assert rel(Cn.T, ref) < TOL["fp32"]
+    assert np.array_equal(Cn, Cn.T)
+    assert torch.equal(C, dmd.dmd_gemm_tn(A, A, n, precision="fp32"))
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_gemm_tn_is_deterministic(dmd, prec):
     A = _tall(200003, 40, 1).cuda()
