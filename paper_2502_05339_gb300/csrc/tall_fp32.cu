@@ -444,8 +444,6 @@ __global__ void __launch_bounds__(GR_THREADS, 1)
     gram_flush(mid, out, I, J, ns, Ka, tid, first);
     first = false;
   };
-  // byte offset of the 16-byte chunk of rows 4 q .. 4 q + 3 of box column c
-  auto at = [&](int c, int q) -> uint32_t { return (uint32_t)c * 128u + ((uint32_t)(q ^ (c & 7)) << 4); };
 
   int stretch = 0;
   for (int qq = 0; qq < nq; ++qq) {
@@ -456,23 +454,36 @@ __global__ void __launch_bounds__(GR_THREADS, 1)
     if (!__all_sync(0xffffffffu, ok)) break;
     if (active) {
       const uint8_t* bx = sm + s * box;
-      // the 8 x 8 block in two 8 x 4 halves (registers): 32 rows each
+      // the 8 x 8 block in two 8 x 4 halves (registers): 32 rows each.  The
+      // byte offset of rows 4 q .. 4 q + 3 of column c is pre(c) ^ (16 q),
+      // pre(c) = 128 c | 16 (c & 7): the 128-byte swizzle as one XOR
+      uint32_t pa[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t c = (uint32_t)(I + ns * i);
+        pa[i] = (c << 7) | ((c & 7u) << 4);
+      }
 #pragma unroll 1
       for (int jh = 0; jh < 2; ++jh) {
+        uint32_t pb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t c = (uint32_t)(J + ns * (4 * jh + j));
+          pb[j] = (c << 7) | ((c & 7u) << 4);
+        }
         float acc[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
         for (int q = 0; q < GR_BR / 4; ++q) {
           float4 bv[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            bv[j] = *reinterpret_cast<const float4*>(bx + at(J + ns * (4 * jh + j), q));
+          for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4*>(bx + (pb[j] ^ (uint32_t)(q << 4)));
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const float4 av = *reinterpret_cast<const float4*>(bx + at(I + ns * i, q));
+            const float4 av = *reinterpret_cast<const float4*>(bx + (pa[i] ^ (uint32_t)(q << 4)));
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               float& c = acc[i][j];
