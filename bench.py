@@ -249,7 +249,7 @@ def run_ours(args):
     kernels = [] if args.no_kernels else kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind)
     kernels.insert(0, roofline(n, r, K, rec_s, prec, peaks, peak_kind))
     for e in kernels:
-        if e["kernel"] in TRAFFIC_PER_ROW and c["N"] == 128:
+        if TRAFFIC_PER_ROW.get(e["kernel"]) is not None and c["N"] == 128:
             e["traffic"] = TRAFFIC_PER_ROW[e["kernel"]] * n
     roof = max(kernels, key=lambda e: e["step_ms"])
     forms = {prec: {"frames_per_s": value, "fit_s": fit_s, "recon_frames_per_s": K / rec_s}}
@@ -802,8 +802,9 @@ def _run_e2e(args, sc, c, dmd, dev, st, out, ks, local):
 # launch divided by its rows) from the ncu captures of the 1,048,576-row cases
 # summarised in profiles/tall_kernels_cfg1_1M_rows.md; traffic grows in
 # proportion to the rows, so a full launch moves these x n bytes.
+GRAM_TRAFFIC_PER_ROW = None   # not yet captured for k_gram_f32
 TRAFFIC_PER_ROW = {
-    "k_gemm_tn_f32 (snapshot Gram W = S^T S)": 1.029e9 / 1048576,
+    "k_gram_f32 (snapshot Gram W = S^T S)": GRAM_TRAFFIC_PER_ROW,
     "k_umma_tn (X^T Q1, Q1^T S)": 1.596e9 / 1048576,
     "k_umma_tn (Gram Q1^T Q1)": 0.737e9 / 1048576,
     "k_umma_nn_bres (sketch Q1 = X M)": 1.463e9 / 1048576,
@@ -871,7 +872,7 @@ def kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind):
     M = torch.randn((l, m), dtype=torch.float64, device=dev, generator=g)
     out = []
     sec = event_time(lambda: dmd.dmd_gemm_tn(S, S, n, precision="fp32"), st)
-    out.append(alu_entry("k_gemm_tn_f32 (snapshot Gram W = S^T S)", float(n) * (m + 1) * (m + 2), sec, 1, peaks,
+    out.append(alu_entry("k_gram_f32 (snapshot Gram W = S^T S)", float(n) * (m + 1) * (m + 2), sec, 1, peaks,
                          "n (m+1)(m+2) flops: 2n per distinct entry of the symmetric W"))
     npass = 1 + c["power_iters"]
     sec = event_time(lambda: dmd.dmd_gemm_tall(X, n, M, precision=prec, out=Q), st)

@@ -354,13 +354,24 @@ __global__ void k_f64_to_f32(int64_t count, const double* __restrict__ in, float
 // that the 128-byte swizzle spreads a warp's loads over the banks).  Per
 // 32-row stage (TMA box {32 rows, 8 NS columns}, 128-byte swizzle, columns
 // past Ka zero-filled) a thread forms its 64 partial dot products in FP32
-// (acc, registers, the block in two 8 x 4 halves), adds them into FP32 sums
-// over 32 stages (mid, 1024 rows; in shared memory, element e of thread t
-// at e * GR_THREADS + t), then into this CTA's FP64 partial, which it alone
-// writes: the accuracy scheme of k_gemm_tn_f32.  Entry (a, b) of the upper triangle lands at
+// (acc, registers, the block in two 8 x 4 halves; packed two-lane FMAs,
+// even and odd rows apart), adds them into FP32 sums over 32 stages (mid,
+// 1024 rows; in shared memory, element e of thread t at e * GR_THREADS + t),
+// then into this CTA's FP64 partial, which it alone writes: the accuracy
+// scheme of k_gemm_tn_f32.  Entry (a, b) of the upper triangle lands at
 // part[cta][min(a, b) + max(a, b) Ka]; a diagonal block's entries below its
 // diagonal are its duplicates and are not written.
 constexpr int GR_THREADS = 352, GR_MAXNS = 26, GR_STAGES = 4, GR_BR = 32;
+
+// c += a * b on two FP32 lanes at once (one packed FMA instruction, each
+// lane rounded as a single fma.rn.f32).
+__device__ __forceinline__ void ffma2(float2& c, float2 a, float2 b) {
+  uint64_t cc = *reinterpret_cast<uint64_t*>(&c);
+  asm("fma.rn.f32x2 %0, %1, %2, %0;"
+      : "+l"(cc)
+      : "l"(*reinterpret_cast<uint64_t*>(&a)), "l"(*reinterpret_cast<uint64_t*>(&b)));
+  c = *reinterpret_cast<float2*>(&cc);
+}
 
 __device__ __forceinline__ void gram_pair(int t, int ns, int& I, int& J) {
   I = 0;
@@ -471,11 +482,13 @@ __global__ void __launch_bounds__(GR_THREADS, 1)
           const uint32_t c = (uint32_t)(J + ns * (4 * jh + j));
           pb[j] = (c << 7) | ((c & 7u) << 4);
         }
-        float acc[8][4];
+        // two partial sums per entry (even and odd rows), formed by packed
+        // FMAs on the (x, y) and (z, w) halves of the 4-row chunks
+        float2 acc[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+          for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int q = 0; q < GR_BR / 4; ++q) {
           float4 bv[4];
@@ -486,18 +499,15 @@ __global__ void __launch_bounds__(GR_THREADS, 1)
             const float4 av = *reinterpret_cast<const float4*>(bx + (pa[i] ^ (uint32_t)(q << 4)));
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              float& c = acc[i][j];
-              c = fmaf(av.x, bv[j].x, c);
-              c = fmaf(av.y, bv[j].y, c);
-              c = fmaf(av.z, bv[j].z, c);
-              c = fmaf(av.w, bv[j].w, c);
+              ffma2(acc[i][j], make_float2(av.x, av.y), make_float2(bv[j].x, bv[j].y));
+              ffma2(acc[i][j], make_float2(av.z, av.w), make_float2(bv[j].z, bv[j].w));
             }
           }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) mid[(i * 8 + 4 * jh + j) * GR_THREADS + tid] += acc[i][j];
+          for (int j = 0; j < 4; ++j) mid[(i * 8 + 4 * jh + j) * GR_THREADS + tid] += acc[i][j].x + acc[i][j].y;
       }
     }
     __syncwarp();
