@@ -114,7 +114,11 @@ def test_dmdc_adjoint_central_differences(dmd, scene):
     the same (device-fitted) model: rollout of the real 2x2-block latent
     recursion, lift by Phi_R.  The loss is quadratic in u and in beta, so the
     differences are exact up to FP64 rounding; the device gradient carries the
-    FP32 rounding of its frames (~1e-5 relative), hence 1e-3."""
+    FP32 rounding of its frames: x_T in FP32 differs from the FP64 lift by
+    ~1e-7 of x_T, which is ~1e-5 of the residual (the target sits 1e-2 from
+    x_T), so every entry of the gradient can be off by ~1e-5 of the
+    gradient's largest entry, whatever its own size.  The bar is 1e-3 of the
+    entry, with a floor of 1e-4 of the largest entry (10x that level)."""
     sc, _ = scene
     model = _fit(dmd, sc, "fp32")
     T, h = 40, 1e-3
@@ -146,14 +150,14 @@ def test_dmdc_adjoint_central_differences(dmd, scene):
         up[ch, t] += h
         um[ch, t] -= h
         fd = (loss(up, beta) - loss(um, beta)) / (2 * h)
-        assert abs(fd - du[t, ch]) <= 1e-3 * max(abs(fd), 1e-2 * np.abs(du).max()), (t, ch, fd, du[t, ch])
+        assert abs(fd - du[t, ch]) <= 1e-3 * max(abs(fd), 1e-1 * np.abs(du).max()), (t, ch, fd, du[t, ch])
     for c in [0, 3, r - 1]:
         bp, bm = beta.copy(), beta.copy()
         bp[c] += h
         bm[c] -= h
         fd = (loss(U64, bp) - loss(U64, bm)) / (2 * h)
         gd = dm[2 * r + c]
-        assert abs(fd - gd) <= 1e-3 * max(abs(fd), 1e-2 * np.abs(dm[2 * r:3 * r]).max()), (c, fd, gd)
+        assert abs(fd - gd) <= 1e-3 * max(abs(fd), 1e-1 * np.abs(dm[2 * r:3 * r]).max()), (c, fd, gd)
 
 
 @pytest.fixture(scope="module")
