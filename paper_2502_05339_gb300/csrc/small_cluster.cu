@@ -394,187 +394,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CL_THREADS)
   cl.sync();
 }
 
-// ------------------------------------------------ blocked Cholesky (FP64)
-
-// The same factorisation as k_cholesky_cl (upper R with G = R^T R, columns
-// whose pivot falls to tau * max diag or below dropped: their R row is zero
-// and counted in info[5]; a non-finite or non-positive scale stops it) with
-// two cluster barriers per 16-column block instead of one per column.
-// Columns are block-cyclic: column b is in block b / CB, owned by CTA
-// (b / CB) % CL at local column ((b / CB) / CL) CB + b % CB.  For block k
-// (rows and columns kb .. ke - 1):
-//   (a) its owner factors the diagonal block (one warp, column by column,
-//       the pivot rule above) and sends it with the stop state to every CTA;
-//                                                              cluster barrier
-//   (b) every CTA solves its columns b >= ke for the block's R rows,
-//       R[kb.., b] = R_kk^-T G[kb.., b] (forward substitution; a dropped
-//       row gives zeros), keeps them and sends them to every CTA's panel;
-//                                                              cluster barrier
-//   (c) every CTA subtracts the block's rank-16 update from its columns
-//       b >= ke: G[a, b] -= sum_p R[p, a] R[p, b], ke <= a <= b.
-constexpr int CB = 16;
-
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CL_THREADS)
-    k_cholesky_blk(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* __restrict__ skip) {
-  if (skip != nullptr && *skip != 0) return;   // every CTA reads the same flag, before any barrier
-  cg::cluster_group cl = cg::this_cluster();
-  const int c = (int)cl.block_rank();
-  const int nb = (n + CB - 1) / CB;
-  const int nbl = (nb + CL - 1) / CL;               // local blocks per CTA (the largest)
-  const int ldw = n | 1;
-  extern __shared__ __align__(16) unsigned char smc[];
-  double* S = reinterpret_cast<double*>(smc);       // local columns, ld ldw
-  double* P = S + (size_t)ldw * nbl * CB;           // [CB][n] the block's R rows
-  double* Rd = P + (size_t)CB * n;                  // [CB][CB] R's diagonal block, Rd[p CB + q] = R[kb + p][kb + q]
-  double* stv = Rd + CB * CB;                       // [1] stop state of the current block
-  double* dm = stv + 4;                             // [CL] per-CTA max of the diagonal
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-  auto lcol = [&](int b) { return ((b / CB) / CL) * CB + b % CB; };
-  const int ncl = nbl * CB;   // local column slots
-  // load the upper triangle of the local columns
-  for (int l = warp; l < ncl; l += nw) {
-    const int b = (c + CL * (l / CB)) * CB + l % CB;
-    if (b >= n) continue;
-    for (int a = lane; a <= b; a += 32) S[a + (size_t)l * ldw] = G[a + (int64_t)b * ld];
-  }
-  // the largest diagonal entry (NaN carried)
-  __shared__ double red[32];
-  double loc = 0.0;
-  for (int l = tid; l < ncl; l += bd) {
-    const int b = (c + CL * (l / CB)) * CB + l % CB;
-    if (b >= n) continue;
-    const double d = G[b + (int64_t)b * ld];
-    loc = (isfinite(loc) && isfinite(d)) ? fmax(loc, d) : (double)NAN;
-  }
-  {
-    double v = loc;
-    for (int o = 16; o > 0; o >>= 1) {
-      const double u = __shfl_xor_sync(0xffffffffu, v, o);
-      v = (isfinite(v) && isfinite(u)) ? fmax(v, u) : (double)NAN;
-    }
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (tid == 0) {
-      double t = red[0];
-      for (int i = 1; i < nw; ++i) t = (isfinite(t) && isfinite(red[i])) ? fmax(t, red[i]) : (double)NAN;
-      for (int r = 0; r < CL; ++r) cl.map_shared_rank(dm, r)[c] = t;
-    }
-  }
-  __syncthreads();
-  cl.sync();
-  double dmax = dm[0];
-  for (int r = 1; r < CL; ++r) dmax = (isfinite(dmax) && isfinite(dm[r])) ? fmax(dmax, dm[r]) : (double)NAN;
-  const double floor_ = tau * dmax;
-
-  bool stopped = false;
-  for (int k = 0; k < nb; ++k) {
-    const int kb = k * CB, ke = min(n, kb + CB), w = ke - kb;
-    // (a) the diagonal block, by its owner's warp 0
-    if (c == k % CL && warp == 0) {
-      const int l0 = lcol(kb);
-      double stop = 0.0;
-      for (int j = 0; j < w; ++j) {
-        double* colj = S + (size_t)(l0 + j) * ldw;
-        const double d = colj[kb + j];
-        double piv = 0.0, ip = 0.0;
-        bool take = false;
-        if (!isfinite(d) || !isfinite(dmax)) {
-          if (lane == 0) raise_status(info, DMD_ENONFINITE, tag * 1000 + kb + j);
-          stop = 2.0;
-        } else if (!(dmax > 0.0)) {
-          if (lane == 0) raise_status(info, DMD_ENUMERIC, tag * 1000 + kb + j);
-          stop = 2.0;
-        } else if (!(d > floor_)) {
-          if (lane == 0 && info) atomicAdd(&info[5], 1);
-        } else {
-          ip = rsqrt(d);
-          piv = d * ip;
-          take = true;
-        }
-        if (stop != 0.0) break;
-        // row j of the block: R[kb + j][kb + q] for q >= j
-        for (int q = j + lane; q < w; q += 32) {
-          const double v = q == j ? piv : (take ? S[kb + j + (size_t)(l0 + q) * ldw] * ip : 0.0);
-          Rd[j * CB + q] = v;
-          S[kb + j + (size_t)(l0 + q) * ldw] = v;
-        }
-        __syncwarp();
-        // the rest of the block: S[a][q] -= R[j][a] R[j][q], j < a <= q < w
-        if (take)
-          for (int e = lane; e < CB * CB; e += 32) {
-            const int a = e / CB, q = e % CB;
-            if (a > j && a <= q && q < w) S[kb + a + (size_t)(l0 + q) * ldw] -= Rd[j * CB + a] * Rd[j * CB + q];
-          }
-        __syncwarp();
-      }
-      // send the block (rows below its diagonal as zeros) and the state
-      for (int e = lane; e < CB * CB; e += 32) {
-        const int p = e / CB, q = e % CB;
-        const double v = (p < w && q < w && q >= p) ? Rd[e] : 0.0;
-        for (int r = 0; r < CL; ++r) cl.map_shared_rank(Rd, r)[e] = v;
-      }
-      if (lane == 0)
-        for (int r = 0; r < CL; ++r) cl.map_shared_rank(stv, r)[0] = stop;
-    }
-    cl.sync();
-    if (stv[0] != 0.0) {
-      stopped = true;
-      break;
-    }
-    // (b) this CTA's columns b >= ke: the block's R rows, kept and sent
-    for (int l = tid; l < ncl; l += bd) {
-      const int b = (c + CL * (l / CB)) * CB + l % CB;
-      if (b < ke || b >= n) continue;
-      double* col = S + (size_t)l * ldw;
-      double x[CB];
-#pragma unroll
-      for (int j = 0; j < CB; ++j) {
-        if (j >= w) break;
-        double v = col[kb + j];
-        for (int p = 0; p < j; ++p) v -= Rd[p * CB + j] * x[p];
-        const double rjj = Rd[j * CB + j];
-        x[j] = rjj != 0.0 ? v / rjj : 0.0;
-        col[kb + j] = x[j];
-      }
-      for (int r = 0; r < CL; ++r) {
-        double* pr = cl.map_shared_rank(P, r);
-        for (int j = 0; j < w; ++j) pr[(size_t)j * n + b] = x[j];
-      }
-    }
-    cl.sync();
-    // (c) rank-w update of this CTA's columns b >= ke, rows ke .. b
-    for (int l = warp; l < ncl; l += nw) {
-      const int b = (c + CL * (l / CB)) * CB + l % CB;
-      if (b < ke || b >= n) continue;
-      double* col = S + (size_t)l * ldw;
-      double pb[CB];
-#pragma unroll
-      for (int j = 0; j < CB; ++j) pb[j] = j < w ? P[(size_t)j * n + b] : 0.0;
-      for (int a = ke + lane; a <= b; a += 32) {
-        double s = col[a];
-#pragma unroll
-        for (int j = 0; j < CB; ++j)
-          if (j < w) s -= P[(size_t)j * n + a] * pb[j];
-        col[a] = s;
-      }
-    }
-    __syncthreads();
-  }
-  if (!stopped) {
-    for (int l = warp; l < ncl; l += nw) {
-      const int b = (c + CL * (l / CB)) * CB + l % CB;
-      if (b >= n) continue;
-      for (int a = lane; a < n; a += 32) G[a + (int64_t)b * ld] = a <= b ? S[a + (size_t)l * ldw] : 0.0;
-    }
-  }
-  cl.sync();
-}
-
-size_t cholesky_blk_smem(int n) {
-  const int nb = (n + CB - 1) / CB, nbl = (nb + CL - 1) / CL;
-  return ((size_t)(n | 1) * nbl * CB + (size_t)CB * n + CB * CB + 4 + CL) * sizeof(double);
-}
-
 template <class Real>
 dmd_status cholesky_cluster_t(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
                               cudaStream_t st) {
@@ -594,14 +413,6 @@ bool cholesky_cluster_fits(int n) { return n >= 96 && n <= 512; }
 
 dmd_status cholesky_cluster(int n, double* G, int ld, double tau, int32_t* info, int tag, bool fp32,
                             const int32_t* skip, cudaStream_t st) {
-  if (!fp32 && n <= 256) {   // blocked: two cluster barriers per 16 columns
-    const size_t smem = cholesky_blk_smem(n);
-    if (smem > 48 * 1024)
-      DMD_CUDA_TRY(cudaFuncSetAttribute(k_cholesky_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cholesky_blk<<<CL, CL_THREADS, smem, st>>>(n, G, ld, tau, info, tag, skip);
-    DMD_LAUNCH_CHECK();
-    return DMD_OK;
-  }
   return fp32 ? cholesky_cluster_t<float>(n, G, ld, tau, info, tag, skip, st)
               : cholesky_cluster_t<double>(n, G, ld, tau, info, tag, skip, st);
 }
