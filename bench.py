@@ -802,7 +802,7 @@ def _run_e2e(args, sc, c, dmd, dev, st, out, ks, local):
 # launch divided by its rows) from the ncu captures of the 1,048,576-row cases
 # summarised in profiles/tall_kernels_cfg1_1M_rows.md; traffic grows in
 # proportion to the rows, so a full launch moves these x n bytes.
-GRAM_TRAFFIC_PER_ROW = None   # not yet captured for k_gram_f32
+GRAM_TRAFFIC_PER_ROW = (1.002e9 + 0.154e9) / 1048576   # k_gram_f32: S once + the FP64 partials' read-modify-writes
 TRAFFIC_PER_ROW = {
     "k_gram_f32 (snapshot Gram W = S^T S)": GRAM_TRAFFIC_PER_ROW,
     "k_umma_tn (X^T Q1, Q1^T S)": 1.596e9 / 1048576,
