@@ -393,11 +393,11 @@ DMD_EXPORT dmd_status dmd_edit_modes(int32_t r, int32_t q, const double* modal_i
 /* Autotuner of the reconstruction (no counterpart in the paper: it picks the
  * tensor-core tile configuration of Phi_R C for this GPU).  With the
  * operands of a dmd_predict call (desc->q must be 0; mixed precision; K > 256
- * frames), every (frame-chunk width, A stages, B buffers) configuration that
+ * frames), every (frame-chunk width, A stages, B ring entries) configuration that
  * fits in shared memory is launched and timed with CUDA events on `stream`,
  * and the fastest is kept for all later predictions with the same number of
  * modes (per process).  chosen (3 int32, may be NULL) receives (chunk width,
- * A stages, B buffers), zeros when nothing was tuned.  `out` is overwritten
+ * A stages, B ring entries), zeros when nothing was tuned.  `out` is overwritten
  * with the frames.  Synchronises `stream`: call it before any capture. */
 DMD_EXPORT dmd_status dmd_autotune_predict(const dmd_predict_desc* desc, const float* Phi_R, const double* modal,
                                 const int32_t* k, float* out, void* workspace, size_t ws_bytes,

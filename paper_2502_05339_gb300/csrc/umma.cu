@@ -252,43 +252,55 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
 // ============================================================ NN, A resident
 
 constexpr int AR_MAXSA = 4;  // TMA stages for the A tile slices (runtime sa <= 4)
-constexpr int AR_MAXNB = 4;  // B chunk buffers (runtime nb <= 4)
+constexpr int AR_MAXNB = 4;  // B ring entries (runtime nb <= 4)
 constexpr int AR_MAXKS = 16; // K-slices of the resident A tile (Kd <= 256)
-constexpr int AR_ACC = 2;    // TMEM accumulators (bn <= 128 columns each)
-constexpr int AR_ACOL = 256; // first TMEM column of the resident A (hi, then lo)
-constexpr int AR_THREADS = 320;
+constexpr int AR_ACC = 2;    // TMEM accumulators (bn columns each)
+constexpr int AR_THREADS = 448;           // producer, issuer, 4 converters, 2 x 4 epilogue warps
+constexpr uint32_t AR_STG = 8 * 2 * 2048;   // epilogue staging: 8 warps x 2 buffers x 2 KB
+
+// Widest frame chunk (a multiple of 16, at most 256) whose two accumulators
+// fit beside the resident A tile (16 columns per K-slice: hi, then lo) in the
+// 512 tensor-memory columns: 176 frames at 150 modes.
+constexpr int ares_bn_max(int ksteps) {
+  return ((512 - 16 * ksteps) / 2 / 16 * 16) < 256 ? ((512 - 16 * ksteps) / 2 / 16 * 16) : 256;
+}
 
 // C = A B with the 128-row tile of A resident in TENSOR memory (split into
 // bf16 hi / lo by the converter warps and written with tcgen05.st: lane =
 // row, 8 columns per 16-wide K-slice), the coefficient matrix B streamed in
-// bn-column chunks (bn <= 128) through a shared-memory ring.  Keeping A in
-// TMEM leaves shared memory for wide chunks: the MMA count per output column
-// is what bounds this kernel (measured: ~2.4 us per 30 MMAs whatever N).
-// Each epilogue warp writes its 32 rows in 16-column TMA stores through a
-// double-buffered 2 KB staging area.
+// bn-column chunks through a shared-memory ring whose entries hold G K-slices
+// of a chunk (hi and lo planes).  A tcgen05.mma holds its issuer for ~100-160
+// cycles whatever N (measured), so the chunk is as wide as tensor memory
+// allows: two bn-column accumulators beside A, M = 128, N = bn.
+// Two sets of four epilogue warps drain the two accumulators (set h takes the
+// chunks in accumulator h), so each set has two chunks' product time for one
+// chunk's epilogue; each warp writes its 32 rows in 16-column TMA stores
+// through a double-buffered 2 KB staging area.
 //
 // kLoss != 0: the frames are not stored.  The epilogue forms each frame's
 // residual against the target field, e = x - tgt (row-wise), and accumulates
 // the weighted per-frame loss w_j rho(e) of the streamed objective: rho(e) =
 // e^2 / 2, or with delta > 0 the Huber function (e^2 / 2 for |e| <= delta,
-// delta (|e| - delta / 2) beyond).  Each thread sums one 128-frame chunk of its
-// row in FP32 and carries the chunk sums in FP64; the CTA's sum (fixed order)
-// goes to loss_part[blockIdx.x].  Phi_R is read once per call.
+// delta (|e| - delta / 2) beyond).  Each thread sums one chunk of its row in
+// FP32 and carries the chunk sums in FP64; the CTA's sum (fixed order) goes
+// to loss_part[blockIdx.x].  Phi_R is read once per call.
 template <int kLoss>
 __global__ void __launch_bounds__(AR_THREADS, 1)
     k_umma_nn_ares(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
-                   const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int sa, int nb,
+                   const uint8_t* __restrict__ Bchunks, int64_t n, int N, int ksteps, int bn, int sa, int nb, int G,
                    int nchunks, int64_t ntiles, const float* __restrict__ tgt, const double* __restrict__ wgt,
                    float delta, double* __restrict__ loss_part, int32_t* err, const int32_t* __restrict__ skip) {
   if (skip != nullptr && *skip != 0) return;   // as in k_umma_nn_bres
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = align1024(smraw);
-  const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * (uint32_t)bn * 32u;
-  const uint32_t bstride = (chunk_bytes + 1023u) & ~1023u;
+  const uint32_t slice_bytes = (uint32_t)bn * 32u;   // one K-slice of one plane of a chunk
+  const uint32_t chunk_bytes = 2u * (uint32_t)ksteps * slice_bytes;
+  const uint32_t estride = (2u * (uint32_t)G * slice_bytes + 1023u) & ~1023u;
+  const int nent = (ksteps + G - 1) / G;   // ring entries per chunk
   uint8_t* stA = sm;
   uint8_t* Bbuf = stA + sa * 8192;
-  uint8_t* stg = Bbuf + nb * bstride;            // 4 warps x 2 buffers x 2 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * 2 * 2048);
+  uint8_t* stg = Bbuf + nb * estride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + AR_STG);
   uint64_t* afull = bars;               // TMA slice landed
   uint64_t* aempty = afull + AR_MAXSA;  // slice converted
   uint64_t* bfull = aempty + AR_MAXSA;
@@ -298,8 +310,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   uint64_t* ares_full = acce + AR_ACC;  // [AR_MAXKS]: slice ks of the tile's A is in TMEM
   uint64_t* ares_free = ares_full + AR_MAXKS;  // MMAs of the tile finished reading A
   uint64_t* tdown = ares_free + 1;
-  double* red = reinterpret_cast<double*>(tdown + 1);   // 4 epilogue warps' loss sums
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 4);
+  double* red = reinterpret_cast<double*>(tdown + 1);   // 8 epilogue warps' loss sums
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 8);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -327,6 +339,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tslot;
+  const uint32_t acol = (uint32_t)(AR_ACC * bn);   // resident A: hi from here, lo 8 ks columns on
 
   if (warp == 0) {
     if (lane == 0) {
@@ -346,18 +359,27 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           a_issued[s] = true;
           a_par[s] = (ait / sa) & 1;
         }
-        for (int c = 0; ok && c < nchunks; ++c, ++bit) {
-          const uint32_t b = bit % nb;
-          if (!mbar_wait(&bempty[b], ((bit / nb) & 1) ^ 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&bfull[b], chunk_bytes);
+        for (int c = 0; ok && c < nchunks; ++c) {
           const uint8_t* src = Bchunks + (int64_t)c * chunk_bytes;
-          for (uint32_t off = 0; off < chunk_bytes; off += 32768u)
-            bulk_g2s(Bbuf + b * bstride + off, src + off, min(32768u, chunk_bytes - off), &bfull[b]);
-          b_issued[b] = true;
-          b_par[b] = (bit / nb) & 1;
+          for (int e = 0; e < nent; ++e, ++bit) {
+            const uint32_t b = bit % nb;
+            if (!mbar_wait(&bempty[b], ((bit / nb) & 1) ^ 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t s0 = (uint32_t)(e * G), gs = (uint32_t)min(G, ksteps - e * G);
+            const uint32_t bytes = gs * slice_bytes;
+            mbar_expect_tx(&bfull[b], 2u * bytes);
+            uint8_t* dst = Bbuf + b * estride;
+            for (uint32_t off = 0; off < bytes; off += 32768u) {
+              const uint32_t len = min(32768u, bytes - off);
+              bulk_g2s(dst + off, src + s0 * slice_bytes + off, len, &bfull[b]);
+              bulk_g2s(dst + (uint32_t)G * slice_bytes + off, src + ((uint32_t)ksteps + s0) * slice_bytes + off, len,
+                       &bfull[b]);
+            }
+            b_issued[b] = true;
+            b_par[b] = (bit / nb) & 1;
+          }
         }
       }
       for (int i = 0; i < sa; ++i)
@@ -368,52 +390,63 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, bn);
-      const uint32_t a_hi = tmem + AR_ACOL, a_lo = tmem + AR_ACOL + (uint32_t)ksteps * 8u;
+      const uint32_t a_hi = tmem + acol, a_lo = tmem + acol + (uint32_t)ksteps * 8u;
+      // descriptors advance by offsets (address field in 16-byte units)
+      const uint64_t bstep = (uint64_t)(slice_bytes >> 4), blo = (uint64_t)(((uint32_t)G * slice_bytes) >> 4);
       uint32_t tit = 0, bit = 0, accit = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tit) {
-        for (int c = 0; c < nchunks; ++c, ++bit, ++accit) {
-          const uint32_t b = bit % nb, ab = accit % AR_ACC;
-          if (!mbar_wait(&bfull[b], (bit / nb) & 1, abort_flag) ||
-              !mbar_wait(&acce[ab], ((accit / AR_ACC) & 1) ^ 1, abort_flag)) {
+        for (int c = 0; ok && c < nchunks; ++c, ++accit) {
+          const uint32_t ab = accit % AR_ACC;
+          if (!mbar_wait(&acce[ab], ((accit / AR_ACC) & 1) ^ 1, abort_flag)) {
             ok = false;
             break;
           }
           tc_after();
-          const uint32_t d = tmem + ab * 128u;
-          // descriptors advance by offsets (address field in 16-byte units)
-          uint64_t bhd = sdesc(su32(Bbuf + b * bstride), kLBO, kSBO);
-          uint64_t bld = bhd + (uint64_t)(((uint32_t)ksteps * (uint32_t)bn * 32u) >> 4);
-          const uint64_t bstep = (uint64_t)(((uint32_t)bn * 32u) >> 4);
-          if (c == 0) {   // the tile's first chunk follows the conversion slice by slice
-            for (int ks = 0; ks < ksteps; ++ks, bhd += bstep, bld += bstep) {
-              if (!mbar_wait(&ares_full[ks], tit & 1, abort_flag)) {
-                ok = false;
-                break;
+          const uint32_t d = tmem + ab * (uint32_t)bn;
+          for (int e = 0; e < nent; ++e, ++bit) {
+            const uint32_t b = bit % nb;
+            if (!mbar_wait(&bfull[b], (bit / nb) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_after();
+            const int s0 = e * G, gs = min(G, ksteps - e * G);
+            uint64_t bhd = sdesc(su32(Bbuf + b * estride), kLBO, kSBO);
+            uint32_t ah = a_hi + (uint32_t)s0 * 8u, al = a_lo + (uint32_t)s0 * 8u;
+            if (c == 0) {   // the tile's first chunk follows the conversion slice by slice
+              for (int s = 0; s < gs; ++s, bhd += bstep, ah += 8u, al += 8u) {
+                if (!mbar_wait(&ares_full[s0 + s], tit & 1, abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                tc_after();
+                umma_bf16_ta(d, ah, bhd, idesc, (s0 + s) > 0 ? 1u : 0u);
+                umma_bf16_ta(d, ah, bhd + blo, idesc, 1u);
+                umma_bf16_ta(d, al, bhd, idesc, 1u);
               }
-              tc_after();
-              const uint32_t ah = a_hi + (uint32_t)ks * 8u, al = a_lo + (uint32_t)ks * 8u;
-              umma_bf16_ta(d, ah, bhd, idesc, ks > 0 ? 1u : 0u);
-              umma_bf16_ta(d, ah, bld, idesc, 1u);
-              umma_bf16_ta(d, al, bhd, idesc, 1u);
+              if (!ok) break;
+            } else {
+              // the issue loop holds nothing but the products and the
+              // descriptor offsets (every extra instruction slows the issue)
+              const uint64_t bend = bhd + (uint64_t)gs * bstep;
+              if (s0 == 0) {
+                umma_bf16_ta(d, ah, bhd, idesc, 0u);
+                umma_bf16_ta(d, ah, bhd + blo, idesc, 1u);
+                umma_bf16_ta(d, al, bhd, idesc, 1u);
+                bhd += bstep;
+                ah += 8u;
+                al += 8u;
+              }
+              for (; bhd < bend; bhd += bstep, ah += 8u, al += 8u) {
+                umma_bf16_ta(d, ah, bhd, idesc, 1u);
+                umma_bf16_ta(d, ah, bhd + blo, idesc, 1u);
+                umma_bf16_ta(d, al, bhd, idesc, 1u);
+              }
             }
-          } else {
-            uint32_t ah = a_hi, al = a_lo;
-            umma_bf16_ta(d, ah, bhd, idesc, 0u);
-            umma_bf16_ta(d, ah, bld, idesc, 1u);
-            umma_bf16_ta(d, al, bhd, idesc, 1u);
-            for (int ks = 1; ks < ksteps; ++ks) {
-              bhd += bstep;
-              bld += bstep;
-              ah += 8u;
-              al += 8u;
-              umma_bf16_ta(d, ah, bhd, idesc, 1u);
-              umma_bf16_ta(d, ah, bld, idesc, 1u);
-              umma_bf16_ta(d, al, bhd, idesc, 1u);
-            }
+            umma_commit(&bempty[b]);
           }
           if (!ok) break;
-          umma_commit(&bempty[b]);
           umma_commit(&accf[ab]);
         }
         if (!ok) break;
@@ -448,8 +481,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
           h[i] = pack2(h0, h1);
           l[i] = pack2(__float2bfloat16_rn(x0 - __bfloat162float(h0)), __float2bfloat16_rn(x1 - __bfloat162float(h1)));
         }
-        tmem_st8(tmem + AR_ACOL + (uint32_t)ks * 8u + lane_base, h);
-        tmem_st8(tmem + AR_ACOL + (uint32_t)(ksteps + ks) * 8u + lane_base, l);
+        tmem_st8(tmem + acol + (uint32_t)ks * 8u + lane_base, h);
+        tmem_st8(tmem + acol + (uint32_t)(ksteps + ks) * 8u + lane_base, l);
         tmem_st_wait();
         mbar_arrive(&aempty[s]);
         tc_before();
@@ -458,8 +491,9 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
       if (!ok) break;
     }
   } else {
-    const int q = warp & 3;
-    float* mystg = reinterpret_cast<float*>(stg + (uint32_t)(warp - 6) * 2u * 2048u);
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; set h = the accumulator it drains
+    const int q = warp & 3, ew = warp - 6, h = ew >> 2;
+    float* mystg = reinterpret_cast<float*>(stg + (uint32_t)ew * 2u * 2048u);
     uint32_t accit = 0;
     int sbuf = 0;
     bool ok = true;
@@ -468,8 +502,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     // (whole chunks; the loss launcher keeps nchunks * bn <= 4096)
     float* wall = reinterpret_cast<float*>(stg);
     if (kLoss) {
-      for (int j = threadIdx.x - 192; j < nchunks * bn; j += 128) wall[j] = j < N ? (float)wgt[j] : 0.f;
-      asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+      for (int j = threadIdx.x - 192; j < nchunks * bn; j += 256) wall[j] = j < N ? (float)wgt[j] : 0.f;
+      asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
     }
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       const int row0 = (int)(tile * 128) + q * 32;
@@ -477,32 +511,33 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
       const float tv = (kLoss && row_ok) ? tgt[row0 + lane] : 0.f;
       for (int c = 0; c < nchunks; ++c, ++accit) {
         const uint32_t ab = accit % AR_ACC;
+        if ((int)ab != h) continue;
         if (!mbar_wait(&accf[ab], (accit / AR_ACC) & 1, abort_flag)) {
           ok = false;
           break;
         }
         tc_after();
         const int cend = min(bn, N - c * bn);   // the last chunk may be ragged
+        const uint32_t acc = tmem + ab * (uint32_t)bn + ((uint32_t)(q * 32) << 16);
         if (kLoss) {
-          // 64 columns per round: four loads in flight, one wait; columns past
-          // the chunk's frames carry weight 0 and are selected away (their
+          // up to 32 columns per round: the round's loads in flight, one
+          // wait; columns past the chunk's frames are selected away (their
           // accumulator entries may hold anything)
           const float* wc = wall + c * bn;
           float s = 0.f;
-          for (int c0 = 0; c0 < cend; c0 += 64) {
-            uint32_t v[64];
-            const uint32_t ta = tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16);
-            tmem_ld16_nw(ta, v);
-            tmem_ld16_nw(ta + 16u, v + 16);
-            tmem_ld16_nw(ta + 32u, v + 32);
-            tmem_ld16_nw(ta + 48u, v + 48);
+          for (int c0 = 0; c0 < cend; c0 += 32) {
+            uint32_t v[32];
+            const int rem = cend - c0;   // the same in every lane
+            tmem_ld16_nw(acc + (uint32_t)c0, v);
+            if (rem > 16) tmem_ld16_nw(acc + (uint32_t)c0 + 16u, v + 16);
             tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
+            for (int j = 0; j < 32; ++j) {
+              const bool in = j < rem;
+              const float wj = wc[c0 + (in ? j : 0)];
               const float e = __uint_as_float(v[j]) - tv, ae = fabsf(e);
               const float rho = (delta > 0.f && ae > delta) ? delta * (ae - 0.5f * delta) : 0.5f * e * e;
-              const float t = wc[c0 + j] * rho;
-              s += (c0 + j < cend) ? t : 0.f;
+              s += in ? wj * rho : 0.f;
             }
           }
           if (row_ok) lacc += (double)s;
@@ -512,7 +547,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         }
         for (int c0 = 0; c0 < cend; c0 += 16) {
           float v[16];
-          tmem_ld16(tmem + ab * 128u + (uint32_t)c0 + ((uint32_t)(q * 32) << 16), v);
+          tmem_ld16(acc + (uint32_t)c0, v);
           // the store issued two rounds ago from this buffer must have read it
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           __syncwarp();
@@ -533,7 +568,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     }
     if (kLoss) {
       const double ws = warp_sum(lacc);
-      if (lane == 0) red[q] = ws;
+      if (lane == 0) red[ew] = ws;
     } else if (lane == 0) {
       bulk_wait0();
     }
@@ -544,7 +579,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     tc_after();
     tmem_dealloc(tmem, 512);
   }
-  if (kLoss && threadIdx.x == 0) loss_part[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3]));
+  if (kLoss && threadIdx.x == 0)
+    loss_part[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(abort_flag)) raise_status(err, DMD_ETIMEOUT, 8002);
 }
 
@@ -855,9 +891,19 @@ int bres_stages(int ksteps, int Np) {
   while (ns > 4 && bres_smem(ksteps, Np, ns) > (size_t)kMaxSmem) --ns;
   return ns;
 }
-size_t ares_smem(int ksteps, int bn, int sa, int nb) {
-  const size_t chunk = ((size_t)2 * ksteps * bn * 32 + 1023) & ~(size_t)1023;
-  return 1024 + (size_t)sa * 8192 + (size_t)nb * chunk + 4 * 2 * 2048 + 512;
+size_t ares_entry_bytes(int bn, int G) { return ((size_t)2 * G * bn * 32 + 1023) & ~(size_t)1023; }
+size_t ares_smem(int bn, int sa, int nb, int G) {
+  return 1024 + (size_t)sa * 8192 + (size_t)nb * ares_entry_bytes(bn, G) + AR_STG + 512;
+}
+// K-slices per B ring entry for (bn, sa, nb): the fewest entries per chunk
+// (G = ceil(ks / E) for E = 1, 2, ...) whose nb entries fit in shared memory;
+// 0 when not even single slices fit.
+int ares_group(int ksteps, int bn, int sa, int nb) {
+  for (int E = 1; E <= ksteps; ++E) {
+    const int G = (ksteps + E - 1) / E;
+    if (ares_smem(bn, sa, nb, G) <= (size_t)kMaxSmem) return G;
+  }
+  return 0;
 }
 
 struct AresCfg {
@@ -869,18 +915,62 @@ AresCfg g_ares_override = {0, 0, 0};
 AresCfg g_ares_tuned[AR_MAXKS + 1] = {};
 std::mutex g_ares_mu;
 
-// Tuned configuration if any, else the widest frame chunk (128 .. 16
-// columns), then the deepest rings, that fit in shared memory.
-AresCfg ares_cfg(int ksteps) {
+// Default chunk width for N output columns: the least padded width
+// (chunks x chunk width) among chunks of at least 128 columns (or N rounded
+// up to 16, if smaller) up to the widest that fits, ties to the wider chunk.
+// The products are bound by the tensor pipe's rate and by the issue cost per
+// instruction together (measured at 6.3M rows and 1000 frames, 150 modes:
+// 7 x 144 = 1008 columns 6.27 ms, 6 x 176 = 1056 6.3-6.4 ms, 8 x 128 = 1024
+// 6.45 ms, 9 x 112 = 1008 6.40 ms).
+int ares_bn(int ksteps, int N) {
+  const int bmax = ares_bn_max(ksteps);
+  const int bmin = (int)std::min<int64_t>(bmax, std::min<int64_t>(128, round_up(N, 16)));
+  int best = bmax;
+  int64_t best_w = ceil_div(N, bmax) * bmax;
+  for (int bn = bmax - 16; bn >= bmin; bn -= 16) {
+    const int64_t w = ceil_div(N, bn) * bn;
+    if (w < best_w) {
+      best = bn;
+      best_w = w;
+    }
+  }
+  return best;
+}
+
+// Default rings for chunk width bn: 3 A stages if any ring fits with them
+// (else 2), then the fewest ring entries per chunk, then the most entries
+// (measured at 6.3M rows, 1000 frames: 150 modes best with 3 entries of 5
+// K-slices, 200 modes with 2 entries of 7 and 6).  bn = 0 when nothing fits.
+AresCfg ares_rings(int ksteps, int bn) {
+  for (int sa = 3; sa >= 2; --sa) {
+    AresCfg best = {0, 0, 0};
+    int bestE = 1 << 30;
+    for (int nb = AR_MAXNB; nb >= 2; --nb) {
+      const int G = ares_group(ksteps, bn, sa, nb);
+      if (G == 0) continue;
+      const int E = (ksteps + G - 1) / G;
+      if (E < bestE) {
+        best = {bn, sa, nb};
+        bestE = E;
+      }
+    }
+    if (best.bn) return best;
+  }
+  return {0, 0, 0};
+}
+
+// Tuned configuration if any, else the default chunk width and its rings
+// (or the first narrower chunk whose rings fit).
+AresCfg ares_cfg(int ksteps, int N) {
   if (g_ares_override.bn) return g_ares_override;
   if (ksteps >= 1 && ksteps <= AR_MAXKS) {
     std::lock_guard<std::mutex> lock(g_ares_mu);
     if (g_ares_tuned[ksteps].bn) return g_ares_tuned[ksteps];
   }
-  for (int bn = 128; bn >= 16; bn -= 16)
-    for (int nb = 3; nb >= 2; --nb)
-      for (int sa = 3; sa >= 2; --sa)
-        if (ares_smem(ksteps, bn, sa, nb) <= (size_t)kMaxSmem) return {bn, sa, nb};
+  for (int bn = ares_bn(ksteps, N); bn >= 16; bn -= 16) {
+    const AresCfg c = ares_rings(ksteps, bn);
+    if (c.bn) return c;
+  }
   return {0, 0, 0};
 }
 size_t tn_smem(int Mt, int Np, int nsplit, int ns) {
@@ -927,7 +1017,7 @@ size_t umma_nn_workspace_bytes(int64_t n, int Kd, int N) {
   const int ksteps = (int)ceil_div(Kd, 16);
   // recon layout (64-column chunks) is the larger of the two layouts
   const int64_t nch = ceil_div(N, 16);   // smallest chunk width gives the largest padding
-  const size_t ares = (size_t)nch * 2 * ksteps * 16 * 32 + (size_t)2 * ksteps * 128 * 32;
+  const size_t ares = (size_t)nch * 2 * ksteps * 16 * 32 + (size_t)2 * ksteps * 256 * 32;
   const size_t bres = (size_t)2 * ksteps * round_up(N, 16) * 32 + 2 * ksteps * 256 * 32;
   return std::max(ares, bres) + 4096;
 }
@@ -963,13 +1053,14 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
     return DMD_OK;
   }
   // many output columns: A tile resident, B streamed in bn-column chunks
-  const AresCfg cfg = ares_cfg(ksteps);
+  const AresCfg cfg = ares_cfg(ksteps, N);
   const int bn = cfg.bn;
-  if (bn == 0 || ksteps > AR_MAXKS || ares_smem(ksteps, bn, cfg.sa, cfg.nb) > (size_t)kMaxSmem) {
+  const int G = bn > 0 && ksteps <= AR_MAXKS ? ares_group(ksteps, bn, cfg.sa, cfg.nb) : 0;
+  if (bn == 0 || ksteps > AR_MAXKS || G == 0 || bn > ares_bn_max(ksteps)) {
     set_error("umma_gemm_nn: inner dimension %d too large for the resident-A layout", Kd);
     return DMD_EINVAL;
   }
-  const size_t smem = ares_smem(ksteps, bn, cfg.sa, cfg.nb);
+  const size_t smem = ares_smem(bn, cfg.sa, cfg.nb, G);
   const int nchunks = (int)ceil_div(N, bn);
   const int64_t work = (int64_t)nchunks * bn * ksteps;
   k_split_b<<<(unsigned)ceil_div(work, 128), 128, 0, st>>>(Kd, N, B, bn, ksteps, nchunks, split, skip);
@@ -977,7 +1068,7 @@ dmd_status umma_gemm_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   CUtensorMap mapC;
   DMD_TRY(make_map(&mapC, C, n, N, ldc, 32, 16));
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_umma_nn_ares<0><<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
+  k_umma_nn_ares<0><<<grid, AR_THREADS, smem, st>>>(mapA, mapC, split, n, N, ksteps, bn, cfg.sa, cfg.nb, G, nchunks,
                                                      ntiles, nullptr, nullptr, 0.f, nullptr, status_word(), skip);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
@@ -992,25 +1083,26 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
                         const double* w, float delta, double* part, int* parts, void* ws, cudaStream_t st) {
   const int ksteps = (int)ceil_div(Kd, 16);
   const int64_t ntiles = ceil_div(n, 128);
-  // 128-frame chunks (the epilogue drains 64 columns per round), the
-  // deepest rings that fit
+  // the default chunk width, narrower only where the chunks' weights would
+  // not fit in the 4096-entry staging area
   AresCfg cfg = {0, 0, 0};
-  for (int nb = 3; nb >= 2 && cfg.bn == 0; --nb)
-    for (int sa = 3; sa >= 2 && cfg.bn == 0; --sa)
-      if (ares_smem(ksteps, 128, sa, nb) <= (size_t)kMaxSmem) cfg = {128, sa, nb};
+  if (ksteps <= AR_MAXKS)
+    for (int bn = ares_bn(ksteps, N); bn >= 16 && cfg.bn == 0; bn -= 16)
+      if (ceil_div(N, bn) * bn <= 4096) cfg = ares_rings(ksteps, bn);
   const int bn = cfg.bn;
-  if (bn == 0 || ksteps > AR_MAXKS) {
+  const int G = bn ? ares_group(ksteps, bn, cfg.sa, cfg.nb) : 0;
+  if (ksteps > AR_MAXKS) {
     set_error("umma_loss_nn: inner dimension %d too large for the resident-A layout", Kd);
     return DMD_EINVAL;
   }
-  if (ceil_div(N, bn) * bn > 4096) {
+  if (bn == 0) {
     set_error("umma_loss_nn: %d frames in one call (at most 4096: the weights are staged in shared memory)", N);
     return DMD_EINVAL;
   }
   CUtensorMap mapA;
   DMD_TRY(make_map(&mapA, A, n, Kd, lda, 128, 16));
   const int grid = umma_loss_parts(n);
-  const size_t smem = ares_smem(ksteps, bn, cfg.sa, cfg.nb);
+  const size_t smem = ares_smem(bn, cfg.sa, cfg.nb, G);
   const int nchunks = (int)ceil_div(N, bn);
   const int64_t work = (int64_t)nchunks * bn * ksteps;
   uint8_t* split = reinterpret_cast<uint8_t*>(ws);
@@ -1018,7 +1110,7 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   DMD_LAUNCH_CHECK();
   DMD_CUDA_TRY(cudaFuncSetAttribute(k_umma_nn_ares<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // no frames are stored: the output map argument is unused (the A map stands in)
-  k_umma_nn_ares<1><<<grid, AR_THREADS, smem, st>>>(mapA, mapA, split, n, N, ksteps, bn, cfg.sa, cfg.nb, nchunks,
+  k_umma_nn_ares<1><<<grid, AR_THREADS, smem, st>>>(mapA, mapA, split, n, N, ksteps, bn, cfg.sa, cfg.nb, G, nchunks,
                                                      ntiles, tgt, w, delta, part, status_word(), nullptr);
   DMD_LAUNCH_CHECK();
   *parts = grid;
@@ -1026,7 +1118,7 @@ dmd_status umma_loss_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
 }
 
 // Autotuner of the resident-A (many output columns) product: every
-// (frame chunk, A stages, B buffers) configuration that fits in shared memory
+// (frame chunk, A stages, B ring entries) configuration that fits in shared memory
 // is launched on the caller's operands -- one warm-up and two timed launches,
 // CUDA events on `st` -- and the fastest is kept for this number of k-slices;
 // later products with the same inner dimension use it.  Synchronises `st`.
@@ -1043,10 +1135,10 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   AresCfg best = {0, 0, 0};
   float best_ms = 0.f;
   dmd_status status = DMD_OK;
-  for (int bn = 128; bn >= 32 && status == DMD_OK; bn -= 16)
-    for (int nb = 2; nb <= 3 && status == DMD_OK; ++nb)
+  for (int bn = ares_bn_max(ksteps); bn >= 64 && status == DMD_OK; bn -= 16)
+    for (int nb = 2; nb <= AR_MAXNB && status == DMD_OK; ++nb)
       for (int sa = 2; sa <= 3 && status == DMD_OK; ++sa) {
-        if (ares_smem(ksteps, bn, sa, nb) > (size_t)kMaxSmem) continue;
+        if (ares_group(ksteps, bn, sa, nb) == 0) continue;
         g_ares_override = {bn, sa, nb};
         status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0, nullptr);
         if (status != DMD_OK) break;

@@ -447,7 +447,7 @@ def dmd_edit_modes(model: DmdModel, threshold: float = 0.01, low=(1.0, 1.0, 1.0)
 
 def dmd_autotune_predict(model: DmdModel, ks, *, precision="mixed") -> tuple:
     """Tune the reconstruction kernel for this model's mode count on these
-    frames; returns the chosen (chunk width, A stages, B buffers)."""
+    frames; returns the chosen (chunk width, A stages, B ring entries)."""
     dev = model.Phi_R.device
     kt = _ks_tensor(ks, dev)
     K = kt.numel()

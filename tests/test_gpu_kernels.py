@@ -97,9 +97,13 @@ def test_gemm_tn_is_deterministic(dmd, prec):
     assert torch.equal(c1, c2)
 
 
-@pytest.mark.parametrize("n,K,N", [(300000, 150, 1000), (5000 + 11, 20, 501), (1000, 1, 65)])
+@pytest.mark.parametrize("n,K,N", [(300000, 150, 1000), (5000 + 11, 20, 501), (1000, 1, 65), (70001, 200, 1000),
+                                   (20011, 256, 700)])
 def test_gemm_tall_many_columns(dmd, n, K, N):
-    """The reconstruction shape (K frames >> 256 columns: resident-A kernel)."""
+    """The reconstruction shape (K frames >> 256 columns: resident-A kernel).
+    The cases cover chunk widths 176 (150 modes), 240, 144 and 128 (256
+    modes), ring entries of whole chunks and of part chunks with a shorter
+    last entry (200 modes: 7 + 6 K-slices), and ragged last chunks."""
     A = _tall(n, K, 7 + n)
     B = np.random.default_rng(N).standard_normal((N, K))
     for prec in PRECS:
