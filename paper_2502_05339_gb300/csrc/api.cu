@@ -105,7 +105,6 @@ dmd_status fit_glue_copy(int64_t count, const double* src, double* dst, cudaStre
 dmd_status fit_glue_fill_int(int64_t count, int* dst, int v, cudaStream_t st);
 dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, int spare, cudaStream_t st);
 dmd_status fit_glue_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip, cudaStream_t st);
-dmd_status fit_glue_eye(int n, double* T, int ld, cudaStream_t st);
 dmd_status dgemm_gated(int M, int N, int K, double alpha, const double* A, int lda, bool ta, const double* B,
                        int ldb, bool tb, double beta, double* C, int ldc, const int32_t* skip, cudaStream_t st);
 dmd_status cholesky_upper_gated(int n, double* G, int ld, double tau, int32_t* info, int tag, const int32_t* skip,
@@ -381,12 +380,8 @@ dmd_status orth_tall_shifted(const Tall& tall, FitBufs& b, const float* X, int64
 // The second Gram Q1^T Q1 (of a well-conditioned matrix, close to I) is a
 // tall reduction and its Cholesky factor is taken in FP32; the second factor
 // is kept as T2 = R2^{-1} and folded into the consumers (Q = Q1 T2).
-// The second pass only re-orthonormalises a basis whose span it leaves
-// unchanged, so a basis that only feeds the next power iteration (Z =
-// X^T Q, then orthonormalised in the small space) skips it: T2 = I there
-// (final_basis false).  Only the basis of the projection takes both passes.
 dmd_status orth_tall(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, const double* Bs, int32_t* info,
-                     int tag, bool final_basis, cudaStream_t st) {
+                     int tag, cudaStream_t st) {
   const int l = b.l, m = b.m;
   DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
   DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
@@ -397,14 +392,37 @@ dmd_status orth_tall(const Tall& tall, FitBufs& b, const float* X, int64_t ldX, 
   DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
   DMD_TRY(dgemm(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, st));   // Bs R1^{-1}
   DMD_TRY(tall.nn(b.n, m, l, X, ldX, b.WB, b.Q1, b.ldY, b.gemm_ws, st));
-  if (final_basis) {
-    DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
-    DMD_TRY(cholesky_upper_f32(l, b.G, l, kTauTall, info, tag + 1, st));
-    DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
-  } else {
-    DMD_TRY(fit_glue_eye(l, b.T2, l, st));
-  }
+  DMD_TRY(tall.tn(b.n, l, l, b.Q1, b.ldY, b.Q1, b.ldY, b.G, b.gemm_ws, st));
+  DMD_TRY(cholesky_upper_f32(l, b.G, l, kTauTall, info, tag + 1, st));
+  DMD_TRY(tri_inv_upper(l, b.G, l, b.T2, l, st));
   return orth_tall_shifted(tall, b, X, ldX, Bs, info, tag, st);
+}
+
+// One power iteration (Sec. 4.3) in the space of the snapshot Gram: with
+// Q = X Bs R^{-1} the basis orth_tall would form from Bs (R = chol(Bs^T W_X
+// Bs), the same first factor, with the same dropping rule and the same
+// shifted fallback), X^T Q = W_X (Bs R^{-1}) exactly, so Z = X^T Q is formed
+// from W_X = X^T X in FP64 and the tall basis is never built: the tall
+// passes of an iteration (X Bs R^{-1} and X^T Q) become two m x m x l
+// products.  The result is b.Z (m x l, not yet orthonormal); Bs may be b.Z.
+dmd_status power_step_gram(FitBufs& b, const double* Bs, int32_t* info, int tag, cudaStream_t st) {
+  const int l = b.l, m = b.m;
+  const int32_t* skip = b.gate + 1;
+  DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, Bs, m, false, 0.0, b.WB, m, st));
+  DMD_TRY(dgemm(l, l, m, 1.0, Bs, m, true, b.WB, m, false, 0.0, b.G, l, st));
+  DMD_TRY(fit_glue_copy((int64_t)l * l, b.G, b.G0, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 0, 0, st));
+  DMD_TRY(cholesky_upper(l, b.G, l, kTauTall, info, tag, st));
+  DMD_TRY(fit_glue_gate(info, b.gate, 1, l - b.r, st));
+  DMD_TRY(tri_inv_upper(l, b.G, l, b.T1, l, st));
+  // more directions dropped than the sketch has spare: R = chol(G + s I)
+  // instead (every direction kept), as the shifted fallback of orth_tall
+  DMD_TRY(fit_glue_shift_diag(l, b.G0, l, 1e-6, skip, st));
+  DMD_TRY(cholesky_upper_gated(l, b.G0, l, 0.0, info, tag + 2, skip, st));
+  DMD_TRY(tri_inv_upper_gated(l, b.G0, l, b.T1, l, skip, st));
+  DMD_TRY(dgemm(m, l, l, 1.0, Bs, m, false, b.T1, l, false, 0.0, b.WB, m, st));     // Bs R^{-1}
+  DMD_TRY(dgemm(m, l, m, 1.0, b.W, m + 1, false, b.WB, m, false, 0.0, b.Z, m, st));  // X^T Q
+  return DMD_OK;
 }
 
 // CholeskyQR2 of a small FP64 matrix Z (rows x l) in place (second factor in
@@ -522,15 +540,15 @@ dmd_status fit_impl(const dmd_fit_desc& d, const float* S, const float* Ups, con
   // 2. snapshot Gram W = S^T S (one pass; also screens the input for NaN/Inf)
   DMD_TRY(tall.tn_accurate(n, m + 1, m + 1, S, d.ldS, S, d.ldS, b.W, b.gemm_ws, st));
   DMD_TRY(fit_glue_check_finite((int64_t)(m + 1) * (m + 1), b.W, info, 91, st));
-  // 3. Y = X Omega, Q = orth(Y)
-  DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Om, info, 1, d.power_iters == 0, st));
-  // 4. power iterations: Z = orth(X^T Q), Y = X Z, Q = orth(Y)
+  // 3-4. Y = X Omega, power iterations Z = orth(X^T Q), Y = X Z (in the
+  // snapshot-Gram space), then Q = orth(Y) for the last Y
+  const double* Bs = b.Om;
   for (int it = 0; it < d.power_iters; ++it) {
-    DMD_TRY(tall.tn(n, m, l, X, d.ldS, b.Q1, b.ldY, b.Zp, b.gemm_ws, st));
-    DMD_TRY(dgemm(m, l, l, 1.0, b.Zp, m, false, b.T2, l, false, 0.0, b.Z, m, st));
+    DMD_TRY(power_step_gram(b, Bs, info, it == 0 ? 1 : 12 + 4 * (it - 1), st));
     DMD_TRY(orth_small(b, m, info, 10 + 4 * it, st));
-    DMD_TRY(orth_tall(tall, b, X, d.ldS, b.Z, info, 12 + 4 * it, it == d.power_iters - 1, st));
+    Bs = b.Z;
   }
+  DMD_TRY(orth_tall(tall, b, X, d.ldS, Bs, info, d.power_iters == 0 ? 1 : 12 + 4 * (d.power_iters - 1), st));
   // 5. projection P = Q^T S = T2^T (Q1^T S): B = P[:, 0:m], Q^T X' = P[:, 1:m+1], Q^T x_0 = P[:, 0]
   DMD_TRY(tall.tn(n, l, m + 1, b.Q1, b.ldY, S, d.ldS, b.Pp, b.gemm_ws, st));
   DMD_TRY(dgemm(l, m + 1, l, 1.0, b.T2, l, true, b.Pp, l, false, 0.0, b.P, l, st));

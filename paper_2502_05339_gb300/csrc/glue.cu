@@ -60,14 +60,6 @@ __global__ void k_shift_diag(int n, double* G, int ld, double rel, const int32_t
   for (int i = threadIdx.x; i < n; i += blockDim.x) G[i + (int64_t)i * ld] += s;
 }
 
-// T (n x n, ld) = I.
-__global__ void k_eye(int n, double* T, int ld) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n) return;
-  const int i = (int)(t % n), j = (int)(t / n);
-  T[i + (int64_t)j * ld] = i == j ? 1.0 : 0.0;
-}
-
 __global__ void k_scale_cols(int rows, int cols, double* A, int lda, const double* s) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)rows * cols) return;
@@ -185,12 +177,6 @@ dmd_status fit_glue_gate(int32_t* info, int32_t* gate, int mode, int spare, cuda
 
 dmd_status fit_glue_shift_diag(int n, double* G, int ld, double rel, const int32_t* skip, cudaStream_t st) {
   k_shift_diag<<<1, 256, 0, st>>>(n, G, ld, rel, skip);
-  DMD_LAUNCH_CHECK();
-  return DMD_OK;
-}
-
-dmd_status fit_glue_eye(int n, double* T, int ld, cudaStream_t st) {
-  k_eye<<<(unsigned)ceil_div((int64_t)n * n, 256), 256, 0, st>>>(n, T, ld);
   DMD_LAUNCH_CHECK();
   return DMD_OK;
 }
