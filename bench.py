@@ -805,7 +805,7 @@ def _run_e2e(args, sc, c, dmd, dev, st, out, ks, local):
 GRAM_TRAFFIC_PER_ROW = (1.002e9 + 0.154e9) / 1048576   # k_gram_f32: S once + the FP64 partials' read-modify-writes
 TRAFFIC_PER_ROW = {
     "k_gram_f32 (snapshot Gram W = S^T S)": GRAM_TRAFFIC_PER_ROW,
-    "k_umma_tn (X^T Q1, Q1^T S)": 1.596e9 / 1048576,
+    "k_umma_tn (projection Q1^T S)": 1.596e9 / 1048576,
     "k_umma_tn (Gram Q1^T Q1)": 0.737e9 / 1048576,
     "k_umma_nn_bres (sketch Q1 = X M)": 1.463e9 / 1048576,
     "k_umma_nn_ares (reconstruction Phi_R C)": 4.786e9 / 1048576,
@@ -861,7 +861,9 @@ def kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind):
     (same kernels, same sizes) and timed with CUDA events on the launching
     stream: the snapshot Gram W = S^T S, the sketch product Q1 = X M, the
     tensor-core reductions Q1^T Q1 and Q1^T S (mixed form; the FP32 form runs
-    them on the CUDA cores)."""
+    them on the CUDA cores).  One fit forms one tall sketch (the power
+    iterations run in the snapshot-Gram space), then its Gram and the
+    projection; the sketch kernel runs again for the modes X' M_R."""
     n, m, r = sc.n, sc.m, c["r"]
     l = min(r + c["oversample"], m)
     S, ld = sc.S, sc.S.shape[1]
@@ -874,7 +876,7 @@ def kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind):
     sec = event_time(lambda: dmd.dmd_gemm_tn(S, S, n, precision="fp32"), st)
     out.append(alu_entry("k_gram_f32 (snapshot Gram W = S^T S)", float(n) * (m + 1) * (m + 2), sec, 1, peaks,
                          "n (m+1)(m+2) flops: 2n per distinct entry of the symmetric W"))
-    npass = 1 + c["power_iters"]
+    npass = 1
     sec = event_time(lambda: dmd.dmd_gemm_tall(X, n, M, precision=prec, out=Q), st)
     name = "k_umma_nn_bres (sketch Q1 = X M)" if prec == "mixed" else "k_gemm_nn_f32 (sketch Q1 = X M)"
     if prec == "mixed":
@@ -889,7 +891,7 @@ def kernel_rooflines(sc, c, dmd, dev, st, prec, peaks, peak_kind):
     else:
         out.append(alu_entry(name, float(n) * l * (l + 1), sec, npass, peaks, "n l (l+1) flops"))
     sec = event_time(lambda: dmd.dmd_gemm_tn(Q, S, n, precision=prec), st)
-    name = "k_umma_tn (X^T Q1, Q1^T S)" if prec == "mixed" else "k_gemm_tn_f32 (X^T Q1, Q1^T S)"
+    name = "k_umma_tn (projection Q1^T S)" if prec == "mixed" else "k_gemm_tn_f32 (projection Q1^T S)"
     if prec == "mixed":
         out.append(hbm_entry(name, 4.0 * n * (l + m + 1), sec, npass, peaks, peak_kind,
                              "4 n (l + m + 1) bytes: Q1 and S read once"))
