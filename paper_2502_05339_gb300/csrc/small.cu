@@ -558,6 +558,377 @@ __global__ void k_hqr(int n, const double* __restrict__ Hin, int ldh, double* wr
   if (lane == 0 && info) info[3] = total;
 }
 
+// --------------------------------------------- Francis QR, multishift chain
+
+// FP32 eigenvalue estimates of an unreduced Hessenberg window by chains of
+// small bulges (the small-bulge multishift form of Francis' algorithm): each
+// sweep of a wide window takes 2 s shifts, the eigenvalues of its trailing
+// 2s x 2s block, and chases s double-shift bulges down the window together,
+// three rows apart, one warp per bulge.  A chain step forms every bulge's
+// reflector from the current matrix, applies them from the left (disjoint
+// row triples), then from the right (disjoint column triples), with a CTA
+// barrier between the two: the same similarity as chasing the bulges one
+// after the other (left and right products commute, and no reflector reads
+// an entry another bulge of the same step writes).  A step costs about what
+// one double-shift step costs, so a sweep applies s times the shifts.  The
+// kernel is bound by the latency of each warp's instruction stream
+// (measured: ~6 cycles per issued instruction, one warp per scheduler), so
+// the step is written for few instructions (compile-time strides, one
+// reciprocal square root for the norm); splitting a bulge over two warps
+// was measured slower (more barrier waits).
+// Narrow windows, every 10th sweep of a window (exceptional shifts) and
+// windows whose shift problem does not converge take one double-shift sweep.
+constexpr int kMsBulges = 4;   // bulges per chain
+constexpr int kMsSplit = 1;    // warps per bulge
+constexpr int kMsWarps = kMsBulges * kMsSplit;
+constexpr int kMsMin = 40;     // narrower windows take double-shift sweeps
+constexpr int kMsT = 5;        // at most this many entries per lane per batch
+constexpr int kMsLd = 2 * kMsBulges + 1;
+
+// P = I - tau v v^T, v = (1, v1, v2), with P (x, y, z)^T = (beta, 0, 0)^T;
+// tau = 0 when there is nothing to annihilate.  Fast divisions: these
+// eigenvalues only seed the FP64 refinement.
+struct Refl3 {
+  float tau, v1, v2;
+};
+__device__ __forceinline__ Refl3 refl3(float x, float y, float z) {
+  Refl3 P{0.f, 0.f, 0.f};
+  const float n2 = x * x + y * y + z * z;
+  if (n2 > 0.f && (y != 0.f || z != 0.f)) {
+    const float nrm = n2 * rsqrtf(n2);
+    const float beta = x <= 0.f ? nrm : -nrm;
+    P.tau = __fdividef(beta - x, beta);
+    const float sc = __fdividef(1.f, x - beta);
+    P.v1 = y * sc;
+    P.v2 = z * sc;
+  }
+  return P;
+}
+
+// Rows k .. k + nr - 1 (nr = 2 or 3) of H (column-major, ld ldw) times P,
+// columns c0 .. c1, by `parts` warps (this one is part `part`): element e of
+// the range goes to lane e % 32 of part (e / 32) % parts.  Each lane loads its
+// entries (up to kMsT batches of 32 parts columns at a time, as many as the
+// range needs) before updating them, so the shared-memory latencies overlap.  Column
+// zc (the bulge just annihilated; -1 for none) gets exact zeros below row k.
+template <int PARTS>
+__device__ __forceinline__ void ms_rows(float* H, int ldw, int k, int nr, int c0, int c1, Refl3 P, int zc,
+                                        int lane, int part) {
+  constexpr int stride = 32 * PARTS;
+  const int nall = (c1 - c0 + stride) / stride;   // batches of the range (c1 >= c0)
+  float* h0 = H + k;
+  for (int b0 = 0; b0 < nall; b0 += kMsT) {
+    const int nt = min(kMsT, nall - b0);
+    const int cfirst = c0 + stride * b0 + part * 32 + lane;
+    float r0[kMsT], r1[kMsT], r2[kMsT];
+#pragma unroll
+    for (int t = 0; t < kMsT; ++t) {
+      const int c = cfirst + stride * t;
+      if (t < nt && c <= c1) {
+        r0[t] = h0[c * ldw];
+        r1[t] = h0[c * ldw + 1];
+        r2[t] = nr == 3 ? h0[c * ldw + 2] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kMsT; ++t) {
+      const int c = cfirst + stride * t;
+      if (t < nt && c <= c1) {
+        const float p = P.tau * (r0[t] + P.v1 * r1[t] + P.v2 * r2[t]);
+        h0[c * ldw] = r0[t] - p;
+        h0[c * ldw + 1] = c == zc ? 0.f : r1[t] - p * P.v1;
+        if (nr == 3) h0[c * ldw + 2] = c == zc ? 0.f : r2[t] - p * P.v2;
+      }
+    }
+  }
+}
+
+// Columns k .. k + nr - 1 of H times P, rows r0 .. r1, by `parts` warps.
+template <int PARTS>
+__device__ __forceinline__ void ms_cols(float* H, int ldw, int k, int nr, int r0, int r1, Refl3 P, int lane,
+                                        int part) {
+  constexpr int stride = 32 * PARTS;
+  const int nall = (r1 - r0 + stride) / stride;
+  float* c0p = H + k * ldw;
+  for (int b0 = 0; b0 < nall; b0 += kMsT) {
+    const int nt = min(kMsT, nall - b0);
+    const int rfirst = r0 + stride * b0 + part * 32 + lane;
+    float q0[kMsT], q1[kMsT], q2[kMsT];
+#pragma unroll
+    for (int t = 0; t < kMsT; ++t) {
+      const int r = rfirst + stride * t;
+      if (t < nt && r <= r1) {
+        q0[t] = c0p[r];
+        q1[t] = c0p[r + ldw];
+        q2[t] = nr == 3 ? c0p[r + 2 * ldw] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kMsT; ++t) {
+      const int r = rfirst + stride * t;
+      if (t < nt && r <= r1) {
+        const float p = P.tau * (q0[t] + P.v1 * q1[t] + P.v2 * q2[t]);
+        c0p[r] = q0[t] - p;
+        c0p[r + ldw] = q1[t] - p * P.v1;
+        if (nr == 3) c0p[r + 2 * ldw] = q2[t] - p * P.v2;
+      }
+    }
+  }
+}
+
+// First column of (H - s1)(H - s2) at the top of window [lo, hi] (s = s1 + s2,
+// t = s1 s2), rows lo .. lo + 2.
+__device__ __forceinline__ void ms_intro(const float* H, int ldw, int lo, float s, float t, float& x, float& y,
+                                         float& z) {
+  const float h00 = H[lo + lo * ldw], h01 = H[lo + (lo + 1) * ldw], h10 = H[lo + 1 + lo * ldw];
+  const float h11 = H[lo + 1 + (lo + 1) * ldw], h21 = H[lo + 2 + (lo + 1) * ldw];
+  x = h00 * h00 + h01 * h10 - s * h00 + t;
+  y = h10 * (h00 + h11 - s);
+  z = h10 * h21;
+}
+
+// One double-shift sweep over window [lo, hi] (hi - lo >= 2) by one warp.
+__device__ void ms_double_sweep(float* H, int ldw, int lo, int hi, float s, float t, int lane) {
+  float x, y, z;
+  ms_intro(H, ldw, lo, s, t, x, y, z);
+  for (int k = lo; k <= hi - 1; ++k) {
+    const int nr = k <= hi - 2 ? 3 : 2;
+    if (k > lo) {
+      x = H[k + (k - 1) * ldw];
+      y = H[k + 1 + (k - 1) * ldw];
+      z = nr == 3 ? H[k + 2 + (k - 1) * ldw] : 0.f;
+    }
+    const Refl3 P = refl3(x, y, nr == 3 ? z : 0.f);
+    if (P.tau != 0.f) {
+      ms_rows<1>(H, ldw, k, nr, max(lo, k - 1), hi, P, k > lo ? k - 1 : -1, lane, 0);
+      __syncwarp();
+      ms_cols<1>(H, ldw, k, nr, lo, min(k + 3, hi), P, lane, 0);
+      __syncwarp();
+    }
+  }
+}
+
+// Bottom of window [lo, hi]: the largest lo <= hi with H(lo, lo-1)
+// negligible relative to its diagonal neighbours (0 if none), i.e. the
+// first such subdiagonal scanning up from hi; the lanes of a warp test 32
+// subdiagonals at once (every lane gets the answer).
+__device__ __forceinline__ int ms_scan(const float* H, int ldw, int hi, float deflate, float anorm, int lane) {
+  for (int top = hi; top > 0; top -= 32) {
+    const int i = top - lane;
+    bool small = false;
+    if (i > 0) {
+      float s = fabsf(H[i - 1 + (i - 1) * ldw]) + fabsf(H[i + i * ldw]);
+      if (s == 0.f) s = anorm;
+      small = fabsf(H[i + (i - 1) * ldw]) <= deflate * s;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, small);
+    if (m) return top - (__ffs(m) - 1);
+  }
+  return 0;
+}
+
+// Standard double shift of window [lo, hi] (sum s, product t): the trailing
+// 2 x 2 block, or every 10th sweep the exceptional shift.
+__device__ __forceinline__ void ms_shift(const float* H, int ldw, int hi, int its, float& s, float& t) {
+  if (its % 10 == 0) {
+    const float w = fabsf(H[hi + (hi - 1) * ldw]) + fabsf(H[hi - 1 + (hi - 2) * ldw]);
+    const float h = 0.75f * w + H[hi + hi * ldw];
+    s = 2.f * h;
+    t = h * h + 0.4375f * w * w;
+  } else {
+    const float a = H[hi - 1 + (hi - 1) * ldw], b = H[hi - 1 + hi * ldw], c = H[hi + (hi - 1) * ldw],
+                d = H[hi + hi * ldw];
+    s = a + d;
+    t = a * d - b * c;
+  }
+}
+
+// Eigenvalues of the k x k Hessenberg matrix A (ld lda, overwritten) by
+// double-shift sweeps, one warp; er / ei written by lane 0 (conjugate pairs
+// adjacent).  false when a window needs more than 30 sweeps.
+__device__ bool ms_small_eigs(float* A, int lda, int k, float* er, float* ei, int lane) {
+  float anorm = 0.f;
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) anorm = fmaxf(anorm, fabsf(A[i + j * lda]));
+  if (anorm == 0.f) anorm = 1.f;
+  int hi = k - 1, its = 0;
+  while (hi >= 0) {
+    __syncwarp();
+    const int lo = ms_scan(A, lda, hi, 1e-5f, anorm, lane);
+    __syncwarp();
+    if (lo > 0 && lane == 0) A[lo + (lo - 1) * lda] = 0.f;
+    if (lo == hi) {
+      if (lane == 0) {
+        er[hi] = A[hi + hi * lda];
+        ei[hi] = 0.f;
+      }
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (lo == hi - 1) {
+      double r1, i1, r2, i2;
+      two_by_two_eigs<float>(A[hi - 1 + (hi - 1) * lda], A[hi - 1 + hi * lda], A[hi + (hi - 1) * lda],
+                             A[hi + hi * lda], r1, i1, r2, i2);
+      if (lane == 0) {
+        er[hi - 1] = (float)r1;
+        ei[hi - 1] = (float)i1;
+        er[hi] = (float)r2;
+        ei[hi] = (float)i2;
+      }
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (its >= 30) return false;
+    ++its;
+    float s, t;
+    ms_shift(A, lda, hi, its, s, t);
+    __syncwarp();
+    ms_double_sweep(A, lda, lo, hi, s, t, lane);
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kMsWarps, 1)
+    k_hqr_ms(int n, const double* __restrict__ Hin, int ldh, double* wr, double* wi, int32_t* info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldw = n | 1;
+  float* H = reinterpret_cast<float*>(smem_raw);
+  float* Hs = H + n * ldw;               // the trailing block whose eigenvalues are the shifts
+  float* ser = Hs + 2 * kMsBulges * kMsLd;
+  float* sei = ser + 2 * kMsBulges;
+  float* bs = sei + 2 * kMsBulges;       // per bulge: shift sum and product
+  float* bt = bs + kMsBulges;
+  float* red = bt + kMsBulges;           // [kMsWarps]
+  int* nbulge = reinterpret_cast<int*>(red + kMsWarps);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float deflate = fmaxf(FLT_EPSILON, 1e-5f);   // as k_hqr: these eigenvalues seed the FP64 refinement
+  float amax = 0.f;
+  for (int j = 0; j < n; ++j)
+    for (int i = tid; i < n; i += blockDim.x) {
+      const float v = (i <= j + 1) ? (float)Hin[i + (int64_t)j * ldh] : 0.f;
+      H[i + j * ldw] = v;
+      amax = fmaxf(amax, fabsf(v));
+    }
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) red[warp] = amax;
+  __syncthreads();
+  float anorm = 0.f;
+  for (int w = 0; w < kMsWarps; ++w) anorm = fmaxf(anorm, red[w]);
+  if (anorm == 0.f) anorm = 1.f;
+  int hi = n - 1, its = 0, total = 0;
+  while (hi >= 0) {
+    __syncthreads();
+    const int lo = ms_scan(H, ldw, hi, deflate, anorm, lane);   // every warp, the same answer
+    __syncthreads();
+    if (lo > 0 && tid == 0) H[lo + (lo - 1) * ldw] = 0.f;
+    if (lo == hi) {
+      if (tid == 0) {
+        wr[hi] = (double)H[hi + hi * ldw];
+        wi[hi] = 0.0;
+      }
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (lo == hi - 1) {
+      double r1, i1, r2, i2;
+      two_by_two_eigs<float>(H[hi - 1 + (hi - 1) * ldw], H[hi - 1 + hi * ldw], H[hi + (hi - 1) * ldw],
+                             H[hi + hi * ldw], r1, i1, r2, i2);
+      if (tid == 0) {
+        wr[hi - 1] = r1;
+        wi[hi - 1] = i1;
+        wr[hi] = r2;
+        wi[hi] = i2;
+      }
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (its >= 90) {
+      if (tid == 0) {
+        raise_status(info, DMD_ENUMERIC, 3000 + hi);
+        for (int i = 0; i <= hi; ++i) wr[i] = wi[i] = nan("");
+      }
+      return;
+    }
+    ++its;
+    ++total;
+    int s = 1;
+    if (hi - lo + 1 >= kMsMin && its % 10 != 0) {
+      // 2 s shifts: eigenvalues of the trailing 2s x 2s block, paired per bulge
+      constexpr int k2 = 2 * kMsBulges;
+      if (warp == 0) {
+        for (int e = lane; e < k2 * k2; e += 32) {
+          const int i = e % k2, j = e / k2;
+          Hs[i + j * kMsLd] = i <= j + 1 ? H[hi - k2 + 1 + i + (hi - k2 + 1 + j) * ldw] : 0.f;
+        }
+        __syncwarp();
+        const bool ok = ms_small_eigs(Hs, kMsLd, k2, ser, sei, lane);
+        if (lane == 0) {
+          int nb = 0;
+          float pend = 0.f;
+          bool have = false;
+          for (int i = 0; ok && i < k2;) {
+            if (sei[i] != 0.f) {   // a conjugate pair (adjacent)
+              bs[nb] = 2.f * ser[i];
+              bt[nb] = ser[i] * ser[i] + sei[i] * sei[i];
+              ++nb;
+              i += 2;
+            } else if (have) {     // two real shifts
+              bs[nb] = pend + ser[i];
+              bt[nb] = pend * ser[i];
+              ++nb;
+              have = false;
+              ++i;
+            } else {
+              pend = ser[i];
+              have = true;
+              ++i;
+            }
+          }
+          *nbulge = (ok && nb == kMsBulges) ? nb : 1;
+        }
+      }
+      __syncthreads();
+      s = *nbulge;
+    }
+    if (s > 1) {
+      const int T = (hi - 1 - lo) + 3 * (s - 1) + 1;
+      const int bulge = warp / kMsSplit, part = warp % kMsSplit;
+      for (int t = 0; t < T; ++t) {
+        const int k = lo + t - 3 * bulge;
+        const bool act = bulge < s && k >= lo && k <= hi - 1;
+        const int nr = k <= hi - 2 ? 3 : 2;
+        Refl3 P{0.f, 0.f, 0.f};
+        if (act) {
+          float x, y, z;
+          if (k == lo) {
+            ms_intro(H, ldw, lo, bs[bulge], bt[bulge], x, y, z);
+          } else {
+            x = H[k + (k - 1) * ldw];
+            y = H[k + 1 + (k - 1) * ldw];
+            z = nr == 3 ? H[k + 2 + (k - 1) * ldw] : 0.f;
+          }
+          P = refl3(x, y, nr == 3 ? z : 0.f);
+          if (P.tau != 0.f)
+            ms_rows<kMsSplit>(H, ldw, k, nr, max(lo, k - 1), hi, P, k > lo ? k - 1 : -1, lane, part);
+        }
+        __syncthreads();
+        if (act && P.tau != 0.f) ms_cols<kMsSplit>(H, ldw, k, nr, lo, min(k + 3, hi), P, lane, part);
+        __syncthreads();
+      }
+    } else if (warp == 0) {
+      float sh, th;
+      ms_shift(H, ldw, hi, its, sh, th);
+      ms_double_sweep(H, ldw, lo, hi, sh, th, lane);
+    }
+  }
+  if (tid == 0 && info) info[3] = total;
+}
+
 // ---------------------------------------------- inverse iteration (Hessenberg)
 
 // Rayleigh-quotient inverse iteration on the FP64 Hessenberg matrix for each
@@ -1863,17 +2234,21 @@ dmd_status apply_q(int n, const double* A, int lda, const double* tau, double* Y
   return DMD_OK;
 }
 
-size_t hqr_smem_bytes(int n) { return (size_t)n * (n | 1) * sizeof(float); }
+size_t hqr_smem_bytes(int n) {
+  return (size_t)n * (n | 1) * sizeof(float) +
+         (size_t)(2 * kMsBulges * kMsLd + 4 * kMsBulges + 2 * kMsBulges + kMsWarps + 1) * sizeof(float) + 16;
+}
 bool hqr_fits_smem(int n) { return hqr_smem_bytes(n) <= 200 * 1024; }
 
-// FP32 Francis QR for the eigenvalue estimates (refined in FP64 by hess_eigvecs).
+// FP32 Francis QR for the eigenvalue estimates (refined in FP64 by hess_eigvecs):
+// multishift chains on one CTA when the matrix fits in shared memory.
 dmd_status hqr(int n, const double* H, int ldh, double* wr, double* wi, double* scratch, int32_t* info,
                cudaStream_t st) {
   if (hqr_fits_smem(n)) {
     const size_t smem = hqr_smem_bytes(n);
     if (smem > 48 * 1024)
-      DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_hqr<float, true><<<1, 32, smem, st>>>(n, H, ldh, wr, wi, nullptr, info);
+      DMD_CUDA_TRY(cudaFuncSetAttribute(k_hqr_ms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_hqr_ms<<<1, 32 * kMsWarps, smem, st>>>(n, H, ldh, wr, wi, info);
   } else {
     k_hqr<float, false><<<1, 32, 0, st>>>(n, H, ldh, wr, wi, reinterpret_cast<float*>(scratch), info);
   }
