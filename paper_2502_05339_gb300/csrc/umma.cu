@@ -82,7 +82,8 @@ __global__ void k_split_b(int Kd, int N, const double* __restrict__ B, int BN, i
 
 constexpr int NN_SMAX = 12; // TMA stages (FP32 128 x 16 tiles, 8 KB): as many as fit, up to 12
 constexpr int NN_CS = 4;   // converted stages (bf16 hi + lo, 8 KB)
-constexpr int NN_THREADS = 320;
+constexpr int NN_CONV = 8; // converter warps: two per 32-row group, one per 8-wide half of a K-slice
+constexpr int NN_THREADS = 32 * (2 + NN_CONV + 4);
 
 __global__ void __launch_bounds__(NN_THREADS, 1)
     k_umma_nn_bres(const __grid_constant__ CUtensorMap tmA, const uint8_t* __restrict__ Bsplit,
@@ -113,10 +114,10 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < ns; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 128);
+      mbar_init(&empty[i], 32 * NN_CONV);
     }
     for (int i = 0; i < NN_CS; ++i) {
-      mbar_init(&cfull[i], 128);
+      mbar_init(&cfull[i], 32 * NN_CONV);
       mbar_init(&cempty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -195,8 +196,11 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
       umma_commit(tdown);          // completes when every MMA issued above has finished
       mbar_wait_drain(tdown, 0);
     }
-  } else if (warp < 6) {
-    const int t = threadIdx.x - 64;   // row of the tile
+  } else if (warp < 2 + NN_CONV) {
+    // converters: thread t splits row t % 128 of the tile, K-columns
+    // 8 h .. 8 h + 7 of each slice (h = t / 128: one 16-byte chunk per plane)
+    const int t = threadIdx.x - 64;
+    const int row = t & 127, h = t >> 7;
     uint32_t it = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -207,12 +211,18 @@ __global__ void __launch_bounds__(NN_THREADS, 1)
           ok = false;
           break;
         }
-        const float* src = reinterpret_cast<const float*>(stA + s * 8192);
-        float x[16];
+        const float* src = reinterpret_cast<const float*>(stA + s * 8192) + 8 * h * 128 + row;
+        uint32_t hv[4], lv[4];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) x[c] = src[c * 128 + t];
-        uint8_t* dst = cv + cs * 8192;
-        split_store_row(x, dst, dst + 4096, t);
+        for (int i = 0; i < 4; ++i) {
+          const float x0 = src[(2 * i) * 128], x1 = src[(2 * i + 1) * 128];
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+          hv[i] = pack2(h0, h1);
+          lv[i] = pack2(__float2bfloat16_rn(x0 - __bfloat162float(h0)), __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+        }
+        uint8_t* dst = cv + cs * 8192 + kslice_off(row, h);
+        *reinterpret_cast<uint4*>(dst) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(dst + 4096) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
         fence_async_smem();
         mbar_arrive(&cfull[cs]);
         mbar_arrive(&empty[s]);
@@ -884,10 +894,12 @@ constexpr int kMaxSmem = 227 * 1024;
 size_t bres_smem(int ksteps, int Np, int ns) {
   return 1024 + (((size_t)2 * ksteps * Np * 32 + 1023) & ~(size_t)1023) + (size_t)ns * 8192 + NN_CS * 8192 + 512;
 }
-// TMA stages of the B-resident kernel: as many as fit (more bytes in flight
-// per SM to cover DRAM latency), at least 4.
+// TMA stages of the B-resident kernel: as many as fit, up to NN_SMAX (bytes
+// in flight per SM against DRAM latency: a load-only probe of 128-row x
+// 16-column boxes over a 6.3M x 200 column-major matrix measured 5.4 TB/s
+// with 4 stages, 6.3 TB/s with 7 to 12), at least 4.
 int bres_stages(int ksteps, int Np) {
-  int ns = 4;   // measured: deeper rings (up to 7 fit) were slower
+  int ns = NN_SMAX;
   while (ns > 4 && bres_smem(ksteps, Np, ns) > (size_t)kMaxSmem) --ns;
   return ns;
 }
@@ -937,12 +949,13 @@ int ares_bn(int ksteps, int N) {
   return best;
 }
 
-// Default rings for chunk width bn: 3 A stages if any ring fits with them
-// (else 2), then the fewest ring entries per chunk, then the most entries
-// (measured at 6.3M rows, 1000 frames: 150 modes best with 3 entries of 5
-// K-slices, 200 modes with 2 entries of 7 and 6).  bn = 0 when nothing fits.
+// Default rings for chunk width bn: the most A stages (4 .. 2) with which
+// any ring fits, then the fewest ring entries per chunk, then the most
+// entries (measured at 6.3M rows, 1000 frames: 3 A stages better than 2 at
+// every chunk width; 150 modes best with 3 entries of 5 K-slices, 200 modes
+// with 2 entries of 7 and 6).  bn = 0 when nothing fits.
 AresCfg ares_rings(int ksteps, int bn) {
-  for (int sa = 3; sa >= 2; --sa) {
+  for (int sa = AR_MAXSA; sa >= 2; --sa) {
     AresCfg best = {0, 0, 0};
     int bestE = 1 << 30;
     for (int nb = AR_MAXNB; nb >= 2; --nb) {
@@ -1137,7 +1150,7 @@ dmd_status umma_tune_nn(int64_t n, int Kd, int N, const float* A, int64_t lda, c
   dmd_status status = DMD_OK;
   for (int bn = ares_bn_max(ksteps); bn >= 64 && status == DMD_OK; bn -= 16)
     for (int nb = 2; nb <= AR_MAXNB && status == DMD_OK; ++nb)
-      for (int sa = 2; sa <= 3 && status == DMD_OK; ++sa) {
+      for (int sa = 2; sa <= AR_MAXSA && status == DMD_OK; ++sa) {
         if (ares_group(ksteps, bn, sa, nb) == 0) continue;
         g_ares_override = {bn, sa, nb};
         status = umma_gemm_nn(n, Kd, N, A, lda, B, C, ldc, ws, st, 0, nullptr);

@@ -138,7 +138,7 @@ def test_autotuned_reconstruction_is_unchanged(dmd):
     ks = list(range(K))
     before = dmd.dmd_predict(model, ks, precision="mixed")
     bn, sa, nb = dmd.dmd_autotune_predict(model, ks, precision="mixed")
-    assert bn % 16 == 0 and 64 <= bn <= 176 and sa in (2, 3) and nb in (2, 3, 4)
+    assert bn % 16 == 0 and 64 <= bn <= 176 and sa in (2, 3, 4) and nb in (2, 3, 4)
     after = dmd.dmd_predict(model, ks, precision="mixed")
     torch.cuda.synchronize()
     assert torch.equal(before[:, :n], after[:, :n])
