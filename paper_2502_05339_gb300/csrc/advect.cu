@@ -24,9 +24,28 @@ __device__ __forceinline__ int wrap(int i, int N) {
   return i < 0 ? i + N : i;
 }
 
-// Cell coordinates of cell e (C order): 32-bit unsigned divisions.
-template <int DIM>
-__device__ __forceinline__ void cell_coords(unsigned e, int N, int* coord, int* stride) {
+// i mod N for N a power of two (two's complement: negative i too).
+__device__ __forceinline__ int wrap_p2(int i, int N) { return i & (N - 1); }
+
+// Cell coordinates of cell e (C order): 32-bit unsigned divisions, or shifts
+// by lgN when N is a power of two (P2).
+template <int DIM, bool P2 = false>
+__device__ __forceinline__ void cell_coords(unsigned e, int N, int* coord, int* stride, int lgN = 0) {
+  if (P2) {
+    const unsigned m = (unsigned)N - 1u;
+    coord[DIM - 1] = (int)(e & m);
+    stride[DIM - 1] = 1;
+    if (DIM == 2) {
+      coord[0] = (int)(e >> lgN);
+      stride[0] = N;
+    } else {
+      coord[1] = (int)((e >> lgN) & m);
+      coord[0] = (int)(e >> (2 * lgN));
+      stride[1] = N;
+      stride[0] = N * N;
+    }
+    return;
+  }
   const unsigned row = e / (unsigned)N;
   coord[DIM - 1] = (int)(e - row * (unsigned)N);
   stride[DIM - 1] = 1;
@@ -72,15 +91,17 @@ __device__ __forceinline__ float sample(const float* __restrict__ rho, const int
 // float4 rows, the coordinates are computed once for the four cells, and the
 // 4 x 2^DIM density samples are independent loads in flight together (one
 // cell per thread is bound by the latency of its two dependent load rounds).
-template <int DIM>
-__global__ void __launch_bounds__(128) k_advect_sl4(int N, const float* __restrict__ rho, float* __restrict__ out,
-                                                    const float* __restrict__ u, float dt) {
+// P2: N a power of two (2^lgN); coordinates and the periodic wrap become
+// shifts and masks (the kernel is bound by its instruction stream).
+template <int DIM, bool P2>
+__global__ void __launch_bounds__(128) k_advect_sl4(int N, int lgN, const float* __restrict__ rho,
+                                                    float* __restrict__ out, const float* __restrict__ u, float dt) {
   const int cells = DIM == 2 ? N * N : N * N * N;
   const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= (unsigned)(cells / 4)) return;
   const int e0 = 4 * (int)f;
   int coord[DIM], stride[DIM];
-  cell_coords<DIM>((unsigned)e0, N, coord, stride);
+  cell_coords<DIM, P2>((unsigned)e0, N, coord, stride, lgN);
   float cen[DIM][4];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -112,8 +133,8 @@ __global__ void __launch_bounds__(128) k_advect_sl4(int N, const float* __restri
       const float fl = floorf(s);
       frac[d] = s - fl;
       const int b = coord[d] + (d == DIM - 1 ? c : 0) + (int)fl;
-      lo[d] = wrap(b, N) * stride[d];
-      hi[d] = wrap(b + 1, N) * stride[d];
+      lo[d] = (P2 ? wrap_p2(b, N) : wrap(b, N)) * stride[d];
+      hi[d] = (P2 ? wrap_p2(b + 1, N) : wrap(b + 1, N)) * stride[d];
     }
     res[c] = sample<DIM>(rho, lo, hi, frac);
   }
@@ -158,8 +179,13 @@ dmd_status launch_advect(int dim, int N, const float* rho, float* out, const flo
   const bool vec = N % 4 == 0 && ((uintptr_t)rho & 15) == 0 && ((uintptr_t)out & 15) == 0 && ((uintptr_t)u & 15) == 0;
   if (vec) {
     const unsigned blocks = (unsigned)ceil_div(cells / 4, 128);
-    if (dim == 2) k_advect_sl4<2><<<blocks, 128, 0, st>>>(N, rho, out, u, dt);
-    else k_advect_sl4<3><<<blocks, 128, 0, st>>>(N, rho, out, u, dt);
+    int lgN = 0;
+    while ((1 << lgN) < N) ++lgN;
+    const bool p2 = (1 << lgN) == N;
+    if (dim == 2 && p2) k_advect_sl4<2, true><<<blocks, 128, 0, st>>>(N, lgN, rho, out, u, dt);
+    else if (dim == 2) k_advect_sl4<2, false><<<blocks, 128, 0, st>>>(N, lgN, rho, out, u, dt);
+    else if (p2) k_advect_sl4<3, true><<<blocks, 128, 0, st>>>(N, lgN, rho, out, u, dt);
+    else k_advect_sl4<3, false><<<blocks, 128, 0, st>>>(N, lgN, rho, out, u, dt);
   } else {
     const unsigned blocks = (unsigned)ceil_div(cells, 128);
     if (dim == 2) k_advect_sl1<2><<<blocks, 128, 0, st>>>(N, rho, out, u, dt);

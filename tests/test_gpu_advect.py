@@ -2,7 +2,8 @@
 the FP64 oracle: the same seeded model (divergence-free MAC-grid modes, FP32,
 and FP64 eigenvalues) on both sides; the oracle predicts the velocity frames
 in FP64 and runs the semi-Lagrangian steps literally.  Grids with
-N % 4 == 0 take the four-cells-per-thread kernel, the others the one-cell
+N % 4 == 0 take the four-cells-per-thread kernel (its power-of-two form for
+N = 16, 64; the general form for N = 48, 20), the others the one-cell
 kernel."""
 import numpy as np
 import pytest
@@ -55,7 +56,7 @@ def _density(N, dim):
     return f.ravel().astype(np.float32)
 
 
-@pytest.mark.parametrize("dim,N,K", [(2, 48, 24), (3, 16, 12), (2, 30, 10), (3, 10, 8)])
+@pytest.mark.parametrize("dim,N,K", [(2, 48, 24), (3, 16, 12), (2, 64, 16), (3, 20, 8), (2, 30, 10), (3, 10, 8)])
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
 def test_advect_matches_oracle(dmd, dim, N, K, prec):
     model, PhiR, lam, beta = _model(dmd, N, dim, 4, seed=21 + dim, speed=0.6)
