@@ -582,7 +582,6 @@ constexpr int kMsBulges = 4;   // bulges per chain
 constexpr int kMsSplit = 1;    // warps per bulge
 constexpr int kMsWarps = kMsBulges * kMsSplit;
 constexpr int kMsMin = 40;     // narrower windows take double-shift sweeps
-constexpr int kMsT = 5;        // at most this many entries per lane per batch
 constexpr int kMsLd = 2 * kMsBulges + 1;
 
 // P = I - tau v v^T, v = (1, v1, v2), with P (x, y, z)^T = (beta, 0, 0)^T;
@@ -607,39 +606,23 @@ __device__ __forceinline__ Refl3 refl3(float x, float y, float z) {
 
 // Rows k .. k + nr - 1 (nr = 2 or 3) of H (column-major, ld ldw) times P,
 // columns c0 .. c1, by `parts` warps (this one is part `part`): element e of
-// the range goes to lane e % 32 of part (e / 32) % parts.  Each lane loads its
-// entries (up to kMsT batches of 32 parts columns at a time, as many as the
-// range needs) before updating them, so the shared-memory latencies overlap.  Column
+// the range goes to lane e % 32 of part (e / 32) % parts, one element after
+// the other (a rolled loop: fewer instructions than batched loads with
+// per-slot guards, which the instruction-latency-bound step pays for).  Column
 // zc (the bulge just annihilated; -1 for none) gets exact zeros below row k.
 template <int PARTS>
 __device__ __forceinline__ void ms_rows(float* H, int ldw, int k, int nr, int c0, int c1, Refl3 P, int zc,
                                         int lane, int part) {
   constexpr int stride = 32 * PARTS;
-  const int nall = (c1 - c0 + stride) / stride;   // batches of the range (c1 >= c0)
   float* h0 = H + k;
-  for (int b0 = 0; b0 < nall; b0 += kMsT) {
-    const int nt = min(kMsT, nall - b0);
-    const int cfirst = c0 + stride * b0 + part * 32 + lane;
-    float r0[kMsT], r1[kMsT], r2[kMsT];
-#pragma unroll
-    for (int t = 0; t < kMsT; ++t) {
-      const int c = cfirst + stride * t;
-      if (t < nt && c <= c1) {
-        r0[t] = h0[c * ldw];
-        r1[t] = h0[c * ldw + 1];
-        r2[t] = nr == 3 ? h0[c * ldw + 2] : 0.f;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < kMsT; ++t) {
-      const int c = cfirst + stride * t;
-      if (t < nt && c <= c1) {
-        const float p = P.tau * (r0[t] + P.v1 * r1[t] + P.v2 * r2[t]);
-        h0[c * ldw] = r0[t] - p;
-        h0[c * ldw + 1] = c == zc ? 0.f : r1[t] - p * P.v1;
-        if (nr == 3) h0[c * ldw + 2] = c == zc ? 0.f : r2[t] - p * P.v2;
-      }
-    }
+#pragma unroll 1
+  for (int c = c0 + part * 32 + lane; c <= c1; c += stride) {
+    float* hc = h0 + c * ldw;
+    const float r0 = hc[0], r1 = hc[1], r2 = nr == 3 ? hc[2] : 0.f;
+    const float p = P.tau * (r0 + P.v1 * r1 + P.v2 * r2);
+    hc[0] = r0 - p;
+    hc[1] = c == zc ? 0.f : r1 - p * P.v1;
+    if (nr == 3) hc[2] = c == zc ? 0.f : r2 - p * P.v2;
   }
 }
 
@@ -648,31 +631,14 @@ template <int PARTS>
 __device__ __forceinline__ void ms_cols(float* H, int ldw, int k, int nr, int r0, int r1, Refl3 P, int lane,
                                         int part) {
   constexpr int stride = 32 * PARTS;
-  const int nall = (r1 - r0 + stride) / stride;
   float* c0p = H + k * ldw;
-  for (int b0 = 0; b0 < nall; b0 += kMsT) {
-    const int nt = min(kMsT, nall - b0);
-    const int rfirst = r0 + stride * b0 + part * 32 + lane;
-    float q0[kMsT], q1[kMsT], q2[kMsT];
-#pragma unroll
-    for (int t = 0; t < kMsT; ++t) {
-      const int r = rfirst + stride * t;
-      if (t < nt && r <= r1) {
-        q0[t] = c0p[r];
-        q1[t] = c0p[r + ldw];
-        q2[t] = nr == 3 ? c0p[r + 2 * ldw] : 0.f;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < kMsT; ++t) {
-      const int r = rfirst + stride * t;
-      if (t < nt && r <= r1) {
-        const float p = P.tau * (q0[t] + P.v1 * q1[t] + P.v2 * q2[t]);
-        c0p[r] = q0[t] - p;
-        c0p[r + ldw] = q1[t] - p * P.v1;
-        if (nr == 3) c0p[r + 2 * ldw] = q2[t] - p * P.v2;
-      }
-    }
+#pragma unroll 1
+  for (int r = r0 + part * 32 + lane; r <= r1; r += stride) {
+    const float q0 = c0p[r], q1 = c0p[r + ldw], q2 = nr == 3 ? c0p[r + 2 * ldw] : 0.f;
+    const float p = P.tau * (q0 + P.v1 * q1 + P.v2 * q2);
+    c0p[r] = q0 - p;
+    c0p[r + ldw] = q1 - p * P.v1;
+    if (nr == 3) c0p[r + 2 * ldw] = q2 - p * P.v2;
   }
 }
 
