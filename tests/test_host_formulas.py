@@ -3,8 +3,9 @@ NumPy): the real 2x2 form of the OptDMD Jacobian that the device assembles
 from r x r products must give the explicit Jacobian's J^T J, and its J^T rho
 must be the gradient of the projected objective of Eq. variable_projection;
 the closed-form high-order evolution of the upsampling kernel must equal the
-recurrence.  These restate the device formulas independently of the CUDA
-code, against the oracle and finite differences."""
+recurrence; the power iterations run on the snapshot Gram must span the
+oracle's range finder.  These restate the device formulas independently of
+the CUDA code, against the oracle and finite differences."""
 import numpy as np
 
 from oracle import dmd_oracle as O
@@ -124,3 +125,31 @@ def test_upsample_closed_form_equals_recurrence():
                 y = lam[c] ** (j + 1) * (P[c, 0] - 1j * P[c + 1, 0])
                 C[c, j], C[c + 1, j] = y.real, -y.imag
     np.testing.assert_allclose(PhiR @ C, ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_gram_space_power_iterations_span_the_range_finder():
+    """The fit runs its power iterations on the snapshot Gram W = X^T X: with
+    R = chol(Bs^T W Bs) (the first CholeskyQR factor of Y = X Bs), the basis
+    Q = X Bs R^-1 has X^T Q = W (Bs R^-1) exactly, so Z = orth(W Bs R^-1) and
+    only the last Y = X Z is formed on the tall side.  Its orthonormalised
+    range equals that of the oracle's range finder (Sec. 4.3: Q = orth(X
+    Omega), then Z = orth(X^T Q), Q = orth(X Z) per power iteration)."""
+    g = np.random.default_rng(17)
+    n, m, l, q = 3000, 40, 12, 2
+    U, _ = np.linalg.qr(g.standard_normal((n, m)))
+    V, _ = np.linalg.qr(g.standard_normal((m, m)))
+    X = (U * np.logspace(0, -3, m)) @ V.T
+    Omega = g.standard_normal((m, l))
+    *_, Q_ref = O.rsvd(X, Omega, l, q)
+    W = X.T @ X
+    Bs = Omega
+    for _ in range(q):
+        R = np.linalg.cholesky(Bs.T @ W @ Bs).T            # upper: Bs^T W Bs = R^T R
+        M = np.linalg.solve(R.T, Bs.T).T                   # Bs R^-1
+        Zp = W @ M
+        np.testing.assert_allclose(Zp, X.T @ (X @ M), atol=1e-12 * np.abs(Zp).max())
+        Bs, _ = np.linalg.qr(Zp)                            # the small-space orthonormalisation
+    R = np.linalg.cholesky(Bs.T @ W @ Bs).T
+    Q = X @ np.linalg.solve(R.T, Bs.T).T                   # the one tall sketch, first pass
+    np.testing.assert_allclose(Q.T @ Q, np.eye(l), atol=1e-9)
+    np.testing.assert_allclose(Q @ Q.T, Q_ref @ Q_ref.T, atol=1e-9)
