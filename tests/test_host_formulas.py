@@ -4,8 +4,10 @@ from r x r products must give the explicit Jacobian's J^T J, and its J^T rho
 must be the gradient of the projected objective of Eq. variable_projection;
 the closed-form high-order evolution of the upsampling kernel must equal the
 recurrence; the power iterations run on the snapshot Gram must span the
-oracle's range finder.  These restate the device formulas independently of
-the CUDA code, against the oracle and finite differences."""
+oracle's range finder; the multishift chain schedule of the Francis kernel
+must be a Hessenberg similarity that converges to the eigenvalues.  These
+restate the device formulas independently of the CUDA code, against the
+oracle, library eigenvalues and finite differences."""
 import numpy as np
 
 from oracle import dmd_oracle as O
@@ -153,3 +155,112 @@ def test_gram_space_power_iterations_span_the_range_finder():
     Q = X @ np.linalg.solve(R.T, Bs.T).T                   # the one tall sketch, first pass
     np.testing.assert_allclose(Q.T @ Q, np.eye(l), atol=1e-9)
     np.testing.assert_allclose(Q @ Q.T, Q_ref @ Q_ref.T, atol=1e-9)
+
+
+def _refl3(x, y, z):
+    """P = I - tau v v^T, v = (1, v1, v2), P (x, y, z) = (beta, 0, 0)."""
+    nrm = np.sqrt(x * x + y * y + z * z)
+    if nrm == 0.0 or (y == 0.0 and z == 0.0):
+        return None
+    beta = nrm if x <= 0 else -nrm
+    return (beta - x) / beta, y / (x - beta), z / (x - beta)
+
+
+def _apply_rows(H, k, nr, c0, c1, P, zc):
+    tau, v1, v2 = P
+    v = np.array([1.0, v1, v2])[:nr]
+    blk = H[k:k + nr, c0:c1 + 1]
+    blk -= tau * np.outer(v, v @ blk)
+    if zc >= 0:
+        H[k + 1:k + nr, zc] = 0.0
+
+
+def _apply_cols(H, k, nr, r0, r1, P):
+    tau, v1, v2 = P
+    v = np.array([1.0, v1, v2])[:nr]
+    blk = H[r0:r1 + 1, k:k + nr]
+    blk -= tau * np.outer(blk @ v, v)
+
+
+def _chain_sweep(H, lo, hi, shifts):
+    """One chain of small bulges over window [lo, hi] in the kernel's order:
+    bulge j (shift sum and product shifts[j]) enters at step 3 j; each step
+    forms every bulge's reflector from the current matrix, applies all of
+    them from the left, then all from the right."""
+    s = len(shifts)
+    for t in range((hi - 1 - lo) + 3 * (s - 1) + 1):
+        steps = []
+        for j, (ss, tt) in enumerate(shifts):
+            k = lo + t - 3 * j
+            if k < lo or k > hi - 1:
+                continue
+            nr = 3 if k <= hi - 2 else 2
+            if k == lo:
+                h = H
+                x = h[lo, lo] ** 2 + h[lo, lo + 1] * h[lo + 1, lo] - ss * h[lo, lo] + tt
+                y = h[lo + 1, lo] * (h[lo, lo] + h[lo + 1, lo + 1] - ss)
+                z = h[lo + 1, lo] * h[lo + 2, lo + 1]
+            else:
+                x, y = H[k, k - 1], H[k + 1, k - 1]
+                z = H[k + 2, k - 1] if nr == 3 else 0.0
+            P = _refl3(x, y, z if nr == 3 else 0.0)
+            if P is not None:
+                steps.append((k, nr, P))
+        for k, nr, P in steps:
+            _apply_rows(H, k, nr, max(lo, k - 1), hi, P, k - 1 if k > lo else -1)
+        for k, nr, P in steps:
+            _apply_cols(H, k, nr, lo, min(k + 3, hi), P)
+
+
+def test_multishift_chain_is_a_hessenberg_similarity():
+    """The schedule of the FP32 Francis kernel (bulges three rows apart, all
+    reflectors of a step applied from the left, then all from the right):
+    one chain sweep over an unreduced Hessenberg matrix keeps it upper
+    Hessenberg and is an orthogonal similarity (eigenvalues and Frobenius
+    norm kept), and repeated sweeps with the trailing block's eigenvalues as
+    shifts deflate the matrix to its eigenvalues."""
+    g = np.random.default_rng(23)
+    n = 48
+    A = g.standard_normal((n, n))
+    H0 = np.triu(A, -1)
+    H = H0.copy()
+    _chain_sweep(H, 0, n - 1, [(0.3, 0.5), (-0.2, 0.8), (1.1, 0.4), (0.0, 1.0)])
+    assert np.abs(np.tril(H, -2)).max() < 1e-12 * np.abs(H0).max()
+    np.testing.assert_allclose(np.linalg.norm(H), np.linalg.norm(H0), rtol=1e-12)
+    ev = np.sort_complex(np.linalg.eigvals(H))
+    np.testing.assert_allclose(ev, np.sort_complex(np.linalg.eigvals(H0)), atol=1e-9)
+    # the iteration: 8 shifts from the trailing 8 x 8 block, deflation at 1e-12
+    H = H0.copy()
+    found = []
+    hi = n - 1
+    for _ in range(400):
+        if hi < 0:
+            break
+        lo = hi
+        while lo > 0 and abs(H[lo, lo - 1]) > 1e-12 * (abs(H[lo - 1, lo - 1]) + abs(H[lo, lo])):
+            lo -= 1
+        if lo > 0:
+            H[lo, lo - 1] = 0.0
+        if lo == hi:
+            found.append(H[hi, hi] + 0j)
+            hi -= 1
+            continue
+        if lo == hi - 1:
+            found += list(np.linalg.eigvals(H[hi - 1:hi + 1, hi - 1:hi + 1]))
+            hi -= 2
+            continue
+        if hi - lo + 1 >= 12:
+            mu = np.linalg.eigvals(H[hi - 7:hi + 1, hi - 7:hi + 1])
+            mu = mu[np.argsort(mu.imag)]                     # conjugates pair up (-im, +im)...
+            shifts = []
+            cplx = sorted([z for z in mu if z.imag > 0], key=lambda z: z.real)
+            real = sorted([z.real for z in mu if z.imag == 0])
+            shifts += [(2 * z.real, abs(z) ** 2) for z in cplx]
+            shifts += [(real[i] + real[i + 1], real[i] * real[i + 1]) for i in range(0, len(real) - 1, 2)]
+            _chain_sweep(H, lo, hi, shifts)
+        else:
+            a, b, c, d = H[hi - 1, hi - 1], H[hi - 1, hi], H[hi, hi - 1], H[hi, hi]
+            _chain_sweep(H, lo, hi, [(a + d, a * d - b * c)])
+    assert hi < 0
+    np.testing.assert_allclose(np.sort_complex(np.array(found)), np.sort_complex(np.linalg.eigvals(H0)),
+                               atol=1e-8)
