@@ -366,9 +366,11 @@ struct EpsOf<float> {
 // Eigenvalues of the upper Hessenberg matrix Hin (n x n, ld; FP64) by Francis
 // double-shift QR in precision Real.  One warp; the matrix is copied into
 // shared memory (leading dimension ldw, odd so that a warp's row accesses hit
-// distinct banks) when `in_smem`, otherwise into the global scratch.  With
+// distinct banks) when kSmem, otherwise into the global scratch.  With
 // Real = float this only supplies starting shifts: every eigenvalue is then
-// refined in FP64 by k_hess_rqi.
+// refined in FP64 by k_hess_rqi.  Matrices that fit in shared memory take the
+// multishift kernel k_hqr_ms instead; this one serves larger n from global
+// scratch.
 constexpr int kHqrT = 5;   // rows per lane per batch of the column update (160 per warp)
 
 // kSmem: the matrix lives in shared memory, addressed as such with 32-bit
